@@ -1,0 +1,130 @@
+"""Kick-drift-kick integrator with individual power-of-two time bins (oracle).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+One call of :meth:`OracleSim.step` advances the system from the current integer
+time ``ti`` to the next time at which some particle's step ends (Sec. II-A):
+
+  (i)   drift every particle to ti (x += v_half dt; drift-all, which gives the
+        same positions as drifting only the relevant particles) and predict
+        v_pred = v_half + a (t - t_mid), A_pred = A + Adot (t - t_mid);
+  (ii)  the active set: particles whose step ends at ti (Eq. 2, read as
+        "every bin n with ti a multiple of 2^n");
+  (iii) density loop with the smoothing-length iteration for the active
+        particles; inactive neighbours keep their last h, rho, f and take
+        P, c from their predicted entropy;
+  (iv)  force loop for the active particles;
+  (v)   closing half-kick of the old step: v += a dt_old/2, A += Adot dt_old/2;
+  (vi)  new time-step (Eq. 1), bin (Eq. 2) and end time;
+  (vii) opening half-kick of the new step: v += a dt_new/2, A += Adot dt_new/2.
+
+The first step (ti = 0, every particle active with a zero-length old step)
+sets the entropy from the initial internal energy after its density pass.
+The integer timeline has ticks of dt_min; the time of tick ti is t_begin + ti dt_min.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+class OracleSim:
+    def __init__(self, pos, vel, m, u, h0, *, box=1.0, eta=1.2348, gamma=5.0 / 3.0,
+                 alpha=0.8, cfl=0.1, dt_min=1e-6, bin_cap=10, h_tol=1e-12, max_iter=100,
+                 use_cells=True, global_step=False):
+        n = pos.shape[0]
+        self.n = n
+        self.box, self.eta, self.gamma, self.alpha = box, eta, gamma, alpha
+        self.cfl, self.dt_min, self.bin_cap = cfl, dt_min, bin_cap
+        self.h_tol, self.max_iter, self.use_cells = h_tol, max_iter, use_cells
+        self.global_step = global_step
+        self.pos = np.array(pos, dtype=np.float64) % box
+        self.vel = np.array(vel, dtype=np.float64)
+        self.m = np.array(m, dtype=np.float64) * np.ones(n)
+        self.u0 = np.array(u, dtype=np.float64) * np.ones(n)
+        self.h = np.array(h0, dtype=np.float64) * np.ones(n)
+        self.acc = np.zeros((n, 3))
+        self.A = np.zeros(n)
+        self.Adot = np.zeros(n)
+        self.rho = np.zeros(n)
+        self.drho_dh = np.zeros(n)
+        self.f = np.ones(n)
+        self.P = np.zeros(n)
+        self.c = np.zeros(n)
+        self.vsig = np.zeros(n)
+        self.bin = np.zeros(n, dtype=np.int8)
+        self.ti_begin = np.zeros(n, dtype=np.int64)
+        self.ti_end = np.zeros(n, dtype=np.int64)
+        self.ti = 0            # current integer time
+        self.ti_drift = 0      # time the positions refer to
+        self.first = True
+        self.n_steps = 0
+        self.pairs_density = 0
+        self.pairs_force = 0
+        self.last_active = None
+        self.E_sync = []       # total energy at steps where every particle is synchronised
+
+    # -- the pieces of one step --------------------------------------------
+    def _drift(self, ti):
+        dt = (ti - self.ti_drift) * self.dt_min
+        if dt != 0.0:
+            self.pos = (self.pos + self.vel * dt) % self.box
+        self.ti_drift = ti
+
+    def _predict(self, ti):
+        """v_pred and A_pred at ti from the half-step state."""
+        step = (np.int64(1) << self.bin.astype(np.int64))
+        dtp = ((ti - self.ti_begin) - 0.5 * step) * self.dt_min
+        return self.vel + self.acc * dtp[:, None], self.A + self.Adot * dtp
+
+    def step(self):
+        import oracle as orc
+        ti = self.ti
+        g = self.gamma
+        self._drift(ti)
+        vpred, Apred = self._predict(ti)
+        active = self.ti_end == ti
+        self.last_active = active.copy()
+        d = orc.density(self.pos, self.m, self.h, active, self.box, self.eta, self.h_tol,
+                        self.max_iter, self.use_cells)
+        self.h[active] = d["h"][active]
+        self.rho[active] = d["rho"][active]
+        self.drho_dh[active] = d["drho_dh"][active]
+        self.pairs_density += int(d["count"][active].sum())
+        self.f[active] = orc.gradh_f(self.h[active], self.rho[active], self.drho_dh[active])
+        if self.first:
+            self.A = orc.entropy_from_u(self.u0, self.rho, g)
+            Apred = self.A.copy()
+        self.P, self.c = orc.eos(Apred, self.rho, g)
+        fr = orc.force(self.pos, vpred, self.m, self.h, self.rho, self.f, self.P, self.c,
+                       active, self.box, self.alpha, g, self.use_cells)
+        self.acc[active] = fr["a"][active]
+        self.Adot[active] = fr["Adot"][active]
+        self.vsig[active] = fr["vsig"][active]
+        self.pairs_force += int(fr["count"][active].sum())
+        # (v) closing half-kick of the old step
+        dt_old = ((self.ti_end - self.ti_begin) * self.dt_min)[active]
+        self.vel[active] += self.acc[active] * (0.5 * dt_old)[:, None]
+        self.A[active] += self.Adot[active] * (0.5 * dt_old)
+        if active.all():
+            v2 = (self.vel ** 2).sum(axis=1)
+            u = orc.u_from_entropy(self.A, self.rho, g)
+            self.E_sync.append(float((self.m * (0.5 * v2 + u)).sum()))
+        # (vi) new time-step and bin
+        cap = 0 if self.global_step else self.bin_cap
+        tb = orc.timestep_bins(self.h, self.vsig, active, self.cfl, self.dt_min, cap, ti,
+                               self.bin)
+        self.n_dt_too_small = tb["n_too_small"]
+        self.bin[active] = tb["bin"][active]
+        self.ti_begin[active] = tb["ti_begin"][active]
+        self.ti_end[active] = tb["ti_end"][active]
+        # (vii) opening half-kick of the new step
+        dt_new = ((self.ti_end - self.ti_begin) * self.dt_min)[active]
+        self.vel[active] += self.acc[active] * (0.5 * dt_new)[:, None]
+        self.A[active] += self.Adot[active] * (0.5 * dt_new)
+        self.first = False
+        self.n_steps += 1
+        self.ti = int(self.ti_end.min())
+        return active
+
+    def momentum(self):
+        return (self.m[:, None] * self.vel).sum(axis=0)
