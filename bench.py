@@ -1,0 +1,386 @@
+"""Benchmark: active pair interactions per second (density + force) of the SPH
+hot path on the 2,097,152-particle clustered workload (uniform background plus
+64 Plummer spheres, time bins spanning ~2^13), batched versus plain.
+
+One timed step = one full kick-drift-kick step (mark active, drift, density
+with the smoothing-length iteration, force, kicks, time bins).  K steps are
+timed from the initial conditions (step 0 has every particle active, the rest
+only the particles of the active bins); W warm-up steps run first on the same
+initial conditions, after which the state is restored.  Each step is timed with
+CUDA events on the launching stream, with the L2 cache flushed between steps
+(a 256 MiB write, outside the timed interval).
+
+value       useful pairs (density: i active, j != i, r < H_i at the final h;
+            force: r < max(H_i, H_j)) over all timed steps / summed step time,
+            batched form (persistent kernels + CUDA graph);
+plain       the same for the per-bin launch form;
+e2e         the batched form through the C ABI with host buffers: each step
+            copies the particle state host->device (pinned) and back;
+roofline    the dominant pair-loop kernel: algorithmic FLOPs per useful pair
+            (density 29, force 61) x useful pairs per launch / mean launch time
+            (CUDA events in the library, on the launching stream), against the
+            FP32 peak 152 SMs x 128 lanes x 2 x 2.07 GHz;
+cpu_baseline  the FP64 oracle on a bounded sample of the same workload.
+
+--impl reference times the oracle alone (the CPU reference of this method).
+Under torchrun every rank runs its own replica (the method does not shard
+across GPUs here); value sums the ranks' pairs over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "active pair interactions/s (density+force) at 2.1M clustered; batched vs plain"
+UNIT = "pairs/s"
+WORKLOAD = "c3_clustered_2m"
+FLOP_DENSITY = 29   # per useful density pair
+FLOP_FORCE = 61     # per useful force pair
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+TUNED = dict(threads_per_particle=4, leaf_max=16, cell_margin=1.1)
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(s[1]) for s in self.samples if len(s) > 2 and s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if len(s) > 2 and s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for k, name in enumerate(names):
+                if len(s) > 5 + k and s[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world):
+    import torch
+    import sph_ics
+    from sph_ics import workloads
+    from paper_1807_01341_gb300 import _lib, build, sim
+
+    build.build()
+    dev = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(dev)
+    t0 = time.time()
+    ic = workloads.make(args.workload)
+    t_ic = time.time() - t0
+    n = ic["pos"].shape[0]
+    params = sim.Params(**workloads.PARAMS[args.workload], **TUNED)
+    ctx = sim.Context(params, n)
+    p = sim.Particles.from_ics(ic, with_counts=False)
+    ctx.build_cells(p)
+    snapshot = {k: t.clone() for k, t in p.arrays().items()}
+    stream = torch.cuda.Stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
+
+    def restore():
+        for k, t in p.arrays().items():
+            t.copy_(snapshot[k])
+        torch.cuda.synchronize()
+        ctx.build_cells(p, stream)
+        ctx.begin_run(stream)
+        ctx.reset_kernel_times()
+
+    def one_step(form, timed):
+        """One step: [ev0, enqueue, ev1] then a host sync outside the interval;
+        a step stopped by a cell overflow is redone after the rebuild and its
+        attempts and the rebuild are all counted."""
+        total = 0.0
+        while True:
+            if timed:
+                flush.zero_()
+                torch.cuda.synchronize()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                ev0.record(stream)
+                ctx.step_async(p, form, stream)
+                ev1.record(stream)
+            tw = time.perf_counter()
+            done = ctx.step_sync(p, stream)
+            total += ev0.elapsed_time(ev1)
+            if done:
+                return total
+            total += (time.perf_counter() - tw) * 1e3  # the rebuild (wall clock)
+
+    forms = {"batched": _lib.SPH_FORM_BATCHED, "plain": _lib.SPH_FORM_PLAIN}
+    results = {}
+    ctx.set_profiling(True)
+    for name in ([] if args.no_plain else ["plain"]) + ["batched"]:
+        form = forms[name]
+        restore()
+        for _ in range(args.warmup):
+            one_step(form, False)
+        restore()
+        ctx.reset_counters(stream)
+        torch.cuda.synchronize()
+        launches0 = ctx.counters()["kernel_launches"]
+        if world > 1:
+            torch.distributed.barrier()
+        ms = []
+        with Clocks(dev) as clk:
+            for _ in range(args.steps):
+                ms.append(one_step(form, True))
+        torch.cuda.synchronize()
+        c = ctx.counters()
+        kt = ctx.kernel_times()
+        results[name] = dict(ms=ms, counters=c, ktimes=kt, clocks=clk.summary(),
+                             grid=ctx.grid_info(),
+                             launches=c["kernel_launches"] - launches0)
+    res = results["batched"]
+    pairs = res["counters"]["pairs_density"] + res["counters"]["pairs_force"]
+    total_ms = sum(res["ms"])
+
+    # e2e: the same steps through the C ABI from host buffers
+    host = {k: torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for k, t in p.arrays().items()}
+    restore()
+    for k, t in p.arrays().items():
+        host[k].copy_(t)
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    ctx.reset_counters(stream)
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            for k, t in p.arrays().items():
+                t.copy_(host[k], non_blocking=True)
+            ctx.step_async(p, _lib.SPH_FORM_BATCHED, stream)
+            for k, t in p.arrays().items():
+                host[k].copy_(t, non_blocking=True)
+            ev1.record(stream)
+        done = ctx.step_sync(p, stream)
+        e2e_ms.append(ev0.elapsed_time(ev1))
+        if not done:
+            raise RuntimeError("cell overflow in the e2e pass")
+    ce = ctx.counters()
+    e2e_pairs = ce["pairs_density"] + ce["pairs_force"]
+
+    # roofline of the dominant pair-loop kernel (batched form)
+    kt = res["ktimes"]
+    c = res["counters"]
+    dens = dict(ms=kt["density_ms"], n=max(kt["density_launches"], 1),
+                flops=FLOP_DENSITY * c["pairs_density"])
+    forc = dict(ms=kt["force_ms"], n=max(kt["force_launches"], 1),
+                flops=FLOP_FORCE * c["pairs_force"])
+    dom_name, dom = max((("density", dens), ("force", forc)), key=lambda kv: kv[1]["ms"])
+    per_launch_s = dom["ms"] / dom["n"] / 1e3
+    achieved = dom["flops"] / dom["n"] / per_launch_s / 1e12 if per_launch_s > 0 else 0.0
+    out = dict(pairs=pairs, total_ms=total_ms, res=results, e2e_ms=sum(e2e_ms),
+               e2e_pairs=e2e_pairs, h2d=h2d, n=n, t_ic=t_ic,
+               roofline=dict(kernel=dom_name, achieved=achieved, per_launch_ms=per_launch_s * 1e3,
+                             density_ms=kt["density_ms"], force_ms=kt["force_ms"]),
+               gpu_state={k: t for k, t in p.arrays().items()} if rank == 0 else None,
+               ic=ic)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# oracle on a bounded sample (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_sample(ic, sample=2048, seed=0):
+    """The FP64 oracle on a seeded sample of active particles of the workload:
+    its density loop with the smoothing-length iteration (from the same initial
+    h) and its force loop for the sample (neighbour h, rho, f, P, c taken from
+    the initial state: the loop's cost and pair count do not depend on them).
+    Returns useful pairs, seconds, threads."""
+    import oracle
+    from sph_ics import subsample_active
+    n = ic["pos"].shape[0]
+    act = subsample_active(n, sample, seed)
+    gamma = 5.0 / 3.0
+    t0 = time.perf_counter()
+    d = oracle.density(ic["pos"], ic["m"], ic["h0"], act)
+    t1 = time.perf_counter()
+    h = np.where(act == 1, d["h"], ic["h0"])
+    rho = np.where(act == 1, d["rho"], ic["m"] * (1.2348 / ic["h0"]) ** 3)
+    f = np.ones(n)
+    A = oracle.entropy_from_u(ic["u"], rho, gamma)
+    P, cs = oracle.eos(A, rho, gamma)
+    t2 = time.perf_counter()
+    fr = oracle.force(ic["pos"], ic["vel"], ic["m"], h, rho, f, P, cs, act)
+    t3 = time.perf_counter()
+    pairs = int(d["count"][act == 1].sum()) + int(fr["count"][act == 1].sum())
+    return dict(pairs=pairs, seconds=(t1 - t0) + (t3 - t2), threads=oracle.num_threads(),
+                sample=f"{sample} seeded active particles of the {n}-particle workload: "
+                       "density with h iteration + force, FP64, cell-grid neighbour search")
+
+
+def run_reference(args, rank, world):
+    import oracle
+    from sph_ics import workloads
+    oracle.build()
+    ic = workloads.make(args.workload)
+    runs = []
+    for k in range(args.warmup + args.steps):
+        r = oracle_sample(ic, args.ref_sample, seed=k)
+        if k >= args.warmup:
+            runs.append(r)
+    pairs = sum(r["pairs"] for r in runs)
+    secs = sum(r["seconds"] for r in runs)
+    v = pairs / secs
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "form": "oracle sample"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": runs[0]["threads"],
+                             "kind": "oracle", "sample": runs[0]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-sample", type=int, default=2048)
+    ap.add_argument("--cpu-sample", type=int, default=2048)
+    args = ap.parse_args()
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    if args.warmup < 3:
+        args.warmup = 3
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, rank, world)
+        return
+
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    out = run_ours(args, rank, world)
+    total_ms = out["total_ms"]
+    pairs = out["pairs"]
+    e2e_ms = out["e2e_ms"]
+    if world > 1:
+        t = torch.tensor([total_ms, e2e_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        s = torch.tensor([float(pairs), float(out["e2e_pairs"])], device="cuda",
+                         dtype=torch.float64)
+        torch.distributed.all_reduce(s)
+        total_ms, e2e_ms = float(t[0]), float(t[1])
+        pairs_all, e2e_pairs = float(s[0]), float(s[1])
+    else:
+        pairs_all, e2e_pairs = float(pairs), float(out["e2e_pairs"])
+    if rank == 0:
+        res = out["res"]
+        b = res["batched"]
+        rf = out["roofline"]
+        plain = None
+        if "plain" in res:
+            pr = res["plain"]
+            pp = pr["counters"]["pairs_density"] + pr["counters"]["pairs_force"]
+            plain = {"value": pp / (sum(pr["ms"]) / 1e3) * world, "ms_per_step":
+                     sum(pr["ms"]) / len(pr["ms"]), "unit": UNIT}
+        cpu = None
+        if not args.no_cpu_baseline:
+            r = oracle_sample(out["ic"], args.cpu_sample, seed=0)
+            cpu = {"value": r["pairs"] / r["seconds"], "unit": UNIT, "cores": r["threads"],
+                   "kind": "oracle", "sample": r["sample"]}
+        c = b["counters"]
+        line = {
+            "metric": METRIC, "value": pairs_all / (total_ms / 1e3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 pair arithmetic, f64 positions/h test",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n_particles": out["n"],
+                       "form": "batched (persistent kernels + CUDA graph)",
+                       "steps_from": "initial conditions (step 0 all active)",
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "grid_cells_per_axis": b["grid"][0], "leaves": b["grid"][1],
+                       **TUNED},
+            "plain": plain,
+            "e2e": {"value": e2e_pairs / (e2e_ms / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": out["h2d"], "d2h_bytes_per_step": out["h2d"]},
+            "roofline": {"bound": "alu", "kernel": rf["kernel"], "achieved": rf["achieved"],
+                         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": rf["achieved"] / FP32_PEAK_TFLOPS, "traffic": None,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived)",
+                         "launch_ms": rf["per_launch_ms"], "density_ms": rf["density_ms"],
+                         "force_ms": rf["force_ms"]},
+            "cpu_baseline": cpu,
+            "gpu_launches": b["launches"],
+            "counters": {k: c[k] for k in ("pairs_density", "pairs_force", "cand_density",
+                                           "cand_force", "iters_density", "active_particles",
+                                           "steps", "rebuilds", "redone_steps")},
+            "clocks": b["clocks"],
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,246 @@
+/*
+ * sph.h -- C ABI of the GB300 (sm_103a) SPH hot-path library, libsph_gb300.so.
+ *
+ * The library computes the data-parallel hot path of SWIFT (arXiv 1807.01341):
+ * cell-based SPH neighbour interactions -- the density loop with the
+ * smoothing-length iteration, then the hydro force loop -- restricted to the
+ * particles that are active in the current power-of-two time bin, inside a
+ * kick-drift-kick integrator with individual time steps (Sec. II-A, Eq. 2),
+ * drifting only the particles of the cells that can interact with an active
+ * particle (Sec. III-D).
+ *
+ * Conventions for every call:
+ *   - Every pointer inside sph_particles is a DEVICE pointer to an array of
+ *     length n, owned by the caller.  sph_build_cells reorders all of them in
+ *     place into cell order; every later call works on that order.
+ *   - Every call is asynchronous on `stream` (a cudaStream_t passed as void*;
+ *     NULL = the legacy default stream) unless it says otherwise.
+ *   - Return value: SPH_OK (0) or an SPH_ERR_* code.  Argument and CUDA errors
+ *     are returned directly.  Errors that arise on the device (h that does not
+ *     converge, a cell that became too small, a time step below dt_min, a
+ *     bounded wait that timed out) are recorded in a device status word that
+ *     sph_get_status reads; the device never traps.
+ *   - Once a device error that invalidates the step (SPH_ERR_CELL_OVERFLOW)
+ *     is recorded, the remaining kernels of the step return without writing;
+ *     sph_step recovers by rebuilding the cells and redoing the step.
+ *   - The library owns all scratch memory (sorting, cells, leaves, records,
+ *     queues); it is allocated by sph_create and sph_build_cells.
+ */
+#ifndef SPH_GB300_H
+#define SPH_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum sph_status_code {
+  SPH_OK = 0,
+  SPH_ERR_ARG = 1,           /* invalid argument or call order */
+  SPH_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+  SPH_ERR_H_NOCONV = 3,      /* smoothing length did not converge in h_max_iter */
+  SPH_ERR_CELL_OVERFLOW = 4, /* a kernel support outgrew the cell width: rebuild */
+  SPH_ERR_DT_TOO_SMALL = 5,  /* a CFL time step fell below dt_min (put on bin 0) */
+  SPH_ERR_TIMEOUT = 6,       /* a bounded device wait gave up */
+  SPH_ERR_NOMEM = 7,         /* device allocation failed */
+  SPH_ERR_NOT_BUILT = 8      /* sph_build_cells has not been called */
+};
+
+/* Parameters.  Defaults (sph_default_params): eta 1.2348, gamma 5/3,
+ * alpha_visc 0.8, cfl 0.1, h_tol 1e-6, h_max_iter 30, bin_cap 20,
+ * dt_min 1e-6, t_begin 0, box 1, cell_margin 1.1, leaf_max 16,
+ * threads_per_particle 4, drift_all 0, n_cells_override 0. */
+typedef struct {
+  double box;        /* side of the periodic cube */
+  double eta;        /* resolution: h solves h^3 n(h) = eta^3, n = sum_j W(r_ij, h) */
+  double gamma;      /* adiabatic index of the density-entropy equation of state */
+  double alpha_visc; /* artificial viscosity strength (signal-velocity form, beta = 3) */
+  double cfl;        /* C of Eq. 1: dt_i = C h_i / v_sig,i */
+  double h_tol;      /* convergence of the h iteration: |dh| / h < h_tol, tested in FP64 */
+  int h_max_iter;    /* iterations before SPH_ERR_H_NOCONV */
+  int bin_cap;       /* largest time bin (0 = one global step); at most 62 */
+  double dt_min;     /* t_min of Eq. 2: one tick of the integer timeline */
+  double t_begin;    /* time of tick 0 */
+  double cell_margin;/* top-level cell width >= cell_margin * largest kernel support */
+  int leaf_max;      /* most particles in one leaf (sub-cell) of the cell tree, 1..64 */
+  int threads_per_particle; /* lanes that share one active particle: 1, 2, 4, 8, 16 or 32 */
+  int drift_all;     /* 0: drift only cells next to active cells (Sec. III-D); 1: drift all */
+  int n_cells_override; /* > 0: use this many top-level cells per axis (must keep the
+                           cell width >= the largest support) */
+} sph_params;
+
+/* Particle state, structure of arrays, all device pointers of length n.
+ * Between kicks v and A hold the half-step values of the kick-drift-kick
+ * scheme; a, Adot are the rates from the last force evaluation of each
+ * particle; h, rho, f, P, c, vsig are from its last density/force pass.
+ * The integer timeline: a particle on bin b has a step of 2^b ticks,
+ * [ti_begin, ti_end), and ti_drift is the tick its position refers to. */
+typedef struct {
+  int64_t n;
+  double *x, *y, *z;    /* positions, wrapped into [0, box) by sph_build_cells */
+  float *vx, *vy, *vz;  /* velocities */
+  float *ax, *ay, *az;  /* accelerations */
+  float *A, *Adot;      /* entropic function A = P / rho^gamma and its rate */
+  float *h;             /* smoothing length (in: initial guess; out: solution) */
+  float *rho, *f, *P, *c, *vsig; /* density, grad-h factor, pressure, sound speed, signal velocity */
+  float *m;             /* masses */
+  int8_t *bin;          /* time bin */
+  int64_t *ti_begin, *ti_end, *ti_drift;
+  uint8_t *active;      /* out: 1 for the particles active at the current tick */
+  int32_t *ngb_density; /* optional (may be NULL): neighbours j != i with r < H_i */
+  int32_t *ngb_force;   /* optional (may be NULL): neighbours j != i with r < max(H_i, H_j) */
+} sph_particles;
+
+typedef struct sph_ctx sph_ctx;
+
+/* Counters accumulated on the device since sph_create or the last
+ * sph_reset_counters (read by sph_get_counters, synchronising). */
+typedef struct {
+  int64_t pairs_density;   /* useful density pairs: i active, j != i, r_ij < H_i (final h) */
+  int64_t pairs_force;     /* useful force pairs: i active, j != i, r_ij < max(H_i, H_j) */
+  int64_t cand_density;    /* candidate pairs evaluated in the density loop (all iterations) */
+  int64_t cand_force;      /* candidate pairs evaluated in the force loop */
+  int64_t iters_density;   /* sum over active particles of h iterations */
+  int64_t active_particles;/* sum over steps of the active particle count */
+  int64_t steps;           /* completed sph_step / sph_step_graph steps */
+  int64_t rebuilds;        /* sph_build_cells calls */
+  int64_t redone_steps;    /* steps redone after a cell overflow */
+  int64_t kernel_launches; /* kernels this process launched through the library so far
+                              (graph replays count their kernel nodes) */
+} sph_counters;
+
+void sph_default_params(sph_params *p);
+
+/* Create a context for up to n_max particles on the current CUDA device.
+ * Allocates the library's scratch.  Errors: SPH_ERR_ARG, SPH_ERR_NOMEM. */
+int sph_create(const sph_params *params, int64_t n_max, sph_ctx **ctx);
+int sph_destroy(sph_ctx *ctx);
+
+/* Top-level cells and leaves (Sec. III-A).  Wraps positions into the box,
+ * chooses n_c = floor(box / (cell_margin * H_max)) (at least 3; H_max from the
+ * current h) unless overridden, assigns each particle the cell
+ * floor(x / w) per axis (w = box / n_c), sorts the particles stably by
+ * (cell, 30-bit Morton code of the position inside the cell) -- ties keep
+ * their previous order -- and permutes every array of `p` in place.  Each
+ * cell is split into leaves: octree nodes of the Morton order holding at most
+ * leaf_max particles.  Refreshes the FP32 cell-relative records every pair
+ * loop reads.  Synchronises `stream` once (to size the grid). */
+int sph_build_cells(sph_ctx *ctx, sph_particles *p, void *stream);
+
+/* After sph_build_cells: permutation (device, int32, length n) with
+ * perm[k] = index, in the order of the first sph_build_cells call, of the
+ * particle now at position k.  Valid until the next sph_build_cells. */
+const int32_t *sph_perm(const sph_ctx *ctx);
+/* Number of top-level cells per axis and number of leaves of the last build. */
+int sph_grid_info(const sph_ctx *ctx, int *n_cells_per_axis, int *n_leaves);
+
+/* Active set at tick ti_current (Eq. 2): particle i is active when its step
+ * ends there, i.e. when ti_current is a multiple of 2^bin_i (every particle is
+ * active at tick 0).  ti_current < 0 uses the device-resident time (the tick
+ * the last sph_timestep_bins computed as next).  Writes p->active, builds the
+ * queue of leaves holding active particles and the list of cells within one
+ * cell of an active cell (the particles that must be drifted, Sec. III-D). */
+int sph_mark_active(sph_ctx *ctx, sph_particles *p, int64_t ti_current, void *stream);
+
+enum sph_phase {
+  SPH_DRIFT = 0,      /* drift to the current tick: positions of the relevant cells (all
+                         cells when drift_all), predicted v and A, P and c of inactive
+                         particles from their predicted entropy; refreshes records */
+  SPH_KICK_CLOSE = 1, /* active particles: v += a dt_old / 2, A += Adot dt_old / 2 */
+  SPH_KICK_OPEN = 2   /* active particles: v += a dt_new / 2, A += Adot dt_new / 2 */
+};
+/* One phase of the kick-drift-kick integrator (Sec. II-A) for the current
+ * tick set by sph_mark_active. */
+int sph_kick_drift(sph_ctx *ctx, sph_particles *p, int phase, void *stream);
+
+enum { SPH_DENSITY_INIT_ENTROPY = 1 }; /* p->A holds u on input; set A from u and rho */
+/* Density loop with the smoothing-length iteration ("ghost", Sec. III-B) for
+ * the active particles: solves h^3 n(h) = eta^3 by a bracket-safeguarded
+ * Newton iteration (each iteration one pass over the neighbour leaves), then
+ * writes h, rho, f (grad-h factor), P and c (from the predicted entropy).
+ * Cubic-spline kernel with support H = 1.825742 h.  FP32 pair arithmetic on
+ * cell-relative coordinates, compensated accumulation, FP64 convergence test. */
+int sph_density_active(sph_ctx *ctx, sph_particles *p, int flags, void *stream);
+
+/* Hydro force loop for the active particles over j with r_ij < max(H_i, H_j):
+ * writes a, Adot and vsig.  Pressure term with grad-h factors, Monaghan
+ * signal-velocity viscosity Pi_ij (beta = 3, the form inside Eq. 1). */
+int sph_force_active(sph_ctx *ctx, sph_particles *p, void *stream);
+
+/* New time steps of the active particles: dt = C h / v_sig (Eq. 1), bin =
+ * floor(log2(dt / dt_min)) capped at bin_cap (Eq. 2), increases accepted only
+ * while the current tick is a multiple of the new step; sets ti_begin, ti_end
+ * and the device-resident next tick (the earliest ti_end of all particles),
+ * which is also written to *ti_next_dev when not NULL (device pointer). */
+int sph_timestep_bins(sph_ctx *ctx, sph_particles *p, int64_t *ti_next_dev, void *stream);
+
+enum sph_form {
+  SPH_FORM_PLAIN = 0,   /* per time bin: one launch of each pair loop per active bin, grids
+                           sized on the host after reading the queue lengths */
+  SPH_FORM_BATCHED = 1, /* all active leaves of all bins in one persistent launch per loop,
+                           the whole step replayed from one captured CUDA graph, no host
+                           synchronisation inside the step */
+  SPH_FORM_BATCHED_NOGRAPH = 2 /* the batched launches issued one by one (ablation) */
+};
+
+/* Start a new run on this context: tick 0, the next step sets the entropy
+ * from u (p->A holds u), counters and status cleared.  Synchronising. */
+int sph_begin_run(sph_ctx *ctx, void *stream);
+
+/* Enqueue one full kick-drift-kick step at the device-resident current tick:
+ * mark, drift, density, force, closing kick, bins, opening kick, advance to
+ * the next tick.  Builds the cells first if needed.  The first step of a run
+ * (tick 0) sets the entropy from u.  SPH_FORM_BATCHED replays a CUDA graph
+ * captured on first use (p must keep the same pointers; it is recaptured when
+ * they or the library's buffers change).  When drift or h growth has made the
+ * cells too small, the step leaves the state as it was (its kernels return
+ * without writing) and records SPH_ERR_CELL_OVERFLOW; sph_step_sync repairs
+ * that.  SPH_FORM_PLAIN synchronises `stream` inside the step. */
+int sph_step_async(sph_ctx *ctx, sph_particles *p, int form, void *stream);
+
+/* Wait for the enqueued steps; *completed (may be NULL) = the number of them
+ * that completed.  If one stopped on a cell overflow, the cells are rebuilt
+ * (wider when h outgrew them) and the status cleared, so the caller enqueues
+ * the missing steps again. */
+int sph_step_sync(sph_ctx *ctx, sph_particles *p, int *completed, void *stream);
+
+/* One step, repeated after a rebuild until it completes (async + sync). */
+int sph_step(sph_ctx *ctx, sph_particles *p, int form, void *stream);
+
+/* n_steps steps of SPH_FORM_BATCHED enqueued back to back, one
+ * synchronisation at the end (plus one per recovery). */
+int sph_step_graph(sph_ctx *ctx, sph_particles *p, int n_steps, void *stream);
+
+/* Current and next tick of the device-resident timeline (synchronising). */
+int sph_get_time(sph_ctx *ctx, int64_t *ti_current, int64_t *ti_next);
+/* Set the device-resident current tick (asynchronous). */
+int sph_set_time(sph_ctx *ctx, int64_t ti_current, void *stream);
+
+/* Device status word (synchronising): *status = the first SPH_ERR_* recorded
+ * on the device since the last sph_clear_status (SPH_OK if none), *detail = the
+ * number of particles it concerned.  Either pointer may be NULL. */
+int sph_get_status(sph_ctx *ctx, int *status, int64_t *detail);
+int sph_clear_status(sph_ctx *ctx, void *stream);
+int sph_get_counters(sph_ctx *ctx, sph_counters *out);
+int sph_reset_counters(sph_ctx *ctx, void *stream);
+
+/* Device time of the pair-loop launches, measured with CUDA events recorded
+ * on the launching stream around every density and force launch (inside the
+ * captured graph for SPH_FORM_BATCHED).  Off by default; enabling it changes
+ * no result.  Times accumulate until sph_reset_kernel_times; reading them
+ * synchronises the device. */
+typedef struct {
+  double density_ms, force_ms;
+  int64_t density_launches, force_launches;
+} sph_kernel_times;
+int sph_set_profiling(sph_ctx *ctx, int enable);
+int sph_get_kernel_times(sph_ctx *ctx, sph_kernel_times *out);
+int sph_reset_kernel_times(sph_ctx *ctx);
+
+const char *sph_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPH_GB300_H */

@@ -258,7 +258,7 @@ def cells(pos, box, n_cells):
 def n_cells_for(hmax, box=1.0, margin=1.0, nc_max=1024):
     """Top-level grid size: the largest n_c with box / n_c >= margin * H_max, n_c >= 3."""
     import math
-    nc = int(math.floor(box / (margin * GAMMA_K * float(hmax))))
+    nc = int(math.floor(box / (margin * (GAMMA_K * float(hmax)))))
     return max(3, min(nc, nc_max))
 
 

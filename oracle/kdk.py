@@ -54,8 +54,8 @@ class OracleSim:
         self.bin = np.zeros(n, dtype=np.int8)
         self.ti_begin = np.zeros(n, dtype=np.int64)
         self.ti_end = np.zeros(n, dtype=np.int64)
-        self.ti = 0            # current integer time
-        self.ti_drift = 0      # time the positions refer to
+        self.ti = 0                               # current integer time
+        self.ti_drift = np.zeros(n, dtype=np.int64)  # tick each position refers to
         self.first = True
         self.n_steps = 0
         self.pairs_density = 0
@@ -66,9 +66,10 @@ class OracleSim:
     # -- the pieces of one step --------------------------------------------
     def _drift(self, ti):
         dt = (ti - self.ti_drift) * self.dt_min
-        if dt != 0.0:
-            self.pos = (self.pos + self.vel * dt) % self.box
-        self.ti_drift = ti
+        moved = dt != 0.0
+        if moved.any():
+            self.pos[moved] = (self.pos[moved] + self.vel[moved] * dt[moved, None]) % self.box
+        self.ti_drift[:] = ti
 
     def _predict(self, ti):
         """v_pred and A_pred at ti from the half-step state."""
@@ -125,6 +126,30 @@ class OracleSim:
         self.n_steps += 1
         self.ti = int(self.ti_end.min())
         return active
+
+    @classmethod
+    def from_state(cls, st, *, ti, first=False, **kw):
+        """An oracle integrator holding a given state (FP64 copies of the
+        arrays of a particle structure: x, y, z, vx.., ax.., A, Adot, h, rho, f,
+        m, bin, ti_begin, ti_end, ti_drift) at integer time ti.  With first,
+        A holds u and the next step is the initial one."""
+        pos = np.stack([st["x"], st["y"], st["z"]], axis=1).astype(np.float64)
+        vel = np.stack([st["vx"], st["vy"], st["vz"]], axis=1).astype(np.float64)
+        s = cls(pos, vel, st["m"].astype(np.float64), st["A"].astype(np.float64),
+                st["h"].astype(np.float64), **kw)
+        s.pos = pos.copy()
+        s.acc = np.stack([st["ax"], st["ay"], st["az"]], axis=1).astype(np.float64)
+        s.A = st["A"].astype(np.float64).copy()
+        s.Adot = st["Adot"].astype(np.float64).copy()
+        s.rho = st["rho"].astype(np.float64).copy()
+        s.f = st["f"].astype(np.float64).copy()
+        s.bin = st["bin"].astype(np.int8).copy()
+        s.ti_begin = st["ti_begin"].astype(np.int64).copy()
+        s.ti_end = st["ti_end"].astype(np.int64).copy()
+        s.ti_drift = st["ti_drift"].astype(np.int64).copy()
+        s.ti = int(ti)
+        s.first = bool(first)
+        return s
 
     def momentum(self):
         return (self.m[:, None] * self.vel).sum(axis=0)

@@ -1,0 +1,843 @@
+// C ABI of libsph_gb300 (declared in include/sph.h): the context, the cell
+// build, the individual hot-path calls and the two forms of a full
+// kick-drift-kick step (plain per-bin launches, and the batched form with
+// persistent pair-loop kernels replayed from a CUDA graph).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sph_internal.cuh"
+
+#include <atomic>
+
+using namespace sph;
+
+namespace sph {
+static std::atomic<unsigned long long> g_launches{0};
+void note_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+}  // namespace sph
+
+namespace {
+
+constexpr int NC_MAX = 255;  // cells per axis (the exclusive scan covers <= 2^24 entries)
+
+struct Buffers {
+  // sort
+  unsigned long long *keys[2] = {nullptr, nullptr};
+  unsigned int *vals[2] = {nullptr, nullptr};
+  unsigned int *hist = nullptr;
+  unsigned int *scan_tmp = nullptr;
+  int n_hist_max = 0;
+  void *scratch = nullptr;  // 8 bytes per particle, permutation staging
+  int32_t *perm = nullptr;  // composed permutation since the first build
+  int32_t *perm_tmp = nullptr;
+  int32_t *pcell = nullptr;
+  // leaves (at most one per particle)
+  int32_t *leaf_start = nullptr, *leaf_cell = nullptr;
+  float4 *leaf_lo = nullptr, *leaf_hi = nullptr;
+  uint8_t *leaf_min_bin = nullptr;
+  unsigned long long *leaf_bin_mask = nullptr;
+  int32_t *q_active = nullptr, *q_drift = nullptr, *q_bin = nullptr;
+  // records
+  float4 *rec_xm = nullptr, *rec_xH = nullptr, *rec_v = nullptr, *rec_h = nullptr;
+  // cells (grown on demand)
+  long long cell_cap = 0;
+  int32_t *cell_start = nullptr, *cell_leaf_start = nullptr;
+  unsigned int *cell_stamp = nullptr, *cell_rel_stamp = nullptr;
+  int32_t *q_act_cells = nullptr;
+  unsigned int *leaf_counts = nullptr, *leaf_offsets = nullptr;
+  // state
+  DevState *ds = nullptr;
+  float *d_hmax = nullptr;
+  DevState *h_ds = nullptr;  // pinned host mirror
+};
+
+}  // namespace
+
+struct sph_ctx {
+  sph_params prm;
+  long long n_max = 0;
+  int device = 0;
+  int num_sms = 0;
+  int grid_util = 0;
+  int grid_dens = 0, grid_force = 0;
+  Buffers b;
+  bool built = false;
+  bool entropy_ready = false;  // the first density pass has converted u to A
+  int nc = 0;
+  double w = 0.0;
+  int n_leaves = 0;
+  float h_floor = 0.0f;  // after an h overflow: the next build sizes cells for this h
+  long long alloc_version = 0;
+  long long rebuilds = 0, redone = 0;
+  long long steps_seen = 0;    // device step counter at the last sph_step_sync
+  int pending = 0;             // steps enqueued since the last sph_step_sync
+  bool init_pending = false;   // the entropy-initialising step is enqueued, not yet confirmed
+  // optional CUDA-event timing of the pair-loop launches (0 density, 1 force)
+  bool prof_on = false;
+  cudaEvent_t prof_ev[2][64][2] = {};
+  int prof_n[2] = {0, 0};
+  double prof_ms[2] = {0.0, 0.0};
+  long long prof_launches[2] = {0, 0};
+  // captured batched step
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  long long graph_version = -1;
+  bool graph_profiled = false;
+  int graph_kernels = 0;       // kernel nodes in the captured step
+  sph_particles graph_p;
+};
+
+namespace {
+
+#define SPH_CUDA(call)                          \
+  do {                                          \
+    cudaError_t e_ = (call);                    \
+    if (e_ != cudaSuccess) return SPH_ERR_CUDA; \
+  } while (0)
+
+template <typename T>
+int dalloc(T **p, size_t count) {
+  if (count == 0) count = 1;
+  if (cudaMalloc((void **)p, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return SPH_ERR_NOMEM;
+  }
+  return SPH_OK;
+}
+
+template <typename T>
+void dfree(T *&p) {
+  if (p) cudaFree((void *)p);
+  p = nullptr;
+}
+
+#define SPH_TRY(x)               \
+  do {                           \
+    int r_ = (x);                \
+    if (r_ != SPH_OK) return r_; \
+  } while (0)
+
+cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+bool valid_params(const sph_params *p) {
+  if (!p) return false;
+  if (!(p->box > 0) || !(p->eta > 0) || !(p->gamma > 1.0) || !(p->alpha_visc >= 0)) return false;
+  if (!(p->cfl > 0) || !(p->h_tol > 0) || p->h_max_iter < 1 || p->bin_cap < 0 || p->bin_cap > 62)
+    return false;
+  if (!(p->dt_min > 0) || !(p->cell_margin >= 1.0)) return false;
+  if (p->leaf_max < 1 || p->leaf_max > LEAF_MAX_LIMIT) return false;
+  int G = p->threads_per_particle;
+  if (G != 1 && G != 2 && G != 4 && G != 8 && G != 16 && G != 32) return false;
+  if (p->n_cells_override < 0 || p->n_cells_override > NC_MAX) return false;
+  return true;
+}
+
+bool valid_particles(const sph_ctx *ctx, const sph_particles *p) {
+  if (!p || p->n < 0 || p->n > ctx->n_max) return false;
+  if (p->n == 0) return true;
+  const void *req[] = {p->x,  p->y,  p->z,   p->vx,  p->vy,   p->vz,       p->ax,     p->ay,
+                       p->az, p->A,  p->Adot, p->h,  p->rho,  p->f,        p->P,      p->c,
+                       p->vsig, p->m, p->bin, p->ti_begin, p->ti_end, p->ti_drift, p->active};
+  for (const void *q : req)
+    if (!q) return false;
+  return true;
+}
+
+View make_view(const sph_ctx *ctx, const sph_particles *p) {
+  View v;
+  std::memset(&v, 0, sizeof(v));
+  v.n = p ? p->n : 0;
+  if (p) {
+    v.x = p->x; v.y = p->y; v.z = p->z;
+    v.vx = p->vx; v.vy = p->vy; v.vz = p->vz;
+    v.ax = p->ax; v.ay = p->ay; v.az = p->az;
+    v.A = p->A; v.Adot = p->Adot; v.h = p->h; v.rho = p->rho; v.f = p->f; v.P = p->P;
+    v.c = p->c; v.vsig = p->vsig; v.m = p->m; v.bin = p->bin;
+    v.ti_begin = reinterpret_cast<long long *>(p->ti_begin);
+    v.ti_end = reinterpret_cast<long long *>(p->ti_end);
+    v.ti_drift = reinterpret_cast<long long *>(p->ti_drift);
+    v.active = p->active;
+    v.ngb_density = p->ngb_density;
+    v.ngb_force = p->ngb_force;
+  }
+  const Buffers &b = ctx->b;
+  v.cell_start = b.cell_start;
+  v.cell_leaf_start = b.cell_leaf_start;
+  v.cell_stamp = b.cell_stamp;
+  v.cell_rel_stamp = b.cell_rel_stamp;
+  v.leaf_start = b.leaf_start;
+  v.leaf_cell = b.leaf_cell;
+  v.leaf_lo = b.leaf_lo;
+  v.leaf_hi = b.leaf_hi;
+  v.leaf_min_bin = b.leaf_min_bin;
+  v.leaf_bin_mask = b.leaf_bin_mask;
+  v.pcell = b.pcell;
+  v.rec_xm = b.rec_xm;
+  v.rec_xH = b.rec_xH;
+  v.rec_v = b.rec_v;
+  v.rec_h = b.rec_h;
+  v.q_active = b.q_active;
+  v.q_act_cells = b.q_act_cells;
+  v.q_drift = b.q_drift;
+  v.q_bin = b.q_bin;
+  v.ds = b.ds;
+  const sph_params &q = ctx->prm;
+  v.box = q.box;
+  v.eta = q.eta;
+  v.gamma = q.gamma;
+  v.alpha = q.alpha_visc;
+  v.cfl = q.cfl;
+  v.h_tol = q.h_tol;
+  v.dt_min = q.dt_min;
+  v.h_max_iter = q.h_max_iter;
+  v.bin_cap = q.bin_cap;
+  v.leaf_max = q.leaf_max;
+  v.G = q.threads_per_particle;
+  v.drift_all = q.drift_all;
+  v.grid_util = ctx->grid_util;
+  return v;
+}
+
+int ensure_cells(sph_ctx *ctx, long long n_cells) {
+  Buffers &b = ctx->b;
+  if (n_cells <= b.cell_cap) return SPH_OK;
+  cudaDeviceSynchronize();
+  dfree(b.cell_start);
+  dfree(b.cell_leaf_start);
+  dfree(b.cell_stamp);
+  dfree(b.cell_rel_stamp);
+  dfree(b.q_act_cells);
+  dfree(b.leaf_counts);
+  dfree(b.leaf_offsets);
+  long long cap = std::max<long long>(n_cells, b.cell_cap * 2);
+  cap = std::min<long long>(cap, (long long)NC_MAX * NC_MAX * NC_MAX);
+  cap = std::max(cap, n_cells);
+  SPH_TRY(dalloc(&b.cell_start, cap + 1));
+  SPH_TRY(dalloc(&b.cell_leaf_start, cap + 1));
+  SPH_TRY(dalloc(&b.cell_stamp, cap));
+  SPH_TRY(dalloc(&b.cell_rel_stamp, cap));
+  SPH_TRY(dalloc(&b.q_act_cells, cap));
+  SPH_TRY(dalloc(&b.leaf_counts, cap + 1));
+  SPH_TRY(dalloc(&b.leaf_offsets, cap + 1));
+  SPH_CUDA(cudaMemset(b.cell_stamp, 0, sizeof(unsigned int) * cap));
+  SPH_CUDA(cudaMemset(b.cell_rel_stamp, 0, sizeof(unsigned int) * cap));
+  b.cell_cap = cap;
+  ctx->alloc_version++;
+  return SPH_OK;
+}
+
+int read_state(sph_ctx *ctx, cudaStream_t st) {
+  SPH_CUDA(cudaMemcpyAsync(ctx->b.h_ds, ctx->b.ds, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+  SPH_CUDA(cudaStreamSynchronize(st));
+  return SPH_OK;
+}
+
+void prof_begin(sph_ctx *ctx, int kind, cudaStream_t st) {
+  if (ctx->prof_on && ctx->prof_n[kind] < 64) cudaEventRecord(ctx->prof_ev[kind][ctx->prof_n[kind]][0], st);
+}
+
+void prof_end(sph_ctx *ctx, int kind, cudaStream_t st) {
+  if (ctx->prof_on && ctx->prof_n[kind] < 64) {
+    cudaEventRecord(ctx->prof_ev[kind][ctx->prof_n[kind]][1], st);
+    ctx->prof_n[kind]++;
+  }
+}
+
+// after a synchronisation: add the recorded launch durations
+void prof_collect(sph_ctx *ctx) {
+  for (int k = 0; k < 2; k++) {
+    for (int i = 0; i < ctx->prof_n[k]; i++) {
+      float ms = 0.0f;
+      if (cudaEventElapsedTime(&ms, ctx->prof_ev[k][i][0], ctx->prof_ev[k][i][1]) == cudaSuccess) {
+        ctx->prof_ms[k] += ms;
+        ctx->prof_launches[k]++;
+      } else {
+        cudaGetLastError();
+      }
+    }
+    ctx->prof_n[k] = 0;
+  }
+}
+
+int permute_array(sph_ctx *ctx, void *arr, int elem, long long n, const unsigned int *perm,
+                  cudaStream_t st) {
+  if (!arr) return SPH_OK;
+  SPH_CUDA(launch_gather(ctx->b.scratch, arr, perm, n, elem, st));
+  SPH_CUDA(cudaMemcpyAsync(arr, ctx->b.scratch, (size_t)n * elem, cudaMemcpyDeviceToDevice, st));
+  return SPH_OK;
+}
+
+int build_cells(sph_ctx *ctx, sph_particles *p, cudaStream_t st) {
+  if (!valid_particles(ctx, p)) return SPH_ERR_ARG;
+  Buffers &b = ctx->b;
+  const long long n = p->n;
+  if (!ctx->built && n > 0) {
+    // the composed permutation starts as the identity
+    std::vector<int32_t> id((size_t)n);
+    for (long long k = 0; k < n; k++) id[(size_t)k] = (int32_t)k;
+    SPH_CUDA(cudaMemcpyAsync(b.perm, id.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+    SPH_CUDA(cudaStreamSynchronize(st));
+  }
+  View v = make_view(ctx, p);
+  // cells per axis from the largest support
+  int nc = ctx->prm.n_cells_override;
+  if (nc <= 0) {
+    SPH_CUDA(launch_reduce_hmax(v, b.d_hmax, st));
+    float hmax = 0.0f;
+    SPH_CUDA(cudaMemcpyAsync(&hmax, b.d_hmax, sizeof(float), cudaMemcpyDeviceToHost, st));
+    SPH_CUDA(cudaStreamSynchronize(st));
+    if (n > 0 && !(hmax > 0.0f && std::isfinite(hmax))) return SPH_ERR_ARG;
+    hmax = std::max(hmax, ctx->h_floor);
+    double Hmax = GAMMA_K_D * (double)hmax;
+    double ncd = n > 0 ? std::floor(ctx->prm.box / (ctx->prm.cell_margin * Hmax)) : 3.0;
+    nc = (int)std::max(3.0, std::min((double)NC_MAX, ncd));
+  }
+  const long long n_cells = (long long)nc * nc * nc;
+  SPH_TRY(ensure_cells(ctx, n_cells));
+  v = make_view(ctx, p);
+  const double w = ctx->prm.box / (double)nc;
+  // keys, stable radix sort, permutation of every particle array
+  SPH_CUDA(launch_cell_keys(v, nc, w, b.keys[0], b.vals[0], st));
+  int cell_bits = 1;
+  while ((1LL << cell_bits) < n_cells) cell_bits++;
+  bool alt = false;
+  SPH_CUDA(radix_sort_pairs(b.keys[0], b.vals[0], b.keys[1], b.vals[1], (int)n,
+                            KEY_MORTON_BITS + cell_bits, b.hist, b.scan_tmp, b.n_hist_max, &alt,
+                            st));
+  unsigned long long *skeys = alt ? b.keys[1] : b.keys[0];
+  unsigned int *perm = alt ? b.vals[1] : b.vals[0];
+  SPH_TRY(permute_array(ctx, p->x, 8, n, perm, st));
+  SPH_TRY(permute_array(ctx, p->y, 8, n, perm, st));
+  SPH_TRY(permute_array(ctx, p->z, 8, n, perm, st));
+  float *f32[] = {p->vx, p->vy, p->vz, p->ax, p->ay, p->az, p->A, p->Adot, p->h,
+                  p->rho, p->f, p->P, p->c, p->vsig, p->m};
+  for (float *a : f32) SPH_TRY(permute_array(ctx, a, 4, n, perm, st));
+  SPH_TRY(permute_array(ctx, p->bin, 1, n, perm, st));
+  SPH_TRY(permute_array(ctx, p->ti_begin, 8, n, perm, st));
+  SPH_TRY(permute_array(ctx, p->ti_end, 8, n, perm, st));
+  SPH_TRY(permute_array(ctx, p->ti_drift, 8, n, perm, st));
+  SPH_TRY(permute_array(ctx, p->ngb_density, 4, n, perm, st));
+  SPH_TRY(permute_array(ctx, p->ngb_force, 4, n, perm, st));
+  if (n > 0) {
+    SPH_CUDA(launch_gather(b.perm_tmp, b.perm, perm, n, 4, st));
+    SPH_CUDA(cudaMemcpyAsync(b.perm, b.perm_tmp, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st));
+    SPH_CUDA(cudaMemsetAsync(p->active, 0, (size_t)n, st));
+  }
+  // cells and leaves
+  SPH_CUDA(launch_cell_start(skeys, n, (int)n_cells, b.cell_start, b.pcell, st));
+  SPH_CUDA(launch_leaf_count(skeys, b.cell_start, (int)n_cells, ctx->prm.leaf_max, b.leaf_counts, st));
+  SPH_CUDA(exclusive_scan_u32(b.leaf_counts, b.leaf_offsets, (int)n_cells + 1, b.scan_tmp, st));
+  SPH_CUDA(launch_leaf_write(skeys, b.cell_start, (int)n_cells, ctx->prm.leaf_max, b.leaf_offsets,
+                             b.leaf_start, b.leaf_cell, b.cell_leaf_start, n, st));
+  // device state of the new structure
+  SPH_CUDA(cudaMemcpyAsync(SPH_DS_FIELD(b.ds, n_leaves), b.leaf_offsets + n_cells, sizeof(int),
+                           cudaMemcpyDeviceToDevice, st));
+  int ncs[2] = {nc, (int)n_cells};
+  SPH_CUDA(cudaMemcpyAsync(SPH_DS_FIELD(b.ds, nc), &ncs[0], sizeof(int), cudaMemcpyHostToDevice, st));
+  SPH_CUDA(cudaMemcpyAsync(SPH_DS_FIELD(b.ds, n_cells), &ncs[1], sizeof(int), cudaMemcpyHostToDevice, st));
+  SPH_CUDA(cudaMemcpyAsync(SPH_DS_FIELD(b.ds, w), &w, sizeof(double), cudaMemcpyHostToDevice, st));
+  SPH_CUDA(cudaMemsetAsync(SPH_DS_FIELD(b.ds, n_active_leaves), 0, sizeof(int), st));
+  SPH_CUDA(cudaMemsetAsync(SPH_DS_FIELD(b.ds, excursion_bits), 0, sizeof(unsigned int), st));
+  SPH_CUDA(cudaMemsetAsync(SPH_DS_FIELD(b.ds, Hmax_bits), 0, sizeof(unsigned int), st));
+  SPH_CUDA(cudaMemsetAsync(SPH_DS_FIELD(b.ds, want_h_bits), 0, sizeof(unsigned int), st));
+  SPH_CUDA(launch_bin_histogram(v, st));
+  SPH_CUDA(launch_refresh_all(v, st));
+  int nl = 0;
+  SPH_CUDA(cudaMemcpyAsync(&nl, b.leaf_offsets + n_cells, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SPH_CUDA(cudaStreamSynchronize(st));
+  ctx->n_leaves = nl;
+  ctx->h_floor = 0.0f;
+  ctx->nc = nc;
+  ctx->w = w;
+  ctx->built = true;
+  ctx->rebuilds++;
+  return SPH_OK;
+}
+
+// --- pieces of a step ------------------------------------------------------
+int dens_flags(const sph_ctx *ctx) { return ctx->entropy_ready ? 0 : SPH_DENSITY_INIT_ENTROPY; }
+
+int batched_body(sph_ctx *ctx, const View &v, int flags, cudaStream_t st) {
+  SPH_CUDA(launch_mark(v, -1, st));
+  SPH_CUDA(launch_drift(v, st));
+  prof_begin(ctx, 0, st);
+  SPH_CUDA(launch_density(v, flags, -1, true, ctx->grid_dens, st));
+  prof_end(ctx, 0, st);
+  if (flags & SPH_DENSITY_INIT_ENTROPY) SPH_CUDA(launch_entropy_from_u(v, st));
+  prof_begin(ctx, 1, st);
+  SPH_CUDA(launch_force(v, -1, true, ctx->grid_force, st));
+  prof_end(ctx, 1, st);
+  SPH_CUDA(launch_kick(v, SPH_KICK_CLOSE, st));
+  SPH_CUDA(launch_bins(v, nullptr, 1, st));
+  SPH_CUDA(launch_kick(v, SPH_KICK_OPEN, st));
+  return SPH_OK;
+}
+
+int plain_body(sph_ctx *ctx, const View &v, int flags, cudaStream_t st) {
+  SPH_CUDA(launch_mark(v, -1, st));
+  SPH_CUDA(launch_drift(v, st));
+  SPH_TRY(read_state(ctx, st));
+  const DevState &h = *ctx->b.h_ds;
+  int bins[MAX_BINS], nb = 0;
+  for (int b = 0; b <= std::min(h.m_act, MAX_BINS - 1); b++)
+    if (h.bin_count[b] > 0) bins[nb++] = b;
+  // one density launch per active bin, the grid sized from the bin's queue
+  for (int k = 0; k < nb; k++) {
+    SPH_CUDA(launch_mark_bin(v, bins[k], st));
+    int nq = 0;
+    SPH_CUDA(cudaMemcpyAsync(&nq, SPH_DS_FIELD(v.ds, n_bin_leaves), sizeof(int),
+                             cudaMemcpyDeviceToHost, st));
+    SPH_CUDA(cudaStreamSynchronize(st));
+    prof_begin(ctx, 0, st);
+    SPH_CUDA(launch_density(v, flags, bins[k], false, (nq + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK, st));
+    prof_end(ctx, 0, st);
+  }
+  if (flags & SPH_DENSITY_INIT_ENTROPY) SPH_CUDA(launch_entropy_from_u(v, st));
+  for (int k = 0; k < nb; k++) {
+    SPH_CUDA(launch_mark_bin(v, bins[k], st));
+    int nq = 0;
+    SPH_CUDA(cudaMemcpyAsync(&nq, SPH_DS_FIELD(v.ds, n_bin_leaves), sizeof(int),
+                             cudaMemcpyDeviceToHost, st));
+    SPH_CUDA(cudaStreamSynchronize(st));
+    prof_begin(ctx, 1, st);
+    SPH_CUDA(launch_force(v, bins[k], false, (nq + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK, st));
+    prof_end(ctx, 1, st);
+  }
+  SPH_CUDA(launch_kick(v, SPH_KICK_CLOSE, st));
+  SPH_CUDA(launch_bins(v, nullptr, 1, st));
+  SPH_CUDA(launch_kick(v, SPH_KICK_OPEN, st));
+  return SPH_OK;
+}
+
+// After a halted step: rebuild with wider cells when the cells overflowed.
+int recover(sph_ctx *ctx, sph_particles *p, cudaStream_t st, bool *redo) {
+  *redo = false;
+  SPH_TRY(read_state(ctx, st));
+  const DevState &h = *ctx->b.h_ds;
+  if (!h.halt) return SPH_OK;
+  if (h.first_error != SPH_ERR_CELL_OVERFLOW) return h.first_error ? h.first_error : SPH_ERR_CUDA;
+  // the cells are too small for the supports: rebuild.  When an h iteration
+  // wanted to grow past the cell, size the new cells for the h it wanted.
+  float want_h, Hmax;
+  std::memcpy(&want_h, &h.want_h_bits, sizeof(float));
+  std::memcpy(&Hmax, &h.Hmax_bits, sizeof(float));
+  if (ctx->nc <= 3 && (double)Hmax > ctx->w)
+    return SPH_ERR_CELL_OVERFLOW;  // even three cells per axis are narrower than a support
+  if (want_h > 0.0f) {
+    if (ctx->nc <= 3 || ctx->prm.n_cells_override > 0)
+      return SPH_ERR_CELL_OVERFLOW;  // the box cannot hold three cells of this support
+    ctx->h_floor = want_h * 1.05f;
+  }
+  SPH_CUDA(cudaMemsetAsync(SPH_DS_FIELD(ctx->b.ds, halt), 0, sizeof(unsigned int), st));
+  SPH_CUDA(cudaMemsetAsync(SPH_DS_FIELD(ctx->b.ds, first_error), 0, sizeof(int), st));
+  SPH_CUDA(cudaMemsetAsync(SPH_DS_FIELD(ctx->b.ds, err_count), 0, sizeof(h.err_count), st));
+  SPH_TRY(build_cells(ctx, p, st));
+  ctx->redone++;
+  *redo = true;
+  return SPH_OK;
+}
+
+int capture_graph(sph_ctx *ctx, sph_particles *p) {
+  if (ctx->graph) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
+  View v = make_view(ctx, p);
+  cudaGraph_t g = nullptr;
+  const int saved_n[2] = {ctx->prof_n[0], ctx->prof_n[1]};
+  ctx->prof_n[0] = ctx->prof_n[1] = 0;  // the graph records into slot 0 of each kind
+  SPH_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+  const unsigned long long before = g_launches.load();
+  int r = batched_body(ctx, v, 0, ctx->cap_stream);
+  ctx->graph_kernels = (int)(g_launches.load() - before);
+  g_launches.fetch_sub((unsigned long long)ctx->graph_kernels);  // captured, not launched
+  cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+  ctx->prof_n[0] = saved_n[0];
+  ctx->prof_n[1] = saved_n[1];
+  ctx->graph_profiled = ctx->prof_on;
+  if (r != SPH_OK) {
+    if (g) cudaGraphDestroy(g);
+    return r;
+  }
+  if (e != cudaSuccess) return SPH_ERR_CUDA;
+  e = cudaGraphInstantiate(&ctx->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return SPH_ERR_CUDA;
+  ctx->graph_version = ctx->alloc_version;
+  ctx->graph_p = *p;
+  return SPH_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void sph_default_params(sph_params *p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->box = 1.0;
+  p->eta = 1.2348;
+  p->gamma = 5.0 / 3.0;
+  p->alpha_visc = 0.8;
+  p->cfl = 0.1;
+  p->h_tol = 1e-6;
+  p->h_max_iter = 30;
+  p->bin_cap = 20;
+  p->dt_min = 1e-6;
+  p->t_begin = 0.0;
+  p->cell_margin = 1.1;
+  p->leaf_max = 16;
+  p->threads_per_particle = 4;
+  p->drift_all = 0;
+  p->n_cells_override = 0;
+}
+
+const char *sph_strerror(int code) {
+  switch (code) {
+    case SPH_OK: return "ok";
+    case SPH_ERR_ARG: return "invalid argument";
+    case SPH_ERR_CUDA: return "CUDA runtime error";
+    case SPH_ERR_H_NOCONV: return "smoothing length did not converge";
+    case SPH_ERR_CELL_OVERFLOW: return "kernel support outgrew the cell width (rebuild needed)";
+    case SPH_ERR_DT_TOO_SMALL: return "time step below dt_min";
+    case SPH_ERR_TIMEOUT: return "bounded device wait timed out";
+    case SPH_ERR_NOMEM: return "device allocation failed";
+    case SPH_ERR_NOT_BUILT: return "cells not built";
+    default: return "unknown error";
+  }
+}
+
+int sph_create(const sph_params *params, int64_t n_max, sph_ctx **out) {
+  if (!out || !valid_params(params) || n_max < 0 || n_max > (1LL << 30)) return SPH_ERR_ARG;
+  *out = nullptr;
+  sph_ctx *ctx = new (std::nothrow) sph_ctx();
+  if (!ctx) return SPH_ERR_NOMEM;
+  ctx->prm = *params;
+  ctx->n_max = n_max;
+  int r = SPH_OK;
+  do {
+    if (cudaGetDevice(&ctx->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device) !=
+            cudaSuccess) {
+      r = SPH_ERR_CUDA;
+      break;
+    }
+    ctx->grid_util = ctx->num_sms * 4;
+    const int G = params->threads_per_particle;
+    ctx->grid_dens = ctx->num_sms * persistent_blocks_per_sm(G, true);
+    ctx->grid_force = ctx->num_sms * persistent_blocks_per_sm(G, false);
+    Buffers &b = ctx->b;
+    const long long n = std::max<long long>(n_max, 1);
+    const long long n_tiles = (n + 4095) / 4096;
+    b.n_hist_max = (int)(256 * n_tiles);
+    if ((r = dalloc(&b.keys[0], n)) || (r = dalloc(&b.keys[1], n)) || (r = dalloc(&b.vals[0], n)) ||
+        (r = dalloc(&b.vals[1], n)) || (r = dalloc(&b.hist, b.n_hist_max)) ||
+        (r = dalloc(&b.scan_tmp, 4096)) || (r = dalloc((char **)&b.scratch, 8 * n)) ||
+        (r = dalloc(&b.perm, n)) || (r = dalloc(&b.perm_tmp, n)) || (r = dalloc(&b.pcell, n)) ||
+        (r = dalloc(&b.leaf_start, n + 1)) || (r = dalloc(&b.leaf_cell, n)) ||
+        (r = dalloc(&b.leaf_lo, n)) || (r = dalloc(&b.leaf_hi, n)) ||
+        (r = dalloc(&b.leaf_min_bin, n)) || (r = dalloc(&b.leaf_bin_mask, n)) ||
+        (r = dalloc(&b.q_active, n)) || (r = dalloc(&b.q_drift, n)) || (r = dalloc(&b.q_bin, n)) ||
+        (r = dalloc(&b.rec_xm, n)) || (r = dalloc(&b.rec_xH, n)) || (r = dalloc(&b.rec_v, n)) ||
+        (r = dalloc(&b.rec_h, n)) || (r = dalloc(&b.ds, 1)) || (r = dalloc(&b.d_hmax, 1)))
+      break;
+    if (cudaMallocHost((void **)&b.h_ds, sizeof(DevState)) != cudaSuccess) {
+      r = SPH_ERR_NOMEM;
+      break;
+    }
+    if (cudaMemset(b.ds, 0, sizeof(DevState)) != cudaSuccess) {
+      r = SPH_ERR_CUDA;
+      break;
+    }
+    if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      r = SPH_ERR_CUDA;
+      break;
+    }
+  } while (0);
+  if (r != SPH_OK) {
+    sph_destroy(ctx);
+    return r;
+  }
+  *out = ctx;
+  return SPH_OK;
+}
+
+int sph_destroy(sph_ctx *ctx) {
+  if (!ctx) return SPH_ERR_ARG;
+  cudaDeviceSynchronize();
+  if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  for (auto &kind : ctx->prof_ev)
+    for (auto &pair : kind)
+      for (auto &ev : pair)
+        if (ev) cudaEventDestroy(ev);
+  Buffers &b = ctx->b;
+  dfree(b.keys[0]); dfree(b.keys[1]); dfree(b.vals[0]); dfree(b.vals[1]);
+  dfree(b.hist); dfree(b.scan_tmp);
+  if (b.scratch) cudaFree(b.scratch);
+  dfree(b.perm); dfree(b.perm_tmp); dfree(b.pcell);
+  dfree(b.leaf_start); dfree(b.leaf_cell); dfree(b.leaf_lo); dfree(b.leaf_hi);
+  dfree(b.leaf_min_bin); dfree(b.leaf_bin_mask);
+  dfree(b.q_active); dfree(b.q_drift); dfree(b.q_bin);
+  dfree(b.rec_xm); dfree(b.rec_xH); dfree(b.rec_v); dfree(b.rec_h);
+  dfree(b.cell_start); dfree(b.cell_leaf_start); dfree(b.cell_stamp); dfree(b.cell_rel_stamp);
+  dfree(b.q_act_cells); dfree(b.leaf_counts); dfree(b.leaf_offsets);
+  dfree(b.ds); dfree(b.d_hmax);
+  if (b.h_ds) cudaFreeHost(b.h_ds);
+  delete ctx;
+  return SPH_OK;
+}
+
+int sph_build_cells(sph_ctx *ctx, sph_particles *p, void *stream) {
+  if (!ctx) return SPH_ERR_ARG;
+  return build_cells(ctx, p, S(stream));
+}
+
+const int32_t *sph_perm(const sph_ctx *ctx) { return ctx && ctx->built ? ctx->b.perm : nullptr; }
+
+int sph_grid_info(const sph_ctx *ctx, int *nc, int *n_leaves) {
+  if (!ctx) return SPH_ERR_ARG;
+  if (!ctx->built) return SPH_ERR_NOT_BUILT;
+  if (nc) *nc = ctx->nc;
+  if (n_leaves) *n_leaves = ctx->n_leaves;
+  return SPH_OK;
+}
+
+int sph_mark_active(sph_ctx *ctx, sph_particles *p, int64_t ti_current, void *stream) {
+  if (!ctx || !valid_particles(ctx, p)) return SPH_ERR_ARG;
+  if (!ctx->built) return SPH_ERR_NOT_BUILT;
+  SPH_CUDA(launch_mark(make_view(ctx, p), ti_current < 0 ? -1 : ti_current, S(stream)));
+  return SPH_OK;
+}
+
+int sph_kick_drift(sph_ctx *ctx, sph_particles *p, int phase, void *stream) {
+  if (!ctx || !valid_particles(ctx, p)) return SPH_ERR_ARG;
+  if (!ctx->built) return SPH_ERR_NOT_BUILT;
+  View v = make_view(ctx, p);
+  switch (phase) {
+    case SPH_DRIFT: SPH_CUDA(launch_drift(v, S(stream))); break;
+    case SPH_KICK_CLOSE:
+    case SPH_KICK_OPEN: SPH_CUDA(launch_kick(v, phase, S(stream))); break;
+    default: return SPH_ERR_ARG;
+  }
+  return SPH_OK;
+}
+
+int sph_density_active(sph_ctx *ctx, sph_particles *p, int flags, void *stream) {
+  if (!ctx || !valid_particles(ctx, p)) return SPH_ERR_ARG;
+  if (!ctx->built) return SPH_ERR_NOT_BUILT;
+  View v = make_view(ctx, p);
+  SPH_CUDA(launch_density(v, flags, -1, true, ctx->grid_dens, S(stream)));
+  if (flags & SPH_DENSITY_INIT_ENTROPY) SPH_CUDA(launch_entropy_from_u(v, S(stream)));
+  return SPH_OK;
+}
+
+int sph_force_active(sph_ctx *ctx, sph_particles *p, void *stream) {
+  if (!ctx || !valid_particles(ctx, p)) return SPH_ERR_ARG;
+  if (!ctx->built) return SPH_ERR_NOT_BUILT;
+  SPH_CUDA(launch_force(make_view(ctx, p), -1, true, ctx->grid_force, S(stream)));
+  return SPH_OK;
+}
+
+int sph_timestep_bins(sph_ctx *ctx, sph_particles *p, int64_t *ti_next_dev, void *stream) {
+  if (!ctx || !valid_particles(ctx, p)) return SPH_ERR_ARG;
+  if (!ctx->built) return SPH_ERR_NOT_BUILT;
+  SPH_CUDA(launch_bins(make_view(ctx, p), reinterpret_cast<long long *>(ti_next_dev), 0, S(stream)));
+  return SPH_OK;
+}
+
+int sph_begin_run(sph_ctx *ctx, void *stream) {
+  if (!ctx) return SPH_ERR_ARG;
+  cudaStream_t st = S(stream);
+  long long zero = 0;
+  SPH_CUDA(cudaMemcpyAsync(SPH_DS_FIELD(ctx->b.ds, ti), &zero, sizeof(zero), cudaMemcpyHostToDevice, st));
+  SPH_CUDA(cudaMemcpyAsync(SPH_DS_FIELD(ctx->b.ds, ti_next), &zero, sizeof(zero), cudaMemcpyHostToDevice, st));
+  SPH_TRY(sph_clear_status(ctx, stream));
+  SPH_TRY(sph_reset_counters(ctx, stream));
+  SPH_CUDA(cudaStreamSynchronize(st));
+  ctx->entropy_ready = false;
+  ctx->pending = 0;
+  ctx->init_pending = false;
+  return SPH_OK;
+}
+
+int sph_step_async(sph_ctx *ctx, sph_particles *p, int form, void *stream) {
+  if (!ctx || !valid_particles(ctx, p) ||
+      (form != SPH_FORM_PLAIN && form != SPH_FORM_BATCHED && form != SPH_FORM_BATCHED_NOGRAPH))
+    return SPH_ERR_ARG;
+  cudaStream_t st = S(stream);
+  if (!ctx->built) SPH_TRY(build_cells(ctx, p, st));
+  View v = make_view(ctx, p);
+  if (!ctx->entropy_ready) {
+    // the first step of a run sets the entropy from u (outside any graph)
+    if (form == SPH_FORM_PLAIN) SPH_TRY(plain_body(ctx, v, SPH_DENSITY_INIT_ENTROPY, st));
+    else SPH_TRY(batched_body(ctx, v, SPH_DENSITY_INIT_ENTROPY, st));
+    ctx->entropy_ready = true;
+    ctx->init_pending = true;
+  } else if (form == SPH_FORM_BATCHED) {
+    if (!ctx->graph || ctx->graph_version != ctx->alloc_version ||
+        ctx->graph_profiled != ctx->prof_on || std::memcmp(&ctx->graph_p, p, sizeof(*p)) != 0) {
+      prof_collect(ctx);
+      SPH_TRY(capture_graph(ctx, p));
+    }
+    SPH_CUDA(cudaGraphLaunch(ctx->graph, st));
+    note_launches(ctx->graph_kernels);
+    if (ctx->prof_on) ctx->prof_n[0] = ctx->prof_n[1] = 1;  // slot 0, recorded by the graph
+  } else if (form == SPH_FORM_BATCHED_NOGRAPH) {
+    SPH_TRY(batched_body(ctx, v, 0, st));
+  } else {
+    SPH_TRY(plain_body(ctx, v, 0, st));
+  }
+  ctx->pending++;
+  return SPH_OK;
+}
+
+int sph_step_sync(sph_ctx *ctx, sph_particles *p, int *completed, void *stream) {
+  if (!ctx || !valid_particles(ctx, p)) return SPH_ERR_ARG;
+  cudaStream_t st = S(stream);
+  SPH_TRY(read_state(ctx, st));
+  prof_collect(ctx);
+  const long long steps = (long long)ctx->b.h_ds->steps;
+  const long long done = steps - ctx->steps_seen;
+  ctx->steps_seen = steps;
+  if (completed) *completed = (int)done;
+  if (ctx->init_pending && done == 0) ctx->entropy_ready = false;  // the first step must rerun
+  if (done > 0) ctx->init_pending = false;
+  ctx->pending = 0;
+  bool redo = false;
+  SPH_TRY(recover(ctx, p, st, &redo));
+  return SPH_OK;
+}
+
+int sph_step(sph_ctx *ctx, sph_particles *p, int form, void *stream) {
+  for (int attempt = 0; attempt < 64; attempt++) {
+    SPH_TRY(sph_step_async(ctx, p, form, stream));
+    int done = 0;
+    SPH_TRY(sph_step_sync(ctx, p, &done, stream));
+    if (done == 1) return SPH_OK;
+  }
+  return SPH_ERR_CELL_OVERFLOW;
+}
+
+int sph_step_graph(sph_ctx *ctx, sph_particles *p, int n_steps, void *stream) {
+  if (!ctx || !valid_particles(ctx, p) || n_steps < 0) return SPH_ERR_ARG;
+  int done = 0, guard = 0;
+  while (done < n_steps) {
+    for (int k = done; k < n_steps; k++) SPH_TRY(sph_step_async(ctx, p, SPH_FORM_BATCHED, stream));
+    int c = 0;
+    SPH_TRY(sph_step_sync(ctx, p, &c, stream));
+    done += c;
+    if (++guard > 64) return SPH_ERR_CELL_OVERFLOW;
+  }
+  return SPH_OK;
+}
+
+int sph_get_time(sph_ctx *ctx, int64_t *ti_current, int64_t *ti_next) {
+  if (!ctx) return SPH_ERR_ARG;
+  SPH_CUDA(cudaMemcpy(ctx->b.h_ds, ctx->b.ds, sizeof(DevState), cudaMemcpyDeviceToHost));
+  if (ti_current) *ti_current = ctx->b.h_ds->ti;
+  if (ti_next) *ti_next = ctx->b.h_ds->ti_next;
+  return SPH_OK;
+}
+
+int sph_set_time(sph_ctx *ctx, int64_t ti_current, void *stream) {
+  if (!ctx || ti_current < 0) return SPH_ERR_ARG;
+  long long t = ti_current;
+  SPH_CUDA(cudaMemcpyAsync(SPH_DS_FIELD(ctx->b.ds, ti), &t, sizeof(t), cudaMemcpyHostToDevice, S(stream)));
+  SPH_CUDA(cudaMemcpyAsync(SPH_DS_FIELD(ctx->b.ds, ti_next), &t, sizeof(t), cudaMemcpyHostToDevice, S(stream)));
+  SPH_CUDA(cudaStreamSynchronize(S(stream)));
+  return SPH_OK;
+}
+
+int sph_get_status(sph_ctx *ctx, int *status, int64_t *detail) {
+  if (!ctx) return SPH_ERR_ARG;
+  SPH_CUDA(cudaDeviceSynchronize());
+  SPH_CUDA(cudaMemcpy(ctx->b.h_ds, ctx->b.ds, sizeof(DevState), cudaMemcpyDeviceToHost));
+  const DevState &h = *ctx->b.h_ds;
+  if (status) *status = h.first_error;
+  if (detail) *detail = h.first_error ? (int64_t)h.err_count[h.first_error & 7] : 0;
+  return SPH_OK;
+}
+
+int sph_clear_status(sph_ctx *ctx, void *stream) {
+  if (!ctx) return SPH_ERR_ARG;
+  cudaStream_t st = S(stream);
+  SPH_CUDA(cudaMemsetAsync(SPH_DS_FIELD(ctx->b.ds, halt), 0, sizeof(unsigned int), st));
+  SPH_CUDA(cudaMemsetAsync(SPH_DS_FIELD(ctx->b.ds, first_error), 0, sizeof(int), st));
+  SPH_CUDA(cudaMemsetAsync(SPH_DS_FIELD(ctx->b.ds, err_count), 0, sizeof(((DevState *)0)->err_count), st));
+  return SPH_OK;
+}
+
+int sph_get_counters(sph_ctx *ctx, sph_counters *out) {
+  if (!ctx || !out) return SPH_ERR_ARG;
+  SPH_CUDA(cudaDeviceSynchronize());
+  SPH_CUDA(cudaMemcpy(ctx->b.h_ds, ctx->b.ds, sizeof(DevState), cudaMemcpyDeviceToHost));
+  const DevState &h = *ctx->b.h_ds;
+  // totals of completed steps plus the calls made outside a step since
+  out->pairs_density = (int64_t)(h.pairs_density + h.s_pairs_density);
+  out->pairs_force = (int64_t)(h.pairs_force + h.s_pairs_force);
+  out->cand_density = (int64_t)(h.cand_density + h.s_cand_density);
+  out->cand_force = (int64_t)(h.cand_force + h.s_cand_force);
+  out->iters_density = (int64_t)(h.iters_density + h.s_iters_density);
+  out->active_particles = (int64_t)(h.active_particles + h.s_active_particles);
+  out->steps = (int64_t)h.steps;
+  out->rebuilds = ctx->rebuilds;
+  out->redone_steps = ctx->redone;
+  out->kernel_launches = (int64_t)g_launches.load();
+  return SPH_OK;
+}
+
+int sph_reset_counters(sph_ctx *ctx, void *stream) {
+  if (!ctx) return SPH_ERR_ARG;
+  cudaStream_t st = S(stream);
+  const size_t off = offsetof(DevState, s_pairs_density);
+  const size_t len = offsetof(DevState, bin_count) - off;
+  SPH_CUDA(cudaMemsetAsync(reinterpret_cast<char *>(ctx->b.ds) + off, 0, len, st));
+  ctx->rebuilds = 0;
+  ctx->redone = 0;
+  ctx->steps_seen = 0;
+  return SPH_OK;
+}
+
+int sph_set_profiling(sph_ctx *ctx, int enable) {
+  if (!ctx) return SPH_ERR_ARG;
+  if (enable && !ctx->prof_ev[0][0][0]) {
+    for (auto &kind : ctx->prof_ev)
+      for (auto &pair : kind)
+        for (auto &ev : pair) SPH_CUDA(cudaEventCreate(&ev));
+  }
+  ctx->prof_on = enable != 0;
+  ctx->prof_n[0] = ctx->prof_n[1] = 0;
+  return SPH_OK;
+}
+
+int sph_get_kernel_times(sph_ctx *ctx, sph_kernel_times *out) {
+  if (!ctx || !out) return SPH_ERR_ARG;
+  SPH_CUDA(cudaDeviceSynchronize());
+  prof_collect(ctx);
+  out->density_ms = ctx->prof_ms[0];
+  out->force_ms = ctx->prof_ms[1];
+  out->density_launches = ctx->prof_launches[0];
+  out->force_launches = ctx->prof_launches[1];
+  return SPH_OK;
+}
+
+int sph_reset_kernel_times(sph_ctx *ctx) {
+  if (!ctx) return SPH_ERR_ARG;
+  SPH_CUDA(cudaDeviceSynchronize());
+  ctx->prof_n[0] = ctx->prof_n[1] = 0;
+  ctx->prof_ms[0] = ctx->prof_ms[1] = 0.0;
+  ctx->prof_launches[0] = ctx->prof_launches[1] = 0;
+  return SPH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,462 @@
+// Top-level cells and leaves (Sec. III-A of arXiv 1807.01341).
+//
+// Particles are binned into an n_c^3 grid whose width is at least the largest
+// kernel support, so a particle only interacts with the 27 cells around its
+// own.  Inside a cell the particles are ordered by the Morton code of their
+// cell-relative position; the Morton order is the cell's octree, and the
+// leaves are octree nodes holding at most leaf_max particles -- the GPU form
+// of the paper's refinement of top-level cells into small sub-cells.  The
+// (cell, Morton) keys are sorted by a stable LSD radix sort, so ties keep the
+// previous particle order and the result is deterministic.
+#include <algorithm>
+#include <cstddef>
+#include <utility>
+
+#include "sph_internal.cuh"
+
+namespace sph {
+
+namespace {
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_ITEMS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+// ---------------------------------------------------------------------------
+// maximum smoothing length
+// ---------------------------------------------------------------------------
+__global__ void k_reduce_hmax(const float *__restrict__ h, long long n, unsigned int *out) {
+  float m = 0.0f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    m = fmaxf(m, h[i]);
+  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomic_max_float_pos(out, m);
+}
+
+// ---------------------------------------------------------------------------
+// cell keys: exact FP64 arithmetic (no contraction) so the cell of every
+// particle is a function of its FP64 position alone
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double wrap_box(double x, double box) {
+  if (x < 0.0) x = __dadd_rn(x, box);
+  if (x >= box) x = __dsub_rn(x, box);
+  return x;
+}
+
+__device__ __forceinline__ int axis_cell(double x, double w, int nc) {
+  int c = (int)floor(__ddiv_rn(x, w));
+  return c < 0 ? 0 : (c > nc - 1 ? nc - 1 : c);
+}
+
+__device__ __forceinline__ unsigned long long axis_morton(double x, int c, double w) {
+  double t = __ddiv_rn(__dsub_rn(x, __dmul_rn((double)c, w)), w);
+  t = __dmul_rn(t, (double)(1 << MORTON_BITS));
+  double ft = floor(t);
+  long long q = (long long)ft;
+  if (ft < 0.0) q = 0;
+  if (q > (1 << MORTON_BITS) - 1) q = (1 << MORTON_BITS) - 1;
+  return (unsigned long long)q;
+}
+
+__device__ __forceinline__ unsigned long long spread3(unsigned long long v) {
+  unsigned long long r = 0;
+#pragma unroll
+  for (int b = 0; b < MORTON_BITS; b++) r |= ((v >> b) & 1ull) << (3 * b);
+  return r;
+}
+
+__global__ void k_cell_keys(View v, int nc, double w, unsigned long long *__restrict__ keys,
+                            unsigned int *__restrict__ vals) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= v.n) return;
+  double x = wrap_box(v.x[i], v.box), y = wrap_box(v.y[i], v.box), z = wrap_box(v.z[i], v.box);
+  v.x[i] = x;
+  v.y[i] = y;
+  v.z[i] = z;
+  int cx = axis_cell(x, w, nc), cy = axis_cell(y, w, nc), cz = axis_cell(z, w, nc);
+  unsigned long long cid = ((unsigned long long)cx * nc + cy) * nc + cz;
+  unsigned long long mort = (spread3(axis_morton(x, cx, w)) << 2) |
+                            (spread3(axis_morton(y, cy, w)) << 1) | spread3(axis_morton(z, cz, w));
+  keys[i] = (cid << KEY_MORTON_BITS) | mort;
+  vals[i] = (unsigned int)i;
+}
+
+// ---------------------------------------------------------------------------
+// block-wide exclusive scan of one value per thread (blockDim.x = SCAN_THREADS)
+// ---------------------------------------------------------------------------
+__device__ unsigned int block_exclusive_scan(unsigned int x, unsigned int *total) {
+  __shared__ unsigned int warp_sums[32];
+  __shared__ unsigned int grand_total;
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned int inc = x;
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned int y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) warp_sums[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    unsigned int s = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0u;
+    unsigned int si = s;
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned int y = __shfl_up_sync(0xffffffffu, si, o);
+      if (lane >= o) si += y;
+    }
+    warp_sums[lane] = si - s;  // exclusive prefix of warp totals
+    if (lane == 31) grand_total = si;
+  }
+  __syncthreads();
+  unsigned int res = warp_sums[wid] + inc - x;
+  if (total) *total = grand_total;
+  __syncthreads();
+  return res;
+}
+
+__global__ void k_scan_reduce(const unsigned int *in, int n,
+                              unsigned int *__restrict__ block_sums) {
+  long long base = (long long)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+  unsigned int s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; k++)
+    if (base + k < n) s += in[base + k];
+  unsigned int tot;
+  block_exclusive_scan(s, &tot);
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_tops(unsigned int *__restrict__ sums, int nb) {
+  // one block: exclusive scan of nb <= SCAN_TILE block sums in place
+  int base = threadIdx.x * SCAN_ITEMS;
+  unsigned int v[SCAN_ITEMS];
+  unsigned int s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; k++) {
+    v[k] = (base + k < nb) ? sums[base + k] : 0u;
+    s += v[k];
+  }
+  unsigned int pre = block_exclusive_scan(s, nullptr);
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; k++) {
+    if (base + k < nb) sums[base + k] = pre;
+    pre += v[k];
+  }
+}
+
+// `in` and `out` may be the same array: each thread reads its items before
+// the block-wide barrier and writes the same items after it.
+__global__ void k_scan_down(const unsigned int *in, unsigned int *out, int n,
+                            const unsigned int *__restrict__ block_sums) {
+  long long base = (long long)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+  unsigned int v[SCAN_ITEMS];
+  unsigned int s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; k++) {
+    v[k] = (base + k < n) ? in[base + k] : 0u;
+    s += v[k];
+  }
+  unsigned int pre = block_exclusive_scan(s, nullptr) + block_sums[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; k++) {
+    if (base + k < n) out[base + k] = pre;
+    pre += v[k];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// stable LSD radix sort, 8-bit digits
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(RS_THREADS)
+    k_rs_hist(const unsigned long long *__restrict__ keys, int n, int shift,
+              unsigned int *__restrict__ hist, int n_tiles) {
+  __shared__ unsigned int h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  long long base = (long long)blockIdx.x * RS_TILE;
+#pragma unroll 4
+  for (int r = 0; r < RS_ITEMS; r++) {
+    long long idx = base + r * RS_THREADS + threadIdx.x;
+    if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  hist[(long long)threadIdx.x * n_tiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(RS_THREADS)
+    k_rs_scatter(const unsigned long long *__restrict__ keys, const unsigned int *__restrict__ vals,
+                 unsigned long long *__restrict__ okeys, unsigned int *__restrict__ ovals, int n,
+                 int shift, const unsigned int *__restrict__ offs, int n_tiles) {
+  __shared__ unsigned int base[256];
+  __shared__ unsigned int goff[256];
+  __shared__ unsigned int wcnt[RS_THREADS / 32][256];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  base[t] = 0;
+  goff[t] = offs[(long long)t * n_tiles + blockIdx.x];
+  const unsigned int lt_mask = (1u << lane) - 1u;
+  long long tile = (long long)blockIdx.x * RS_TILE;
+  for (int r = 0; r < RS_ITEMS; r++) {
+#pragma unroll
+    for (int k = 0; k < RS_THREADS / 32; k++) wcnt[k][t] = 0;
+    __syncthreads();
+    long long idx = tile + r * RS_THREADS + t;
+    bool valid = idx < n;
+    unsigned long long key = valid ? keys[idx] : 0ull;
+    unsigned int d = valid ? (unsigned int)((key >> shift) & 255u) : 256u + lane;
+    unsigned int peers = __match_any_sync(0xffffffffu, d);
+    unsigned int rank = __popc(peers & lt_mask);
+    if (valid && rank == 0) wcnt[warp][d] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      unsigned int pre = base[d];
+      for (int k = 0; k < warp; k++) pre += wcnt[k][d];
+      unsigned int pos = goff[d] + pre + rank;
+      okeys[pos] = key;
+      ovals[pos] = vals[idx];
+    }
+    __syncthreads();
+    unsigned int s = 0;
+#pragma unroll
+    for (int k = 0; k < RS_THREADS / 32; k++) s += wcnt[k][t];
+    base[t] += s;
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// gather
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_gather(T *__restrict__ dst, const T *__restrict__ src,
+                         const unsigned int *__restrict__ idx, long long n) {
+  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k < n) dst[k] = src[idx[k]];
+}
+
+// ---------------------------------------------------------------------------
+// cell boundaries and leaves
+// ---------------------------------------------------------------------------
+__global__ void k_cell_start(const unsigned long long *__restrict__ keys, long long n, int n_cells,
+                             int32_t *__restrict__ cell_start, int32_t *__restrict__ pcell) {
+  long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  int c = (int)(keys[k] >> KEY_MORTON_BITS);
+  pcell[k] = c;
+  int cp = (k > 0) ? (int)(keys[k - 1] >> KEY_MORTON_BITS) : -1;
+  for (int cc = cp + 1; cc <= c; cc++) cell_start[cc] = (int32_t)k;
+  if (k == n - 1)
+    for (int cc = c + 1; cc <= n_cells; cc++) cell_start[cc] = (int32_t)n;
+}
+
+__device__ __forceinline__ unsigned int child_of(unsigned long long key, int shift) {
+  return (unsigned int)((key >> shift) & 7ull);
+}
+
+// Walks the octree of one cell's Morton-ordered particles depth first and
+// emits, in particle order, every node with at most leaf_max particles (or
+// chunks of leaf_max at the deepest level).  Returns the number of leaves.
+__device__ int split_cell(const unsigned long long *__restrict__ keys, int a0, int b0,
+                          int leaf_max, int32_t *leaf_start, int32_t *leaf_cell, int cell,
+                          int out_base) {
+  int sa[8 * MORTON_BITS + 8], sb[8 * MORTON_BITS + 8];
+  signed char sl[8 * MORTON_BITS + 8];
+  int top = 0, count = 0;
+  sa[0] = a0;
+  sb[0] = b0;
+  sl[0] = 0;
+  top = 1;
+  while (top > 0) {
+    top--;
+    int a = sa[top], b = sb[top], L = sl[top];
+    int cnt = b - a;
+    if (cnt <= 0) continue;
+    if (cnt <= leaf_max || L == MORTON_BITS) {
+      for (int s = a; s < b; s += leaf_max) {
+        if (leaf_start) {
+          leaf_start[out_base + count] = s;
+          leaf_cell[out_base + count] = cell;
+        }
+        count++;
+      }
+      continue;
+    }
+    int shift = 3 * (MORTON_BITS - 1 - L);
+    int bnd[9];
+    bnd[0] = a;
+    bnd[8] = b;
+    for (int k = 1; k < 8; k++) {
+      // first index in [bnd[k-1], b) whose child digit is >= k
+      int lo = bnd[k - 1], hi = b;
+      while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (child_of(keys[mid], shift) < (unsigned int)k) lo = mid + 1;
+        else hi = mid;
+      }
+      bnd[k] = lo;
+    }
+    for (int k = 7; k >= 0; k--) {
+      if (bnd[k + 1] > bnd[k]) {
+        sa[top] = bnd[k];
+        sb[top] = bnd[k + 1];
+        sl[top] = (signed char)(L + 1);
+        top++;
+      }
+    }
+  }
+  return count;
+}
+
+__global__ void k_leaf_count(const unsigned long long *__restrict__ keys,
+                             const int32_t *__restrict__ cell_start, int n_cells, int leaf_max,
+                             unsigned int *__restrict__ counts) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c > n_cells) return;
+  if (c == n_cells) {
+    counts[c] = 0;
+    return;
+  }
+  counts[c] = (unsigned int)split_cell(keys, cell_start[c], cell_start[c + 1], leaf_max, nullptr,
+                                       nullptr, c, 0);
+}
+
+__global__ void k_leaf_write(const unsigned long long *__restrict__ keys,
+                             const int32_t *__restrict__ cell_start, int n_cells, int leaf_max,
+                             const unsigned int *__restrict__ offsets,
+                             int32_t *__restrict__ leaf_start, int32_t *__restrict__ leaf_cell,
+                             int32_t *__restrict__ cell_leaf_start, long long n) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c > n_cells) return;
+  cell_leaf_start[c] = (int32_t)offsets[c];
+  if (c == n_cells) {
+    leaf_start[offsets[c]] = (int32_t)n;
+    return;
+  }
+  split_cell(keys, cell_start[c], cell_start[c + 1], leaf_max, leaf_start, leaf_cell, c,
+             (int)offsets[c]);
+}
+
+__global__ void k_bin_hist(const int8_t *__restrict__ bin, long long n, int *__restrict__ out) {
+  __shared__ int h[MAX_BINS];
+  if (threadIdx.x < MAX_BINS) h[threadIdx.x] = 0;
+  __syncthreads();
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    atomicAdd(&h[bin[i] & (MAX_BINS - 1)], 1);
+  __syncthreads();
+  if (threadIdx.x < MAX_BINS && h[threadIdx.x]) atomicAdd(&out[threadIdx.x], h[threadIdx.x]);
+}
+
+inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_reduce_hmax(const View &v, float *out_max, cudaStream_t st) {
+  note_launches(1);
+  cudaError_t e = cudaMemsetAsync(out_max, 0, sizeof(float), st);
+  if (e != cudaSuccess) return e;
+  int blocks = (int)std::min<long long>(1024, std::max<long long>(1, (v.n + 255) / 256));
+  k_reduce_hmax<<<blocks, 256, 0, st>>>(v.h, v.n, reinterpret_cast<unsigned int *>(out_max));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cell_keys(const View &v, int nc, double w, unsigned long long *keys,
+                             unsigned int *vals, cudaStream_t st) {
+  note_launches(1);
+  if (v.n == 0) return cudaSuccess;
+  k_cell_keys<<<blocks_for(v.n, 256), 256, 0, st>>>(v, nc, w, keys, vals);
+  return cudaGetLastError();
+}
+
+cudaError_t exclusive_scan_u32(const unsigned int *in, unsigned int *out, int n,
+                               unsigned int *tmp, cudaStream_t st) {
+  note_launches(3);
+  if (n <= 0) return cudaSuccess;
+  int nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+  if (nb > SCAN_TILE) return cudaErrorInvalidValue;
+  k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(in, n, tmp);
+  k_scan_tops<<<1, SCAN_THREADS, 0, st>>>(tmp, nb);
+  k_scan_down<<<nb, SCAN_THREADS, 0, st>>>(in, out, n, tmp);
+  return cudaGetLastError();
+}
+
+cudaError_t radix_sort_pairs(unsigned long long *keys, unsigned int *vals,
+                             unsigned long long *keys_alt, unsigned int *vals_alt, int n,
+                             int nbits, unsigned int *hist, unsigned int *scan_tmp,
+                             int n_hist_max, bool *result_in_alt, cudaStream_t st) {
+  *result_in_alt = false;
+  if (n <= 1) return cudaSuccess;
+  int n_tiles = (n + RS_TILE - 1) / RS_TILE;
+  if (256LL * n_tiles > n_hist_max) return cudaErrorInvalidValue;
+  unsigned long long *ka = keys, *kb = keys_alt;
+  unsigned int *va = vals, *vb = vals_alt;
+  for (int shift = 0; shift < nbits; shift += 8) {
+    note_launches(2);
+    k_rs_hist<<<n_tiles, RS_THREADS, 0, st>>>(ka, n, shift, hist, n_tiles);
+    cudaError_t e = exclusive_scan_u32(hist, hist, 256 * n_tiles, scan_tmp, st);
+    if (e != cudaSuccess) return e;
+    k_rs_scatter<<<n_tiles, RS_THREADS, 0, st>>>(ka, va, kb, vb, n, shift, hist, n_tiles);
+    std::swap(ka, kb);
+    std::swap(va, vb);
+    *result_in_alt = !*result_in_alt;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather(void *dst, const void *src, const unsigned int *idx, long long n,
+                          int elem_bytes, cudaStream_t st) {
+  note_launches(1);
+  if (n == 0) return cudaSuccess;
+  int b = blocks_for(n, 256);
+  switch (elem_bytes) {
+    case 1: k_gather<uint8_t><<<b, 256, 0, st>>>((uint8_t *)dst, (const uint8_t *)src, idx, n); break;
+    case 4: k_gather<uint32_t><<<b, 256, 0, st>>>((uint32_t *)dst, (const uint32_t *)src, idx, n); break;
+    case 8: k_gather<unsigned long long><<<b, 256, 0, st>>>((unsigned long long *)dst,
+                                                          (const unsigned long long *)src, idx, n); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cell_start(const unsigned long long *sorted_keys, long long n, int n_cells,
+                              int32_t *cell_start, int32_t *pcell, cudaStream_t st) {
+  note_launches(1);
+  if (n == 0) return cudaMemsetAsync(cell_start, 0, sizeof(int32_t) * (n_cells + 1), st);
+  k_cell_start<<<blocks_for(n, 256), 256, 0, st>>>(sorted_keys, n, n_cells, cell_start, pcell);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_count(const unsigned long long *sorted_keys, const int32_t *cell_start,
+                              int n_cells, int leaf_max, unsigned int *counts, cudaStream_t st) {
+  note_launches(1);
+  k_leaf_count<<<blocks_for(n_cells + 1, 128), 128, 0, st>>>(sorted_keys, cell_start, n_cells,
+                                                              leaf_max, counts);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_write(const unsigned long long *sorted_keys, const int32_t *cell_start,
+                              int n_cells, int leaf_max, const unsigned int *offsets,
+                              int32_t *leaf_start, int32_t *leaf_cell, int32_t *cell_leaf_start,
+                              long long n, cudaStream_t st) {
+  note_launches(1);
+  k_leaf_write<<<blocks_for(n_cells + 1, 128), 128, 0, st>>>(
+      sorted_keys, cell_start, n_cells, leaf_max, offsets, leaf_start, leaf_cell, cell_leaf_start, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin_histogram(const View &v, cudaStream_t st) {
+  note_launches(1);
+  int *counts = reinterpret_cast<int *>(reinterpret_cast<char *>(v.ds) +
+                                         offsetof(DevState, bin_count));
+  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int) * MAX_BINS, st);
+  if (e != cudaSuccess || v.n == 0) return e;
+  int blocks = (int)std::min<long long>(1024, (v.n + 255) / 256);
+  k_bin_hist<<<blocks, 256, 0, st>>>(v.bin, v.n, counts);
+  return cudaGetLastError();
+}
+
+}  // namespace sph

@@ -1,0 +1,402 @@
+// Time integration around the pair loops (Sec. II-A and Sec. III-D of
+// arXiv 1807.01341): the active set of the current tick, the cells that must
+// be drifted (active cells and their neighbours), the drift with prediction of
+// v and A, the two half-kicks, the CFL time step (Eq. 1) and the power-of-two
+// time bins (Eq. 2) with the synchronisation of bin increases.
+//
+// All kernels read their sizes and the current tick from the device-resident
+// DevState and loop grid-stride, so the same launches serve every step and a
+// captured CUDA graph stays valid.
+#include <climits>
+#include <cstddef>
+
+#include "sph_internal.cuh"
+
+namespace sph {
+
+namespace {
+
+constexpr int UT = 256;  // threads per block of the utility kernels
+constexpr int UW = UT / 32;
+
+__device__ __forceinline__ int gwarp() { return (blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
+__device__ __forceinline__ int nwarps() { return (gridDim.x * blockDim.x) >> 5; }
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+// ---------------------------------------------------------------------------
+// active set
+// ---------------------------------------------------------------------------
+
+// Clears `active` for the previous step's active leaves (their queue is still
+// in place), then starts the step: current tick, largest active bin, epoch,
+// empty queues.
+__global__ void k_mark_clear(View v) {
+  DevState *ds = v.ds;
+  int nq = ds->n_active_leaves;
+  for (int k = gwarp(); k < nq; k += nwarps()) {
+    int leaf = v.q_active[k];
+    int a = v.leaf_start[leaf], b = v.leaf_start[leaf + 1];
+    for (int i = a + lane_id(); i < b; i += 32) v.active[i] = 0;
+  }
+}
+
+__global__ void k_begin_step(View v, long long ti_arg) {
+  DevState *ds = v.ds;
+  long long ti = ti_arg >= 0 ? ti_arg : ds->ti_next;
+  ds->ti = ti;
+  ds->m_act = max_active_bin(ti);
+  ds->epoch += 1u;
+  ds->n_active_leaves = 0;
+  ds->n_active_cells = 0;
+  ds->n_drift_leaves = 0;
+  ds->n_bin_leaves = 0;
+  ds->head_density = ds->head_force = ds->head_drift = ds->head_kick = 0;
+  ds->head_open = ds->head_bins = ds->head_misc = 0;
+  ds->s_pairs_density = ds->s_pairs_force = 0ull;
+  ds->s_cand_density = ds->s_cand_force = 0ull;
+  ds->s_iters_density = ds->s_active_particles = 0ull;
+}
+
+// One thread per leaf: a leaf holds active particles when its smallest bin is
+// active.  Queues the leaf, and the first leaf of each cell queues the cell.
+__global__ void k_mark_leaves(View v) {
+  DevState *ds = v.ds;
+  const int nl = ds->n_leaves, m_act = ds->m_act;
+  const unsigned int epoch = ds->epoch;
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nl; l += gridDim.x * blockDim.x) {
+    if ((int)v.leaf_min_bin[l] > m_act) continue;
+    v.q_active[atomicAdd(&ds->n_active_leaves, 1)] = l;
+    int c = v.leaf_cell[l];
+    if (atomicExch(&v.cell_stamp[c], epoch) != epoch)
+      v.q_act_cells[atomicAdd(&ds->n_active_cells, 1)] = c;
+  }
+}
+
+// One warp per active leaf: writes `active` for its particles.
+__global__ void k_mark_particles(View v) {
+  DevState *ds = v.ds;
+  const int nq = ds->n_active_leaves, m_act = ds->m_act;
+  for (int k = gwarp(); k < nq; k += nwarps()) {
+    int leaf = v.q_active[k];
+    int a = v.leaf_start[leaf], b = v.leaf_start[leaf + 1];
+    int cnt = 0;
+    for (int i = a + lane_id(); i < b; i += 32) {
+      bool act = (int)v.bin[i] <= m_act;
+      v.active[i] = act ? 1 : 0;
+      cnt += __popc(__ballot_sync(__activemask(), act));
+    }
+    if (lane_id() == 0 && cnt) atomicAdd(&ds->s_active_particles, (unsigned long long)cnt);
+  }
+}
+
+// One thread per active cell: queues the leaves of the 27 cells around it
+// that are not queued yet (Sec. III-D: only these particles need drifting).
+__global__ void k_relevant(View v) {
+  DevState *ds = v.ds;
+  const int nq = ds->n_active_cells, nc = ds->nc;
+  const unsigned int epoch = ds->epoch;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nq; k += gridDim.x * blockDim.x) {
+    int c = v.q_act_cells[k];
+    int cx = c / (nc * nc), cy = (c / nc) % nc, cz = c % nc;
+    for (int dx = -1; dx <= 1; dx++)
+      for (int dy = -1; dy <= 1; dy++)
+        for (int dz = -1; dz <= 1; dz++) {
+          int cc = (wrap_cell(cx + dx, nc) * nc + wrap_cell(cy + dy, nc)) * nc + wrap_cell(cz + dz, nc);
+          if (atomicExch(&v.cell_rel_stamp[cc], epoch) == epoch) continue;
+          int l0 = v.cell_leaf_start[cc], l1 = v.cell_leaf_start[cc + 1];
+          if (l1 <= l0) continue;
+          int pos = atomicAdd(&ds->n_drift_leaves, l1 - l0);
+          for (int t = 0; t < l1 - l0; t++) v.q_drift[pos + t] = l0 + t;
+        }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// drift / refresh of one leaf (one warp)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double rel_periodic(double d, double box) {
+  if (d > 0.5 * box) d -= box;
+  else if (d < -0.5 * box) d += box;
+  return d;
+}
+
+__device__ __forceinline__ double wrap_pos(double x, double box) {
+  if (x < 0.0) x += box;
+  if (x >= box) x -= box;
+  return x;
+}
+
+// Drifts (when do_drift) the particles of one leaf to the current tick,
+// predicts v and A at that tick, refreshes the FP32 records the pair loops
+// read, and recomputes the leaf's bounding box and largest support.  Inactive
+// particles get P and c from their frozen density and predicted entropy.
+__device__ void leaf_update(const View &v, int leaf, bool do_drift, bool do_bins) {
+  const DevState *ds = v.ds;
+  const int lane = lane_id();
+  const int a = v.leaf_start[leaf], b = v.leaf_start[leaf + 1];
+  const int cell = v.leaf_cell[leaf];
+  const int nc = ds->nc;
+  const double w = ds->w;
+  const long long ti = ds->ti;
+  const int cx = cell / (nc * nc), cy = (cell / nc) % nc, cz = cell % nc;
+  const double ox = cx * w, oy = cy * w, oz = cz * w;
+  const float g = (float)v.gamma;
+  float lox = INFINITY, loy = INFINITY, loz = INFINITY;
+  float hix = -INFINITY, hiy = -INFINITY, hiz = -INFINITY;
+  float Hm = 0.0f, exc = 0.0f;
+  int minb = 127;
+  unsigned long long mask = 0ull;
+  for (int i = a + lane; i < b; i += 32) {
+    double x = v.x[i], y = v.y[i], z = v.z[i];
+    if (do_drift) {
+      long long td = v.ti_drift[i];
+      if (td != ti) {
+        double dt = (double)(ti - td) * v.dt_min;
+        x = wrap_pos(x + (double)v.vx[i] * dt, v.box);
+        y = wrap_pos(y + (double)v.vy[i] * dt, v.box);
+        z = wrap_pos(z + (double)v.vz[i] * dt, v.box);
+        v.x[i] = x;
+        v.y[i] = y;
+        v.z[i] = z;
+        v.ti_drift[i] = ti;
+      }
+    }
+    double rx = rel_periodic(x - ox, v.box), ry = rel_periodic(y - oy, v.box),
+           rz = rel_periodic(z - oz, v.box);
+    float e = (float)fmax(fmax(fmax(-rx, rx - w), fmax(-ry, ry - w)), fmax(-rz, rz - w));
+    exc = fmaxf(exc, e);
+    const int bi = v.bin[i];
+    const double dtp = ((double)(ti - v.ti_begin[i]) - 0.5 * (double)(1ll << bi)) * v.dt_min;
+    const float fdtp = (float)dtp;
+    const float vpx = v.vx[i] + v.ax[i] * fdtp;
+    const float vpy = v.vy[i] + v.ay[i] * fdtp;
+    const float vpz = v.vz[i] + v.az[i] * fdtp;
+    const float Ap = (float)((double)v.A[i] + (double)v.Adot[i] * dtp);
+    const float hh = v.h[i], H = GAMMA_K * hh, m = v.m[i];
+    const float fx = (float)rx, fy = (float)ry, fz = (float)rz;
+    v.rec_xm[i] = make_float4(fx, fy, fz, m);
+    v.rec_xH[i] = make_float4(fx, fy, fz, H);
+    v.rec_v[i] = make_float4(vpx, vpy, vpz, m);
+    const float rho = v.rho[i];
+    float fP = 0.0f, c = 0.0f;
+    if (rho > 0.0f) {
+      float P = Ap * powf(rho, g);
+      c = sqrtf(g * P / rho);
+      fP = v.f[i] * P / (rho * rho);
+      v.P[i] = P;
+      v.c[i] = c;
+    }
+    v.rec_h[i] = make_float4(rho, fP, c, 1.0f / H);
+    lox = fminf(lox, fx); loy = fminf(loy, fy); loz = fminf(loz, fz);
+    hix = fmaxf(hix, fx); hiy = fmaxf(hiy, fy); hiz = fmaxf(hiz, fz);
+    Hm = fmaxf(Hm, H);
+    minb = min(minb, bi);
+    mask |= 1ull << bi;
+  }
+  for (int o = 16; o; o >>= 1) {
+    lox = fminf(lox, __shfl_xor_sync(0xffffffffu, lox, o));
+    loy = fminf(loy, __shfl_xor_sync(0xffffffffu, loy, o));
+    loz = fminf(loz, __shfl_xor_sync(0xffffffffu, loz, o));
+    hix = fmaxf(hix, __shfl_xor_sync(0xffffffffu, hix, o));
+    hiy = fmaxf(hiy, __shfl_xor_sync(0xffffffffu, hiy, o));
+    hiz = fmaxf(hiz, __shfl_xor_sync(0xffffffffu, hiz, o));
+    Hm = fmaxf(Hm, __shfl_xor_sync(0xffffffffu, Hm, o));
+    exc = fmaxf(exc, __shfl_xor_sync(0xffffffffu, exc, o));
+    minb = min(minb, __shfl_xor_sync(0xffffffffu, minb, o));
+    mask |= __shfl_xor_sync(0xffffffffu, mask, o);
+  }
+  if (lane == 0) {
+    v.leaf_lo[leaf] = make_float4(lox, loy, loz, Hm);
+    v.leaf_hi[leaf] = make_float4(hix, hiy, hiz, 0.0f);
+    if (do_bins) {
+      v.leaf_min_bin[leaf] = (uint8_t)minb;
+      v.leaf_bin_mask[leaf] = mask;
+    }
+    atomic_max_float_pos(&v.ds->excursion_bits, exc);
+    atomic_max_float_pos(&v.ds->Hmax_bits, Hm);
+  }
+}
+
+__global__ void k_refresh(View v) {
+  const int nl = v.ds->n_leaves;
+  for (int l = gwarp(); l < nl; l += nwarps()) leaf_update(v, l, false, true);
+}
+
+__global__ void k_drift(View v) {
+  const DevState *ds = v.ds;
+  const int nq = v.drift_all ? ds->n_leaves : ds->n_drift_leaves;
+  for (int k = gwarp(); k < nq; k += nwarps()) {
+    int leaf = v.drift_all ? k : v.q_drift[k];
+    leaf_update(v, leaf, true, false);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// kicks and time bins (one warp per active leaf)
+// ---------------------------------------------------------------------------
+__global__ void k_kick(View v, int phase) {
+  DevState *ds = v.ds;
+  if (ds->halt) return;
+  const int nq = ds->n_active_leaves, m_act = ds->m_act;
+  for (int k = gwarp(); k < nq; k += nwarps()) {
+    int leaf = v.q_active[k];
+    int a = v.leaf_start[leaf], b = v.leaf_start[leaf + 1];
+    for (int i = a + lane_id(); i < b; i += 32) {
+      if ((int)v.bin[i] > m_act) continue;
+      // half of the step that closes (its end is now) or opens (its start is now)
+      double half = 0.5 * (double)(v.ti_end[i] - v.ti_begin[i]) * v.dt_min;
+      float hf = (float)half;
+      v.vx[i] += v.ax[i] * hf;
+      v.vy[i] += v.ay[i] * hf;
+      v.vz[i] += v.az[i] * hf;
+      v.A[i] = (float)((double)v.A[i] + (double)v.Adot[i] * half);
+    }
+  }
+  (void)phase;
+}
+
+__global__ void k_bins(View v) {
+  DevState *ds = v.ds;
+  __shared__ int delta[MAX_BINS];
+  __shared__ unsigned int too_small;
+  for (int t = threadIdx.x; t < MAX_BINS; t += blockDim.x) delta[t] = 0;
+  if (threadIdx.x == 0) too_small = 0u;
+  __syncthreads();
+  const bool halted = ds->halt != 0u;
+  const int nq = ds->n_active_leaves, m_act = ds->m_act;
+  const long long ti = ds->ti;
+  for (int k = gwarp(); k < nq && !halted; k += nwarps()) {
+    int leaf = v.q_active[k];
+    int a = v.leaf_start[leaf], b = v.leaf_start[leaf + 1];
+    int minb = 127;
+    unsigned long long mask = 0ull;
+    for (int i = a + lane_id(); i < b; i += 32) {
+      int old = v.bin[i];
+      int nb = old;
+      if (old <= m_act) {
+        // Eq. 1: dt = C h / v_sig; Eq. 2: largest n with dt >= 2^n dt_min
+        double dt = __ddiv_rn(__dmul_rn(v.cfl, (double)v.h[i]), (double)v.vsig[i]);
+        double q = __ddiv_rn(dt, v.dt_min);
+        if (!(q >= 1.0)) {
+          atomicAdd(&too_small, 1u);
+          nb = 0;
+        } else {
+          int e;
+          frexp(q, &e);
+          nb = e - 1;
+          if (nb > v.bin_cap) nb = v.bin_cap;
+        }
+        // a longer step only when the current tick is a multiple of it
+        while (nb > old && (ti & ((1ll << nb) - 1)) != 0) nb--;
+        v.bin[i] = (int8_t)nb;
+        v.ti_begin[i] = ti;
+        v.ti_end[i] = ti + (1ll << nb);
+        if (nb != old) {
+          atomicSub(&delta[old], 1);
+          atomicAdd(&delta[nb], 1);
+        }
+      }
+      minb = min(minb, nb);
+      mask |= 1ull << nb;
+    }
+    for (int o = 16; o; o >>= 1) {
+      minb = min(minb, __shfl_xor_sync(0xffffffffu, minb, o));
+      mask |= __shfl_xor_sync(0xffffffffu, mask, o);
+    }
+    if (lane_id() == 0) {
+      v.leaf_min_bin[leaf] = (uint8_t)minb;
+      v.leaf_bin_mask[leaf] = mask;
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < MAX_BINS; t += blockDim.x)
+    if (delta[t]) atomicAdd(&ds->bin_count[t], delta[t]);
+  if (threadIdx.x == 0 && too_small) record_error(ds, SPH_ERR_DT_TOO_SMALL, too_small, false);
+}
+
+// Next tick: a particle on bin b ends its step at the next multiple of 2^b
+// after the current tick, so the earliest end over all particles is the
+// smallest such multiple over the occupied bins.
+__global__ void k_next_time(View v, long long *out, int count_step) {
+  DevState *ds = v.ds;
+  if (ds->halt) return;
+  const long long ti = ds->ti;
+  long long tn = LLONG_MAX;
+  for (int b = 0; b < MAX_BINS; b++)
+    if (ds->bin_count[b] > 0) {
+      long long t = ((ti >> b) + 1) << b;
+      if (t < tn) tn = t;
+    }
+  ds->ti_next = tn;
+  if (out) *out = tn;
+  // the step completed: its counters join the totals
+  ds->pairs_density += ds->s_pairs_density;
+  ds->pairs_force += ds->s_pairs_force;
+  ds->cand_density += ds->s_cand_density;
+  ds->cand_force += ds->s_cand_force;
+  ds->iters_density += ds->s_iters_density;
+  ds->active_particles += ds->s_active_particles;
+  ds->s_pairs_density = ds->s_pairs_force = 0ull;
+  ds->s_cand_density = ds->s_cand_force = 0ull;
+  ds->s_iters_density = ds->s_active_particles = 0ull;
+  if (count_step) ds->steps += 1ull;
+}
+
+__global__ void k_mark_bin(View v, int bin) {
+  DevState *ds = v.ds;
+  const int nq = ds->n_active_leaves;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nq; k += gridDim.x * blockDim.x) {
+    int leaf = v.q_active[k];
+    if ((v.leaf_bin_mask[leaf] >> bin) & 1ull) v.q_bin[atomicAdd(&ds->n_bin_leaves, 1)] = leaf;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_refresh_all(const View &v, cudaStream_t st) {
+  note_launches(1);
+  k_refresh<<<v.grid_util, UT, 0, st>>>(v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mark(const View &v, long long ti_or_neg, cudaStream_t st) {
+  note_launches(v.drift_all ? 4 : 5);
+  k_mark_clear<<<v.grid_util, UT, 0, st>>>(v);
+  k_begin_step<<<1, 1, 0, st>>>(v, ti_or_neg);
+  k_mark_leaves<<<v.grid_util, UT, 0, st>>>(v);
+  k_mark_particles<<<v.grid_util, UT, 0, st>>>(v);
+  if (!v.drift_all) k_relevant<<<v.grid_util, UT, 0, st>>>(v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_drift(const View &v, cudaStream_t st) {
+  note_launches(1);
+  k_drift<<<v.grid_util, UT, 0, st>>>(v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kick(const View &v, int phase, cudaStream_t st) {
+  note_launches(1);
+  k_kick<<<v.grid_util, UT, 0, st>>>(v, phase);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bins(const View &v, long long *ti_next_out, int count_step, cudaStream_t st) {
+  note_launches(2);
+  k_bins<<<v.grid_util, UT, 0, st>>>(v);
+  k_next_time<<<1, 1, 0, st>>>(v, ti_next_out, count_step);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mark_bin(const View &v, int bin, cudaStream_t st) {
+  note_launches(1);
+  cudaError_t e = cudaMemsetAsync(SPH_DS_FIELD(v.ds, n_bin_leaves), 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  k_mark_bin<<<v.grid_util, UT, 0, st>>>(v, bin);
+  return cudaGetLastError();
+}
+
+}  // namespace sph

@@ -1,0 +1,185 @@
+// Internal declarations shared by the CUDA translation units of libsph_gb300.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/sph.h"
+
+namespace sph {
+
+// Support of the cubic spline in units of the smoothing length (Dehnen & Aly
+// 2012): H = GAMMA_K h.  With eta = 1.2348 this gives ~48 neighbours.
+constexpr float GAMMA_K = 1.825742f;
+constexpr double GAMMA_K_D = 1.825742;
+constexpr float KERNEL_NORM = 2.5464790894703255f;  // 8 / pi
+constexpr int MORTON_BITS = 10;                       // per axis inside a top-level cell
+constexpr int KEY_MORTON_BITS = 3 * MORTON_BITS;
+constexpr int MAX_BINS = 64;
+constexpr int WARPS_PER_BLOCK = 8;
+constexpr int LEAF_MAX_LIMIT = 64;
+
+// Device-resident state of the context: the integer timeline, the sizes of
+// the cell structure, work queues, error flags and counters.  Everything a
+// kernel needs that can change between steps lives here, so a captured CUDA
+// graph stays valid across steps and rebuilds.
+struct DevState {
+  long long ti;          // current tick
+  long long ti_next;     // next tick (set by the bins kernel)
+  unsigned int epoch;    // incremented by every mark, stamps active cells
+  int m_act;             // largest active bin at ti (63 at tick 0)
+  // cell structure (written at build)
+  int nc;                // cells per axis
+  int n_cells;           // nc^3
+  int n_leaves;
+  int pad0;
+  double w;              // cell width
+  // queues (written by mark)
+  int n_active_leaves;   // leaves holding active particles
+  int n_active_cells;    // cells holding active particles
+  int n_drift_leaves;    // leaves of the cells within one cell of an active cell
+  int n_bin_leaves;      // plain form: active leaves holding particles of one bin
+  // persistent-kernel work heads
+  int head_density, head_force, head_drift, head_kick;
+  int head_open, head_bins, head_misc, pad2;
+  // errors
+  unsigned int halt;      // a step-invalidating error happened: kernels return
+  int first_error;        // first SPH_ERR_* code recorded
+  unsigned long long err_count[8];
+  // rebuild criterion
+  unsigned int excursion_bits;  // max distance (float bits) of a particle outside its cell
+  unsigned int Hmax_bits;       // max kernel support H (float bits) over all particles
+  unsigned int want_h_bits;     // largest h an iteration wanted beyond the cell limit
+  unsigned int pad3;
+  // counters of the step in progress (reset when a step starts, added to the
+  // totals when it completes, so a halted attempt leaves no trace)
+  unsigned long long s_pairs_density, s_pairs_force, s_cand_density, s_cand_force;
+  unsigned long long s_iters_density, s_active_particles;
+  // totals over completed steps
+  unsigned long long pairs_density, pairs_force, cand_density, cand_force;
+  unsigned long long iters_density, active_particles;
+  unsigned long long steps;
+  // time-bin occupancy
+  int bin_count[MAX_BINS];
+};
+
+// Pointers and constants handed to every kernel (by value).
+struct View {
+  long long n;
+  // caller particle arrays (cell order after a build)
+  double *x, *y, *z;
+  float *vx, *vy, *vz, *ax, *ay, *az, *A, *Adot, *h, *rho, *f, *P, *c, *vsig, *m;
+  int8_t *bin;
+  long long *ti_begin, *ti_end, *ti_drift;
+  uint8_t *active;
+  int32_t *ngb_density, *ngb_force;
+  // cell structure
+  int32_t *cell_start;       // [n_cells + 1] first particle of each cell
+  int32_t *cell_leaf_start;  // [n_cells + 1] first leaf of each cell
+  unsigned int *cell_stamp;  // [n_cells] epoch at which the cell was last marked active
+  unsigned int *cell_rel_stamp;  // [n_cells] epoch at which the cell was queued for drift
+  int32_t *leaf_start;       // [n_leaves + 1] first particle of each leaf
+  int32_t *leaf_cell;        // [n_leaves]
+  float4 *leaf_lo;           // bbox min (cell-relative), w = max H in the leaf
+  float4 *leaf_hi;           // bbox max (cell-relative)
+  uint8_t *leaf_min_bin;     // smallest bin in the leaf
+  unsigned long long *leaf_bin_mask;  // bins present in the leaf
+  int32_t *pcell;            // [n] cell of each particle
+  // FP32 records read by the pair loops (cell-relative positions)
+  float4 *rec_xm;  // x, y, z, m
+  float4 *rec_xH;  // x, y, z, H
+  float4 *rec_v;   // predicted v, m
+  float4 *rec_h;   // rho, f P / rho^2, c, 1 / H
+  // queues
+  int32_t *q_active;         // leaves holding active particles
+  int32_t *q_act_cells;      // cells holding active particles
+  int32_t *q_drift;          // leaves to drift (cells next to an active cell)
+  int32_t *q_bin;            // plain form: active leaves holding particles of one bin
+  DevState *ds;
+  // parameters
+  double box, eta, gamma, alpha, cfl, h_tol, dt_min;
+  int h_max_iter, bin_cap, leaf_max, G, drift_all;
+  int grid_util;             // blocks of the grid-stride utility kernels
+};
+
+// address of a DevState field on the device, computed on the host
+#define SPH_DS_FIELD(ds, field) \
+  (reinterpret_cast<decltype(&((DevState *)nullptr)->field)>( \
+      reinterpret_cast<char *>(ds) + offsetof(DevState, field)))
+
+// ---------------------------------------------------------------------------
+// small device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void record_error(DevState *ds, int code, unsigned long long count,
+                                             bool halt) {
+  atomicCAS(&ds->first_error, 0, code);
+  atomicAdd(&ds->err_count[code & 7], count);
+  if (halt) atomicExch(&ds->halt, 1u);
+}
+
+__device__ __forceinline__ void atomic_max_float_pos(unsigned int *addr, float v) {
+  // non-negative floats order like their bit patterns
+  atomicMax(addr, __float_as_uint(fmaxf(v, 0.0f)));
+}
+
+__device__ __forceinline__ int wrap_cell(int c, int nc) {
+  return c < 0 ? c + nc : (c >= nc ? c - nc : c);
+}
+
+// Number of integer bins active at tick ti: particles on bin b are active
+// when ti is a multiple of 2^b, i.e. b <= ctz(ti) (every bin at tick 0).
+__host__ __device__ __forceinline__ int max_active_bin(long long ti) {
+  if (ti == 0) return MAX_BINS - 1;
+#ifdef __CUDA_ARCH__
+  return __ffsll(ti) - 1;
+#else
+  return __builtin_ctzll((unsigned long long)ti);
+#endif
+}
+
+// Host-side count of kernel launches issued by the library (graph replays add
+// the kernels of the captured graph); reported by sph_get_counters.
+void note_launches(int n);
+
+// ---------------------------------------------------------------------------
+// launchers implemented in the .cu files (all asynchronous on `st`)
+// ---------------------------------------------------------------------------
+// sph_cells.cu
+cudaError_t launch_reduce_hmax(const View &v, float *out_max, cudaStream_t st);
+cudaError_t launch_cell_keys(const View &v, int nc, double w, unsigned long long *keys,
+                             unsigned int *vals, cudaStream_t st);
+cudaError_t radix_sort_pairs(unsigned long long *keys, unsigned int *vals,
+                             unsigned long long *keys_alt, unsigned int *vals_alt, int n,
+                             int nbits, unsigned int *hist, unsigned int *scan_tmp,
+                             int n_hist_max, bool *result_in_alt, cudaStream_t st);
+cudaError_t exclusive_scan_u32(const unsigned int *in, unsigned int *out, int n,
+                               unsigned int *tmp, cudaStream_t st);
+cudaError_t launch_gather(void *dst, const void *src, const unsigned int *idx, long long n,
+                          int elem_bytes, cudaStream_t st);
+cudaError_t launch_cell_start(const unsigned long long *sorted_keys, long long n, int n_cells,
+                              int32_t *cell_start, int32_t *pcell, cudaStream_t st);
+cudaError_t launch_leaf_count(const unsigned long long *sorted_keys, const int32_t *cell_start,
+                              int n_cells, int leaf_max, unsigned int *counts,
+                              cudaStream_t st);
+cudaError_t launch_leaf_write(const unsigned long long *sorted_keys, const int32_t *cell_start,
+                              int n_cells, int leaf_max, const unsigned int *offsets,
+                              int32_t *leaf_start, int32_t *leaf_cell,
+                              int32_t *cell_leaf_start, long long n, cudaStream_t st);
+cudaError_t launch_bin_histogram(const View &v, cudaStream_t st);
+// sph_integrate.cu
+cudaError_t launch_refresh_all(const View &v, cudaStream_t st);
+cudaError_t launch_mark(const View &v, long long ti_or_neg, cudaStream_t st);
+cudaError_t launch_drift(const View &v, cudaStream_t st);
+cudaError_t launch_kick(const View &v, int phase, cudaStream_t st);
+cudaError_t launch_bins(const View &v, long long *ti_next_out, int count_step, cudaStream_t st);
+cudaError_t launch_mark_bin(const View &v, int bin, cudaStream_t st);
+// sph_pairs.cu
+cudaError_t launch_density(const View &v, int flags, int bin_filter, bool persistent,
+                           int grid, cudaStream_t st);
+cudaError_t launch_force(const View &v, int bin_filter, bool persistent, int grid,
+                         cudaStream_t st);
+cudaError_t launch_entropy_from_u(const View &v, cudaStream_t st);
+int persistent_blocks_per_sm(int G, bool density);
+
+}  // namespace sph

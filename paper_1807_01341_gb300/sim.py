@@ -1,0 +1,233 @@
+"""Thin Python front end over the C ABI: particle arrays as torch CUDA tensors,
+a context object whose methods map one-to-one onto the sph_* calls.
+
+Only argument marshalling happens here; every computation runs in
+libsph_gb300.so.  Calls are asynchronous on the current torch CUDA stream
+unless the C ABI documents a synchronisation.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, fields
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check
+
+_TORCH = {"f8": torch.float64, "f4": torch.float32, "i1": torch.int8, "i8": torch.int64,
+          "u1": torch.uint8, "i4": torch.int32}
+_NP = {"f8": np.float64, "f4": np.float32, "i1": np.int8, "i8": np.int64, "u1": np.uint8,
+       "i4": np.int32}
+
+
+@dataclass
+class Params:
+    box: float = 1.0
+    eta: float = 1.2348
+    gamma: float = 5.0 / 3.0
+    alpha_visc: float = 0.8
+    cfl: float = 0.1
+    h_tol: float = 1e-6
+    h_max_iter: int = 30
+    bin_cap: int = 20
+    dt_min: float = 1e-6
+    t_begin: float = 0.0
+    cell_margin: float = 1.1
+    leaf_max: int = 16
+    threads_per_particle: int = 4
+    drift_all: int = 0
+    n_cells_override: int = 0
+
+    def to_c(self) -> _lib.sph_params:
+        p = _lib.sph_params()
+        for f in fields(self):
+            setattr(p, f.name, getattr(self, f.name))
+        return p
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Particles:
+    """Structure-of-arrays particle state on one CUDA device (caller-owned)."""
+
+    def __init__(self, n: int, device="cuda", with_counts: bool = True):
+        self.n = int(n)
+        self.device = torch.device(device)
+        for name, dt in _lib.PARTICLE_FIELDS:
+            if name in ("ngb_density", "ngb_force") and not with_counts:
+                setattr(self, name, None)
+                continue
+            setattr(self, name, torch.zeros(self.n, dtype=_TORCH[dt], device=self.device))
+        self._struct = None
+
+    @classmethod
+    def from_ics(cls, ic: dict, device="cuda", with_counts: bool = True):
+        """Initial state: positions, velocities, masses, u (held in A until the
+        first density pass converts it), h guess; every particle on bin 0 at
+        tick 0."""
+        n = ic["pos"].shape[0]
+        p = cls(n, device, with_counts)
+        pos = torch.as_tensor(np.ascontiguousarray(ic["pos"]), dtype=torch.float64)
+        vel = torch.as_tensor(np.ascontiguousarray(ic["vel"]), dtype=torch.float32)
+        p.x.copy_(pos[:, 0]); p.y.copy_(pos[:, 1]); p.z.copy_(pos[:, 2])
+        p.vx.copy_(vel[:, 0]); p.vy.copy_(vel[:, 1]); p.vz.copy_(vel[:, 2])
+        p.m.copy_(torch.as_tensor(ic["m"], dtype=torch.float32))
+        p.A.copy_(torch.as_tensor(ic["u"], dtype=torch.float32))
+        p.h.copy_(torch.as_tensor(ic["h0"], dtype=torch.float32))
+        return p
+
+    def struct(self) -> _lib.sph_particles:
+        s = _lib.sph_particles()
+        s.n = self.n
+        for name, _ in _lib.PARTICLE_FIELDS:
+            t = getattr(self, name)
+            setattr(s, name, None if t is None else t.data_ptr())
+        self._struct = s
+        return s
+
+    def numpy(self, perm=None) -> dict:
+        """Host copy of every array; with perm (int array), in the order of the
+        first build (out[perm[k]] = state[k])."""
+        out = {}
+        for name, dt in _lib.PARTICLE_FIELDS:
+            t = getattr(self, name)
+            if t is None:
+                continue
+            a = t.cpu().numpy()
+            if perm is not None:
+                b = np.empty_like(a)
+                b[perm] = a
+                a = b
+            out[name] = a
+        return out
+
+    def arrays(self):
+        return {name: getattr(self, name) for name, _ in _lib.PARTICLE_FIELDS
+                if getattr(self, name) is not None}
+
+
+class _DevArray:
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3}
+
+
+class Context:
+    """An sph_ctx: scratch for up to n_max particles on the current device."""
+
+    def __init__(self, params: Params, n_max: int):
+        self.L = _lib.load()
+        self.params = params
+        self._cp = params.to_c()
+        h = ctypes.c_void_p()
+        check(self.L.sph_create(ctypes.byref(self._cp), int(n_max), ctypes.byref(h)), "sph_create")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            self.L.sph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- the C ABI, one method per call ------------------------------------
+    def build_cells(self, p: Particles, stream=None):
+        check(self.L.sph_build_cells(self.h, ctypes.byref(p.struct()), _stream_ptr(stream)),
+              "sph_build_cells")
+
+    def perm_tensor(self, n: int) -> torch.Tensor:
+        ptr = self.L.sph_perm(self.h)
+        if not ptr:
+            raise RuntimeError("cells not built")
+        return torch.as_tensor(_DevArray(ptr, n, "<i4"), device="cuda").clone()
+
+    def grid_info(self):
+        nc, nl = ctypes.c_int(), ctypes.c_int()
+        check(self.L.sph_grid_info(self.h, ctypes.byref(nc), ctypes.byref(nl)), "sph_grid_info")
+        return nc.value, nl.value
+
+    def mark_active(self, p: Particles, ti: int = -1, stream=None):
+        check(self.L.sph_mark_active(self.h, ctypes.byref(p.struct()), int(ti),
+                                     _stream_ptr(stream)), "sph_mark_active")
+
+    def kick_drift(self, p: Particles, phase: int, stream=None):
+        check(self.L.sph_kick_drift(self.h, ctypes.byref(p.struct()), int(phase),
+                                    _stream_ptr(stream)), "sph_kick_drift")
+
+    def density_active(self, p: Particles, flags: int = 0, stream=None):
+        check(self.L.sph_density_active(self.h, ctypes.byref(p.struct()), int(flags),
+                                        _stream_ptr(stream)), "sph_density_active")
+
+    def force_active(self, p: Particles, stream=None):
+        check(self.L.sph_force_active(self.h, ctypes.byref(p.struct()), _stream_ptr(stream)),
+              "sph_force_active")
+
+    def timestep_bins(self, p: Particles, ti_next_dev: torch.Tensor | None = None, stream=None):
+        ptr = None if ti_next_dev is None else ctypes.c_void_p(ti_next_dev.data_ptr())
+        check(self.L.sph_timestep_bins(self.h, ctypes.byref(p.struct()), ptr,
+                                       _stream_ptr(stream)), "sph_timestep_bins")
+
+    def begin_run(self, stream=None):
+        check(self.L.sph_begin_run(self.h, _stream_ptr(stream)), "sph_begin_run")
+
+    def step_async(self, p: Particles, form: int = _lib.SPH_FORM_BATCHED, stream=None):
+        check(self.L.sph_step_async(self.h, ctypes.byref(p.struct()), int(form),
+                                    _stream_ptr(stream)), "sph_step_async")
+
+    def step_sync(self, p: Particles, stream=None) -> int:
+        c = ctypes.c_int()
+        check(self.L.sph_step_sync(self.h, ctypes.byref(p.struct()), ctypes.byref(c),
+                                   _stream_ptr(stream)), "sph_step_sync")
+        return c.value
+
+    def step(self, p: Particles, form: int = _lib.SPH_FORM_BATCHED, stream=None):
+        check(self.L.sph_step(self.h, ctypes.byref(p.struct()), int(form), _stream_ptr(stream)),
+              "sph_step")
+
+    def step_graph(self, p: Particles, n_steps: int, stream=None):
+        check(self.L.sph_step_graph(self.h, ctypes.byref(p.struct()), int(n_steps),
+                                    _stream_ptr(stream)), "sph_step_graph")
+
+    def get_time(self):
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        check(self.L.sph_get_time(self.h, ctypes.byref(a), ctypes.byref(b)), "sph_get_time")
+        return a.value, b.value
+
+    def set_time(self, ti: int, stream=None):
+        check(self.L.sph_set_time(self.h, int(ti), _stream_ptr(stream)), "sph_set_time")
+
+    def status(self):
+        s, d = ctypes.c_int(), ctypes.c_int64()
+        check(self.L.sph_get_status(self.h, ctypes.byref(s), ctypes.byref(d)), "sph_get_status")
+        return s.value, d.value
+
+    def clear_status(self, stream=None):
+        check(self.L.sph_clear_status(self.h, _stream_ptr(stream)), "sph_clear_status")
+
+    def counters(self) -> dict:
+        c = _lib.sph_counters()
+        check(self.L.sph_get_counters(self.h, ctypes.byref(c)), "sph_get_counters")
+        return {k: getattr(c, k) for k, _ in c._fields_}
+
+    def set_profiling(self, enable: bool = True):
+        check(self.L.sph_set_profiling(self.h, int(bool(enable))), "sph_set_profiling")
+
+    def kernel_times(self) -> dict:
+        t = _lib.sph_kernel_times()
+        check(self.L.sph_get_kernel_times(self.h, ctypes.byref(t)), "sph_get_kernel_times")
+        return {k: getattr(t, k) for k, _ in t._fields_}
+
+    def reset_kernel_times(self):
+        check(self.L.sph_reset_kernel_times(self.h), "sph_reset_kernel_times")
+
+    def reset_counters(self, stream=None):
+        check(self.L.sph_reset_counters(self.h, _stream_ptr(stream)), "sph_reset_counters")

@@ -1,0 +1,261 @@
+"""GPU (sm_103a) results of the C-ABI library against the FP64 oracle.
+
+Integer work (cell order, active sets, time bins, neighbour sets on the same
+positions and h) must match exactly; floating point within the tolerances of
+the hot path: h and rho rel 1e-5 per particle, accelerations and dA/dt within
+1e-4 of their rms, signal velocity rel 1e-5.  A neighbour pair whose
+|r^2 - H^2| lies within 1e-6 H^2 may flip under FP32 rounding; such pairs are
+counted and allowed.
+"""
+import numpy as np
+import pytest
+
+import sph_ics
+from _gpu_helpers import band_pairs, band_pairs_sym, gpu_setup
+
+pytestmark = pytest.mark.gpu
+
+H_TOL = 1e-5
+RHO_TOL = 1e-5
+ACC_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def sim():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1807_01341_gb300 import build
+    build.build()
+    from paper_1807_01341_gb300 import sim as S
+    return S
+
+
+def _lib():
+    from paper_1807_01341_gb300 import _lib
+    return _lib
+
+
+def _sync():
+    import torch
+    torch.cuda.synchronize()
+
+
+def _pos(g):
+    return np.stack([g["x"], g["y"], g["z"]], axis=1)
+
+
+def _f64(a):
+    return np.asarray(a, dtype=np.float64)
+
+
+def _density_pass(sim, ctx, p, init=True):
+    L = _lib()
+    ctx.mark_active(p, 0)
+    ctx.kick_drift(p, L.SPH_DRIFT)
+    ctx.density_active(p, L.SPH_DENSITY_INIT_ENTROPY if init else 0)
+    _sync()
+
+
+# ---------------------------------------------------------------------------
+# cells
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", ["lattice", "clumpy", "duplicates"])
+def test_build_cells_order_matches_oracle(sim, orc, kind):
+    if kind == "lattice":
+        ic = sph_ics.lattice(16, 0.1, seed=1)
+    else:
+        ic = sph_ics.clumpy_lattice(nside=16, n_clumps=2, per_clump=400, seed=3)
+    if kind == "duplicates":
+        ic["pos"][100:140] = ic["pos"][0]          # ties in (cell, Morton) keep index order
+    ic["pos"][::97, 0] -= 1.0                       # outside the box: wrapped by the build
+    ic["pos"][5::89, 1] += 1.0
+    n = ic["pos"].shape[0]
+    params = sim.Params()
+    ctx, p = gpu_setup(ic, params)
+    nc, nl = ctx.grid_info()
+    h32 = np.float32(ic["h0"]).max()
+    assert nc == orc.n_cells_for(float(h32), margin=params.cell_margin, nc_max=255)
+    perm = ctx.perm_tensor(n).cpu().numpy()
+    ref = orc.cells(ic["pos"], 1.0, nc)
+    assert np.array_equal(perm, ref["perm"])
+    g = p.numpy()
+    assert np.array_equal(_pos(g), ref["pos"][perm])            # bit-exact wrap and order
+    assert np.array_equal(g["h"], np.float32(ic["h0"])[perm])   # every array moved with it
+    assert 1 <= nl <= n
+
+
+def test_build_cells_explicit_grid_and_rebuild(sim, orc):
+    ic = sph_ics.clumpy_lattice(nside=12, n_clumps=1, per_clump=300, seed=5)
+    n = ic["pos"].shape[0]
+    for nc in (3, 7, 20):
+        ctx, p = gpu_setup(ic, sim.Params(n_cells_override=nc, leaf_max=8))
+        assert ctx.grid_info()[0] == nc
+        perm = ctx.perm_tensor(n).cpu().numpy()
+        assert np.array_equal(perm, orc.cells(ic["pos"], 1.0, nc)["perm"])
+        # a second build of the sorted set keeps the order (stable) and the
+        # composed permutation still maps back to the input order
+        ctx.build_cells(p)
+        assert np.array_equal(ctx.perm_tensor(n).cpu().numpy(), perm)
+
+
+# ---------------------------------------------------------------------------
+# density loop + smoothing length
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("G,leaf_max", [(4, 16), (1, 64), (32, 8), (8, 32)])
+def test_density_parity_all_active(sim, orc, G, leaf_max):
+    """4,096 jittered lattice particles, all active, one density pass."""
+    ic = sph_ics.lattice(16, 0.1, seed=1)
+    n = ic["pos"].shape[0]
+    ctx, p = gpu_setup(ic, sim.Params(threads_per_particle=G, leaf_max=leaf_max))
+    _density_pass(sim, ctx, p)
+    assert ctx.status()[0] == 0
+    perm = ctx.perm_tensor(n).cpu().numpy()
+    g = p.numpy()
+    pos = _pos(g)
+    ref = orc.density(pos, _f64(g["m"]), _f64(np.float32(ic["h0"])[perm]), np.ones(n, np.uint8))
+    assert ref["n_unconverged"] == 0
+    assert np.max(np.abs(g["h"] / ref["h"] - 1)) < H_TOL
+    assert np.max(np.abs(g["rho"] / ref["rho"] - 1)) < RHO_TOL
+    f_ref = orc.gradh_f(ref["h"], ref["rho"], ref["drho_dh"])
+    assert np.max(np.abs(g["f"] - f_ref)) < 1e-5
+    u = ic["u"][perm]
+    A_ref = orc.entropy_from_u(u, ref["rho"], 5 / 3)
+    assert np.max(np.abs(g["A"] / A_ref - 1)) < 2e-5
+    P_ref, c_ref = orc.eos(A_ref, ref["rho"], 5 / 3)
+    assert np.max(np.abs(g["P"] / P_ref - 1)) < 3e-5
+    assert np.max(np.abs(g["c"] / c_ref - 1)) < 2e-5
+    # neighbour sets at the GPU's own h: exact up to pairs on the support edge
+    fx = orc.density_fixed_h(pos, _f64(g["m"]), _f64(g["h"]))
+    diff = np.abs(g["ngb_density"] - fx["count"])
+    bad = np.nonzero(diff)[0]
+    if bad.size:
+        assert np.all(diff[bad] <= band_pairs(pos, _f64(g["h"]), bad))
+    assert bad.size <= n // 500
+
+
+def test_density_clumpy_subset_and_inactive_untouched(sim, orc):
+    """Clumps (leaves at depth, many leaves per cell) and a random active subset
+    selected through the time bins: inactive particles are not written."""
+    ic = sph_ics.clumpy_lattice(nside=16, n_clumps=3, per_clump=300, seed=7)
+    n = ic["pos"].shape[0]
+    rng = np.random.default_rng(0)
+    bins = np.where(rng.uniform(size=n) < 0.3, 0, 5)     # at tick 4 only bin <= 2 is active
+    ctx, p = gpu_setup(ic, sim.Params(leaf_max=16), bins=bins, ti=4)
+    perm = ctx.perm_tensor(n).cpu().numpy()
+    g0 = p.numpy()
+    L = _lib()
+    ctx.mark_active(p, 4)
+    ctx.kick_drift(p, L.SPH_DRIFT)
+    ctx.density_active(p, L.SPH_DENSITY_INIT_ENTROPY)
+    _sync()
+    assert ctx.status()[0] == 0
+    g = p.numpy()
+    act = g["active"].astype(bool)
+    assert np.array_equal(act, bins[perm] == 0)
+    assert np.array_equal(g["h"][~act], g0["h"][~act])
+    assert np.all(g["rho"][~act] == 0)
+    pos = _pos(g)
+    ref = orc.density(pos, _f64(g["m"]), _f64(g0["h"]), act.astype(np.uint8))
+    assert np.max(np.abs(g["h"][act] / ref["h"][act] - 1)) < H_TOL
+    assert np.max(np.abs(g["rho"][act] / ref["rho"][act] - 1)) < RHO_TOL
+
+
+# ---------------------------------------------------------------------------
+# force loop
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("G", [4, 1, 16])
+def test_force_parity(sim, orc, G):
+    """Force on the GPU's own density state (same inputs to both sides), with
+    random velocities so the viscosity acts."""
+    ic = sph_ics.clumpy_lattice(nside=16, n_clumps=2, per_clump=300, seed=11)
+    n = ic["pos"].shape[0]
+    rng = np.random.default_rng(3)
+    ic["vel"] = rng.normal(scale=0.5, size=(n, 3))
+    ic["u"] = rng.uniform(0.5, 1.5, n)
+    ctx, p = gpu_setup(ic, sim.Params(threads_per_particle=G))
+    _density_pass(sim, ctx, p)
+    ctx.force_active(p)
+    _sync()
+    assert ctx.status()[0] == 0
+    g = p.numpy()
+    pos = _pos(g)
+    vel = np.stack([g["vx"], g["vy"], g["vz"]], 1).astype(np.float64)
+    ref = orc.force(pos, vel, _f64(g["m"]), _f64(g["h"]), _f64(g["rho"]), _f64(g["f"]),
+                    _f64(g["P"]), _f64(g["c"]), np.ones(n, np.uint8))
+    a = np.stack([g["ax"], g["ay"], g["az"]], 1)
+    a_rms = np.sqrt((ref["a"] ** 2).sum(1).mean())
+    assert np.max(np.abs(a - ref["a"])) < ACC_TOL * a_rms
+    ad_rms = np.sqrt((ref["Adot"] ** 2).mean())
+    assert np.max(np.abs(g["Adot"] - ref["Adot"])) < ACC_TOL * ad_rms
+    assert np.max(np.abs(g["vsig"] / ref["vsig"] - 1)) < 1e-5
+    diff = np.abs(g["ngb_force"] - ref["count"])
+    bad = np.nonzero(diff)[0]
+    if bad.size:
+        assert np.all(diff[bad] <= band_pairs_sym(pos, _f64(g["h"]), bad))
+    assert bad.size <= n // 500
+
+
+def test_force_coincident_pair(sim, orc):
+    """Two particles at the same position: no direction, no force term, the
+    pair still enters the signal velocity."""
+    ic = sph_ics.lattice(10, 0.1, seed=2)
+    ic["pos"][1] = ic["pos"][0]
+    n = ic["pos"].shape[0]
+    ctx, p = gpu_setup(ic, sim.Params())
+    _density_pass(sim, ctx, p)
+    ctx.force_active(p)
+    _sync()
+    g = p.numpy()
+    assert np.all(np.isfinite(g["ax"])) and np.all(np.isfinite(g["vsig"]))
+    vel = np.zeros((n, 3))
+    ref = orc.force(_pos(g), vel, _f64(g["m"]), _f64(g["h"]), _f64(g["rho"]), _f64(g["f"]),
+                    _f64(g["P"]), _f64(g["c"]), np.ones(n, np.uint8))
+    a = np.stack([g["ax"], g["ay"], g["az"]], 1)
+    a_rms = np.sqrt((ref["a"] ** 2).sum(1).mean())
+    assert np.max(np.abs(a - ref["a"])) < ACC_TOL * a_rms
+
+
+# ---------------------------------------------------------------------------
+# time bins
+# ---------------------------------------------------------------------------
+def test_timestep_bins_exact(sim, orc):
+    import torch
+    ic = sph_ics.lattice(18, 0.1, seed=4)
+    n = ic["pos"].shape[0]
+    rng = np.random.default_rng(9)
+    old = rng.integers(0, 9, n)
+    ti = 48                                          # bins <= 4 are active
+    ctx, p = gpu_setup(ic, sim.Params(bin_cap=12, dt_min=1e-6, cfl=0.1, n_cells_override=8))
+    perm = ctx.perm_tensor(n).cpu().numpy()
+    ob = old[perm]
+    tb = (ti // (1 << ob)) * (1 << ob)
+    te = np.where(ob <= 4, ti, tb + (1 << ob))
+    tb = np.where(ob <= 4, ti - (1 << ob), tb)
+    h = rng.uniform(0.005, 0.05, n).astype(np.float32)
+    vs = np.exp(rng.uniform(np.log(0.5), np.log(4000.0), n)).astype(np.float32)
+    vs[:50] = np.float32(0.1) * h[:50] / np.float32(1e-6) / np.float32(2.0 ** 3)  # near 2^3 dt_min
+    p.bin.copy_(torch.as_tensor(ob.astype(np.int8)))
+    p.ti_begin.copy_(torch.as_tensor(tb))
+    p.ti_end.copy_(torch.as_tensor(te))
+    p.h.copy_(torch.as_tensor(h))
+    p.vsig.copy_(torch.as_tensor(vs))
+    ctx.build_cells(p)                               # refresh leaf bin summaries (stable order)
+    p_perm = ctx.perm_tensor(n).cpu().numpy()
+    assert np.array_equal(p_perm, perm)
+    ctx.mark_active(p, ti)
+    tnext = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ctx.timestep_bins(p, tnext)
+    _sync()
+    g = p.numpy()
+    act = (ob <= 4)
+    assert np.array_equal(g["active"].astype(bool), act)
+    ref = orc.timestep_bins(_f64(h), _f64(vs), act.astype(np.uint8), 0.1, 1e-6, 12, ti,
+                            ob.astype(np.int8))
+    assert np.array_equal(g["bin"], ref["bin"])
+    assert np.array_equal(g["ti_begin"][act], ref["ti_begin"][act])
+    assert np.array_equal(g["ti_end"][act], ref["ti_end"][act])
+    assert np.array_equal(g["ti_end"][~act], te[~act])
+    assert int(tnext.item()) == int(g["ti_end"].min())
+    st, detail = ctx.status()
+    assert (st == 0) == (ref["n_too_small"] == 0)

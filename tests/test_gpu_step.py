@@ -1,0 +1,185 @@
+"""Whole kick-drift-kick steps on the GPU against the oracle, and the three
+execution forms (plain per-bin launches, batched persistent kernels, CUDA
+graph replay) against each other."""
+import numpy as np
+import pytest
+
+import sph_ics
+from _gpu_helpers import gpu_setup
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sim():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1807_01341_gb300 import build
+    build.build()
+    from paper_1807_01341_gb300 import sim as S
+    return S
+
+
+def _lib():
+    from paper_1807_01341_gb300 import _lib
+    return _lib
+
+
+def _ic_step(seed=13, nside=12):
+    ic = sph_ics.clumpy_lattice(nside=nside, n_clumps=1, per_clump=200, seed=seed)
+    n = ic["pos"].shape[0]
+    rng = np.random.default_rng(seed)
+    ic["vel"] = rng.normal(scale=0.1, size=(n, 3))
+    ic["u"] = rng.uniform(0.5, 2.0, n)
+    return ic
+
+
+STEP_PARAMS = dict(dt_min=1e-6, bin_cap=14, cfl=0.1)
+
+
+def test_step_parity_each_step_from_same_state(sim, orc):
+    """Before every GPU step the oracle integrator is loaded with the GPU's
+    state and advanced one step: active sets and bins must agree exactly
+    (bins up to dt values within 2e-5 of a power of two), and the floating
+    point state within the hot-path tolerances."""
+    ic = _ic_step()
+    n = ic["pos"].shape[0]
+    ctx, p = gpu_setup(ic, sim.Params(**STEP_PARAMS))
+    L = _lib()
+    n_partial = 0
+    for k in range(10):
+        st0 = p.numpy()
+        _, ti = ctx.get_time()
+        osim = orc.OracleSim.from_state(st0, ti=ti, first=(k == 0), use_cells=True,
+                                        **STEP_PARAMS)
+        act_ref = osim.step()
+        ctx.step(p, L.SPH_FORM_BATCHED)
+        st = p.numpy()
+        act = st["active"].astype(bool)
+        assert np.array_equal(act, act_ref), k
+        n_partial += int(0 < act.sum() < n)
+        pos = np.stack([st["x"], st["y"], st["z"]], 1)
+        moved = st["ti_drift"] == ti
+        assert moved[act].all()
+        d = pos[moved] - osim.pos[moved]
+        d -= np.round(d)
+        assert np.abs(d).max() < 1e-12
+        assert np.max(np.abs(st["h"][act] / osim.h[act] - 1)) < 1e-5
+        assert np.max(np.abs(st["rho"][act] / osim.rho[act] - 1)) < 1e-5
+        a = np.stack([st["ax"], st["ay"], st["az"]], 1)[act]
+        a_ref = osim.acc[act]
+        a_rms = np.sqrt((a_ref ** 2).sum(1).mean())
+        assert np.max(np.abs(a - a_ref)) < 1e-4 * a_rms
+        assert np.max(np.abs(st["vsig"][act] / osim.vsig[act] - 1)) < 1e-5
+        # bins: exact unless the oracle's dt sits on a power-of-two edge
+        q = osim.cfl * osim.h / osim.vsig / osim.dt_min
+        edge = np.abs(np.log2(q) - np.round(np.log2(q))) < 2e-5
+        ok = act & ~edge
+        assert np.array_equal(st["bin"][ok], osim.bin[ok])
+        assert np.array_equal(st["ti_end"][ok], osim.ti_end[ok])
+        # velocities after both half-kicks
+        v = np.stack([st["vx"], st["vy"], st["vz"]], 1)[ok]
+        dt = (osim.ti_end - osim.ti_begin)[ok] * osim.dt_min
+        scale = np.sqrt((osim.vel[ok] ** 2).sum(1).mean()) + a_rms * dt.max()
+        assert np.max(np.abs(v - osim.vel[ok])) < 1e-4 * scale
+    assert n_partial >= 3          # the run exercised individual time bins
+
+
+def _run_form(sim, ic, form, steps, params):
+    import torch
+    ctx, p = gpu_setup(ic, sim.Params(**params))
+    if form == "graph":
+        ctx.step_graph(p, steps)
+    else:
+        L = _lib()
+        f = L.SPH_FORM_PLAIN if form == "plain" else L.SPH_FORM_BATCHED_NOGRAPH
+        for _ in range(steps):
+            ctx.step(p, f)
+    torch.cuda.synchronize()
+    return p.numpy(), ctx.counters(), ctx.get_time()
+
+
+def test_plain_batched_graph_bitwise_identical(sim):
+    ic = _ic_step(seed=17)
+    res = {f: _run_form(sim, ic, f, 12, STEP_PARAMS) for f in ("plain", "batched", "graph")}
+    ref, cref, tref = res["batched"]
+    for f in ("plain", "graph"):
+        st, c, t = res[f]
+        assert t == tref, f
+        for k in ref:
+            assert np.array_equal(st[k], ref[k]), (f, k)
+        for k in ("pairs_density", "pairs_force", "steps", "active_particles"):
+            assert c[k] == cref[k], (f, k)
+
+
+def test_drift_all_same_result_as_relevant_drift(sim):
+    """Drifting every particle each step (the ablation) gives the same state
+    as drifting only the cells next to active cells (Sec. III-D), up to the
+    rounding of split drifts."""
+    ic = _ic_step(seed=19)
+    a, ca, _ = _run_form(sim, ic, "batched", 8, dict(STEP_PARAMS, drift_all=0))
+    b, cb, _ = _run_form(sim, ic, "batched", 8, dict(STEP_PARAMS, drift_all=1))
+    assert ca["pairs_density"] == cb["pairs_density"]
+    for k in ("bin", "ti_end", "active"):
+        assert np.array_equal(a[k], b[k]), k
+    # positions agree once brought to the same tick
+    for k in ("h", "rho", "ax"):
+        assert np.allclose(a[k], b[k], rtol=1e-5, atol=1e-6 * np.abs(b[k]).max()), k
+
+
+def test_global_step_ablation(sim):
+    """bin_cap = 0 puts every particle on the smallest step: every step is
+    all-active."""
+    ic = _ic_step(seed=23)
+    n = ic["pos"].shape[0]
+    params = dict(STEP_PARAMS, bin_cap=0, dt_min=1e-5)
+    st, c, (ti, tn) = _run_form(sim, ic, "batched", 5, params)
+    assert c["active_particles"] == 5 * n
+    assert tn == 5
+
+
+def test_empty_and_degenerate_sizes(sim):
+    import torch
+    L = _lib()
+    # no particles at all
+    ctx = sim.Context(sim.Params(), 1)
+    p = sim.Particles(0)
+    ctx.build_cells(p)
+    ctx.step(p, L.SPH_FORM_BATCHED)
+    ctx.step(p, L.SPH_FORM_PLAIN)
+    assert ctx.status()[0] == 0
+    # the smallest grid (3 cells per axis)
+    ic = sph_ics.lattice(8, 0.1, seed=3)
+    ctx, p = gpu_setup(ic, sim.Params(**STEP_PARAMS))
+    assert ctx.grid_info()[0] == 3
+    ctx.step(p, L.SPH_FORM_BATCHED)
+    torch.cuda.synchronize()
+    assert np.all(np.isfinite(p.numpy()["rho"]))
+    # supports wider than a third of the box: reported, not faulted
+    ic = sph_ics.lattice(4, 0.0, seed=3)
+    ctx, p = gpu_setup(ic, sim.Params(**STEP_PARAMS))
+    with pytest.raises(L.SphError) as e:
+        ctx.step(p, L.SPH_FORM_BATCHED)
+    assert e.value.code == L.SPH_ERR_CELL_OVERFLOW
+
+
+def test_h_growth_triggers_rebuild_and_redo(sim, orc):
+    """Initial h guesses far too small with a coarse grid forced narrow by
+    them: the h iteration outgrows the cells, the step is redone after a
+    rebuild, and the result still matches the oracle."""
+    ic = sph_ics.lattice(16, 0.1, seed=29)
+    n = ic["pos"].shape[0]
+    ic["h0"] = ic["h0"] * 0.3
+    ctx, p = gpu_setup(ic, sim.Params(**STEP_PARAMS))
+    nc0 = ctx.grid_info()[0]
+    L = _lib()
+    ctx.step(p, L.SPH_FORM_BATCHED)
+    c = ctx.counters()
+    assert c["redone_steps"] >= 1 and ctx.grid_info()[0] < nc0
+    st = p.numpy()
+    pos = np.stack([st["x"], st["y"], st["z"]], 1)
+    perm = ctx.perm_tensor(n).cpu().numpy()
+    ref = orc.density(pos, st["m"].astype(np.float64),
+                      np.float32(ic["h0"])[perm].astype(np.float64), np.ones(n, np.uint8))
+    assert np.max(np.abs(st["h"] / ref["h"] - 1)) < 1e-5
