@@ -38,6 +38,10 @@ struct Buffers {
   int32_t *pcell = nullptr;
   // leaves (at most one per particle)
   int32_t *leaf_start = nullptr, *leaf_cell = nullptr;
+  uint32_t *leaf_k = nullptr;
+  // chunks of 32 leaves (at most one per particle)
+  int32_t *chunk_cell = nullptr;
+  float4 *chunk_lo = nullptr, *chunk_hi = nullptr;
   float4 *leaf_lo = nullptr, *leaf_hi = nullptr;
   uint8_t *leaf_min_bin = nullptr;
   unsigned long long *leaf_bin_mask = nullptr;
@@ -46,7 +50,7 @@ struct Buffers {
   float4 *rec_xm = nullptr, *rec_xH = nullptr, *rec_v = nullptr, *rec_h = nullptr;
   // cells (grown on demand)
   long long cell_cap = 0;
-  int32_t *cell_start = nullptr, *cell_leaf_start = nullptr;
+  int32_t *cell_start = nullptr, *cell_leaf_start = nullptr, *cell_chunk_start = nullptr;
   unsigned int *cell_stamp = nullptr, *cell_rel_stamp = nullptr;
   int32_t *q_act_cells = nullptr;
   unsigned int *leaf_counts = nullptr, *leaf_offsets = nullptr;
@@ -169,10 +173,15 @@ View make_view(const sph_ctx *ctx, const sph_particles *p) {
   const Buffers &b = ctx->b;
   v.cell_start = b.cell_start;
   v.cell_leaf_start = b.cell_leaf_start;
+  v.cell_chunk_start = b.cell_chunk_start;
+  v.chunk_cell = b.chunk_cell;
+  v.chunk_lo = b.chunk_lo;
+  v.chunk_hi = b.chunk_hi;
   v.cell_stamp = b.cell_stamp;
   v.cell_rel_stamp = b.cell_rel_stamp;
   v.leaf_start = b.leaf_start;
   v.leaf_cell = b.leaf_cell;
+  v.leaf_k = b.leaf_k;
   v.leaf_lo = b.leaf_lo;
   v.leaf_hi = b.leaf_hi;
   v.leaf_min_bin = b.leaf_min_bin;
@@ -210,6 +219,7 @@ int ensure_cells(sph_ctx *ctx, long long n_cells) {
   cudaDeviceSynchronize();
   dfree(b.cell_start);
   dfree(b.cell_leaf_start);
+  dfree(b.cell_chunk_start);
   dfree(b.cell_stamp);
   dfree(b.cell_rel_stamp);
   dfree(b.q_act_cells);
@@ -220,6 +230,7 @@ int ensure_cells(sph_ctx *ctx, long long n_cells) {
   cap = std::max(cap, n_cells);
   SPH_TRY(dalloc(&b.cell_start, cap + 1));
   SPH_TRY(dalloc(&b.cell_leaf_start, cap + 1));
+  SPH_TRY(dalloc(&b.cell_chunk_start, cap + 1));
   SPH_TRY(dalloc(&b.cell_stamp, cap));
   SPH_TRY(dalloc(&b.cell_rel_stamp, cap));
   SPH_TRY(dalloc(&b.q_act_cells, cap));
@@ -238,13 +249,22 @@ int read_state(sph_ctx *ctx, cudaStream_t st) {
   return SPH_OK;
 }
 
+// Event record on `st`; inside a stream capture it becomes an event-record
+// node of the graph, so every replay records it.
+void record_event(cudaEvent_t ev, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cs);
+  if (cs == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+  else cudaEventRecord(ev, st);
+}
+
 void prof_begin(sph_ctx *ctx, int kind, cudaStream_t st) {
-  if (ctx->prof_on && ctx->prof_n[kind] < 64) cudaEventRecord(ctx->prof_ev[kind][ctx->prof_n[kind]][0], st);
+  if (ctx->prof_on && ctx->prof_n[kind] < 64) record_event(ctx->prof_ev[kind][ctx->prof_n[kind]][0], st);
 }
 
 void prof_end(sph_ctx *ctx, int kind, cudaStream_t st) {
   if (ctx->prof_on && ctx->prof_n[kind] < 64) {
-    cudaEventRecord(ctx->prof_ev[kind][ctx->prof_n[kind]][1], st);
+    record_event(ctx->prof_ev[kind][ctx->prof_n[kind]][1], st);
     ctx->prof_n[kind]++;
   }
 }
@@ -334,10 +354,15 @@ int build_cells(sph_ctx *ctx, sph_particles *p, cudaStream_t st) {
   SPH_CUDA(launch_leaf_count(skeys, b.cell_start, (int)n_cells, ctx->prm.leaf_max, b.leaf_counts, st));
   SPH_CUDA(exclusive_scan_u32(b.leaf_counts, b.leaf_offsets, (int)n_cells + 1, b.scan_tmp, st));
   SPH_CUDA(launch_leaf_write(skeys, b.cell_start, (int)n_cells, ctx->prm.leaf_max, b.leaf_offsets,
-                             b.leaf_start, b.leaf_cell, b.cell_leaf_start, n, st));
-  // device state of the new structure
+                             b.leaf_start, b.leaf_cell, b.leaf_k, b.cell_leaf_start, n, st));
   SPH_CUDA(cudaMemcpyAsync(SPH_DS_FIELD(b.ds, n_leaves), b.leaf_offsets + n_cells, sizeof(int),
                            cudaMemcpyDeviceToDevice, st));
+  // chunks of CHUNK consecutive leaves per cell (the leaf counters are free again)
+  SPH_CUDA(launch_chunks(b.cell_leaf_start, (int)n_cells, b.leaf_counts, b.leaf_offsets, b.scan_tmp,
+                         b.cell_chunk_start, b.chunk_cell, st));
+  SPH_CUDA(cudaMemcpyAsync(SPH_DS_FIELD(b.ds, n_chunks), b.leaf_offsets + n_cells, sizeof(int),
+                           cudaMemcpyDeviceToDevice, st));
+  // device state of the new structure
   int ncs[2] = {nc, (int)n_cells};
   SPH_CUDA(cudaMemcpyAsync(SPH_DS_FIELD(b.ds, nc), &ncs[0], sizeof(int), cudaMemcpyHostToDevice, st));
   SPH_CUDA(cudaMemcpyAsync(SPH_DS_FIELD(b.ds, n_cells), &ncs[1], sizeof(int), cudaMemcpyHostToDevice, st));
@@ -349,7 +374,7 @@ int build_cells(sph_ctx *ctx, sph_particles *p, cudaStream_t st) {
   SPH_CUDA(launch_bin_histogram(v, st));
   SPH_CUDA(launch_refresh_all(v, st));
   int nl = 0;
-  SPH_CUDA(cudaMemcpyAsync(&nl, b.leaf_offsets + n_cells, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SPH_CUDA(cudaMemcpyAsync(&nl, SPH_DS_FIELD(b.ds, n_leaves), sizeof(int), cudaMemcpyDeviceToHost, st));
   SPH_CUDA(cudaStreamSynchronize(st));
   ctx->n_leaves = nl;
   ctx->h_floor = 0.0f;
@@ -361,8 +386,6 @@ int build_cells(sph_ctx *ctx, sph_particles *p, cudaStream_t st) {
 }
 
 // --- pieces of a step ------------------------------------------------------
-int dens_flags(const sph_ctx *ctx) { return ctx->entropy_ready ? 0 : SPH_DENSITY_INIT_ENTROPY; }
-
 int batched_body(sph_ctx *ctx, const View &v, int flags, cudaStream_t st) {
   SPH_CUDA(launch_mark(v, -1, st));
   SPH_CUDA(launch_drift(v, st));
@@ -535,6 +558,10 @@ int sph_create(const sph_params *params, int64_t n_max, sph_ctx **out) {
     const int G = params->threads_per_particle;
     ctx->grid_dens = ctx->num_sms * persistent_blocks_per_sm(G, true);
     ctx->grid_force = ctx->num_sms * persistent_blocks_per_sm(G, false);
+    if (ctx->grid_dens == 0 || ctx->grid_force == 0) {
+      r = SPH_ERR_CUDA;  // the pair kernels cannot be resident with their shared memory
+      break;
+    }
     Buffers &b = ctx->b;
     const long long n = std::max<long long>(n_max, 1);
     const long long n_tiles = (n + 4095) / 4096;
@@ -543,7 +570,8 @@ int sph_create(const sph_params *params, int64_t n_max, sph_ctx **out) {
         (r = dalloc(&b.vals[1], n)) || (r = dalloc(&b.hist, b.n_hist_max)) ||
         (r = dalloc(&b.scan_tmp, 4096)) || (r = dalloc((char **)&b.scratch, 8 * n)) ||
         (r = dalloc(&b.perm, n)) || (r = dalloc(&b.perm_tmp, n)) || (r = dalloc(&b.pcell, n)) ||
-        (r = dalloc(&b.leaf_start, n + 1)) || (r = dalloc(&b.leaf_cell, n)) ||
+        (r = dalloc(&b.leaf_start, n + 1)) || (r = dalloc(&b.leaf_cell, n)) || (r = dalloc(&b.leaf_k, n)) ||
+        (r = dalloc(&b.chunk_cell, n)) || (r = dalloc(&b.chunk_lo, n)) || (r = dalloc(&b.chunk_hi, n)) ||
         (r = dalloc(&b.leaf_lo, n)) || (r = dalloc(&b.leaf_hi, n)) ||
         (r = dalloc(&b.leaf_min_bin, n)) || (r = dalloc(&b.leaf_bin_mask, n)) ||
         (r = dalloc(&b.q_active, n)) || (r = dalloc(&b.q_drift, n)) || (r = dalloc(&b.q_bin, n)) ||
@@ -585,7 +613,8 @@ int sph_destroy(sph_ctx *ctx) {
   dfree(b.hist); dfree(b.scan_tmp);
   if (b.scratch) cudaFree(b.scratch);
   dfree(b.perm); dfree(b.perm_tmp); dfree(b.pcell);
-  dfree(b.leaf_start); dfree(b.leaf_cell); dfree(b.leaf_lo); dfree(b.leaf_hi);
+  dfree(b.leaf_start); dfree(b.leaf_cell); dfree(b.leaf_k);
+  dfree(b.chunk_cell); dfree(b.chunk_lo); dfree(b.chunk_hi); dfree(b.leaf_lo); dfree(b.leaf_hi);
   dfree(b.leaf_min_bin); dfree(b.leaf_bin_mask);
   dfree(b.q_active); dfree(b.q_drift); dfree(b.q_bin);
   dfree(b.rec_xm); dfree(b.rec_xH); dfree(b.rec_v); dfree(b.rec_h);

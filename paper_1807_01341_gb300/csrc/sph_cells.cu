@@ -257,9 +257,25 @@ __device__ __forceinline__ unsigned int child_of(unsigned long long key, int shi
 // Walks the octree of one cell's Morton-ordered particles depth first and
 // emits, in particle order, every node with at most leaf_max particles (or
 // chunks of leaf_max at the deepest level).  Returns the number of leaves.
+__device__ __forceinline__ uint32_t compact3(unsigned long long m) {
+  uint32_t r = 0;
+#pragma unroll
+  for (int b = 0; b < MORTON_BITS; b++) r |= (uint32_t)((m >> (3 * b)) & 1ull) << b;
+  return r;
+}
+
+// Morton-grid corner (packed kx | ky << 10 | kz << 20) of a particle's code,
+// truncated to the octree level of its node
+__device__ __forceinline__ uint32_t corner_of(unsigned long long key, int level) {
+  const unsigned long long m = key & ((1ull << KEY_MORTON_BITS) - 1ull);
+  const int drop = 3 * (MORTON_BITS - level);
+  const unsigned long long t = drop >= KEY_MORTON_BITS ? 0ull : (m >> drop) << drop;
+  return compact3(t >> 2) | (compact3(t >> 1) << 10) | (compact3(t) << 20);
+}
+
 __device__ int split_cell(const unsigned long long *__restrict__ keys, int a0, int b0,
-                          int leaf_max, int32_t *leaf_start, int32_t *leaf_cell, int cell,
-                          int out_base) {
+                          int leaf_max, int32_t *leaf_start, int32_t *leaf_cell,
+                          uint32_t *leaf_k, int cell, int out_base) {
   int sa[8 * MORTON_BITS + 8], sb[8 * MORTON_BITS + 8];
   signed char sl[8 * MORTON_BITS + 8];
   int top = 0, count = 0;
@@ -277,6 +293,7 @@ __device__ int split_cell(const unsigned long long *__restrict__ keys, int a0, i
         if (leaf_start) {
           leaf_start[out_base + count] = s;
           leaf_cell[out_base + count] = cell;
+          leaf_k[out_base + count] = corner_of(keys[a], L);
         }
         count++;
       }
@@ -318,14 +335,15 @@ __global__ void k_leaf_count(const unsigned long long *__restrict__ keys,
     return;
   }
   counts[c] = (unsigned int)split_cell(keys, cell_start[c], cell_start[c + 1], leaf_max, nullptr,
-                                       nullptr, c, 0);
+                                       nullptr, nullptr, c, 0);
 }
 
 __global__ void k_leaf_write(const unsigned long long *__restrict__ keys,
                              const int32_t *__restrict__ cell_start, int n_cells, int leaf_max,
                              const unsigned int *__restrict__ offsets,
                              int32_t *__restrict__ leaf_start, int32_t *__restrict__ leaf_cell,
-                             int32_t *__restrict__ cell_leaf_start, long long n) {
+                             uint32_t *__restrict__ leaf_k, int32_t *__restrict__ cell_leaf_start,
+                             long long n) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c > n_cells) return;
   cell_leaf_start[c] = (int32_t)offsets[c];
@@ -333,7 +351,7 @@ __global__ void k_leaf_write(const unsigned long long *__restrict__ keys,
     leaf_start[offsets[c]] = (int32_t)n;
     return;
   }
-  split_cell(keys, cell_start[c], cell_start[c + 1], leaf_max, leaf_start, leaf_cell, c,
+  split_cell(keys, cell_start[c], cell_start[c + 1], leaf_max, leaf_start, leaf_cell, leaf_k, c,
              (int)offsets[c]);
 }
 
@@ -346,6 +364,23 @@ __global__ void k_bin_hist(const int8_t *__restrict__ bin, long long n, int *__r
     atomicAdd(&h[bin[i] & (MAX_BINS - 1)], 1);
   __syncthreads();
   if (threadIdx.x < MAX_BINS && h[threadIdx.x]) atomicAdd(&out[threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void k_chunk_count(const int32_t *__restrict__ cell_leaf_start, int n_cells,
+                              unsigned int *__restrict__ counts) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c > n_cells) return;
+  counts[c] = c == n_cells ? 0u
+                           : (unsigned int)((cell_leaf_start[c + 1] - cell_leaf_start[c] + CHUNK - 1) / CHUNK);
+}
+
+__global__ void k_chunk_write(const unsigned int *__restrict__ offsets, int n_cells,
+                              int32_t *__restrict__ cell_chunk_start, int32_t *__restrict__ chunk_cell) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c > n_cells) return;
+  cell_chunk_start[c] = (int32_t)offsets[c];
+  if (c == n_cells) return;
+  for (unsigned int g = offsets[c]; g < offsets[c + 1]; g++) chunk_cell[g] = c;
 }
 
 inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
@@ -440,11 +475,25 @@ cudaError_t launch_leaf_count(const unsigned long long *sorted_keys, const int32
 
 cudaError_t launch_leaf_write(const unsigned long long *sorted_keys, const int32_t *cell_start,
                               int n_cells, int leaf_max, const unsigned int *offsets,
-                              int32_t *leaf_start, int32_t *leaf_cell, int32_t *cell_leaf_start,
-                              long long n, cudaStream_t st) {
+                              int32_t *leaf_start, int32_t *leaf_cell, uint32_t *leaf_k,
+                              int32_t *cell_leaf_start, long long n, cudaStream_t st) {
   note_launches(1);
   k_leaf_write<<<blocks_for(n_cells + 1, 128), 128, 0, st>>>(
-      sorted_keys, cell_start, n_cells, leaf_max, offsets, leaf_start, leaf_cell, cell_leaf_start, n);
+      sorted_keys, cell_start, n_cells, leaf_max, offsets, leaf_start, leaf_cell, leaf_k,
+      cell_leaf_start, n);
+  return cudaGetLastError();
+}
+
+// Chunks: the leaves of each cell in groups of CHUNK, numbered cell by cell.
+cudaError_t launch_chunks(const int32_t *cell_leaf_start, int n_cells, unsigned int *counts,
+                          unsigned int *offsets, unsigned int *scan_tmp, int32_t *cell_chunk_start,
+                          int32_t *chunk_cell, cudaStream_t st) {
+  note_launches(2);
+  k_chunk_count<<<blocks_for(n_cells + 1, 256), 256, 0, st>>>(cell_leaf_start, n_cells, counts);
+  cudaError_t e = exclusive_scan_u32(counts, offsets, n_cells + 1, scan_tmp, st);
+  if (e != cudaSuccess) return e;
+  k_chunk_write<<<blocks_for(n_cells + 1, 256), 256, 0, st>>>(offsets, n_cells, cell_chunk_start,
+                                                              chunk_cell);
   return cudaGetLastError();
 }
 

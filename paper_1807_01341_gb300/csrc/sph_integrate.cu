@@ -17,7 +17,6 @@ namespace sph {
 namespace {
 
 constexpr int UT = 256;  // threads per block of the utility kernels
-constexpr int UW = UT / 32;
 
 __device__ __forceinline__ int gwarp() { return (blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
 __device__ __forceinline__ int nwarps() { return (gridDim.x * blockDim.x) >> 5; }
@@ -48,7 +47,7 @@ __global__ void k_begin_step(View v, long long ti_arg) {
   ds->epoch += 1u;
   ds->n_active_leaves = 0;
   ds->n_active_cells = 0;
-  ds->n_drift_leaves = 0;
+  ds->n_drift_chunks = 0;
   ds->n_bin_leaves = 0;
   ds->head_density = ds->head_force = ds->head_drift = ds->head_kick = 0;
   ds->head_open = ds->head_bins = ds->head_misc = 0;
@@ -89,25 +88,23 @@ __global__ void k_mark_particles(View v) {
   }
 }
 
-// One thread per active cell: queues the leaves of the 27 cells around it
-// that are not queued yet (Sec. III-D: only these particles need drifting).
+// One thread per (active cell, neighbour offset): queues the leaf chunks of
+// every cell next to an active cell that is not queued yet (Sec. III-D: only
+// these particles can be neighbours of an active particle and need drifting).
 __global__ void k_relevant(View v) {
   DevState *ds = v.ds;
-  const int nq = ds->n_active_cells, nc = ds->nc;
+  const int nq = ds->n_active_cells * 27, nc = ds->nc;
   const unsigned int epoch = ds->epoch;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nq; k += gridDim.x * blockDim.x) {
-    int c = v.q_act_cells[k];
-    int cx = c / (nc * nc), cy = (c / nc) % nc, cz = c % nc;
-    for (int dx = -1; dx <= 1; dx++)
-      for (int dy = -1; dy <= 1; dy++)
-        for (int dz = -1; dz <= 1; dz++) {
-          int cc = (wrap_cell(cx + dx, nc) * nc + wrap_cell(cy + dy, nc)) * nc + wrap_cell(cz + dz, nc);
-          if (atomicExch(&v.cell_rel_stamp[cc], epoch) == epoch) continue;
-          int l0 = v.cell_leaf_start[cc], l1 = v.cell_leaf_start[cc + 1];
-          if (l1 <= l0) continue;
-          int pos = atomicAdd(&ds->n_drift_leaves, l1 - l0);
-          for (int t = 0; t < l1 - l0; t++) v.q_drift[pos + t] = l0 + t;
-        }
+    const int c = v.q_act_cells[k / 27], o = k % 27;
+    const int dx = o / 9 - 1, dy = (o / 3) % 3 - 1, dz = o % 3 - 1;
+    const int cx = c / (nc * nc), cy = (c / nc) % nc, cz = c % nc;
+    const int cc = (wrap_cell(cx + dx, nc) * nc + wrap_cell(cy + dy, nc)) * nc + wrap_cell(cz + dz, nc);
+    if (atomicExch(&v.cell_rel_stamp[cc], epoch) == epoch) continue;
+    const int g0 = v.cell_chunk_start[cc], g1 = v.cell_chunk_start[cc + 1];
+    if (g1 <= g0) continue;
+    const int pos = atomicAdd(&ds->n_drift_chunks, g1 - g0);
+    for (int t = 0; t < g1 - g0; t++) v.q_drift[pos + t] = g0 + t;
   }
 }
 
@@ -130,7 +127,11 @@ __device__ __forceinline__ double wrap_pos(double x, double box) {
 // predicts v and A at that tick, refreshes the FP32 records the pair loops
 // read, and recomputes the leaf's bounding box and largest support.  Inactive
 // particles get P and c from their frozen density and predicted entropy.
-__device__ void leaf_update(const View &v, int leaf, bool do_drift, bool do_bins) {
+struct LeafBox {
+  float lx, ly, lz, hx, hy, hz, H;
+};
+
+__device__ LeafBox leaf_update(const View &v, int leaf, bool do_drift, bool do_bins) {
   const DevState *ds = v.ds;
   const int lane = lane_id();
   const int a = v.leaf_start[leaf], b = v.leaf_start[leaf + 1];
@@ -140,6 +141,12 @@ __device__ void leaf_update(const View &v, int leaf, bool do_drift, bool do_bins
   const long long ti = ds->ti;
   const int cx = cell / (nc * nc), cy = (cell / nc) % nc, cz = cell % nc;
   const double ox = cx * w, oy = cy * w, oz = cz * w;
+  // leaf corner on the cell's Morton grid (the origin of the FP32 records)
+  const uint32_t lk = v.leaf_k[leaf];
+  const double wq = w / (double)(1 << MORTON_BITS);
+  const double lx = (double)(cx * (1 << MORTON_BITS) + leaf_kx(lk)) * wq;
+  const double ly = (double)(cy * (1 << MORTON_BITS) + leaf_ky(lk)) * wq;
+  const double lz = (double)(cz * (1 << MORTON_BITS) + leaf_kz(lk)) * wq;
   const float g = (float)v.gamma;
   float lox = INFINITY, loy = INFINITY, loz = INFINITY;
   float hix = -INFINITY, hiy = -INFINITY, hiz = -INFINITY;
@@ -161,10 +168,14 @@ __device__ void leaf_update(const View &v, int leaf, bool do_drift, bool do_bins
         v.ti_drift[i] = ti;
       }
     }
-    double rx = rel_periodic(x - ox, v.box), ry = rel_periodic(y - oy, v.box),
-           rz = rel_periodic(z - oz, v.box);
-    float e = (float)fmax(fmax(fmax(-rx, rx - w), fmax(-ry, ry - w)), fmax(-rz, rz - w));
+    // distance outside the particle's cell (the rebuild criterion)
+    const double cxr = rel_periodic(x - ox, v.box), cyr = rel_periodic(y - oy, v.box),
+                 czr = rel_periodic(z - oz, v.box);
+    float e = (float)fmax(fmax(fmax(-cxr, cxr - w), fmax(-cyr, cyr - w)), fmax(-czr, czr - w));
     exc = fmaxf(exc, e);
+    // position relative to the leaf corner
+    const double rx = rel_periodic(x - lx, v.box), ry = rel_periodic(y - ly, v.box),
+                 rz = rel_periodic(z - lz, v.box);
     const int bi = v.bin[i];
     const double dtp = ((double)(ti - v.ti_begin[i]) - 0.5 * (double)(1ll << bi)) * v.dt_min;
     const float fdtp = (float)dtp;
@@ -215,19 +226,46 @@ __device__ void leaf_update(const View &v, int leaf, bool do_drift, bool do_bins
     atomic_max_float_pos(&v.ds->excursion_bits, exc);
     atomic_max_float_pos(&v.ds->Hmax_bits, Hm);
   }
+  LeafBox r = {lox, loy, loz, hix, hiy, hiz, Hm};
+  return r;
+}
+
+// One warp per chunk: updates its leaves one after the other, then the
+// chunk's bounding box in the cell frame (leaf boxes shifted by their Morton
+// corners) and its largest support.
+__device__ void chunk_update(const View &v, int g, bool do_drift, bool do_bins) {
+  const DevState *ds = v.ds;
+  const int cell = v.chunk_cell[g];
+  const int l0 = v.cell_leaf_start[cell] + CHUNK * (g - v.cell_chunk_start[cell]);
+  const int l1 = min(l0 + CHUNK, v.cell_leaf_start[cell + 1]);
+  const float wq = (float)(ds->w / (double)(1 << MORTON_BITS));
+  float lx = INFINITY, ly = INFINITY, lz = INFINITY;
+  float hx = -INFINITY, hy = -INFINITY, hz = -INFINITY, H = 0.0f;
+  for (int l = l0; l < l1; l++) {
+    const LeafBox b = leaf_update(v, l, do_drift, do_bins);
+    const uint32_t k = v.leaf_k[l];
+    const float ox = leaf_kx(k) * wq, oy = leaf_ky(k) * wq, oz = leaf_kz(k) * wq;
+    lx = fminf(lx, b.lx + ox); ly = fminf(ly, b.ly + oy); lz = fminf(lz, b.lz + oz);
+    hx = fmaxf(hx, b.hx + ox); hy = fmaxf(hy, b.hy + oy); hz = fmaxf(hz, b.hz + oz);
+    H = fmaxf(H, b.H);
+  }
+  if (lane_id() == 0) {
+    v.chunk_lo[g] = make_float4(lx, ly, lz, H);
+    v.chunk_hi[g] = make_float4(hx, hy, hz, 0.0f);
+  }
 }
 
 __global__ void k_refresh(View v) {
-  const int nl = v.ds->n_leaves;
-  for (int l = gwarp(); l < nl; l += nwarps()) leaf_update(v, l, false, true);
+  const int ng = v.ds->n_chunks;
+  for (int g = gwarp(); g < ng; g += nwarps()) chunk_update(v, g, false, true);
 }
 
 __global__ void k_drift(View v) {
   const DevState *ds = v.ds;
-  const int nq = v.drift_all ? ds->n_leaves : ds->n_drift_leaves;
+  const int nq = v.drift_all ? ds->n_chunks : ds->n_drift_chunks;
   for (int k = gwarp(); k < nq; k += nwarps()) {
-    int leaf = v.drift_all ? k : v.q_drift[k];
-    leaf_update(v, leaf, true, false);
+    const int g = v.drift_all ? k : v.q_drift[k];
+    chunk_update(v, g, true, false);
   }
 }
 

@@ -19,6 +19,7 @@ constexpr int KEY_MORTON_BITS = 3 * MORTON_BITS;
 constexpr int MAX_BINS = 64;
 constexpr int WARPS_PER_BLOCK = 8;
 constexpr int LEAF_MAX_LIMIT = 64;
+constexpr int CHUNK = 32;          // leaves per chunk (one warp ballot)
 
 // Device-resident state of the context: the integer timeline, the sizes of
 // the cell structure, work queues, error flags and counters.  Everything a
@@ -33,12 +34,12 @@ struct DevState {
   int nc;                // cells per axis
   int n_cells;           // nc^3
   int n_leaves;
-  int pad0;
+  int n_chunks;          // groups of up to CHUNK consecutive leaves of one cell
   double w;              // cell width
   // queues (written by mark)
   int n_active_leaves;   // leaves holding active particles
   int n_active_cells;    // cells holding active particles
-  int n_drift_leaves;    // leaves of the cells within one cell of an active cell
+  int n_drift_chunks;    // leaf chunks of the cells within one cell of an active cell
   int n_bin_leaves;      // plain form: active leaves holding particles of one bin
   // persistent-kernel work heads
   int head_density, head_force, head_drift, head_kick;
@@ -79,8 +80,15 @@ struct View {
   int32_t *cell_leaf_start;  // [n_cells + 1] first leaf of each cell
   unsigned int *cell_stamp;  // [n_cells] epoch at which the cell was last marked active
   unsigned int *cell_rel_stamp;  // [n_cells] epoch at which the cell was queued for drift
+  int32_t *cell_chunk_start; // [n_cells + 1] first chunk of each cell
+  int32_t *chunk_cell;       // [n_chunks] cell of each chunk (its leaves: CHUNK from
+                             // cell_leaf_start + CHUNK * (chunk - cell_chunk_start))
+  float4 *chunk_lo;          // chunk bbox min, cell frame; w = max H in the chunk
+  float4 *chunk_hi;          // chunk bbox max, cell frame
   int32_t *leaf_start;       // [n_leaves + 1] first particle of each leaf
   int32_t *leaf_cell;        // [n_leaves]
+  uint32_t *leaf_k;          // [n_leaves] Morton-grid corner of the leaf inside its cell:
+                             // kx | ky << 10 | kz << 20, in units of w / 1024
   float4 *leaf_lo;           // bbox min (cell-relative), w = max H in the leaf
   float4 *leaf_hi;           // bbox max (cell-relative)
   uint8_t *leaf_min_bin;     // smallest bin in the leaf
@@ -94,7 +102,7 @@ struct View {
   // queues
   int32_t *q_active;         // leaves holding active particles
   int32_t *q_act_cells;      // cells holding active particles
-  int32_t *q_drift;          // leaves to drift (cells next to an active cell)
+  int32_t *q_drift;          // chunks to drift (cells next to an active cell)
   int32_t *q_bin;            // plain form: active leaves holding particles of one bin
   DevState *ds;
   // parameters
@@ -122,6 +130,14 @@ __device__ __forceinline__ void atomic_max_float_pos(unsigned int *addr, float v
   // non-negative floats order like their bit patterns
   atomicMax(addr, __float_as_uint(fmaxf(v, 0.0f)));
 }
+
+// Morton-grid corner of a leaf: integer coordinates (0..1023 per axis) inside
+// its cell.  Positions in the FP32 records are relative to this corner, so
+// their precision follows the leaf's size, not the cell's; the offset between
+// two leaves is an exact integer number of grid steps.
+__host__ __device__ __forceinline__ int leaf_kx(uint32_t k) { return (int)(k & 1023u); }
+__host__ __device__ __forceinline__ int leaf_ky(uint32_t k) { return (int)((k >> 10) & 1023u); }
+__host__ __device__ __forceinline__ int leaf_kz(uint32_t k) { return (int)((k >> 20) & 1023u); }
 
 __device__ __forceinline__ int wrap_cell(int c, int nc) {
   return c < 0 ? c + nc : (c >= nc ? c - nc : c);
@@ -164,9 +180,12 @@ cudaError_t launch_leaf_count(const unsigned long long *sorted_keys, const int32
                               cudaStream_t st);
 cudaError_t launch_leaf_write(const unsigned long long *sorted_keys, const int32_t *cell_start,
                               int n_cells, int leaf_max, const unsigned int *offsets,
-                              int32_t *leaf_start, int32_t *leaf_cell,
+                              int32_t *leaf_start, int32_t *leaf_cell, uint32_t *leaf_k,
                               int32_t *cell_leaf_start, long long n, cudaStream_t st);
 cudaError_t launch_bin_histogram(const View &v, cudaStream_t st);
+cudaError_t launch_chunks(const int32_t *cell_leaf_start, int n_cells, unsigned int *counts,
+                          unsigned int *offsets, unsigned int *scan_tmp, int32_t *cell_chunk_start,
+                          int32_t *chunk_cell, cudaStream_t st);
 // sph_integrate.cu
 cudaError_t launch_refresh_all(const View &v, cudaStream_t st);
 cudaError_t launch_mark(const View &v, long long ti_or_neg, cudaStream_t st);

@@ -4,15 +4,23 @@
 //
 // Work item: one leaf (octree sub-cell of <= 64 particles) that holds active
 // particles, processed by one warp.  The warp splits into groups of G lanes;
-// each group owns one active particle i and its lanes stride over the
-// candidate particles j of every neighbour leaf whose bounding box comes
-// within the search radius of the leaf's bounding box.  Neighbour leaves are
-// found in the 27 top-level cells around the leaf's cell; their bounding boxes
-// are tested 32 at a time with a warp ballot.  Pair arithmetic is FP32 on
-// cell-relative coordinates (the periodic shift of a neighbour cell is a
-// multiple of the cell width applied once per cell); per-cell partial sums are
-// folded into compensated (hi, lo) accumulators, the G lanes of a group are
-// combined in FP64, and the Newton update of h is done in FP64.
+// each group owns one active particle i, and its lanes stride over the
+// candidate particles j.  Candidates come from the 27 top-level cells around
+// the leaf's cell: cells holding more than 32 leaves are first pruned by
+// chunk (32 consecutive leaves) bounding boxes, then leaves by their own
+// boxes, 32 boxes per warp ballot.  The records of the accepted leaves
+// (contiguous in memory) are staged into shared memory by cp.async.bulk
+// (TMA bulk copies) completing on a per-warp mbarrier, a batch at a time, and
+// every group of the warp reads the staged batch.
+//
+// Record positions are relative to each leaf's corner on its cell's 1024^3
+// Morton grid; the offset between two leaves is an exact integer number of
+// grid steps times w / 1024, so FP32 keeps a relative precision set by the
+// leaf size even deep inside clumps.  Per-cell partial sums are folded into
+// compensated (hi, lo) accumulators, the G lanes of a group are combined in
+// FP64, and the Newton update of h is done in FP64.  The order of every sum
+// depends only on the particle, so the plain and batched forms agree bit for
+// bit.
 //
 // The work queue is read either one item per warp (grid sized on the host) or
 // by persistent warps pulling items from a device counter (batched form).
@@ -26,9 +34,77 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int PT = WARPS_PER_BLOCK * 32;
+constexpr int S_DENS = 256;   // staged candidate records per warp, density loop
+constexpr int S_FORCE = 128;  // staged candidates per warp, force loop (3 records each)
+constexpr long long WAIT_LIMIT = 1ll << 22;  // bounded mbarrier wait (iterations)
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
+// ---------------------------------------------------------------------------
+// mbarrier + bulk copy (inline PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\tmbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n\t}" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+
+// bounded wait for the completion of the barrier phase with this parity
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  for (long long k = 0; k < WAIT_LIMIT; k++) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (k > 16) __nanosleep(64);
+  }
+  return false;
+}
+
+// global -> shared bulk copy (TMA), bytes a multiple of 16, both ends 16-byte aligned
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// orders this thread's earlier shared-memory reads before later bulk writes
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
 // compensated accumulation: hi + lo holds the sum of the parts
 __device__ __forceinline__ void fold(float &hi, float &lo, float part) {
   float s = hi + part;
@@ -65,6 +141,16 @@ __device__ __forceinline__ float warp_max(float x) {
   return x;
 }
 
+__device__ __forceinline__ int warp_incl_scan(int x) {
+  const int lane = lane_id();
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
 // Active particles of leaf [a, b) (bin <= m_act, and == bin_filter when that
 // is >= 0) written to s_act in particle order; returns their number.
 __device__ __forceinline__ int leaf_actives(const View &v, int a, int b, int m_act,
@@ -87,16 +173,17 @@ __device__ __forceinline__ int leaf_actives(const View &v, int a, int b, int m_a
   return n;
 }
 
-// squared gap between leaf i's box and leaf j's box shifted by s
-__device__ __forceinline__ float box_gap2(const float4 &loi, const float4 &hii, const float4 &loj,
-                                          const float4 &hij, float sx, float sy, float sz) {
-  float gx = fmaxf(0.0f, fmaxf(loj.x + sx - hii.x, loi.x - (hij.x + sx)));
-  float gy = fmaxf(0.0f, fmaxf(loj.y + sy - hii.y, loi.y - (hij.y + sy)));
-  float gz = fmaxf(0.0f, fmaxf(loj.z + sz - hii.z, loi.z - (hij.z + sz)));
+// squared gap between box i and box j shifted by s
+__device__ __forceinline__ float box_gap2(float lix, float liy, float liz, float hix, float hiy,
+                                          float hiz, const float4 &loj, const float4 &hij, float sx,
+                                          float sy, float sz) {
+  float gx = fmaxf(0.0f, fmaxf(loj.x + sx - hix, lix - (hij.x + sx)));
+  float gy = fmaxf(0.0f, fmaxf(loj.y + sy - hiy, liy - (hij.y + sy)));
+  float gz = fmaxf(0.0f, fmaxf(loj.z + sz - hiz, liz - (hij.z + sz)));
   return gx * gx + gy * gy + gz * gz;
 }
 
-// Cubic spline: w(q) / (8/pi) and q w'(q) / (8/pi)-weighted derivative, q in [0, 1)
+// Cubic spline: w(q) / (8/pi) and w'(q) / (8/pi), q in [0, 1)
 __device__ __forceinline__ void kernel_wd(float q, float &wq, float &dwq) {
   const float s = 1.0f - q;
   const float s2 = s * s;
@@ -119,96 +206,252 @@ __device__ __forceinline__ float kernel_dw(float q) {
 
 struct CellFrame {
   int cx, cy, cz, nc;
-  float wf;
+  float wq;        // Morton grid step w / 1024
+  float wf;        // cell width
+  int kx, ky, kz;  // the work leaf's corner on its cell's Morton grid
 };
 
-__device__ __forceinline__ int neighbour_cell(const CellFrame &F, int dx, int dy, int dz) {
-  return (wrap_cell(F.cx + dx, F.nc) * F.nc + wrap_cell(F.cy + dy, F.nc)) * F.nc +
-         wrap_cell(F.cz + dz, F.nc);
+__device__ __forceinline__ CellFrame frame_of(const View &v, const DevState *ds, int leaf) {
+  CellFrame F;
+  const int cell = v.leaf_cell[leaf];
+  const uint32_t k = v.leaf_k[leaf];
+  F.nc = ds->nc;
+  F.cx = cell / (F.nc * F.nc);
+  F.cy = (cell / F.nc) % F.nc;
+  F.cz = cell % F.nc;
+  F.wq = (float)(ds->w / (double)(1 << MORTON_BITS));
+  F.wf = (float)ds->w;
+  F.kx = leaf_kx(k);
+  F.ky = leaf_ky(k);
+  F.kz = leaf_kz(k);
+  return F;
+}
+
+struct WarpCounters {
+  unsigned long long pairs, cand, iters, noconv, overflow, timeout;
+};
+
+// ---------------------------------------------------------------------------
+// per-warp staging area in dynamic shared memory
+// ---------------------------------------------------------------------------
+template <int S, int NREC>
+struct Stage {
+  float4 *rec;      // NREC arrays of S records, back to back
+  float4 *shift;    // per staged leaf: offset of its corner (x, y, z), first particle (w bits)
+  int *pack;        // per staged leaf: slot | count << 10 | cell index << 20
+  int *act;         // active particles of the work leaf
+  uint64_t *bar;
+  uint32_t phase;
+  int fill, nmeta;
+  bool failed;
+  static constexpr size_t bytes() {
+    return sizeof(float4) * (size_t)S * (NREC + 1) + sizeof(int) * S + sizeof(int) * LEAF_MAX_LIMIT + 16;
+  }
+  __device__ void carve(char *base) {
+    rec = reinterpret_cast<float4 *>(base);
+    shift = rec + (size_t)S * NREC;
+    pack = reinterpret_cast<int *>(shift + S);
+    act = pack + S;
+    bar = reinterpret_cast<uint64_t *>(act + LEAF_MAX_LIMIT);
+  }
+};
+
+// The 27 neighbour cells, their chunks and leaves around the work leaf:
+// every leaf whose box passes `leaf_ok` (and whose chunk passes `chunk_ok`
+// in cells of more than CHUNK leaves) is staged, in cell-then-leaf order, and
+// `consume` is called on each full batch and once at the end.
+template <int S, int NREC, class LeafOk, class ChunkOk, class Consume>
+__device__ __forceinline__ void gather(const View &v, const CellFrame &F, const float4 *const *srcs,
+                                       Stage<S, NREC> &st, LeafOk leaf_ok, ChunkOk chunk_ok,
+                                       Consume consume, WarpCounters &wc) {
+  const int lane = lane_id();
+  auto flush = [&]() {
+    if (st.nmeta == 0) return;
+    if (lane == 0) mbar_arrive(st.bar);
+    if (!mbar_wait(st.bar, st.phase)) {
+      st.failed = true;
+      wc.timeout++;
+    }
+    st.phase ^= 1u;
+    if (!st.failed) consume();
+    __syncwarp();
+    fence_proxy_async();
+    st.fill = 0;
+    st.nmeta = 0;
+  };
+  auto stage_leaves = [&](int la, int lb, int ci, int bx, int by, int bz) {
+    const int l = la + lane;
+    bool ok = false;
+    int ja = 0, cnt = 0;
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+    if (l < lb) {
+      const uint32_t kl = v.leaf_k[l];
+      sx = (float)(bx + leaf_kx(kl)) * F.wq;
+      sy = (float)(by + leaf_ky(kl)) * F.wq;
+      sz = (float)(bz + leaf_kz(kl)) * F.wq;
+      ok = leaf_ok(l, sx, sy, sz);
+      if (ok) {
+        ja = v.leaf_start[l];
+        cnt = v.leaf_start[l + 1] - ja;
+      }
+    }
+    unsigned mk = __ballot_sync(FULL, ok);
+    while (mk && !st.failed) {
+      const bool mine = (mk >> lane) & 1u;
+      const int c = mine ? cnt : 0;
+      const int incl = warp_incl_scan(c);
+      const int total = __shfl_sync(FULL, incl, 31);
+      unsigned take = mk;
+      if (st.fill + total > S) {
+        take = __ballot_sync(FULL, mine && st.fill + incl <= S);
+        if (take == 0u) {
+          flush();
+          continue;
+        }
+      }
+      const int last = 31 - __clz(take);
+      const int taken = __shfl_sync(FULL, incl, last);
+      if (lane == 0) mbar_expect_tx(st.bar, (uint32_t)(taken * NREC * (int)sizeof(float4)));
+      __syncwarp();
+      if ((take >> lane) & 1u) {
+        const int slot = st.fill + incl - c;
+        const int m = st.nmeta + __popc(take & ((1u << lane) - 1u));
+        st.shift[m] = make_float4(sx, sy, sz, __int_as_float(ja));
+        st.pack[m] = slot | (c << 10) | (ci << 20);
+        for (int r = 0; r < NREC; r++)
+          bulk_g2s(st.rec + (size_t)r * S + slot, srcs[r] + ja, (uint32_t)(c * sizeof(float4)), st.bar);
+      }
+      wc.cand += (unsigned long long)taken;
+      st.fill += taken;
+      st.nmeta += __popc(take);
+      mk &= ~take;
+      __syncwarp();
+      if (mk) flush();
+    }
+  };
+
+  for (int ci = 0; ci < 27 && !st.failed; ci++) {
+    const int dxc = ci / 9 - 1, dyc = (ci / 3) % 3 - 1, dzc = ci % 3 - 1;
+    const int cj = (wrap_cell(F.cx + dxc, F.nc) * F.nc + wrap_cell(F.cy + dyc, F.nc)) * F.nc +
+                   wrap_cell(F.cz + dzc, F.nc);
+    // grid-step offset of the neighbour cell's corner from the work leaf's corner
+    const int bx = dxc * (1 << MORTON_BITS) - F.kx;
+    const int by = dyc * (1 << MORTON_BITS) - F.ky;
+    const int bz = dzc * (1 << MORTON_BITS) - F.kz;
+    const int l0 = v.cell_leaf_start[cj], l1 = v.cell_leaf_start[cj + 1];
+    if (l1 - l0 <= CHUNK) {
+      if (l1 > l0) stage_leaves(l0, l1, ci, bx, by, bz);
+      continue;
+    }
+    const int g0 = v.cell_chunk_start[cj], g1 = v.cell_chunk_start[cj + 1];
+    const float csx = dxc * F.wf, csy = dyc * F.wf, csz = dzc * F.wf;
+    for (int gb = g0; gb < g1 && !st.failed; gb += 32) {
+      const int g = gb + lane;
+      const bool okc = g < g1 && chunk_ok(g, csx, csy, csz);
+      unsigned mc = __ballot_sync(FULL, okc);
+      while (mc && !st.failed) {
+        const int src = __ffs(mc) - 1;
+        mc &= mc - 1;
+        const int la = l0 + CHUNK * (gb + src - g0);
+        stage_leaves(la, min(la + CHUNK, l1), ci, bx, by, bz);
+      }
+    }
+  }
+  if (!st.failed) flush();
 }
 
 // ---------------------------------------------------------------------------
 // density loop + smoothing-length iteration for the active particles of a leaf
 // ---------------------------------------------------------------------------
-struct WarpCounters {
-  unsigned long long pairs, cand, iters, noconv, overflow;
-};
-
 template <int G>
 __device__ void density_leaf(const View &v, int leaf, int flags, int bin_filter, int m_act,
-                             const CellFrame &F, float hcap, long long ti, int *s_act,
-                             WarpCounters &wc) {
+                             const CellFrame &F, float hcap, long long ti,
+                             Stage<S_DENS, 1> &st, WarpCounters &wc) {
   const int lane = lane_id();
   const int a = v.leaf_start[leaf], b = v.leaf_start[leaf + 1];
-  const int nact = leaf_actives(v, a, b, m_act, bin_filter, s_act);
+  const int nact = leaf_actives(v, a, b, m_act, bin_filter, st.act);
   if (nact == 0) return;
   constexpr int P = 32 / G;
   const int grp = lane / G, sub = lane % G;
   const float4 blo = v.leaf_lo[leaf], bhi = v.leaf_hi[leaf];
+  // the leaf's box in its cell's frame (for the chunk tests)
+  const float qox = F.kx * F.wq, qoy = F.ky * F.wq, qoz = F.kz * F.wq;
+  const float clx = blo.x + qox, cly = blo.y + qoy, clz = blo.z + qoz;
+  const float chx = bhi.x + qox, chy = bhi.y + qoy, chz = bhi.z + qoz;
+  const float ceps = 1e-5f * F.wf;
   const double eta3 = v.eta * v.eta * v.eta;
   const bool init_entropy = (flags & SPH_DENSITY_INIT_ENTROPY) != 0;
+  const float4 *srcs[1] = {v.rec_xm};
 
-  for (int r = 0; r < nact; r += P) {
+  for (int r = 0; r < nact && !st.failed; r += P) {
     const int slot = r + grp;
     const bool valid = slot < nact;
-    const int i = valid ? s_act[slot] : a;
+    const int i = valid ? st.act[slot] : a;
     const float4 xi = v.rec_xm[i];
     float h = v.h[i];
     double lo = 0.0, hi = INFINITY;
     bool done = !valid;
-    for (int it = 0; it < v.h_max_iter; it++) {
+    for (int it = 0; it < v.h_max_iter && !st.failed; it++) {
       const float H = GAMMA_K * h;
       const float Hs = warp_max(done ? 0.0f : H);
       if (Hs == 0.0f) break;  // every particle of the round has converged
       const float H2 = H * H, Hinv = 1.0f / H;
       const float Hs2 = Hs * Hs * 1.0002f;
+      const float Hc = Hs + ceps;
       float n_hi = 0.f, n_lo = 0.f, t_hi = 0.f, t_lo = 0.f;
       float r_hi = 0.f, r_lo = 0.f, rt_hi = 0.f, rt_lo = 0.f;
-      int cnt = 0;
-      for (int dxc = -1; dxc <= 1; dxc++)
-        for (int dyc = -1; dyc <= 1; dyc++)
-          for (int dzc = -1; dzc <= 1; dzc++) {
-            const int cj = neighbour_cell(F, dxc, dyc, dzc);
-            const float sx = dxc * F.wf, sy = dyc * F.wf, sz = dzc * F.wf;
-            const float xx = xi.x - sx, xy = xi.y - sy, xz = xi.z - sz;
-            const int l0 = v.cell_leaf_start[cj], l1 = v.cell_leaf_start[cj + 1];
-            float pn = 0.f, pt = 0.f, pr = 0.f, prt = 0.f;
-            for (int lb = l0; lb < l1; lb += 32) {
-              const int l = lb + lane;
-              bool ok = false;
-              if (l < l1) ok = box_gap2(blo, bhi, v.leaf_lo[l], v.leaf_hi[l], sx, sy, sz) < Hs2;
-              unsigned mk = __ballot_sync(FULL, ok);
-              while (mk) {
-                const int jl = lb + __ffs(mk) - 1;
-                mk &= mk - 1;
-                const int ja = v.leaf_start[jl], jb = v.leaf_start[jl + 1];
-                wc.cand += (unsigned long long)(jb - ja);
-                for (int j = ja + sub; j < jb; j += G) {
-                  const float4 pj = __ldg(&v.rec_xm[j]);
-                  const float dx = xx - pj.x, dy = xy - pj.y, dz = xz - pj.z;
-                  const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                  if (!done && r2 < H2) {
-                    const float rr = r2 * rsqrtf(fmaxf(r2, 1e-30f));
-                    const float q = rr * Hinv;
-                    float wq, dwq;
-                    kernel_wd(q, wq, dwq);
-                    const float t = fmaf(q, dwq, 3.0f * wq);
-                    pn += wq;
-                    pt += t;
-                    pr = fmaf(pj.w, wq, pr);
-                    prt = fmaf(pj.w, t, prt);
-                    cnt += (j != i);
-                  }
-                }
-              }
-            }
+      float pn = 0.f, pt = 0.f, pr = 0.f, prt = 0.f;
+      int cur = -1, cnt = 0;
+      auto leaf_ok = [&](int l, float sx, float sy, float sz) {
+        return box_gap2(blo.x, blo.y, blo.z, bhi.x, bhi.y, bhi.z, v.leaf_lo[l], v.leaf_hi[l], sx, sy,
+                        sz) < Hs2;
+      };
+      auto chunk_ok = [&](int g, float sx, float sy, float sz) {
+        return box_gap2(clx, cly, clz, chx, chy, chz, v.chunk_lo[g], v.chunk_hi[g], sx, sy, sz) <
+               Hc * Hc;
+      };
+      auto consume = [&]() {
+        for (int k = 0; k < st.nmeta; k++) {
+          const float4 sh = st.shift[k];
+          const int pk = st.pack[k];
+          const int ci = pk >> 20, off = pk & 1023, c = (pk >> 10) & 1023;
+          if (ci != cur) {
             fold(n_hi, n_lo, pn);
             fold(t_hi, t_lo, pt);
             fold(r_hi, r_lo, pr);
             fold(rt_hi, rt_lo, prt);
+            pn = pt = pr = prt = 0.f;
+            cur = ci;
           }
+          const int ja = __float_as_int(sh.w);
+          const float xx = xi.x - sh.x, xy = xi.y - sh.y, xz = xi.z - sh.z;
+          for (int t = sub; t < c; t += G) {
+            const float4 pj = st.rec[off + t];
+            const float dx = xx - pj.x, dy = xy - pj.y, dz = xz - pj.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (!done && r2 < H2) {
+              const float rr = r2 * rsqrtf(fmaxf(r2, 1e-30f));
+              const float q = rr * Hinv;
+              float wq, dwq;
+              kernel_wd(q, wq, dwq);
+              const float tt = fmaf(q, dwq, 3.0f * wq);
+              pn += wq;
+              pt += tt;
+              pr = fmaf(pj.w, wq, pr);
+              prt = fmaf(pj.w, tt, prt);
+              cnt += (ja + t != i);
+            }
+          }
+        }
+      };
+      gather<S_DENS, 1>(v, F, srcs, st, leaf_ok, chunk_ok, consume, wc);
+      if (st.failed) break;
+      fold(n_hi, n_lo, pn);
+      fold(t_hi, t_lo, pt);
+      fold(r_hi, r_lo, pr);
+      fold(rt_hi, rt_lo, prt);
       const double sn = group_sum<G>((double)n_hi + (double)n_lo);
-      const double st = group_sum<G>((double)t_hi + (double)t_lo);
+      const double stt = group_sum<G>((double)t_hi + (double)t_lo);
       const double sr = group_sum<G>((double)r_hi + (double)r_lo);
       const double srt = group_sum<G>((double)rt_hi + (double)rt_lo);
       cnt = group_sum_i<G>(cnt);
@@ -217,7 +460,7 @@ __device__ void density_leaf(const View &v, int leaf, int flags, int bin_filter,
         const double Hd = (double)H, Hi = 1.0 / Hd;
         const double Hi3 = Hi * Hi * Hi, Hi4 = Hi3 * Hi;
         const double nn = (double)KERNEL_NORM * sn * Hi3;
-        const double dndh = -GAMMA_K_D * (double)KERNEL_NORM * st * Hi4;
+        const double dndh = -GAMMA_K_D * (double)KERNEL_NORM * stt * Hi4;
         const double hd = (double)h;
         const double F3 = hd * hd * hd * nn - eta3;
         const double dF = 3.0 * hd * hd * nn + hd * hd * hd * dndh;
@@ -240,8 +483,9 @@ __device__ void density_leaf(const View &v, int leaf, int flags, int bin_filter,
             if (over) {
               wc.overflow++;
               atomic_max_float_pos(&v.ds->want_h_bits, (float)hn);
+            } else if (!conv) {
+              wc.noconv++;
             }
-            else if (!conv) wc.noconv++;
             // density, grad-h factor, equation of state at the final h
             const double rho_d = (double)KERNEL_NORM * sr * Hi3;
             const double drho = -GAMMA_K_D * (double)KERNEL_NORM * srt * Hi4;
@@ -270,13 +514,16 @@ __device__ void density_leaf(const View &v, int leaf, int flags, int bin_filter,
       }
     }
   }
-  // largest support in the leaf after the update
+  // largest support in the leaf after the update; the chunk's keeps a bound
   __syncwarp();
   float Hm = 0.0f;
   for (int k = a + lane; k < b; k += 32) Hm = fmaxf(Hm, v.rec_xH[k].w);
   Hm = warp_max(Hm);
   if (lane == 0) {
     reinterpret_cast<float *>(&v.leaf_lo[leaf])[3] = Hm;
+    const int cell = v.leaf_cell[leaf];
+    const int g = v.cell_chunk_start[cell] + (leaf - v.cell_leaf_start[cell]) / CHUNK;
+    atomic_max_float_pos(reinterpret_cast<unsigned int *>(&v.chunk_lo[g]) + 3, Hm);
     atomic_max_float_pos(&v.ds->Hmax_bits, Hm);
   }
 }
@@ -286,21 +533,27 @@ __device__ void density_leaf(const View &v, int leaf, int flags, int bin_filter,
 // ---------------------------------------------------------------------------
 template <int G>
 __device__ void force_leaf(const View &v, int leaf, int bin_filter, int m_act, const CellFrame &F,
-                           int *s_act, WarpCounters &wc) {
+                           Stage<S_FORCE, 3> &st, WarpCounters &wc) {
   const int lane = lane_id();
   const int a = v.leaf_start[leaf], b = v.leaf_start[leaf + 1];
-  const int nact = leaf_actives(v, a, b, m_act, bin_filter, s_act);
+  const int nact = leaf_actives(v, a, b, m_act, bin_filter, st.act);
   if (nact == 0) return;
   constexpr int P = 32 / G;
   const int grp = lane / G, sub = lane % G;
   const float4 blo = v.leaf_lo[leaf], bhi = v.leaf_hi[leaf];
+  const float qox = F.kx * F.wq, qoy = F.ky * F.wq, qoz = F.kz * F.wq;
+  const float clx = blo.x + qox, cly = blo.y + qoy, clz = blo.z + qoz;
+  const float chx = bhi.x + qox, chy = bhi.y + qoy, chz = bhi.z + qoz;
+  const float ceps = 1e-5f * F.wf;
   const float alpha = (float)v.alpha;
   const float g = (float)v.gamma;
+  const float4 *srcs[3] = {v.rec_xH, v.rec_v, v.rec_h};
+  const float4 *sx_rec = st.rec, *sv_rec = st.rec + S_FORCE, *sh_rec = st.rec + 2 * S_FORCE;
 
-  for (int r = 0; r < nact; r += P) {
+  for (int r = 0; r < nact && !st.failed; r += P) {
     const int slot = r + grp;
     const bool valid = slot < nact;
-    const int i = valid ? s_act[slot] : a;
+    const int i = valid ? st.act[slot] : a;
     const float4 xi = v.rec_xH[i];
     const float4 vi = v.rec_v[i];
     const float4 hi4 = v.rec_h[i];
@@ -310,70 +563,75 @@ __device__ void force_leaf(const View &v, int leaf, int bin_filter, int m_act, c
     const float Hs = warp_max(valid ? xi.w : 0.0f);
     float ax_hi = 0.f, ax_lo = 0.f, ay_hi = 0.f, ay_lo = 0.f, az_hi = 0.f, az_lo = 0.f;
     float ad_hi = 0.f, ad_lo = 0.f;
+    float pax = 0.f, pay = 0.f, paz = 0.f, pad = 0.f;
     float vs = 2.0f * hi4.z;
-    int cnt = 0;
-    for (int dxc = -1; dxc <= 1; dxc++)
-      for (int dyc = -1; dyc <= 1; dyc++)
-        for (int dzc = -1; dzc <= 1; dzc++) {
-          const int cj = neighbour_cell(F, dxc, dyc, dzc);
-          const float sx = dxc * F.wf, sy = dyc * F.wf, sz = dzc * F.wf;
-          const float xx = xi.x - sx, xy = xi.y - sy, xz = xi.z - sz;
-          const int l0 = v.cell_leaf_start[cj], l1 = v.cell_leaf_start[cj + 1];
-          float pax = 0.f, pay = 0.f, paz = 0.f, pad = 0.f;
-          for (int lb = l0; lb < l1; lb += 32) {
-            const int l = lb + lane;
-            bool ok = false;
-            if (l < l1) {
-              const float4 loj = v.leaf_lo[l];
-              const float R = fmaxf(Hs, loj.w);
-              ok = box_gap2(blo, bhi, loj, v.leaf_hi[l], sx, sy, sz) < R * R * 1.0002f;
-            }
-            unsigned mk = __ballot_sync(FULL, ok);
-            while (mk) {
-              const int jl = lb + __ffs(mk) - 1;
-              mk &= mk - 1;
-              const int ja = v.leaf_start[jl], jb = v.leaf_start[jl + 1];
-              wc.cand += (unsigned long long)(jb - ja);
-              for (int j = ja + sub; j < jb; j += G) {
-                const float4 pj = __ldg(&v.rec_xH[j]);
-                const float dx = xx - pj.x, dy = xy - pj.y, dz = xz - pj.z;
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                if (valid && j != i && (r2 < Hi2 || r2 < pj.w * pj.w)) {
-                  const float4 vj = __ldg(&v.rec_v[j]);
-                  const float4 hj = __ldg(&v.rec_h[j]);
-                  cnt++;
-                  if (r2 > 0.0f) {
-                    const float rinv = rsqrtf(r2);
-                    const float rr = r2 * rinv;
-                    const float qi = rr * hi4.w, qj = rr * hj.w;
-                    const float dwi = qi < 1.0f ? kernel_dw(qi) * nHi4 : 0.0f;
-                    const float hj2 = hj.w * hj.w;
-                    const float dwj = qj < 1.0f ? kernel_dw(qj) * (KERNEL_NORM * hj2 * hj2) : 0.0f;
-                    const float dvdr =
-                        fmaf(vi.x - vj.x, dx, fmaf(vi.y - vj.y, dy, (vi.z - vj.z) * dz));
-                    // Monaghan signal-velocity viscosity, beta = 3 (as in Eq. 1)
-                    const float wij = fminf(0.0f, dvdr * rinv);
-                    const float vsij = hi4.z + hj.z - 3.0f * wij;
-                    const float Pi = -alpha * vsij * wij / (hi4.x + hj.x);
-                    const float dWb = 0.5f * (dwi + dwj);
-                    const float sc = vj.w * fmaf(hi4.y, dwi, fmaf(hj.y, dwj, Pi * dWb)) * rinv;
-                    pax = fmaf(-sc, dx, pax);
-                    pay = fmaf(-sc, dy, pay);
-                    paz = fmaf(-sc, dz, paz);
-                    pad = fmaf(vj.w * Pi * dWb, dvdr * rinv, pad);
-                    vs = fmaxf(vs, vsij);
-                  } else {
-                    vs = fmaxf(vs, hi4.z + hj.z);
-                  }
-                }
-              }
-            }
-          }
+    int cur = -1, cnt = 0;
+    auto leaf_ok = [&](int l, float sx, float sy, float sz) {
+      const float4 loj = v.leaf_lo[l];
+      const float R = fmaxf(Hs, loj.w);
+      return box_gap2(blo.x, blo.y, blo.z, bhi.x, bhi.y, bhi.z, loj, v.leaf_hi[l], sx, sy, sz) <
+             R * R * 1.0002f;
+    };
+    auto chunk_ok = [&](int gg, float sx, float sy, float sz) {
+      const float4 loc = v.chunk_lo[gg];
+      const float R = fmaxf(Hs, loc.w) + ceps;
+      return box_gap2(clx, cly, clz, chx, chy, chz, loc, v.chunk_hi[gg], sx, sy, sz) < R * R;
+    };
+    auto consume = [&]() {
+      for (int k = 0; k < st.nmeta; k++) {
+        const float4 sh = st.shift[k];
+        const int pk = st.pack[k];
+        const int ci = pk >> 20, off = pk & 1023, c = (pk >> 10) & 1023;
+        if (ci != cur) {
           fold(ax_hi, ax_lo, pax);
           fold(ay_hi, ay_lo, pay);
           fold(az_hi, az_lo, paz);
           fold(ad_hi, ad_lo, pad);
+          pax = pay = paz = pad = 0.f;
+          cur = ci;
         }
+        const int ja = __float_as_int(sh.w);
+        const float xx = xi.x - sh.x, xy = xi.y - sh.y, xz = xi.z - sh.z;
+        for (int t = sub; t < c; t += G) {
+          const float4 pj = sx_rec[off + t];
+          const float dx = xx - pj.x, dy = xy - pj.y, dz = xz - pj.z;
+          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          if (valid && ja + t != i && (r2 < Hi2 || r2 < pj.w * pj.w)) {
+            const float4 vj = sv_rec[off + t];
+            const float4 hj = sh_rec[off + t];
+            cnt++;
+            if (r2 > 0.0f) {
+              const float rinv = rsqrtf(r2);
+              const float rr = r2 * rinv;
+              const float qi = rr * hi4.w, qj = rr * hj.w;
+              const float dwi = qi < 1.0f ? kernel_dw(qi) * nHi4 : 0.0f;
+              const float hj2 = hj.w * hj.w;
+              const float dwj = qj < 1.0f ? kernel_dw(qj) * (KERNEL_NORM * hj2 * hj2) : 0.0f;
+              const float dvdr = fmaf(vi.x - vj.x, dx, fmaf(vi.y - vj.y, dy, (vi.z - vj.z) * dz));
+              // Monaghan signal-velocity viscosity, beta = 3 (as in Eq. 1)
+              const float wij = fminf(0.0f, dvdr * rinv);
+              const float vsij = hi4.z + hj.z - 3.0f * wij;
+              const float Pi = -alpha * vsij * wij / (hi4.x + hj.x);
+              const float dWb = 0.5f * (dwi + dwj);
+              const float sc = vj.w * fmaf(hi4.y, dwi, fmaf(hj.y, dwj, Pi * dWb)) * rinv;
+              pax = fmaf(-sc, dx, pax);
+              pay = fmaf(-sc, dy, pay);
+              paz = fmaf(-sc, dz, paz);
+              pad = fmaf(vj.w * Pi * dWb, dvdr * rinv, pad);
+              vs = fmaxf(vs, vsij);
+            } else {
+              vs = fmaxf(vs, hi4.z + hj.z);
+            }
+          }
+        }
+      }
+    };
+    gather<S_FORCE, 3>(v, F, srcs, st, leaf_ok, chunk_ok, consume, wc);
+    if (st.failed) break;
+    fold(ax_hi, ax_lo, pax);
+    fold(ay_hi, ay_lo, pay);
+    fold(az_hi, az_lo, paz);
+    fold(ad_hi, ad_lo, pad);
     const double sax = group_sum<G>((double)ax_hi + (double)ax_lo);
     const double say = group_sum<G>((double)ay_hi + (double)ay_lo);
     const double saz = group_sum<G>((double)az_hi + (double)az_lo);
@@ -396,42 +654,48 @@ __device__ void force_leaf(const View &v, int leaf, int bin_filter, int m_act, c
 // kernels
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void flush_counters(DevState *ds, WarpCounters &wc, bool density) {
-  // every lane holds its own share; sum over the warp, one atomic per counter
-  unsigned long long p = wc.pairs, c = wc.cand, it = wc.iters, nc = wc.noconv, ov = wc.overflow;
+  // pairs and iterations are held by group leaders; sum over the warp
+  unsigned long long p = wc.pairs, it = wc.iters, nc = wc.noconv, ov = wc.overflow;
   for (int o = 16; o; o >>= 1) {
     p += __shfl_xor_sync(FULL, p, o);
     it += __shfl_xor_sync(FULL, it, o);
     nc += __shfl_xor_sync(FULL, nc, o);
     ov += __shfl_xor_sync(FULL, ov, o);
   }
-  // the candidate count is warp-uniform (every lane counted the same leaves)
+  // candidates and timeouts are warp-uniform (every lane counted the same)
   if (lane_id() == 0) {
     if (density) {
       if (p) atomicAdd(&ds->s_pairs_density, p);
-      if (c) atomicAdd(&ds->s_cand_density, c);
+      if (wc.cand) atomicAdd(&ds->s_cand_density, wc.cand);
       if (it) atomicAdd(&ds->s_iters_density, it);
       if (nc) record_error(ds, SPH_ERR_H_NOCONV, nc, false);
       if (ov) record_error(ds, SPH_ERR_CELL_OVERFLOW, ov, true);
     } else {
       if (p) atomicAdd(&ds->s_pairs_force, p);
-      if (c) atomicAdd(&ds->s_cand_force, c);
+      if (wc.cand) atomicAdd(&ds->s_cand_force, wc.cand);
     }
+    if (wc.timeout) record_error(ds, SPH_ERR_TIMEOUT, wc.timeout, true);
   }
 }
 
-__device__ __forceinline__ CellFrame frame_of(const DevState *ds, int cell) {
-  CellFrame F;
-  F.nc = ds->nc;
-  F.cx = cell / (F.nc * F.nc);
-  F.cy = (cell / F.nc) % F.nc;
-  F.cz = cell % F.nc;
-  F.wf = (float)ds->w;
-  return F;
+template <class St>
+__device__ __forceinline__ void stage_init(St &st) {
+  extern __shared__ __align__(16) char smem_dyn[];
+  const int warp = threadIdx.x >> 5;
+  st.carve(smem_dyn + (size_t)warp * St::bytes());
+  st.phase = 0u;
+  st.fill = 0;
+  st.nmeta = 0;
+  st.failed = false;
+  if (lane_id() == 0) {
+    mbar_init(st.bar, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
 }
 
 template <int G>
-__global__ void __launch_bounds__(PT) k_density(View v, int flags, int bin_filter, int persistent) {
-  __shared__ int s_act[WARPS_PER_BLOCK][LEAF_MAX_LIMIT];
+__global__ void __launch_bounds__(PT, 2) k_density(View v, int flags, int bin_filter, int persistent) {
   DevState *ds = v.ds;
   if (ds->halt) return;
   const int warp = threadIdx.x >> 5, lane = lane_id();
@@ -444,57 +708,58 @@ __global__ void __launch_bounds__(PT) k_density(View v, int flags, int bin_filte
     if (blockIdx.x == 0 && threadIdx.x == 0) record_error(ds, SPH_ERR_CELL_OVERFLOW, 1, true);
     return;
   }
+  Stage<S_DENS, 1> st;
+  stage_init(st);
   const float hcap = (float)((w - 2.0 * (double)exc) / GAMMA_K_D * (1.0 - 1e-6));
   const int m_act = ds->m_act;
   const long long ti = ds->ti;
   const int *q = bin_filter >= 0 ? v.q_bin : v.q_active;
   const int nq = bin_filter >= 0 ? ds->n_bin_leaves : ds->n_active_leaves;
-  WarpCounters wc = {0, 0, 0, 0, 0};
+  WarpCounters wc = {0, 0, 0, 0, 0, 0};
   if (persistent) {
     for (;;) {
       int item = 0;
       if (lane == 0) item = atomicAdd(&ds->head_density, 1);
       item = __shfl_sync(FULL, item, 0);
-      if (item >= nq) break;
+      if (item >= nq || st.failed) break;
       const int leaf = q[item];
-      density_leaf<G>(v, leaf, flags, bin_filter, m_act, frame_of(ds, v.leaf_cell[leaf]), hcap, ti,
-                      s_act[warp], wc);
+      density_leaf<G>(v, leaf, flags, bin_filter, m_act, frame_of(v, ds, leaf), hcap, ti, st, wc);
     }
   } else {
     const int item = blockIdx.x * WARPS_PER_BLOCK + warp;
     if (item < nq) {
       const int leaf = q[item];
-      density_leaf<G>(v, leaf, flags, bin_filter, m_act, frame_of(ds, v.leaf_cell[leaf]), hcap, ti,
-                      s_act[warp], wc);
+      density_leaf<G>(v, leaf, flags, bin_filter, m_act, frame_of(v, ds, leaf), hcap, ti, st, wc);
     }
   }
   flush_counters(ds, wc, true);
 }
 
 template <int G>
-__global__ void __launch_bounds__(PT) k_force(View v, int bin_filter, int persistent) {
-  __shared__ int s_act[WARPS_PER_BLOCK][LEAF_MAX_LIMIT];
+__global__ void __launch_bounds__(PT, 2) k_force(View v, int bin_filter, int persistent) {
   DevState *ds = v.ds;
   if (ds->halt) return;
   const int warp = threadIdx.x >> 5, lane = lane_id();
+  Stage<S_FORCE, 3> st;
+  stage_init(st);
   const int m_act = ds->m_act;
   const int *q = bin_filter >= 0 ? v.q_bin : v.q_active;
   const int nq = bin_filter >= 0 ? ds->n_bin_leaves : ds->n_active_leaves;
-  WarpCounters wc = {0, 0, 0, 0, 0};
+  WarpCounters wc = {0, 0, 0, 0, 0, 0};
   if (persistent) {
     for (;;) {
       int item = 0;
       if (lane == 0) item = atomicAdd(&ds->head_force, 1);
       item = __shfl_sync(FULL, item, 0);
-      if (item >= nq) break;
+      if (item >= nq || st.failed) break;
       const int leaf = q[item];
-      force_leaf<G>(v, leaf, bin_filter, m_act, frame_of(ds, v.leaf_cell[leaf]), s_act[warp], wc);
+      force_leaf<G>(v, leaf, bin_filter, m_act, frame_of(v, ds, leaf), st, wc);
     }
   } else {
     const int item = blockIdx.x * WARPS_PER_BLOCK + warp;
     if (item < nq) {
       const int leaf = q[item];
-      force_leaf<G>(v, leaf, bin_filter, m_act, frame_of(ds, v.leaf_cell[leaf]), s_act[warp], wc);
+      force_leaf<G>(v, leaf, bin_filter, m_act, frame_of(v, ds, leaf), st, wc);
     }
   }
   flush_counters(ds, wc, false);
@@ -516,17 +781,37 @@ __global__ void k_entropy_from_u(View v) {
   }
 }
 
+constexpr size_t DENS_SMEM = Stage<S_DENS, 1>::bytes() * WARPS_PER_BLOCK;
+constexpr size_t FORCE_SMEM = Stage<S_FORCE, 3>::bytes() * WARPS_PER_BLOCK;
+
 template <int G>
 cudaError_t density_g(const View &v, int flags, int bin_filter, bool persistent, int grid,
                       cudaStream_t st) {
-  k_density<G><<<grid, PT, 0, st>>>(v, flags, bin_filter, persistent ? 1 : 0);
+  k_density<G><<<grid, PT, DENS_SMEM, st>>>(v, flags, bin_filter, persistent ? 1 : 0);
   return cudaGetLastError();
 }
 
 template <int G>
 cudaError_t force_g(const View &v, int bin_filter, bool persistent, int grid, cudaStream_t st) {
-  k_force<G><<<grid, PT, 0, st>>>(v, bin_filter, persistent ? 1 : 0);
+  k_force<G><<<grid, PT, FORCE_SMEM, st>>>(v, bin_filter, persistent ? 1 : 0);
   return cudaGetLastError();
+}
+
+template <int G>
+int blocks_per_sm_g(bool density) {
+  const void *fn = density ? (const void *)k_density<G> : (const void *)k_force<G>;
+  const size_t smem = density ? DENS_SMEM : FORCE_SMEM;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, PT, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nb;
 }
 
 }  // namespace
@@ -563,20 +848,18 @@ cudaError_t launch_force(const View &v, int bin_filter, bool persistent, int gri
   }
 }
 
+// Sets the dynamic shared-memory limit of the pair kernels for this G and
+// returns the resident blocks per SM (0 when the configuration cannot run).
 int persistent_blocks_per_sm(int G, bool density) {
-  int nb = 0;
-  const void *fn = nullptr;
   switch (G) {
-    case 1: fn = density ? (const void *)k_density<1> : (const void *)k_force<1>; break;
-    case 2: fn = density ? (const void *)k_density<2> : (const void *)k_force<2>; break;
-    case 4: fn = density ? (const void *)k_density<4> : (const void *)k_force<4>; break;
-    case 8: fn = density ? (const void *)k_density<8> : (const void *)k_force<8>; break;
-    case 16: fn = density ? (const void *)k_density<16> : (const void *)k_force<16>; break;
-    case 32: fn = density ? (const void *)k_density<32> : (const void *)k_force<32>; break;
-    default: return 1;
+    case 1: return blocks_per_sm_g<1>(density);
+    case 2: return blocks_per_sm_g<2>(density);
+    case 4: return blocks_per_sm_g<4>(density);
+    case 8: return blocks_per_sm_g<8>(density);
+    case 16: return blocks_per_sm_g<16>(density);
+    case 32: return blocks_per_sm_g<32>(density);
+    default: return 0;
   }
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, PT, 0) != cudaSuccess || nb < 1) nb = 1;
-  return nb;
 }
 
 cudaError_t launch_entropy_from_u(const View &v, cudaStream_t st) {

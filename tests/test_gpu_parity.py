@@ -141,7 +141,7 @@ def test_density_clumpy_subset_and_inactive_untouched(sim, orc):
     n = ic["pos"].shape[0]
     rng = np.random.default_rng(0)
     bins = np.where(rng.uniform(size=n) < 0.3, 0, 5)     # at tick 4 only bin <= 2 is active
-    ctx, p = gpu_setup(ic, sim.Params(leaf_max=16), bins=bins, ti=4)
+    ctx, p = gpu_setup(ic, sim.Params(leaf_max=16, cell_margin=1.5), bins=bins, ti=4)
     perm = ctx.perm_tensor(n).cpu().numpy()
     g0 = p.numpy()
     L = _lib()
@@ -173,7 +173,8 @@ def test_force_parity(sim, orc, G):
     rng = np.random.default_rng(3)
     ic["vel"] = rng.normal(scale=0.5, size=(n, 3))
     ic["u"] = rng.uniform(0.5, 1.5, n)
-    ctx, p = gpu_setup(ic, sim.Params(threads_per_particle=G))
+    # standalone calls do not rebuild: cells wide enough for the h growth
+    ctx, p = gpu_setup(ic, sim.Params(threads_per_particle=G, cell_margin=1.5))
     _density_pass(sim, ctx, p)
     ctx.force_active(p)
     _sync()
@@ -259,3 +260,22 @@ def test_timestep_bins_exact(sim, orc):
     assert int(tnext.item()) == int(g["ti_end"].min())
     st, detail = ctx.status()
     assert (st == 0) == (ref["n_too_small"] == 0)
+
+
+def test_density_deep_clump_precision(sim, orc):
+    """A compact clump (scale radius 1e-3) inside cells ~100x wider than its
+    inter-particle spacing: FP32 positions relative to the leaf corners keep
+    the density within the tolerance."""
+    ic = sph_ics.clumpy_lattice(nside=14, n_clumps=1, per_clump=1500, a_min=1e-3, a_max=1e-3,
+                                seed=31)
+    n = ic["pos"].shape[0]
+    ctx, p = gpu_setup(ic, sim.Params(cell_margin=1.5))
+    _density_pass(sim, ctx, p)
+    assert ctx.status()[0] == 0
+    perm = ctx.perm_tensor(n).cpu().numpy()
+    g = p.numpy()
+    pos = _pos(g)
+    ref = orc.density(pos, _f64(g["m"]), _f64(np.float32(ic["h0"])[perm]), np.ones(n, np.uint8))
+    assert g["h"].min() < 2e-3 * ctx.grid_info()[0] ** -1          # really deep inside a cell
+    assert np.max(np.abs(g["h"] / ref["h"] - 1)) < H_TOL
+    assert np.max(np.abs(g["rho"] / ref["rho"] - 1)) < RHO_TOL
