@@ -238,6 +238,31 @@ int sph_set_profiling(sph_ctx *ctx, int enable);
 int sph_get_kernel_times(sph_ctx *ctx, sph_kernel_times *out);
 int sph_reset_kernel_times(sph_ctx *ctx);
 
+/* Allocation-free cell ordering, for callers that must not allocate device
+ * memory: a host program that has handed all of the device's memory to its
+ * own pool or runs under a fixed memory budget, or a latency-critical loop in
+ * which cudaMalloc (and the device synchronisation it can imply) is not
+ * allowed.  The paper has no counterpart; this is a variant of the ordering
+ * step of sph_build_cells.
+ * Writes to perm (device, int32, length n, caller-allocated) the stable order
+ * of the n particles by (cell, Morton code inside the cell) in an
+ * n_cells_per_axis^3 grid of the periodic box of side `box` -- exactly the
+ * order sph_build_cells produces for that grid from the same positions.  x, y,
+ * z (device, FP64) are read, not modified.  No allocation: the sort buffers are
+ * one 1.6 MB array in device memory that the library defines statically, held
+ * by every GPU that loads the library until the process exits.
+ * Limits and errors: n <= 65536 and 1 <= n_cells_per_axis <= 255, else
+ * SPH_ERR_ARG before anything is launched; SPH_ERR_CUDA if a launch or copy
+ * fails.  The first call on a device looks up the array's device address
+ * (with that device current); make that first call before any stream
+ * capture.  Every call on a device uses the same array, so calls whose work
+ * overlaps on the GPU (different streams, or host threads) race and must be
+ * serialised by the caller; each call writes every part of the array it reads,
+ * so a call needs nothing cleared from the last one.  Asynchronous on
+ * `stream`. */
+int sph_cell_order_noalloc(const double *x, const double *y, const double *z, int64_t n,
+                           double box, int n_cells_per_axis, int32_t *perm, void *stream);
+
 const char *sph_strerror(int code);
 
 #ifdef __cplusplus

@@ -101,6 +101,8 @@ def load(path: str = LIB_PATH):
     L.sph_set_profiling.argtypes = [_vp, _i]
     L.sph_get_kernel_times.argtypes = [_vp, P(sph_kernel_times)]
     L.sph_reset_kernel_times.argtypes = [_vp]
+    L.sph_cell_order_noalloc.argtypes = [_vp, _vp, _vp, _i64, _d, _i, _vp, _vp]
+    L.sph_cell_order_noalloc.restype = _i
     L.sph_strerror.argtypes = [_i]
     L.sph_strerror.restype = ctypes.c_char_p
     for name in ("sph_create", "sph_destroy", "sph_build_cells", "sph_grid_info",
@@ -123,7 +125,8 @@ def exported_symbols():
             "sph_step_sync", "sph_step", "sph_step_graph",
             "sph_get_time", "sph_set_time", "sph_get_status", "sph_clear_status",
             "sph_get_counters", "sph_reset_counters", "sph_set_profiling",
-            "sph_get_kernel_times", "sph_reset_kernel_times", "sph_strerror"]
+            "sph_get_kernel_times", "sph_reset_kernel_times", "sph_cell_order_noalloc",
+            "sph_strerror"]
 
 
 class SphError(RuntimeError):
