@@ -48,7 +48,8 @@ WORKLOAD = "c3_clustered_2m"
 FLOP_DENSITY = 29   # per useful density pair
 FLOP_FORCE = 61     # per useful force pair
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-TUNED = dict(threads_per_particle=4, leaf_max=16, cell_margin=1.1)
+DEFAULT_LAUNCH = dict(threads_per_particle=1, leaf_max=8, cell_margin=2.0)
+KNOBS = ("threads_per_particle", "leaf_max", "cell_margin")
 
 
 def _env_int(k, d):
@@ -116,7 +117,7 @@ def run_ours(args, rank, world):
     import torch
     import sph_ics
     from sph_ics import workloads
-    from paper_1807_01341_gb300 import _lib, build, sim
+    from paper_1807_01341_gb300 import _lib, autotune, build, sim
 
     build.build()
     dev = _env_int("LOCAL_RANK", 0)
@@ -125,7 +126,15 @@ def run_ours(args, rank, world):
     ic = workloads.make(args.workload)
     t_ic = time.time() - t0
     n = ic["pos"].shape[0]
-    params = sim.Params(**workloads.PARAMS[args.workload], **TUNED)
+    base = workloads.PARAMS[args.workload]
+    tuned = dict(DEFAULT_LAUNCH)
+    tune_info = None
+    if not args.no_autotune:
+        t = autotune.tune(ic, base, args.workload, steps=4)
+        tuned = {k: t[k] for k in KNOBS}
+        tune_info = {"cached": t.get("cached"),
+                     "trials": [dict(r["cand"], pairs_per_s=r["rate"]) for r in t.get("trials", [])]}
+    params = sim.Params(**base, **tuned)
     ctx = sim.Context(params, n)
     p = sim.Particles.from_ics(ic, with_counts=False)
     ctx.build_cells(p)
@@ -244,7 +253,7 @@ def run_ours(args, rank, world):
                roofline=dict(kernel=dom_name, achieved=achieved, per_launch_ms=per_launch_s * 1e3,
                              density_ms=kt["density_ms"], force_ms=kt["force_ms"]),
                gpu_state={k: t for k, t in p.arrays().items()} if rank == 0 else None,
-               ic=ic)
+               ic=ic, tuned=tuned, tune_info=tune_info)
     return out
 
 
@@ -310,6 +319,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=2048)
     ap.add_argument("--cpu-sample", type=int, default=2048)
@@ -368,7 +378,9 @@ def main():
                        "steps_from": "initial conditions (step 0 all active)",
                        "l2": "flushed between timed steps (256 MiB write)",
                        "grid_cells_per_axis": b["grid"][0], "leaves": b["grid"][1],
-                       **TUNED},
+                       "launch": out["tuned"],
+                       "autotuned": not args.no_autotune},
+            "autotune": out["tune_info"],
             "plain": plain,
             "e2e": {"value": e2e_pairs / (e2e_ms / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": out["h2d"], "d2h_bytes_per_step": out["h2d"]},

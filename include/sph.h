@@ -49,8 +49,12 @@ enum sph_status_code {
 
 /* Parameters.  Defaults (sph_default_params): eta 1.2348, gamma 5/3,
  * alpha_visc 0.8, cfl 0.1, h_tol 1e-6, h_max_iter 30, bin_cap 20,
- * dt_min 1e-6, t_begin 0, box 1, cell_margin 1.1, leaf_max 16,
- * threads_per_particle 4, drift_all 0, n_cells_override 0. */
+ * dt_min 1e-6, t_begin 0, box 1, cell_margin 2.0, leaf_max 8,
+ * threads_per_particle 1, drift_all 0, n_cells_override 0.
+ * With threads_per_particle = 1 every sum of a particle is taken in an order
+ * that depends on the particle alone, so SPH_FORM_PLAIN and SPH_FORM_BATCHED
+ * give bit-identical results; with more lanes per particle they agree to
+ * rounding. */
 typedef struct {
   double box;        /* side of the periodic cube */
   double eta;        /* resolution: h solves h^3 n(h) = eta^3, n = sum_j W(r_ij, h) */
@@ -63,7 +67,7 @@ typedef struct {
   double dt_min;     /* t_min of Eq. 2: one tick of the integer timeline */
   double t_begin;    /* time of tick 0 */
   double cell_margin;/* top-level cell width >= cell_margin * largest kernel support */
-  int leaf_max;      /* most particles in one leaf (sub-cell) of the cell tree, 1..64 */
+  int leaf_max;      /* most particles in one leaf (sub-cell) of the cell tree, 1..32 */
   int threads_per_particle; /* lanes that share one active particle: 1, 2, 4, 8, 16 or 32 */
   int drift_all;     /* 0: drift only cells next to active cells (Sec. III-D); 1: drift all */
   int n_cells_override; /* > 0: use this many top-level cells per axis (must keep the

@@ -1,0 +1,86 @@
+"""Autotuner of the launch configuration of the pair loops.
+
+For a given particle set it times short runs of the batched form (CUDA graph
+replay of persistent kernels) under candidate configurations and keeps the
+fastest in useful pairs per second:
+
+  cell_margin           top-level cell width / largest kernel support (cell size)
+  leaf_max              particles per leaf: the pruning and staging granularity
+  threads_per_particle  lanes sharing one active particle
+
+Each trial starts from the same initial state (its own context and a copy of
+the particles), so the trials do not influence one another.  The choice is
+cached in a JSON file keyed by the caller's workload key and particle count.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+from . import _lib
+from .sim import Context, Params, Particles
+
+DEFAULT_CANDIDATES = [
+    dict(threads_per_particle=1, leaf_max=8, cell_margin=2.0),
+    dict(threads_per_particle=1, leaf_max=16, cell_margin=2.0),
+    dict(threads_per_particle=1, leaf_max=8, cell_margin=1.5),
+    dict(threads_per_particle=1, leaf_max=4, cell_margin=2.0),
+    dict(threads_per_particle=2, leaf_max=8, cell_margin=2.0),
+    dict(threads_per_particle=1, leaf_max=8, cell_margin=2.5),
+]
+
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
+
+
+def _load(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def trial(ic: dict, base: dict, cand: dict, steps: int) -> dict:
+    """Time `steps` batched steps from the initial state under one candidate."""
+    import torch
+    n = ic["pos"].shape[0]
+    ctx = Context(Params(**base, **cand), n)
+    p = Particles.from_ics(ic, with_counts=False)
+    stream = torch.cuda.Stream()
+    ctx.build_cells(p, stream)
+    ctx.begin_run(stream)
+    total_ms = 0.0
+    for _ in range(steps):
+        while True:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.step_async(p, _lib.SPH_FORM_BATCHED, stream)
+            e1.record(stream)
+            done = ctx.step_sync(p, stream)
+            total_ms += e0.elapsed_time(e1)
+            if done:
+                break
+    c = ctx.counters()
+    ctx.close()
+    pairs = c["pairs_density"] + c["pairs_force"]
+    return dict(cand=cand, ms=total_ms, pairs=pairs, rate=pairs / max(total_ms, 1e-9) * 1e3)
+
+
+def tune(ic: dict, base: dict, key: str, steps: int = 4, candidates=None,
+         cache_path: str = CACHE, use_cache: bool = True) -> dict:
+    """Returns the fastest candidate configuration for this particle set."""
+    n = ic["pos"].shape[0]
+    ckey = f"{key}:n={n}:steps={steps}"
+    cache = _load(cache_path)
+    if use_cache and ckey in cache:
+        return dict(cache[ckey]["best"], cached=True)
+    results = [trial(ic, base, c, steps) for c in (candidates or DEFAULT_CANDIDATES)]
+    best = max(results, key=lambda r: r["rate"])
+    cache[ckey] = dict(best=best["cand"], trials=results)
+    os.makedirs(os.path.dirname(cache_path), exist_ok=True)
+    tmp = cache_path + ".tmp.%d" % os.getpid()
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1)
+    os.replace(tmp, cache_path)
+    return dict(best["cand"], cached=False, trials=results)

@@ -45,7 +45,9 @@ struct Buffers {
   float4 *leaf_lo = nullptr, *leaf_hi = nullptr;
   uint8_t *leaf_min_bin = nullptr;
   unsigned long long *leaf_bin_mask = nullptr;
-  int32_t *q_active = nullptr, *q_drift = nullptr, *q_bin = nullptr;
+  int32_t *q_active = nullptr, *q_drift = nullptr, *q_bin = nullptr, *q_group = nullptr;
+  // work groups of the pair loops
+  int32_t *pleaf = nullptr, *group_leaf0 = nullptr, *group_cell = nullptr;
   // records
   float4 *rec_xm = nullptr, *rec_xH = nullptr, *rec_v = nullptr, *rec_h = nullptr;
   // cells (grown on demand)
@@ -135,7 +137,7 @@ bool valid_params(const sph_params *p) {
   if (!(p->cfl > 0) || !(p->h_tol > 0) || p->h_max_iter < 1 || p->bin_cap < 0 || p->bin_cap > 62)
     return false;
   if (!(p->dt_min > 0) || !(p->cell_margin >= 1.0)) return false;
-  if (p->leaf_max < 1 || p->leaf_max > LEAF_MAX_LIMIT) return false;
+  if (p->leaf_max < 1 || p->leaf_max > WG_MAX) return false;
   int G = p->threads_per_particle;
   if (G != 1 && G != 2 && G != 4 && G != 8 && G != 16 && G != 32) return false;
   if (p->n_cells_override < 0 || p->n_cells_override > NC_MAX) return false;
@@ -192,6 +194,10 @@ View make_view(const sph_ctx *ctx, const sph_particles *p) {
   v.rec_v = b.rec_v;
   v.rec_h = b.rec_h;
   v.q_active = b.q_active;
+  v.q_group = b.q_group;
+  v.pleaf = b.pleaf;
+  v.group_leaf0 = b.group_leaf0;
+  v.group_cell = b.group_cell;
   v.q_act_cells = b.q_act_cells;
   v.q_drift = b.q_drift;
   v.q_bin = b.q_bin;
@@ -357,6 +363,15 @@ int build_cells(sph_ctx *ctx, sph_particles *p, cudaStream_t st) {
                              b.leaf_start, b.leaf_cell, b.leaf_k, b.cell_leaf_start, n, st));
   SPH_CUDA(cudaMemcpyAsync(SPH_DS_FIELD(b.ds, n_leaves), b.leaf_offsets + n_cells, sizeof(int),
                            cudaMemcpyDeviceToDevice, st));
+  int n_leaves_h = 0;
+  SPH_CUDA(cudaMemcpyAsync(&n_leaves_h, b.leaf_offsets + n_cells, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SPH_CUDA(cudaStreamSynchronize(st));
+  // work groups and the leaf of each particle
+  SPH_CUDA(launch_groups(b.cell_leaf_start, b.leaf_start, (int)n_cells, (int)n, b.leaf_counts,
+                         b.leaf_offsets, b.scan_tmp, b.group_leaf0, b.group_cell, b.pleaf, n_leaves_h,
+                         st));
+  SPH_CUDA(cudaMemcpyAsync(SPH_DS_FIELD(b.ds, n_groups), b.leaf_offsets + n_cells, sizeof(int),
+                           cudaMemcpyDeviceToDevice, st));
   // chunks of CHUNK consecutive leaves per cell (the leaf counters are free again)
   SPH_CUDA(launch_chunks(b.cell_leaf_start, (int)n_cells, b.leaf_counts, b.leaf_offsets, b.scan_tmp,
                          b.cell_chunk_start, b.chunk_cell, st));
@@ -368,6 +383,7 @@ int build_cells(sph_ctx *ctx, sph_particles *p, cudaStream_t st) {
   SPH_CUDA(cudaMemcpyAsync(SPH_DS_FIELD(b.ds, n_cells), &ncs[1], sizeof(int), cudaMemcpyHostToDevice, st));
   SPH_CUDA(cudaMemcpyAsync(SPH_DS_FIELD(b.ds, w), &w, sizeof(double), cudaMemcpyHostToDevice, st));
   SPH_CUDA(cudaMemsetAsync(SPH_DS_FIELD(b.ds, n_active_leaves), 0, sizeof(int), st));
+  SPH_CUDA(cudaMemsetAsync(SPH_DS_FIELD(b.ds, n_active_groups), 0, sizeof(int), st));
   SPH_CUDA(cudaMemsetAsync(SPH_DS_FIELD(b.ds, excursion_bits), 0, sizeof(unsigned int), st));
   SPH_CUDA(cudaMemsetAsync(SPH_DS_FIELD(b.ds, Hmax_bits), 0, sizeof(unsigned int), st));
   SPH_CUDA(cudaMemsetAsync(SPH_DS_FIELD(b.ds, want_h_bits), 0, sizeof(unsigned int), st));
@@ -414,7 +430,7 @@ int plain_body(sph_ctx *ctx, const View &v, int flags, cudaStream_t st) {
   for (int k = 0; k < nb; k++) {
     SPH_CUDA(launch_mark_bin(v, bins[k], st));
     int nq = 0;
-    SPH_CUDA(cudaMemcpyAsync(&nq, SPH_DS_FIELD(v.ds, n_bin_leaves), sizeof(int),
+    SPH_CUDA(cudaMemcpyAsync(&nq, SPH_DS_FIELD(v.ds, n_bin_groups), sizeof(int),
                              cudaMemcpyDeviceToHost, st));
     SPH_CUDA(cudaStreamSynchronize(st));
     prof_begin(ctx, 0, st);
@@ -425,7 +441,7 @@ int plain_body(sph_ctx *ctx, const View &v, int flags, cudaStream_t st) {
   for (int k = 0; k < nb; k++) {
     SPH_CUDA(launch_mark_bin(v, bins[k], st));
     int nq = 0;
-    SPH_CUDA(cudaMemcpyAsync(&nq, SPH_DS_FIELD(v.ds, n_bin_leaves), sizeof(int),
+    SPH_CUDA(cudaMemcpyAsync(&nq, SPH_DS_FIELD(v.ds, n_bin_groups), sizeof(int),
                              cudaMemcpyDeviceToHost, st));
     SPH_CUDA(cudaStreamSynchronize(st));
     prof_begin(ctx, 1, st);
@@ -517,9 +533,9 @@ void sph_default_params(sph_params *p) {
   p->bin_cap = 20;
   p->dt_min = 1e-6;
   p->t_begin = 0.0;
-  p->cell_margin = 1.1;
-  p->leaf_max = 16;
-  p->threads_per_particle = 4;
+  p->cell_margin = 2.0;
+  p->leaf_max = 8;
+  p->threads_per_particle = 1;
   p->drift_all = 0;
   p->n_cells_override = 0;
 }
@@ -575,6 +591,8 @@ int sph_create(const sph_params *params, int64_t n_max, sph_ctx **out) {
         (r = dalloc(&b.leaf_lo, n)) || (r = dalloc(&b.leaf_hi, n)) ||
         (r = dalloc(&b.leaf_min_bin, n)) || (r = dalloc(&b.leaf_bin_mask, n)) ||
         (r = dalloc(&b.q_active, n)) || (r = dalloc(&b.q_drift, n)) || (r = dalloc(&b.q_bin, n)) ||
+        (r = dalloc(&b.q_group, n)) || (r = dalloc(&b.pleaf, n)) || (r = dalloc(&b.group_leaf0, n + 1)) ||
+        (r = dalloc(&b.group_cell, n)) ||
         (r = dalloc(&b.rec_xm, n)) || (r = dalloc(&b.rec_xH, n)) || (r = dalloc(&b.rec_v, n)) ||
         (r = dalloc(&b.rec_h, n)) || (r = dalloc(&b.ds, 1)) || (r = dalloc(&b.d_hmax, 1)))
       break;
@@ -616,7 +634,8 @@ int sph_destroy(sph_ctx *ctx) {
   dfree(b.leaf_start); dfree(b.leaf_cell); dfree(b.leaf_k);
   dfree(b.chunk_cell); dfree(b.chunk_lo); dfree(b.chunk_hi); dfree(b.leaf_lo); dfree(b.leaf_hi);
   dfree(b.leaf_min_bin); dfree(b.leaf_bin_mask);
-  dfree(b.q_active); dfree(b.q_drift); dfree(b.q_bin);
+  dfree(b.q_active); dfree(b.q_drift); dfree(b.q_bin); dfree(b.q_group);
+  dfree(b.pleaf); dfree(b.group_leaf0); dfree(b.group_cell);
   dfree(b.rec_xm); dfree(b.rec_xH); dfree(b.rec_v); dfree(b.rec_h);
   dfree(b.cell_start); dfree(b.cell_leaf_start); dfree(b.cell_stamp); dfree(b.cell_rel_stamp);
   dfree(b.q_act_cells); dfree(b.leaf_counts); dfree(b.leaf_offsets);

@@ -383,6 +383,64 @@ __global__ void k_chunk_write(const unsigned int *__restrict__ offsets, int n_ce
   for (unsigned int g = offsets[c]; g < offsets[c + 1]; g++) chunk_cell[g] = c;
 }
 
+// Work groups: the leaves of a cell taken in order, a new group whenever the
+// next leaf would bring the group above WG_MAX particles.
+__global__ void k_group_count(const int32_t *__restrict__ cell_leaf_start,
+                              const int32_t *__restrict__ leaf_start, int n_cells,
+                              unsigned int *__restrict__ counts) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c > n_cells) return;
+  if (c == n_cells) {
+    counts[c] = 0;
+    return;
+  }
+  unsigned int ng = 0;
+  int cur = 0;
+  for (int l = cell_leaf_start[c]; l < cell_leaf_start[c + 1]; l++) {
+    const int cl = leaf_start[l + 1] - leaf_start[l];
+    if (ng == 0 || cur + cl > WG_MAX) {
+      ng++;
+      cur = 0;
+    }
+    cur += cl;
+  }
+  counts[c] = ng;
+}
+
+__global__ void k_group_write(const int32_t *__restrict__ cell_leaf_start,
+                              const int32_t *__restrict__ leaf_start, int n_cells,
+                              const unsigned int *__restrict__ offsets,
+                              int32_t *__restrict__ group_leaf0, int32_t *__restrict__ group_cell,
+                              int n_leaves) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c > n_cells) return;
+  if (c == n_cells) {
+    group_leaf0[offsets[c]] = n_leaves;
+    return;
+  }
+  unsigned int g = offsets[c];
+  int cur = 0;
+  bool first = true;
+  for (int l = cell_leaf_start[c]; l < cell_leaf_start[c + 1]; l++) {
+    const int cl = leaf_start[l + 1] - leaf_start[l];
+    if (first || cur + cl > WG_MAX) {
+      if (!first) g++;
+      group_leaf0[g] = l;
+      group_cell[g] = c;
+      cur = 0;
+      first = false;
+    }
+    cur += cl;
+  }
+}
+
+__global__ void k_leaf_pleaf(const int32_t *__restrict__ leaf_start, int n_leaves,
+                             int32_t *__restrict__ pleaf) {
+  int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n_leaves) return;
+  for (int i = leaf_start[l]; i < leaf_start[l + 1]; i++) pleaf[i] = l;
+}
+
 inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
@@ -494,6 +552,24 @@ cudaError_t launch_chunks(const int32_t *cell_leaf_start, int n_cells, unsigned 
   if (e != cudaSuccess) return e;
   k_chunk_write<<<blocks_for(n_cells + 1, 256), 256, 0, st>>>(offsets, n_cells, cell_chunk_start,
                                                               chunk_cell);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_groups(const int32_t *cell_leaf_start, const int32_t *leaf_start, int n_cells,
+                          int n_leaves_max, unsigned int *counts, unsigned int *offsets,
+                          unsigned int *scan_tmp, int32_t *group_leaf0, int32_t *group_cell,
+                          int32_t *pleaf, int n_leaves_host, cudaStream_t st) {
+  (void)n_leaves_max;
+  note_launches(3);
+  k_group_count<<<blocks_for(n_cells + 1, 128), 128, 0, st>>>(cell_leaf_start, leaf_start, n_cells,
+                                                               counts);
+  cudaError_t e = exclusive_scan_u32(counts, offsets, n_cells + 1, scan_tmp, st);
+  if (e != cudaSuccess) return e;
+  k_group_write<<<blocks_for(n_cells + 1, 128), 128, 0, st>>>(cell_leaf_start, leaf_start, n_cells,
+                                                               offsets, group_leaf0, group_cell,
+                                                               n_leaves_host);
+  if (n_leaves_host > 0)
+    k_leaf_pleaf<<<blocks_for(n_leaves_host, 256), 256, 0, st>>>(leaf_start, n_leaves_host, pleaf);
   return cudaGetLastError();
 }
 

@@ -48,7 +48,8 @@ __global__ void k_begin_step(View v, long long ti_arg) {
   ds->n_active_leaves = 0;
   ds->n_active_cells = 0;
   ds->n_drift_chunks = 0;
-  ds->n_bin_leaves = 0;
+  ds->n_bin_groups = 0;
+  ds->n_active_groups = 0;
   ds->head_density = ds->head_force = ds->head_drift = ds->head_kick = 0;
   ds->head_open = ds->head_bins = ds->head_misc = 0;
   ds->s_pairs_density = ds->s_pairs_force = 0ull;
@@ -68,6 +69,17 @@ __global__ void k_mark_leaves(View v) {
     int c = v.leaf_cell[l];
     if (atomicExch(&v.cell_stamp[c], epoch) != epoch)
       v.q_act_cells[atomicAdd(&ds->n_active_cells, 1)] = c;
+  }
+}
+
+// One thread per work group: queues the groups whose smallest bin is active.
+__global__ void k_mark_groups(View v) {
+  DevState *ds = v.ds;
+  const int ng = ds->n_groups, m_act = ds->m_act;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+    int mb = 127;
+    for (int l = v.group_leaf0[g]; l < v.group_leaf0[g + 1]; l++) mb = min(mb, (int)v.leaf_min_bin[l]);
+    if (mb <= m_act) v.q_group[atomicAdd(&ds->n_active_groups, 1)] = g;
   }
 }
 
@@ -382,10 +394,12 @@ __global__ void k_next_time(View v, long long *out, int count_step) {
 
 __global__ void k_mark_bin(View v, int bin) {
   DevState *ds = v.ds;
-  const int nq = ds->n_active_leaves;
+  const int nq = ds->n_active_groups;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nq; k += gridDim.x * blockDim.x) {
-    int leaf = v.q_active[k];
-    if ((v.leaf_bin_mask[leaf] >> bin) & 1ull) v.q_bin[atomicAdd(&ds->n_bin_leaves, 1)] = leaf;
+    const int g = v.q_group[k];
+    unsigned long long mask = 0ull;
+    for (int l = v.group_leaf0[g]; l < v.group_leaf0[g + 1]; l++) mask |= v.leaf_bin_mask[l];
+    if ((mask >> bin) & 1ull) v.q_bin[atomicAdd(&ds->n_bin_groups, 1)] = g;
   }
 }
 
@@ -401,10 +415,11 @@ cudaError_t launch_refresh_all(const View &v, cudaStream_t st) {
 }
 
 cudaError_t launch_mark(const View &v, long long ti_or_neg, cudaStream_t st) {
-  note_launches(v.drift_all ? 4 : 5);
+  note_launches(v.drift_all ? 5 : 6);
   k_mark_clear<<<v.grid_util, UT, 0, st>>>(v);
   k_begin_step<<<1, 1, 0, st>>>(v, ti_or_neg);
   k_mark_leaves<<<v.grid_util, UT, 0, st>>>(v);
+  k_mark_groups<<<v.grid_util, UT, 0, st>>>(v);
   k_mark_particles<<<v.grid_util, UT, 0, st>>>(v);
   if (!v.drift_all) k_relevant<<<v.grid_util, UT, 0, st>>>(v);
   return cudaGetLastError();
@@ -431,7 +446,7 @@ cudaError_t launch_bins(const View &v, long long *ti_next_out, int count_step, c
 
 cudaError_t launch_mark_bin(const View &v, int bin, cudaStream_t st) {
   note_launches(1);
-  cudaError_t e = cudaMemsetAsync(SPH_DS_FIELD(v.ds, n_bin_leaves), 0, sizeof(int), st);
+  cudaError_t e = cudaMemsetAsync(SPH_DS_FIELD(v.ds, n_bin_groups), 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   k_mark_bin<<<v.grid_util, UT, 0, st>>>(v, bin);
   return cudaGetLastError();

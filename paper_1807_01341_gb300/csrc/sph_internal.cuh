@@ -20,6 +20,7 @@ constexpr int MAX_BINS = 64;
 constexpr int WARPS_PER_BLOCK = 8;
 constexpr int LEAF_MAX_LIMIT = 64;
 constexpr int CHUNK = 32;          // leaves per chunk (one warp ballot)
+constexpr int WG_MAX = 32;         // particles per work group of the pair loops (one per lane)
 
 // Device-resident state of the context: the integer timeline, the sizes of
 // the cell structure, work queues, error flags and counters.  Everything a
@@ -35,12 +36,14 @@ struct DevState {
   int n_cells;           // nc^3
   int n_leaves;
   int n_chunks;          // groups of up to CHUNK consecutive leaves of one cell
+  int n_groups;          // work groups: runs of consecutive leaves of one cell, <= WG_MAX particles
+  int n_active_groups;   // work groups holding active particles
   double w;              // cell width
   // queues (written by mark)
   int n_active_leaves;   // leaves holding active particles
   int n_active_cells;    // cells holding active particles
   int n_drift_chunks;    // leaf chunks of the cells within one cell of an active cell
-  int n_bin_leaves;      // plain form: active leaves holding particles of one bin
+  int n_bin_groups;      // plain form: active work groups holding particles of one bin
   // persistent-kernel work heads
   int head_density, head_force, head_drift, head_kick;
   int head_open, head_bins, head_misc, pad2;
@@ -94,6 +97,9 @@ struct View {
   uint8_t *leaf_min_bin;     // smallest bin in the leaf
   unsigned long long *leaf_bin_mask;  // bins present in the leaf
   int32_t *pcell;            // [n] cell of each particle
+  int32_t *pleaf;            // [n] leaf of each particle
+  int32_t *group_leaf0;      // [n_groups + 1] first leaf of each work group
+  int32_t *group_cell;       // [n_groups] cell of each work group
   // FP32 records read by the pair loops (cell-relative positions)
   float4 *rec_xm;  // x, y, z, m
   float4 *rec_xH;  // x, y, z, H
@@ -103,7 +109,8 @@ struct View {
   int32_t *q_active;         // leaves holding active particles
   int32_t *q_act_cells;      // cells holding active particles
   int32_t *q_drift;          // chunks to drift (cells next to an active cell)
-  int32_t *q_bin;            // plain form: active leaves holding particles of one bin
+  int32_t *q_group;          // work groups holding active particles
+  int32_t *q_bin;            // plain form: active work groups holding particles of one bin
   DevState *ds;
   // parameters
   double box, eta, gamma, alpha, cfl, h_tol, dt_min;
@@ -183,6 +190,10 @@ cudaError_t launch_leaf_write(const unsigned long long *sorted_keys, const int32
                               int32_t *leaf_start, int32_t *leaf_cell, uint32_t *leaf_k,
                               int32_t *cell_leaf_start, long long n, cudaStream_t st);
 cudaError_t launch_bin_histogram(const View &v, cudaStream_t st);
+cudaError_t launch_groups(const int32_t *cell_leaf_start, const int32_t *leaf_start, int n_cells,
+                          int n_leaves_max, unsigned int *counts, unsigned int *offsets,
+                          unsigned int *scan_tmp, int32_t *group_leaf0, int32_t *group_cell,
+                          int32_t *pleaf, int n_leaves_host, cudaStream_t st);
 cudaError_t launch_chunks(const int32_t *cell_leaf_start, int n_cells, unsigned int *counts,
                           unsigned int *offsets, unsigned int *scan_tmp, int32_t *cell_chunk_start,
                           int32_t *chunk_cell, cudaStream_t st);

@@ -2,8 +2,9 @@
 // arXiv 1807.01341): the density loop with the smoothing-length iteration
 // (the "ghost" task) and the hydro force loop, for the active particles only.
 //
-// Work item: one leaf (octree sub-cell of <= 64 particles) that holds active
-// particles, processed by one warp.  The warp splits into groups of G lanes;
+// Work item: one work group -- a run of consecutive leaves (octree sub-cells)
+// of one cell holding at most 32 particles, some of them active -- processed
+// by one warp.  The warp splits into groups of G lanes;
 // each group owns one active particle i, and its lanes stride over the
 // candidate particles j.  Candidates come from the 27 top-level cells around
 // the leaf's cell: cells holding more than 32 leaves are first pruned by
@@ -211,10 +212,10 @@ struct CellFrame {
   int kx, ky, kz;  // the work leaf's corner on its cell's Morton grid
 };
 
-__device__ __forceinline__ CellFrame frame_of(const View &v, const DevState *ds, int leaf) {
+__device__ __forceinline__ CellFrame frame_of(const View &v, const DevState *ds, int grp) {
   CellFrame F;
-  const int cell = v.leaf_cell[leaf];
-  const uint32_t k = v.leaf_k[leaf];
+  const int cell = v.group_cell[grp];
+  const uint32_t k = v.leaf_k[v.group_leaf0[grp]];
   F.nc = ds->nc;
   F.cx = cell / (F.nc * F.nc);
   F.cy = (cell / F.nc) % F.nc;
@@ -231,155 +232,237 @@ struct WarpCounters {
   unsigned long long pairs, cand, iters, noconv, overflow, timeout;
 };
 
+// A work group: particles [a, b) in leaves [L0, L1) of one cell, and the
+// group's bounding box in the frame of its first leaf's corner (all lanes).
+struct Group {
+  int a, b, L0, L1;
+  float lx, ly, lz, hx, hy, hz;
+};
+
+__device__ __forceinline__ Group group_of(const View &v, int g, const CellFrame &F) {
+  Group G;
+  G.L0 = v.group_leaf0[g];
+  G.L1 = v.group_leaf0[g + 1];
+  G.a = v.leaf_start[G.L0];
+  G.b = v.leaf_start[G.L1];
+  const int lane = lane_id();
+  float lx = INFINITY, ly = INFINITY, lz = INFINITY, hx = -INFINITY, hy = -INFINITY, hz = -INFINITY;
+  if (G.L0 + lane < G.L1) {
+    const int l = G.L0 + lane;
+    const uint32_t k = v.leaf_k[l];
+    const float ox = (float)(leaf_kx(k) - F.kx) * F.wq;
+    const float oy = (float)(leaf_ky(k) - F.ky) * F.wq;
+    const float oz = (float)(leaf_kz(k) - F.kz) * F.wq;
+    const float4 lo = v.leaf_lo[l], hi = v.leaf_hi[l];
+    lx = lo.x + ox; ly = lo.y + oy; lz = lo.z + oz;
+    hx = hi.x + ox; hy = hi.y + oy; hz = hi.z + oz;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lx = fminf(lx, __shfl_xor_sync(FULL, lx, o));
+    ly = fminf(ly, __shfl_xor_sync(FULL, ly, o));
+    lz = fminf(lz, __shfl_xor_sync(FULL, lz, o));
+    hx = fmaxf(hx, __shfl_xor_sync(FULL, hx, o));
+    hy = fmaxf(hy, __shfl_xor_sync(FULL, hy, o));
+    hz = fmaxf(hz, __shfl_xor_sync(FULL, hz, o));
+  }
+  G.lx = lx; G.ly = ly; G.lz = lz; G.hx = hx; G.hy = hy; G.hz = hz;
+  return G;
+}
+
+// offset of particle i's leaf corner from the group frame's corner
+__device__ __forceinline__ float3 leaf_offset(const View &v, int i, const CellFrame &F) {
+  const uint32_t k = v.leaf_k[v.pleaf[i]];
+  return make_float3((float)(leaf_kx(k) - F.kx) * F.wq, (float)(leaf_ky(k) - F.ky) * F.wq,
+                     (float)(leaf_kz(k) - F.kz) * F.wq);
+}
+
 // ---------------------------------------------------------------------------
 // per-warp staging area in dynamic shared memory
 // ---------------------------------------------------------------------------
-template <int S, int NREC>
+template <int S, int NREC, int LC>
 struct Stage {
-  float4 *rec;      // NREC arrays of S records, back to back
-  float4 *shift;    // per staged leaf: offset of its corner (x, y, z), first particle (w bits)
-  int *pack;        // per staged leaf: slot | count << 10 | cell index << 20
-  int *act;         // active particles of the work leaf
+  static constexpr int LCAP = LC;  // accepted neighbour leaves listed per search pass
+  float4 *rec;     // NREC arrays of S staged records, back to back (first: positions)
+  float4 *lshift;  // per listed leaf: offset of its corner (x, y, z), first particle (w bits)
+  int *lpack;      // per listed leaf: count | cell index << 16
+  int *act;        // active particles of the work group
+  int *recj;       // per staged record: particle index
+  uint8_t *recc;   // per staged record: neighbour-cell index (0..26)
   uint64_t *bar;
   uint32_t phase;
-  int fill, nmeta;
   bool failed;
   static constexpr size_t bytes() {
-    return sizeof(float4) * (size_t)S * (NREC + 1) + sizeof(int) * S + sizeof(int) * LEAF_MAX_LIMIT + 16;
+    return sizeof(float4) * ((size_t)S * NREC + LC) + sizeof(int) * (LC + LEAF_MAX_LIMIT + S) +
+           (size_t)S + 16;
   }
   __device__ void carve(char *base) {
     rec = reinterpret_cast<float4 *>(base);
-    shift = rec + (size_t)S * NREC;
-    pack = reinterpret_cast<int *>(shift + S);
-    act = pack + S;
-    bar = reinterpret_cast<uint64_t *>(act + LEAF_MAX_LIMIT);
+    lshift = rec + (size_t)S * NREC;
+    lpack = reinterpret_cast<int *>(lshift + LC);
+    act = lpack + LC;
+    recj = act + LEAF_MAX_LIMIT;
+    recc = reinterpret_cast<uint8_t *>(recj + S);
+    bar = reinterpret_cast<uint64_t *>(recc + S);
   }
 };
 
-// The 27 neighbour cells, their chunks and leaves around the work leaf:
-// every leaf whose box passes `leaf_ok` (and whose chunk passes `chunk_ok`
-// in cells of more than CHUNK leaves) is staged, in cell-then-leaf order, and
-// `consume` is called on each full batch and once at the end.
-template <int S, int NREC, class LeafOk, class ChunkOk, class Consume>
-__device__ __forceinline__ void gather(const View &v, const CellFrame &F, const float4 *const *srcs,
-                                       Stage<S, NREC> &st, LeafOk leaf_ok, ChunkOk chunk_ok,
-                                       Consume consume, WarpCounters &wc) {
+// Lists, in cell-then-leaf order, the leaves of the 27 cells around the work
+// group that pass `leaf_ok` (in cells of more than CHUNK leaves, only those of
+// chunks passing `chunk_ok`): accepted leaves skip, skip + 1, ... up to LCAP
+// of them.  Returns how many were listed; `more` tells whether the list
+// stopped because it was full.
+template <class St, class LeafOk, class ChunkOk>
+__device__ __forceinline__ int search(const View &v, const CellFrame &F, St &st, LeafOk leaf_ok,
+                                      ChunkOk chunk_ok, int skip, bool &more) {
+  constexpr int LCAP = St::LCAP;
   const int lane = lane_id();
-  auto flush = [&]() {
-    if (st.nmeta == 0) return;
+  int seen = 0;
+  more = false;
+  const int limit = skip + LCAP;
+  for (int ci = 0; ci < 27; ci++) {
+    const int dxc = ci / 9 - 1, dyc = (ci / 3) % 3 - 1, dzc = ci % 3 - 1;
+    const int cj = (wrap_cell(F.cx + dxc, F.nc) * F.nc + wrap_cell(F.cy + dyc, F.nc)) * F.nc +
+                   wrap_cell(F.cz + dzc, F.nc);
+    // grid-step offset of the neighbour cell's corner from the work group's corner
+    const int bx = dxc * (1 << MORTON_BITS) - F.kx;
+    const int by = dyc * (1 << MORTON_BITS) - F.ky;
+    const int bz = dzc * (1 << MORTON_BITS) - F.kz;
+    const int l0 = v.cell_leaf_start[cj], l1 = v.cell_leaf_start[cj + 1];
+    const int g0 = v.cell_chunk_start[cj], g1 = v.cell_chunk_start[cj + 1];
+    const bool chunked = l1 - l0 > CHUNK;
+    const float csx = dxc * F.wf, csy = dyc * F.wf, csz = dzc * F.wf;
+    // chunks of this cell, 32 at a time (a cell of <= CHUNK leaves is one chunk)
+    for (int gb = g0; gb < g1; gb += 32) {
+      const int g = gb + lane;
+      bool okc = g < g1;
+      if (chunked && okc) okc = chunk_ok(g, csx, csy, csz);
+      unsigned mc = __ballot_sync(FULL, okc);
+      while (mc) {
+        const int src = __ffs(mc) - 1;
+        mc &= mc - 1;
+        const int la = l0 + CHUNK * (gb + src - g0);
+        const int lb = min(la + CHUNK, l1);
+        const int l = la + lane;
+        bool ok = false;
+        int ja = 0, cnt = 0;
+        float sx = 0.f, sy = 0.f, sz = 0.f;
+        if (l < lb) {
+          const uint32_t kl = v.leaf_k[l];
+          sx = (float)(bx + leaf_kx(kl)) * F.wq;
+          sy = (float)(by + leaf_ky(kl)) * F.wq;
+          sz = (float)(bz + leaf_kz(kl)) * F.wq;
+          ok = leaf_ok(l, sx, sy, sz);
+          if (ok) {
+            ja = v.leaf_start[l];
+            cnt = v.leaf_start[l + 1] - ja;
+          }
+        }
+        const unsigned mk = __ballot_sync(FULL, ok);
+        const int idx = seen + __popc(mk & ((1u << lane) - 1u));
+        if (ok && idx >= skip && idx < limit) {
+          st.lshift[idx - skip] = make_float4(sx, sy, sz, __int_as_float(ja));
+          st.lpack[idx - skip] = cnt | (ci << 16);
+        }
+        seen += __popc(mk);
+        if (seen > limit) {
+          more = true;
+          __syncwarp();
+          return LCAP;
+        }
+      }
+    }
+  }
+  __syncwarp();
+  return max(0, min(seen - skip, LCAP));
+}
+
+// Stages the records of listed leaves [0, nlist) into shared memory by bulk
+// copies, as many leaves per batch as fit S records.  When a batch has
+// landed, each position record is moved into the work group's frame (its
+// leaf's corner offset added) and tagged with its particle index and
+// neighbour-cell index; then consume(total) sees records 0 .. total-1.
+template <int S, int NREC, int LC, class Consume>
+__device__ __forceinline__ void stage_list(const float4 *const *srcs, Stage<S, NREC, LC> &st,
+                                           int nlist, Consume consume, WarpCounters &wc) {
+  const int lane = lane_id();
+  for (int e = 0; e < nlist && !st.failed;) {
+    const bool in = e + lane < nlist;
+    const int c = in ? (st.lpack[e + lane] & 0xffff) : 0;
+    const int incl = warp_incl_scan(c);
+    const unsigned take = __ballot_sync(FULL, in && incl <= S);  // a prefix; never empty
+    const int k = __popc(take);
+    const int total = __shfl_sync(FULL, incl, k - 1);
+    if (lane == 0) mbar_expect_tx(st.bar, (uint32_t)(total * NREC * (int)sizeof(float4)));
+    __syncwarp();
+    if ((take >> lane) & 1u) {
+      const int ja = __float_as_int(st.lshift[e + lane].w);
+      const int slot = incl - c;
+      for (int r = 0; r < NREC; r++)
+        bulk_g2s(st.rec + (size_t)r * S + slot, srcs[r] + ja, (uint32_t)(c * sizeof(float4)), st.bar);
+    }
+    __syncwarp();
     if (lane == 0) mbar_arrive(st.bar);
     if (!mbar_wait(st.bar, st.phase)) {
       st.failed = true;
       wc.timeout++;
     }
     st.phase ^= 1u;
-    if (!st.failed) consume();
+    if (!st.failed) {
+      int base = 0;
+      for (int q = 0; q < k; q++) {
+        const float4 sh = st.lshift[e + q];
+        const int pk = st.lpack[e + q];
+        const int cq = pk & 0xffff;
+        const int ja = __float_as_int(sh.w);
+        for (int t = lane; t < cq; t += 32) {
+          float4 rr = st.rec[base + t];
+          rr.x += sh.x;
+          rr.y += sh.y;
+          rr.z += sh.z;
+          st.rec[base + t] = rr;
+          st.recj[base + t] = ja + t;
+          st.recc[base + t] = (uint8_t)(pk >> 16);
+        }
+        base += cq;
+      }
+      __syncwarp();
+      consume(total);
+    }
+    wc.cand += (unsigned long long)total;
     __syncwarp();
     fence_proxy_async();
-    st.fill = 0;
-    st.nmeta = 0;
-  };
-  auto stage_leaves = [&](int la, int lb, int ci, int bx, int by, int bz) {
-    const int l = la + lane;
-    bool ok = false;
-    int ja = 0, cnt = 0;
-    float sx = 0.f, sy = 0.f, sz = 0.f;
-    if (l < lb) {
-      const uint32_t kl = v.leaf_k[l];
-      sx = (float)(bx + leaf_kx(kl)) * F.wq;
-      sy = (float)(by + leaf_ky(kl)) * F.wq;
-      sz = (float)(bz + leaf_kz(kl)) * F.wq;
-      ok = leaf_ok(l, sx, sy, sz);
-      if (ok) {
-        ja = v.leaf_start[l];
-        cnt = v.leaf_start[l + 1] - ja;
-      }
-    }
-    unsigned mk = __ballot_sync(FULL, ok);
-    while (mk && !st.failed) {
-      const bool mine = (mk >> lane) & 1u;
-      const int c = mine ? cnt : 0;
-      const int incl = warp_incl_scan(c);
-      const int total = __shfl_sync(FULL, incl, 31);
-      unsigned take = mk;
-      if (st.fill + total > S) {
-        take = __ballot_sync(FULL, mine && st.fill + incl <= S);
-        if (take == 0u) {
-          flush();
-          continue;
-        }
-      }
-      const int last = 31 - __clz(take);
-      const int taken = __shfl_sync(FULL, incl, last);
-      if (lane == 0) mbar_expect_tx(st.bar, (uint32_t)(taken * NREC * (int)sizeof(float4)));
-      __syncwarp();
-      if ((take >> lane) & 1u) {
-        const int slot = st.fill + incl - c;
-        const int m = st.nmeta + __popc(take & ((1u << lane) - 1u));
-        st.shift[m] = make_float4(sx, sy, sz, __int_as_float(ja));
-        st.pack[m] = slot | (c << 10) | (ci << 20);
-        for (int r = 0; r < NREC; r++)
-          bulk_g2s(st.rec + (size_t)r * S + slot, srcs[r] + ja, (uint32_t)(c * sizeof(float4)), st.bar);
-      }
-      wc.cand += (unsigned long long)taken;
-      st.fill += taken;
-      st.nmeta += __popc(take);
-      mk &= ~take;
-      __syncwarp();
-      if (mk) flush();
-    }
-  };
-
-  for (int ci = 0; ci < 27 && !st.failed; ci++) {
-    const int dxc = ci / 9 - 1, dyc = (ci / 3) % 3 - 1, dzc = ci % 3 - 1;
-    const int cj = (wrap_cell(F.cx + dxc, F.nc) * F.nc + wrap_cell(F.cy + dyc, F.nc)) * F.nc +
-                   wrap_cell(F.cz + dzc, F.nc);
-    // grid-step offset of the neighbour cell's corner from the work leaf's corner
-    const int bx = dxc * (1 << MORTON_BITS) - F.kx;
-    const int by = dyc * (1 << MORTON_BITS) - F.ky;
-    const int bz = dzc * (1 << MORTON_BITS) - F.kz;
-    const int l0 = v.cell_leaf_start[cj], l1 = v.cell_leaf_start[cj + 1];
-    if (l1 - l0 <= CHUNK) {
-      if (l1 > l0) stage_leaves(l0, l1, ci, bx, by, bz);
-      continue;
-    }
-    const int g0 = v.cell_chunk_start[cj], g1 = v.cell_chunk_start[cj + 1];
-    const float csx = dxc * F.wf, csy = dyc * F.wf, csz = dzc * F.wf;
-    for (int gb = g0; gb < g1 && !st.failed; gb += 32) {
-      const int g = gb + lane;
-      const bool okc = g < g1 && chunk_ok(g, csx, csy, csz);
-      unsigned mc = __ballot_sync(FULL, okc);
-      while (mc && !st.failed) {
-        const int src = __ffs(mc) - 1;
-        mc &= mc - 1;
-        const int la = l0 + CHUNK * (gb + src - g0);
-        stage_leaves(la, min(la + CHUNK, l1), ci, bx, by, bz);
-      }
-    }
+    e += k;
   }
-  if (!st.failed) flush();
 }
 
+using StageD = Stage<S_DENS, 1, 384>;
+using StageF = Stage<S_FORCE, 3, 256>;
+
 // ---------------------------------------------------------------------------
-// density loop + smoothing-length iteration for the active particles of a leaf
+// density loop + smoothing-length iteration for the active particles of a group
 // ---------------------------------------------------------------------------
+// Newton step on F(h) = h^3 n(h) - eta^3 in dimensionless form: with H = GAMMA_K h,
+// h^3 n = (8/pi) S_w / GAMMA_K^3 and h dF/dh = 3 h^3 n + h^4 dn/dh, so
+// dh / h = -(S_w - C) / (3 S_w - S_t), C = eta^3 GAMMA_K^3 / (8/pi),
+// S_w = sum w(q), S_t = sum (3 w + q w').
 template <int G>
-__device__ void density_leaf(const View &v, int leaf, int flags, int bin_filter, int m_act,
-                             const CellFrame &F, float hcap, long long ti,
-                             Stage<S_DENS, 1> &st, WarpCounters &wc) {
+__device__ void density_group(const View &v, int wg, int flags, int bin_filter, int m_act,
+                              const CellFrame &F, float hcap, long long ti,
+                              StageD &st, WarpCounters &wc) {
   const int lane = lane_id();
-  const int a = v.leaf_start[leaf], b = v.leaf_start[leaf + 1];
+  const Group W = group_of(v, wg, F);
+  const int a = W.a, b = W.b;
   const int nact = leaf_actives(v, a, b, m_act, bin_filter, st.act);
   if (nact == 0) return;
   constexpr int P = 32 / G;
   const int grp = lane / G, sub = lane % G;
-  const float4 blo = v.leaf_lo[leaf], bhi = v.leaf_hi[leaf];
-  // the leaf's box in its cell's frame (for the chunk tests)
+  // the group's box in its cell's frame (for the chunk tests)
   const float qox = F.kx * F.wq, qoy = F.ky * F.wq, qoz = F.kz * F.wq;
-  const float clx = blo.x + qox, cly = blo.y + qoy, clz = blo.z + qoz;
-  const float chx = bhi.x + qox, chy = bhi.y + qoy, chz = bhi.z + qoz;
+  const float clx = W.lx + qox, cly = W.ly + qoy, clz = W.lz + qoz;
+  const float chx = W.hx + qox, chy = W.hy + qoy, chz = W.hz + qoz;
   const float ceps = 1e-5f * F.wf;
-  const double eta3 = v.eta * v.eta * v.eta;
+  const double Cw = v.eta * v.eta * v.eta * GAMMA_K_D * GAMMA_K_D * GAMMA_K_D / (double)KERNEL_NORM;
   const bool init_entropy = (flags & SPH_DENSITY_INIT_ENTROPY) != 0;
   const float4 *srcs[1] = {v.rec_xm};
 
@@ -387,64 +470,88 @@ __device__ void density_leaf(const View &v, int leaf, int flags, int bin_filter,
     const int slot = r + grp;
     const bool valid = slot < nact;
     const int i = valid ? st.act[slot] : a;
-    const float4 xi = v.rec_xm[i];
+    const float4 xl = v.rec_xm[i];  // position in its own leaf's frame
+    const float3 lo3 = leaf_offset(v, i, F);
+    const float4 xi = make_float4(xl.x + lo3.x, xl.y + lo3.y, xl.z + lo3.z, xl.w);
     float h = v.h[i];
     double lo = 0.0, hi = INFINITY;
     bool done = !valid;
+    float Rs = 0.0f;      // radius of the leaf list in shared memory (0: none)
+    int nlist = 0;
     for (int it = 0; it < v.h_max_iter && !st.failed; it++) {
       const float H = GAMMA_K * h;
       const float Hs = warp_max(done ? 0.0f : H);
       if (Hs == 0.0f) break;  // every particle of the round has converged
       const float H2 = H * H, Hinv = 1.0f / H;
-      const float Hs2 = Hs * Hs * 1.0002f;
-      const float Hc = Hs + ceps;
       float n_hi = 0.f, n_lo = 0.f, t_hi = 0.f, t_lo = 0.f;
       float r_hi = 0.f, r_lo = 0.f, rt_hi = 0.f, rt_lo = 0.f;
       float pn = 0.f, pt = 0.f, pr = 0.f, prt = 0.f;
       int cur = -1, cnt = 0;
-      auto leaf_ok = [&](int l, float sx, float sy, float sz) {
-        return box_gap2(blo.x, blo.y, blo.z, bhi.x, bhi.y, bhi.z, v.leaf_lo[l], v.leaf_hi[l], sx, sy,
-                        sz) < Hs2;
-      };
-      auto chunk_ok = [&](int g, float sx, float sy, float sz) {
-        return box_gap2(clx, cly, clz, chx, chy, chz, v.chunk_lo[g], v.chunk_hi[g], sx, sy, sz) <
-               Hc * Hc;
-      };
-      auto consume = [&]() {
-        for (int k = 0; k < st.nmeta; k++) {
-          const float4 sh = st.shift[k];
-          const int pk = st.pack[k];
-          const int ci = pk >> 20, off = pk & 1023, c = (pk >> 10) & 1023;
-          if (ci != cur) {
-            fold(n_hi, n_lo, pn);
-            fold(t_hi, t_lo, pt);
-            fold(r_hi, r_lo, pr);
-            fold(rt_hi, rt_lo, prt);
-            pn = pt = pr = prt = 0.f;
-            cur = ci;
-          }
-          const int ja = __float_as_int(sh.w);
-          const float xx = xi.x - sh.x, xy = xi.y - sh.y, xz = xi.z - sh.z;
-          for (int t = sub; t < c; t += G) {
-            const float4 pj = st.rec[off + t];
-            const float dx = xx - pj.x, dy = xy - pj.y, dz = xz - pj.z;
+      // test 32 staged records per pass without branching, then evaluate the
+      // accepted ones; partial sums are folded at neighbour-cell boundaries
+      auto consume = [&](int total) {
+        for (int k0 = 0; k0 < total; k0 += 32) {
+          unsigned mask = 0u;
+#pragma unroll
+          for (int u = sub; u < 32; u += G) {
+            const float4 pj = st.rec[min(k0 + u, S_DENS - 1)];
+            const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            if (!done && r2 < H2) {
-              const float rr = r2 * rsqrtf(fmaxf(r2, 1e-30f));
-              const float q = rr * Hinv;
-              float wq, dwq;
-              kernel_wd(q, wq, dwq);
-              const float tt = fmaf(q, dwq, 3.0f * wq);
-              pn += wq;
-              pt += tt;
-              pr = fmaf(pj.w, wq, pr);
-              prt = fmaf(pj.w, tt, prt);
-              cnt += (ja + t != i);
+            mask |= (k0 + u < total && r2 < H2) ? (1u << u) : 0u;
+          }
+          if (done) mask = 0u;
+          while (mask) {
+            const int k = k0 + __ffs(mask) - 1;
+            mask &= mask - 1;
+            const int ci = st.recc[k];
+            if (ci != cur) {
+              fold(n_hi, n_lo, pn);
+              fold(t_hi, t_lo, pt);
+              fold(r_hi, r_lo, pr);
+              fold(rt_hi, rt_lo, prt);
+              pn = pt = pr = prt = 0.f;
+              cur = ci;
             }
+            const float4 pj = st.rec[k];
+            const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float rr = r2 * rsqrtf(fmaxf(r2, 1e-30f));
+            const float qq = rr * Hinv;
+            float wq, dwq;
+            kernel_wd(qq, wq, dwq);
+            const float tt = fmaf(qq, dwq, 3.0f * wq);
+            pn += wq;
+            pt += tt;
+            pr = fmaf(pj.w, wq, pr);
+            prt = fmaf(pj.w, tt, prt);
+            cnt += (st.recj[k] != i);
           }
         }
       };
-      gather<S_DENS, 1>(v, F, srcs, st, leaf_ok, chunk_ok, consume, wc);
+      // the leaf list in shared memory is reused while it covers every support
+      // of the round; otherwise search again (in passes of LCAP leaves)
+      const bool reuse = Rs > 0.0f && Hs <= Rs;
+      const float R = reuse ? Rs : Hs * 1.05f;  // room for the next iterations to grow h
+      const float R2 = R * R * 1.0002f, Rc = R + ceps;
+      auto leaf_ok = [&](int l, float sx, float sy, float sz) {
+        return box_gap2(W.lx, W.ly, W.lz, W.hx, W.hy, W.hz, v.leaf_lo[l], v.leaf_hi[l], sx, sy,
+                        sz) < R2;
+      };
+      auto chunk_ok = [&](int g, float sx, float sy, float sz) {
+        return box_gap2(clx, cly, clz, chx, chy, chz, v.chunk_lo[g], v.chunk_hi[g], sx, sy, sz) <
+               Rc * Rc;
+      };
+      int skip = 0;
+      bool more = false, complete = true;
+      do {
+        if (!reuse) {
+          nlist = search(v, F, st, leaf_ok, chunk_ok, skip, more);
+          complete = complete && !more;
+        }
+        stage_list(srcs, st, nlist, consume, wc);
+        skip += nlist;
+      } while (!reuse && more && !st.failed);
+      if (!reuse) Rs = complete ? R : 0.0f;
       if (st.failed) break;
       fold(n_hi, n_lo, pn);
       fold(t_hi, t_lo, pt);
@@ -452,27 +559,23 @@ __device__ void density_leaf(const View &v, int leaf, int flags, int bin_filter,
       fold(rt_hi, rt_lo, prt);
       const double sn = group_sum<G>((double)n_hi + (double)n_lo);
       const double stt = group_sum<G>((double)t_hi + (double)t_lo);
-      const double sr = group_sum<G>((double)r_hi + (double)r_lo);
-      const double srt = group_sum<G>((double)rt_hi + (double)rt_lo);
+      const float sr = (float)group_sum<G>((double)r_hi + (double)r_lo);
+      const float srt = (float)group_sum<G>((double)rt_hi + (double)rt_lo);
       cnt = group_sum_i<G>(cnt);
       if (!done) {
-        // Newton step on F(h) = h^3 n(h) - eta^3, kept inside a bracket
-        const double Hd = (double)H, Hi = 1.0 / Hd;
-        const double Hi3 = Hi * Hi * Hi, Hi4 = Hi3 * Hi;
-        const double nn = (double)KERNEL_NORM * sn * Hi3;
-        const double dndh = -GAMMA_K_D * (double)KERNEL_NORM * stt * Hi4;
+        // Newton step in FP64, kept inside the bracket [lo, hi] (F grows with h)
         const double hd = (double)h;
-        const double F3 = hd * hd * hd * nn - eta3;
-        const double dF = 3.0 * hd * hd * nn + hd * hd * hd * dndh;
-        if (F3 < 0.0) lo = hd;
+        const double Fr = sn - Cw;              // sign of F(h)
+        const double dFr = 3.0 * sn - stt;      // h dF/dh, same scale
+        if (Fr < 0.0) lo = hd;
         else hi = hd;
         double hn;
-        if (F3 == 0.0) hn = hd;
-        else if (dF > 0.0) hn = hd - F3 / dF;
+        if (Fr == 0.0) hn = hd;
+        else if (dFr > 0.0) hn = hd - hd * (Fr / dFr);
         else hn = NAN;
         if (!(hn >= lo && hn <= hi)) hn = isinf(hi) ? 2.0 * hd : 0.5 * (lo + hi);
         hn = fmin(fmax(hn, 0.5 * hd), 2.0 * hd);
-        bool conv = fabs(hn - hd) <= v.h_tol * hd;
+        const bool conv = fabs(hn - hd) <= v.h_tol * hd;
         const bool over = !conv && hn > (double)hcap;
         const bool last = it == v.h_max_iter - 1;
         if (conv || over || last) {
@@ -486,15 +589,14 @@ __device__ void density_leaf(const View &v, int leaf, int flags, int bin_filter,
             } else if (!conv) {
               wc.noconv++;
             }
-            // density, grad-h factor, equation of state at the final h
-            const double rho_d = (double)KERNEL_NORM * sr * Hi3;
-            const double drho = -GAMMA_K_D * (double)KERNEL_NORM * srt * Hi4;
-            const float rho = (float)rho_d;
-            const float f = (float)(1.0 / (1.0 + hd / (3.0 * rho_d) * drho));
-            const int bi = v.bin[i];
+            // density, grad-h factor f = [1 + h/(3 rho) drho/dh]^-1, equation of state
+            const float Hinv3 = Hinv * Hinv * Hinv;
+            const float rho = KERNEL_NORM * sr * Hinv3;
+            const float f = 3.0f * sr / (3.0f * sr - srt);
+            const int bi = v.bin[i] & (MAX_BINS - 1);
             const double dtp =
                 ((double)(ti - v.ti_begin[i]) - 0.5 * (double)(1ll << bi)) * v.dt_min;
-            float Ap = (float)((double)v.A[i] + (double)v.Adot[i] * dtp);
+            float Ap = v.A[i] + v.Adot[i] * (float)dtp;
             const float g = (float)v.gamma;
             if (init_entropy) Ap = (g - 1.0f) * v.A[i] / powf(rho, g - 1.0f);  // A holds u
             const float P = Ap * powf(rho, g);
@@ -504,7 +606,7 @@ __device__ void density_leaf(const View &v, int leaf, int flags, int bin_filter,
             v.f[i] = f;
             v.P[i] = P;
             v.c[i] = c;
-            v.rec_xH[i] = make_float4(xi.x, xi.y, xi.z, H);
+            v.rec_xH[i] = make_float4(xl.x, xl.y, xl.z, H);
             v.rec_h[i] = make_float4(rho, f * P / (rho * rho), c, Hinv);
             if (v.ngb_density) v.ngb_density[i] = cnt;
           }
@@ -514,36 +616,37 @@ __device__ void density_leaf(const View &v, int leaf, int flags, int bin_filter,
       }
     }
   }
-  // largest support in the leaf after the update; the chunk's keeps a bound
+  // largest support of each leaf after the update; the chunk's keeps a bound
   __syncwarp();
-  float Hm = 0.0f;
-  for (int k = a + lane; k < b; k += 32) Hm = fmaxf(Hm, v.rec_xH[k].w);
-  Hm = warp_max(Hm);
-  if (lane == 0) {
+  if (W.L0 + lane < W.L1) {
+    const int leaf = W.L0 + lane;
+    float Hm = 0.0f;
+    for (int k = v.leaf_start[leaf]; k < v.leaf_start[leaf + 1]; k++) Hm = fmaxf(Hm, v.rec_xH[k].w);
     reinterpret_cast<float *>(&v.leaf_lo[leaf])[3] = Hm;
     const int cell = v.leaf_cell[leaf];
     const int g = v.cell_chunk_start[cell] + (leaf - v.cell_leaf_start[cell]) / CHUNK;
     atomic_max_float_pos(reinterpret_cast<unsigned int *>(&v.chunk_lo[g]) + 3, Hm);
     atomic_max_float_pos(&v.ds->Hmax_bits, Hm);
   }
+  __syncwarp();
 }
 
 // ---------------------------------------------------------------------------
-// force loop for the active particles of a leaf
+// force loop for the active particles of a group
 // ---------------------------------------------------------------------------
 template <int G>
-__device__ void force_leaf(const View &v, int leaf, int bin_filter, int m_act, const CellFrame &F,
-                           Stage<S_FORCE, 3> &st, WarpCounters &wc) {
+__device__ void force_group(const View &v, int wg, int bin_filter, int m_act, const CellFrame &F,
+                            StageF &st, WarpCounters &wc) {
   const int lane = lane_id();
-  const int a = v.leaf_start[leaf], b = v.leaf_start[leaf + 1];
+  const Group W = group_of(v, wg, F);
+  const int a = W.a, b = W.b;
   const int nact = leaf_actives(v, a, b, m_act, bin_filter, st.act);
   if (nact == 0) return;
   constexpr int P = 32 / G;
   const int grp = lane / G, sub = lane % G;
-  const float4 blo = v.leaf_lo[leaf], bhi = v.leaf_hi[leaf];
   const float qox = F.kx * F.wq, qoy = F.ky * F.wq, qoz = F.kz * F.wq;
-  const float clx = blo.x + qox, cly = blo.y + qoy, clz = blo.z + qoz;
-  const float chx = bhi.x + qox, chy = bhi.y + qoy, chz = bhi.z + qoz;
+  const float clx = W.lx + qox, cly = W.ly + qoy, clz = W.lz + qoz;
+  const float chx = W.hx + qox, chy = W.hy + qoy, chz = W.hz + qoz;
   const float ceps = 1e-5f * F.wf;
   const float alpha = (float)v.alpha;
   const float g = (float)v.gamma;
@@ -554,7 +657,9 @@ __device__ void force_leaf(const View &v, int leaf, int bin_filter, int m_act, c
     const int slot = r + grp;
     const bool valid = slot < nact;
     const int i = valid ? st.act[slot] : a;
-    const float4 xi = v.rec_xH[i];
+    const float4 xl = v.rec_xH[i];
+    const float3 lo3 = leaf_offset(v, i, F);
+    const float4 xi = make_float4(xl.x + lo3.x, xl.y + lo3.y, xl.z + lo3.z, xl.w);
     const float4 vi = v.rec_v[i];
     const float4 hi4 = v.rec_h[i];
     const float Hi2 = xi.w * xi.w;
@@ -569,7 +674,7 @@ __device__ void force_leaf(const View &v, int leaf, int bin_filter, int m_act, c
     auto leaf_ok = [&](int l, float sx, float sy, float sz) {
       const float4 loj = v.leaf_lo[l];
       const float R = fmaxf(Hs, loj.w);
-      return box_gap2(blo.x, blo.y, blo.z, bhi.x, bhi.y, bhi.z, loj, v.leaf_hi[l], sx, sy, sz) <
+      return box_gap2(W.lx, W.ly, W.lz, W.hx, W.hy, W.hz, loj, v.leaf_hi[l], sx, sy, sz) <
              R * R * 1.0002f;
     };
     auto chunk_ok = [&](int gg, float sx, float sy, float sz) {
@@ -577,56 +682,68 @@ __device__ void force_leaf(const View &v, int leaf, int bin_filter, int m_act, c
       const float R = fmaxf(Hs, loc.w) + ceps;
       return box_gap2(clx, cly, clz, chx, chy, chz, loc, v.chunk_hi[gg], sx, sy, sz) < R * R;
     };
-    auto consume = [&]() {
-      for (int k = 0; k < st.nmeta; k++) {
-        const float4 sh = st.shift[k];
-        const int pk = st.pack[k];
-        const int ci = pk >> 20, off = pk & 1023, c = (pk >> 10) & 1023;
-        if (ci != cur) {
-          fold(ax_hi, ax_lo, pax);
-          fold(ay_hi, ay_lo, pay);
-          fold(az_hi, az_lo, paz);
-          fold(ad_hi, ad_lo, pad);
-          pax = pay = paz = pad = 0.f;
-          cur = ci;
-        }
-        const int ja = __float_as_int(sh.w);
-        const float xx = xi.x - sh.x, xy = xi.y - sh.y, xz = xi.z - sh.z;
-        for (int t = sub; t < c; t += G) {
-          const float4 pj = sx_rec[off + t];
-          const float dx = xx - pj.x, dy = xy - pj.y, dz = xz - pj.z;
+    auto consume = [&](int total) {
+      for (int k0 = 0; k0 < total; k0 += 32) {
+        unsigned mask = 0u;
+#pragma unroll
+        for (int u = sub; u < 32; u += G) {
+          const float4 pj = sx_rec[min(k0 + u, S_FORCE - 1)];
+          const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
           const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          if (valid && ja + t != i && (r2 < Hi2 || r2 < pj.w * pj.w)) {
-            const float4 vj = sv_rec[off + t];
-            const float4 hj = sh_rec[off + t];
-            cnt++;
-            if (r2 > 0.0f) {
-              const float rinv = rsqrtf(r2);
-              const float rr = r2 * rinv;
-              const float qi = rr * hi4.w, qj = rr * hj.w;
-              const float dwi = qi < 1.0f ? kernel_dw(qi) * nHi4 : 0.0f;
-              const float hj2 = hj.w * hj.w;
-              const float dwj = qj < 1.0f ? kernel_dw(qj) * (KERNEL_NORM * hj2 * hj2) : 0.0f;
-              const float dvdr = fmaf(vi.x - vj.x, dx, fmaf(vi.y - vj.y, dy, (vi.z - vj.z) * dz));
-              // Monaghan signal-velocity viscosity, beta = 3 (as in Eq. 1)
-              const float wij = fminf(0.0f, dvdr * rinv);
-              const float vsij = hi4.z + hj.z - 3.0f * wij;
-              const float Pi = -alpha * vsij * wij / (hi4.x + hj.x);
-              const float dWb = 0.5f * (dwi + dwj);
-              const float sc = vj.w * fmaf(hi4.y, dwi, fmaf(hj.y, dwj, Pi * dWb)) * rinv;
-              pax = fmaf(-sc, dx, pax);
-              pay = fmaf(-sc, dy, pay);
-              paz = fmaf(-sc, dz, paz);
-              pad = fmaf(vj.w * Pi * dWb, dvdr * rinv, pad);
-              vs = fmaxf(vs, vsij);
-            } else {
-              vs = fmaxf(vs, hi4.z + hj.z);
-            }
+          mask |= (k0 + u < total && (r2 < Hi2 || r2 < pj.w * pj.w)) ? (1u << u) : 0u;
+        }
+        if (!valid) mask = 0u;
+        while (mask) {
+          const int k = k0 + __ffs(mask) - 1;
+          mask &= mask - 1;
+          if (st.recj[k] == i) continue;
+          const int ci = st.recc[k];
+          if (ci != cur) {
+            fold(ax_hi, ax_lo, pax);
+            fold(ay_hi, ay_lo, pay);
+            fold(az_hi, az_lo, paz);
+            fold(ad_hi, ad_lo, pad);
+            pax = pay = paz = pad = 0.f;
+            cur = ci;
+          }
+          const float4 pj = sx_rec[k];
+          const float4 vj = sv_rec[k];
+          const float4 hj = sh_rec[k];
+          const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
+          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          cnt++;
+          if (r2 > 0.0f) {
+            const float rinv = rsqrtf(r2);
+            const float rr = r2 * rinv;
+            const float qi = rr * hi4.w, qj = rr * hj.w;
+            const float dwi = qi < 1.0f ? kernel_dw(qi) * nHi4 : 0.0f;
+            const float hj2 = hj.w * hj.w;
+            const float dwj = qj < 1.0f ? kernel_dw(qj) * (KERNEL_NORM * hj2 * hj2) : 0.0f;
+            const float dvdr = fmaf(vi.x - vj.x, dx, fmaf(vi.y - vj.y, dy, (vi.z - vj.z) * dz));
+            // Monaghan signal-velocity viscosity, beta = 3 (as in Eq. 1)
+            const float wij = fminf(0.0f, dvdr * rinv);
+            const float vsij = hi4.z + hj.z - 3.0f * wij;
+            const float Pi = -alpha * vsij * wij / (hi4.x + hj.x);
+            const float dWb = 0.5f * (dwi + dwj);
+            const float sc = vj.w * fmaf(hi4.y, dwi, fmaf(hj.y, dwj, Pi * dWb)) * rinv;
+            pax = fmaf(-sc, dx, pax);
+            pay = fmaf(-sc, dy, pay);
+            paz = fmaf(-sc, dz, paz);
+            pad = fmaf(vj.w * Pi * dWb, dvdr * rinv, pad);
+            vs = fmaxf(vs, vsij);
+          } else {
+            vs = fmaxf(vs, hi4.z + hj.z);
           }
         }
       }
     };
-    gather<S_FORCE, 3>(v, F, srcs, st, leaf_ok, chunk_ok, consume, wc);
+    int skip = 0, nlist = 0;
+    bool more = false;
+    do {
+      nlist = search(v, F, st, leaf_ok, chunk_ok, skip, more);
+      stage_list(srcs, st, nlist, consume, wc);
+      skip += nlist;
+    } while (more && !st.failed);
     if (st.failed) break;
     fold(ax_hi, ax_lo, pax);
     fold(ay_hi, ay_lo, pay);
@@ -643,7 +760,7 @@ __device__ void force_leaf(const View &v, int leaf, int bin_filter, int m_act, c
       v.ax[i] = (float)sax;
       v.ay[i] = (float)say;
       v.az[i] = (float)saz;
-      v.Adot[i] = (float)(0.5 * ((double)g - 1.0) * (double)powf(hi4.x, 1.0f - g) * sad);
+      v.Adot[i] = 0.5f * (g - 1.0f) * powf(hi4.x, 1.0f - g) * (float)sad;
       v.vsig[i] = vs;
       if (v.ngb_force) v.ngb_force[i] = cnt;
     }
@@ -684,8 +801,6 @@ __device__ __forceinline__ void stage_init(St &st) {
   const int warp = threadIdx.x >> 5;
   st.carve(smem_dyn + (size_t)warp * St::bytes());
   st.phase = 0u;
-  st.fill = 0;
-  st.nmeta = 0;
   st.failed = false;
   if (lane_id() == 0) {
     mbar_init(st.bar, 1);
@@ -708,13 +823,13 @@ __global__ void __launch_bounds__(PT, 2) k_density(View v, int flags, int bin_fi
     if (blockIdx.x == 0 && threadIdx.x == 0) record_error(ds, SPH_ERR_CELL_OVERFLOW, 1, true);
     return;
   }
-  Stage<S_DENS, 1> st;
+  StageD st;
   stage_init(st);
   const float hcap = (float)((w - 2.0 * (double)exc) / GAMMA_K_D * (1.0 - 1e-6));
   const int m_act = ds->m_act;
   const long long ti = ds->ti;
-  const int *q = bin_filter >= 0 ? v.q_bin : v.q_active;
-  const int nq = bin_filter >= 0 ? ds->n_bin_leaves : ds->n_active_leaves;
+  const int *q = bin_filter >= 0 ? v.q_bin : v.q_group;
+  const int nq = bin_filter >= 0 ? ds->n_bin_groups : ds->n_active_groups;
   WarpCounters wc = {0, 0, 0, 0, 0, 0};
   if (persistent) {
     for (;;) {
@@ -722,14 +837,14 @@ __global__ void __launch_bounds__(PT, 2) k_density(View v, int flags, int bin_fi
       if (lane == 0) item = atomicAdd(&ds->head_density, 1);
       item = __shfl_sync(FULL, item, 0);
       if (item >= nq || st.failed) break;
-      const int leaf = q[item];
-      density_leaf<G>(v, leaf, flags, bin_filter, m_act, frame_of(v, ds, leaf), hcap, ti, st, wc);
+      const int wg = q[item];
+      density_group<G>(v, wg, flags, bin_filter, m_act, frame_of(v, ds, wg), hcap, ti, st, wc);
     }
   } else {
     const int item = blockIdx.x * WARPS_PER_BLOCK + warp;
     if (item < nq) {
-      const int leaf = q[item];
-      density_leaf<G>(v, leaf, flags, bin_filter, m_act, frame_of(v, ds, leaf), hcap, ti, st, wc);
+      const int wg = q[item];
+      density_group<G>(v, wg, flags, bin_filter, m_act, frame_of(v, ds, wg), hcap, ti, st, wc);
     }
   }
   flush_counters(ds, wc, true);
@@ -740,11 +855,11 @@ __global__ void __launch_bounds__(PT, 2) k_force(View v, int bin_filter, int per
   DevState *ds = v.ds;
   if (ds->halt) return;
   const int warp = threadIdx.x >> 5, lane = lane_id();
-  Stage<S_FORCE, 3> st;
+  StageF st;
   stage_init(st);
   const int m_act = ds->m_act;
-  const int *q = bin_filter >= 0 ? v.q_bin : v.q_active;
-  const int nq = bin_filter >= 0 ? ds->n_bin_leaves : ds->n_active_leaves;
+  const int *q = bin_filter >= 0 ? v.q_bin : v.q_group;
+  const int nq = bin_filter >= 0 ? ds->n_bin_groups : ds->n_active_groups;
   WarpCounters wc = {0, 0, 0, 0, 0, 0};
   if (persistent) {
     for (;;) {
@@ -752,14 +867,14 @@ __global__ void __launch_bounds__(PT, 2) k_force(View v, int bin_filter, int per
       if (lane == 0) item = atomicAdd(&ds->head_force, 1);
       item = __shfl_sync(FULL, item, 0);
       if (item >= nq || st.failed) break;
-      const int leaf = q[item];
-      force_leaf<G>(v, leaf, bin_filter, m_act, frame_of(v, ds, leaf), st, wc);
+      const int wg = q[item];
+      force_group<G>(v, wg, bin_filter, m_act, frame_of(v, ds, wg), st, wc);
     }
   } else {
     const int item = blockIdx.x * WARPS_PER_BLOCK + warp;
     if (item < nq) {
-      const int leaf = q[item];
-      force_leaf<G>(v, leaf, bin_filter, m_act, frame_of(v, ds, leaf), st, wc);
+      const int wg = q[item];
+      force_group<G>(v, wg, bin_filter, m_act, frame_of(v, ds, wg), st, wc);
     }
   }
   flush_counters(ds, wc, false);
@@ -781,8 +896,8 @@ __global__ void k_entropy_from_u(View v) {
   }
 }
 
-constexpr size_t DENS_SMEM = Stage<S_DENS, 1>::bytes() * WARPS_PER_BLOCK;
-constexpr size_t FORCE_SMEM = Stage<S_FORCE, 3>::bytes() * WARPS_PER_BLOCK;
+constexpr size_t DENS_SMEM = StageD::bytes() * WARPS_PER_BLOCK;
+constexpr size_t FORCE_SMEM = StageF::bytes() * WARPS_PER_BLOCK;
 
 template <int G>
 cudaError_t density_g(const View &v, int flags, int bin_filter, bool persistent, int grid,

@@ -34,9 +34,9 @@ class Params:
     bin_cap: int = 20
     dt_min: float = 1e-6
     t_begin: float = 0.0
-    cell_margin: float = 1.1
-    leaf_max: int = 16
-    threads_per_particle: int = 4
+    cell_margin: float = 2.0
+    leaf_max: int = 8
+    threads_per_particle: int = 1
     drift_all: int = 0
     n_cells_override: int = 0
 

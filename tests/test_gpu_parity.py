@@ -102,7 +102,7 @@ def test_build_cells_explicit_grid_and_rebuild(sim, orc):
 # ---------------------------------------------------------------------------
 # density loop + smoothing length
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("G,leaf_max", [(4, 16), (1, 64), (32, 8), (8, 32)])
+@pytest.mark.parametrize("G,leaf_max", [(4, 16), (1, 32), (32, 8), (8, 32), (1, 8)])
 def test_density_parity_all_active(sim, orc, G, leaf_max):
     """4,096 jittered lattice particles, all active, one density pass."""
     ic = sph_ics.lattice(16, 0.1, seed=1)

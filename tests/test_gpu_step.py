@@ -101,6 +101,7 @@ def _run_form(sim, ic, form, steps, params):
 
 
 def test_plain_batched_graph_bitwise_identical(sim):
+    """One lane per particle: every sum's order depends on the particle only."""
     ic = _ic_step(seed=17)
     res = {f: _run_form(sim, ic, f, 12, STEP_PARAMS) for f in ("plain", "batched", "graph")}
     ref, cref, tref = res["batched"]
@@ -111,6 +112,20 @@ def test_plain_batched_graph_bitwise_identical(sim):
             assert np.array_equal(st[k], ref[k]), (f, k)
         for k in ("pairs_density", "pairs_force", "steps", "active_particles"):
             assert c[k] == cref[k], (f, k)
+
+
+def test_forms_agree_with_several_lanes_per_particle(sim):
+    """Four lanes per particle: the forms agree to rounding, and exactly on
+    every integer result."""
+    ic = _ic_step(seed=18)
+    params = dict(STEP_PARAMS, threads_per_particle=4)
+    a, ca, ta = _run_form(sim, ic, "plain", 6, params)
+    b, cb, tb = _run_form(sim, ic, "graph", 6, params)
+    assert ta == tb
+    for k in ("bin", "ti_end", "active"):
+        assert np.array_equal(a[k], b[k]), k
+    for k in ("h", "rho", "ax", "vx"):
+        assert np.allclose(a[k], b[k], rtol=1e-5, atol=1e-5 * np.abs(b[k]).max()), k
 
 
 def test_drift_all_same_result_as_relevant_drift(sim):
