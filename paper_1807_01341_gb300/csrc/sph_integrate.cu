@@ -135,42 +135,35 @@ __device__ __forceinline__ double wrap_pos(double x, double box) {
   return x;
 }
 
-// Drifts (when do_drift) the particles of one leaf to the current tick,
-// predicts v and A at that tick, refreshes the FP32 records the pair loops
-// read, and recomputes the leaf's bounding box and largest support.  Inactive
-// particles get P and c from their frozen density and predicted entropy.
-struct LeafBox {
-  float lx, ly, lz, hx, hy, hz, H;
-};
-
-__device__ LeafBox leaf_update(const View &v, int leaf, bool do_drift, bool do_bins) {
+// One warp per chunk (up to CHUNK leaves of one cell, contiguous particles):
+// drifts (when do_drift) its particles to the current tick, predicts v and A
+// at that tick, refreshes the FP32 records the pair loops read (positions
+// relative to each particle's leaf corner), gives inactive particles P and c
+// from their frozen density and predicted entropy; then recomputes, one leaf
+// per lane, each leaf's bounding box and largest support (and, when do_bins,
+// its smallest bin and bin mask), and the chunk's box in the cell frame.
+__device__ void chunk_update(const View &v, int g, bool do_drift, bool do_bins) {
   const DevState *ds = v.ds;
   const int lane = lane_id();
-  const int a = v.leaf_start[leaf], b = v.leaf_start[leaf + 1];
-  const int cell = v.leaf_cell[leaf];
+  const int cell = v.chunk_cell[g];
+  const int l0 = v.cell_leaf_start[cell] + CHUNK * (g - v.cell_chunk_start[cell]);
+  const int l1 = min(l0 + CHUNK, v.cell_leaf_start[cell + 1]);
+  const int pa = v.leaf_start[l0], pb = v.leaf_start[l1];
   const int nc = ds->nc;
   const double w = ds->w;
   const long long ti = ds->ti;
   const int cx = cell / (nc * nc), cy = (cell / nc) % nc, cz = cell % nc;
   const double ox = cx * w, oy = cy * w, oz = cz * w;
-  // leaf corner on the cell's Morton grid (the origin of the FP32 records)
-  const uint32_t lk = v.leaf_k[leaf];
   const double wq = w / (double)(1 << MORTON_BITS);
-  const double lx = (double)(cx * (1 << MORTON_BITS) + leaf_kx(lk)) * wq;
-  const double ly = (double)(cy * (1 << MORTON_BITS) + leaf_ky(lk)) * wq;
-  const double lz = (double)(cz * (1 << MORTON_BITS) + leaf_kz(lk)) * wq;
-  const float g = (float)v.gamma;
-  float lox = INFINITY, loy = INFINITY, loz = INFINITY;
-  float hix = -INFINITY, hiy = -INFINITY, hiz = -INFINITY;
-  float Hm = 0.0f, exc = 0.0f;
-  int minb = 127;
-  unsigned long long mask = 0ull;
-  for (int i = a + lane; i < b; i += 32) {
+  const float g_ = (float)v.gamma;
+  float exc = 0.0f;
+  // phase 1: particles, coalesced
+  for (int i = pa + lane; i < pb; i += 32) {
     double x = v.x[i], y = v.y[i], z = v.z[i];
     if (do_drift) {
-      long long td = v.ti_drift[i];
+      const long long td = v.ti_drift[i];
       if (td != ti) {
-        double dt = (double)(ti - td) * v.dt_min;
+        const double dt = (double)(ti - td) * v.dt_min;
         x = wrap_pos(x + (double)v.vx[i] * dt, v.box);
         y = wrap_pos(y + (double)v.vy[i] * dt, v.box);
         z = wrap_pos(z + (double)v.vz[i] * dt, v.box);
@@ -183,87 +176,86 @@ __device__ LeafBox leaf_update(const View &v, int leaf, bool do_drift, bool do_b
     // distance outside the particle's cell (the rebuild criterion)
     const double cxr = rel_periodic(x - ox, v.box), cyr = rel_periodic(y - oy, v.box),
                  czr = rel_periodic(z - oz, v.box);
-    float e = (float)fmax(fmax(fmax(-cxr, cxr - w), fmax(-cyr, cyr - w)), fmax(-czr, czr - w));
+    const float e = (float)fmax(fmax(fmax(-cxr, cxr - w), fmax(-cyr, cyr - w)), fmax(-czr, czr - w));
     exc = fmaxf(exc, e);
     // position relative to the leaf corner
-    const double rx = rel_periodic(x - lx, v.box), ry = rel_periodic(y - ly, v.box),
-                 rz = rel_periodic(z - lz, v.box);
-    const int bi = v.bin[i];
+    const uint32_t lk = v.leaf_k[v.pleaf[i]];
+    const double lx = (double)(cx * (1 << MORTON_BITS) + leaf_kx(lk)) * wq;
+    const double ly = (double)(cy * (1 << MORTON_BITS) + leaf_ky(lk)) * wq;
+    const double lz = (double)(cz * (1 << MORTON_BITS) + leaf_kz(lk)) * wq;
+    const float fx = (float)rel_periodic(x - lx, v.box), fy = (float)rel_periodic(y - ly, v.box),
+                fz = (float)rel_periodic(z - lz, v.box);
+    const int bi = v.bin[i] & (MAX_BINS - 1);
     const double dtp = ((double)(ti - v.ti_begin[i]) - 0.5 * (double)(1ll << bi)) * v.dt_min;
     const float fdtp = (float)dtp;
     const float vpx = v.vx[i] + v.ax[i] * fdtp;
     const float vpy = v.vy[i] + v.ay[i] * fdtp;
     const float vpz = v.vz[i] + v.az[i] * fdtp;
     const float Ap = (float)((double)v.A[i] + (double)v.Adot[i] * dtp);
-    const float hh = v.h[i], H = GAMMA_K * hh, m = v.m[i];
-    const float fx = (float)rx, fy = (float)ry, fz = (float)rz;
+    const float H = GAMMA_K * v.h[i], m = v.m[i];
     v.rec_xm[i] = make_float4(fx, fy, fz, m);
     v.rec_xH[i] = make_float4(fx, fy, fz, H);
     v.rec_v[i] = make_float4(vpx, vpy, vpz, m);
     const float rho = v.rho[i];
     float fP = 0.0f, c = 0.0f;
     if (rho > 0.0f) {
-      float P = Ap * powf(rho, g);
-      c = sqrtf(g * P / rho);
+      const float P = Ap * powf(rho, g_);
+      c = sqrtf(g_ * P / rho);
       fP = v.f[i] * P / (rho * rho);
       v.P[i] = P;
       v.c[i] = c;
     }
     v.rec_h[i] = make_float4(rho, fP, c, 1.0f / H);
-    lox = fminf(lox, fx); loy = fminf(loy, fy); loz = fminf(loz, fz);
-    hix = fmaxf(hix, fx); hiy = fmaxf(hiy, fy); hiz = fmaxf(hiz, fz);
-    Hm = fmaxf(Hm, H);
-    minb = min(minb, bi);
-    mask |= 1ull << bi;
   }
-  for (int o = 16; o; o >>= 1) {
-    lox = fminf(lox, __shfl_xor_sync(0xffffffffu, lox, o));
-    loy = fminf(loy, __shfl_xor_sync(0xffffffffu, loy, o));
-    loz = fminf(loz, __shfl_xor_sync(0xffffffffu, loz, o));
-    hix = fmaxf(hix, __shfl_xor_sync(0xffffffffu, hix, o));
-    hiy = fmaxf(hiy, __shfl_xor_sync(0xffffffffu, hiy, o));
-    hiz = fmaxf(hiz, __shfl_xor_sync(0xffffffffu, hiz, o));
-    Hm = fmaxf(Hm, __shfl_xor_sync(0xffffffffu, Hm, o));
-    exc = fmaxf(exc, __shfl_xor_sync(0xffffffffu, exc, o));
-    minb = min(minb, __shfl_xor_sync(0xffffffffu, minb, o));
-    mask |= __shfl_xor_sync(0xffffffffu, mask, o);
-  }
-  if (lane == 0) {
-    v.leaf_lo[leaf] = make_float4(lox, loy, loz, Hm);
-    v.leaf_hi[leaf] = make_float4(hix, hiy, hiz, 0.0f);
+  __syncwarp();
+  // phase 2: one leaf per lane
+  float lx = INFINITY, ly = INFINITY, lz = INFINITY;
+  float hx = -INFINITY, hy = -INFINITY, hz = -INFINITY, Hm = 0.0f;
+  if (l0 + lane < l1) {
+    const int leaf = l0 + lane;
+    const int a = v.leaf_start[leaf], b = v.leaf_start[leaf + 1];
+    float bx = INFINITY, by = INFINITY, bz = INFINITY, tx = -INFINITY, ty = -INFINITY, tz = -INFINITY;
+    int minb = 127;
+    unsigned long long mask = 0ull;
+#pragma unroll 4
+    for (int k = a; k < b; k++) {
+      const float4 r = v.rec_xH[k];
+      bx = fminf(bx, r.x); by = fminf(by, r.y); bz = fminf(bz, r.z);
+      tx = fmaxf(tx, r.x); ty = fmaxf(ty, r.y); tz = fmaxf(tz, r.z);
+      Hm = fmaxf(Hm, r.w);
+      if (do_bins) {
+        const int bk = v.bin[k] & (MAX_BINS - 1);
+        minb = min(minb, bk);
+        mask |= 1ull << bk;
+      }
+    }
+    v.leaf_lo[leaf] = make_float4(bx, by, bz, Hm);
+    v.leaf_hi[leaf] = make_float4(tx, ty, tz, 0.0f);
     if (do_bins) {
       v.leaf_min_bin[leaf] = (uint8_t)minb;
       v.leaf_bin_mask[leaf] = mask;
     }
+    const uint32_t k = v.leaf_k[leaf];
+    const float wqf = (float)wq;
+    const float sx = leaf_kx(k) * wqf, sy = leaf_ky(k) * wqf, sz = leaf_kz(k) * wqf;
+    lx = bx + sx; ly = by + sy; lz = bz + sz;
+    hx = tx + sx; hy = ty + sy; hz = tz + sz;
+  }
+  for (int o = 16; o; o >>= 1) {
+    lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
+    ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
+    lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
+    hx = fmaxf(hx, __shfl_xor_sync(0xffffffffu, hx, o));
+    hy = fmaxf(hy, __shfl_xor_sync(0xffffffffu, hy, o));
+    hz = fmaxf(hz, __shfl_xor_sync(0xffffffffu, hz, o));
+    Hm = fmaxf(Hm, __shfl_xor_sync(0xffffffffu, Hm, o));
+    exc = fmaxf(exc, __shfl_xor_sync(0xffffffffu, exc, o));
+  }
+  if (lane == 0) {
+    v.chunk_lo[g] = make_float4(lx, ly, lz, Hm);
+    v.chunk_hi[g] = make_float4(hx, hy, hz, 0.0f);
     atomic_max_float_pos(&v.ds->excursion_bits, exc);
     atomic_max_float_pos(&v.ds->Hmax_bits, Hm);
-  }
-  LeafBox r = {lox, loy, loz, hix, hiy, hiz, Hm};
-  return r;
-}
-
-// One warp per chunk: updates its leaves one after the other, then the
-// chunk's bounding box in the cell frame (leaf boxes shifted by their Morton
-// corners) and its largest support.
-__device__ void chunk_update(const View &v, int g, bool do_drift, bool do_bins) {
-  const DevState *ds = v.ds;
-  const int cell = v.chunk_cell[g];
-  const int l0 = v.cell_leaf_start[cell] + CHUNK * (g - v.cell_chunk_start[cell]);
-  const int l1 = min(l0 + CHUNK, v.cell_leaf_start[cell + 1]);
-  const float wq = (float)(ds->w / (double)(1 << MORTON_BITS));
-  float lx = INFINITY, ly = INFINITY, lz = INFINITY;
-  float hx = -INFINITY, hy = -INFINITY, hz = -INFINITY, H = 0.0f;
-  for (int l = l0; l < l1; l++) {
-    const LeafBox b = leaf_update(v, l, do_drift, do_bins);
-    const uint32_t k = v.leaf_k[l];
-    const float ox = leaf_kx(k) * wq, oy = leaf_ky(k) * wq, oz = leaf_kz(k) * wq;
-    lx = fminf(lx, b.lx + ox); ly = fminf(ly, b.ly + oy); lz = fminf(lz, b.lz + oz);
-    hx = fmaxf(hx, b.hx + ox); hy = fmaxf(hy, b.hy + oy); hz = fmaxf(hz, b.hz + oz);
-    H = fmaxf(H, b.H);
-  }
-  if (lane_id() == 0) {
-    v.chunk_lo[g] = make_float4(lx, ly, lz, H);
-    v.chunk_hi[g] = make_float4(hx, hy, hz, 0.0f);
   }
 }
 
