@@ -48,7 +48,7 @@ WORKLOAD = "c3_clustered_2m"
 FLOP_DENSITY = 29   # per useful density pair
 FLOP_FORCE = 61     # per useful force pair
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-DEFAULT_LAUNCH = dict(threads_per_particle=1, leaf_max=8, cell_margin=2.0)
+DEFAULT_LAUNCH = dict(threads_per_particle=1, leaf_max=16, cell_margin=2.0)
 KNOBS = ("threads_per_particle", "leaf_max", "cell_margin")
 
 

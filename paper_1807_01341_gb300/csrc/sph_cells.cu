@@ -254,9 +254,6 @@ __device__ __forceinline__ unsigned int child_of(unsigned long long key, int shi
   return (unsigned int)((key >> shift) & 7ull);
 }
 
-// Walks the octree of one cell's Morton-ordered particles depth first and
-// emits, in particle order, every node with at most leaf_max particles (or
-// chunks of leaf_max at the deepest level).  Returns the number of leaves.
 __device__ __forceinline__ uint32_t compact3(unsigned long long m) {
   uint32_t r = 0;
 #pragma unroll
@@ -273,33 +270,49 @@ __device__ __forceinline__ uint32_t corner_of(unsigned long long key, int level)
   return compact3(t >> 2) | (compact3(t >> 1) << 10) | (compact3(t) << 20);
 }
 
+// Walks the octree of one cell's Morton-ordered particles depth first and
+// emits its leaves in particle order.  A node holding more than leaf_max
+// particles is split into its 8 children; consecutive children that hold at
+// most leaf_max particles between them are merged into one leaf (siblings, so
+// the leaf stays inside the parent node), and larger children are split in
+// turn.  At the deepest level a node is cut into chunks of leaf_max.  Each
+// leaf records the corner of the node it lies in.  Returns the leaf count.
 __device__ int split_cell(const unsigned long long *__restrict__ keys, int a0, int b0,
                           int leaf_max, int32_t *leaf_start, int32_t *leaf_cell,
                           uint32_t *leaf_k, int cell, int out_base) {
+  // stack entries: [a, b) and level; a negative level -(L+1) marks a merged
+  // run of children of a node at level L, emitted as one leaf
   int sa[8 * MORTON_BITS + 8], sb[8 * MORTON_BITS + 8];
   signed char sl[8 * MORTON_BITS + 8];
   int top = 0, count = 0;
+  auto emit = [&](int a, int b, int level) {
+    for (int s = a; s < b; s += leaf_max) {
+      if (leaf_start) {
+        leaf_start[out_base + count] = s;
+        leaf_cell[out_base + count] = cell;
+        leaf_k[out_base + count] = corner_of(keys[a], level);
+      }
+      count++;
+    }
+  };
+  if (b0 <= a0) return 0;
   sa[0] = a0;
   sb[0] = b0;
   sl[0] = 0;
   top = 1;
   while (top > 0) {
     top--;
-    int a = sa[top], b = sb[top], L = sl[top];
-    int cnt = b - a;
-    if (cnt <= 0) continue;
-    if (cnt <= leaf_max || L == MORTON_BITS) {
-      for (int s = a; s < b; s += leaf_max) {
-        if (leaf_start) {
-          leaf_start[out_base + count] = s;
-          leaf_cell[out_base + count] = cell;
-          leaf_k[out_base + count] = corner_of(keys[a], L);
-        }
-        count++;
-      }
+    const int a = sa[top], b = sb[top], L = sl[top];
+    if (L < 0) {  // merged siblings
+      emit(a, b, -L - 1);
       continue;
     }
-    int shift = 3 * (MORTON_BITS - 1 - L);
+    const int cnt = b - a;
+    if (cnt <= leaf_max || L == MORTON_BITS) {
+      emit(a, b, L);
+      continue;
+    }
+    const int shift = 3 * (MORTON_BITS - 1 - L);
     int bnd[9];
     bnd[0] = a;
     bnd[8] = b;
@@ -307,19 +320,46 @@ __device__ int split_cell(const unsigned long long *__restrict__ keys, int a0, i
       // first index in [bnd[k-1], b) whose child digit is >= k
       int lo = bnd[k - 1], hi = b;
       while (lo < hi) {
-        int mid = (lo + hi) >> 1;
+        const int mid = (lo + hi) >> 1;
         if (child_of(keys[mid], shift) < (unsigned int)k) lo = mid + 1;
         else hi = mid;
       }
       bnd[k] = lo;
     }
-    for (int k = 7; k >= 0; k--) {
-      if (bnd[k + 1] > bnd[k]) {
-        sa[top] = bnd[k];
-        sb[top] = bnd[k + 1];
-        sl[top] = (signed char)(L + 1);
-        top++;
+    // entries in child order: big children to split, runs of small ones
+    int ea[8], eb[8];
+    signed char el[8];
+    int ne = 0;
+    for (int k = 0; k < 8;) {
+      const int c = bnd[k + 1] - bnd[k];
+      if (c == 0) {
+        k++;
+        continue;
       }
+      if (c > leaf_max) {
+        ea[ne] = bnd[k];
+        eb[ne] = bnd[k + 1];
+        el[ne] = (signed char)(L + 1);
+        ne++;
+        k++;
+        continue;
+      }
+      int k2 = k + 1, sum = c;
+      while (k2 < 8 && sum + (bnd[k2 + 1] - bnd[k2]) <= leaf_max) {
+        sum += bnd[k2 + 1] - bnd[k2];
+        k2++;
+      }
+      ea[ne] = bnd[k];
+      eb[ne] = bnd[k2];
+      el[ne] = (signed char)(-(L + 1));
+      ne++;
+      k = k2;
+    }
+    for (int e = ne - 1; e >= 0; e--) {
+      sa[top] = ea[e];
+      sb[top] = eb[e];
+      sl[top] = el[e];
+      top++;
     }
   }
   return count;

@@ -184,6 +184,26 @@ __device__ __forceinline__ float box_gap2(float lix, float liy, float liz, float
   return gx * gx + gy * gy + gz * gz;
 }
 
+// Whether any of the n spheres (centre, radius in w; a radius <= 0 never
+// reaches) comes within its radius of box [lo, hi] (j's box shifted by s);
+// `grow` is the leaf's own support, a lower bound of every radius when > 0.
+__device__ __forceinline__ bool spheres_reach(const float4 *sph, int n, const float4 &lo,
+                                              const float4 &hi, float sx, float sy, float sz,
+                                              float grow) {
+  const float lx = lo.x + sx, ly = lo.y + sy, lz = lo.z + sz;
+  const float hx = hi.x + sx, hy = hi.y + sy, hz = hi.z + sz;
+  for (int p = 0; p < n; p++) {
+    const float4 c = sph[p];
+    const float R = fmaxf(c.w, grow);
+    if (c.w <= 0.0f) continue;
+    const float gx = fmaxf(0.0f, fmaxf(lx - c.x, c.x - hx));
+    const float gy = fmaxf(0.0f, fmaxf(ly - c.y, c.y - hy));
+    const float gz = fmaxf(0.0f, fmaxf(lz - c.z, c.z - hz));
+    if (gx * gx + gy * gy + gz * gz < R * R * 1.0002f) return true;
+  }
+  return false;
+}
+
 // Cubic spline: w(q) / (8/pi) and w'(q) / (8/pi), q in [0, 1)
 __device__ __forceinline__ void kernel_wd(float q, float &wq, float &dwq) {
   const float s = 1.0f - q;
@@ -283,23 +303,28 @@ __device__ __forceinline__ float3 leaf_offset(const View &v, int i, const CellFr
 template <int S, int NREC, int LC>
 struct Stage {
   static constexpr int LCAP = LC;  // accepted neighbour leaves listed per search pass
+  static constexpr int CCAP = 128; // accepted chunks gathered per search segment
   float4 *rec;     // NREC arrays of S staged records, back to back (first: positions)
   float4 *lshift;  // per listed leaf: offset of its corner (x, y, z), first particle (w bits)
   int *lpack;      // per listed leaf: count | cell index << 16
   int *act;        // active particles of the work group
   int *recj;       // per staged record: particle index
   uint8_t *recc;   // per staged record: neighbour-cell index (0..26)
+  float4 *sph;     // the round's particles: position (group frame), search radius
+  int2 *chk;       // accepted chunks of a search segment: first leaf, count | cell << 16
   uint64_t *bar;
   uint32_t phase;
   bool failed;
   static constexpr size_t bytes() {
-    return sizeof(float4) * ((size_t)S * NREC + LC) + sizeof(int) * (LC + LEAF_MAX_LIMIT + S) +
-           (size_t)S + 16;
+    return sizeof(float4) * ((size_t)S * NREC + LC + 32) + sizeof(int2) * CCAP +
+           sizeof(int) * (LC + LEAF_MAX_LIMIT + S) + (size_t)S + 16;
   }
   __device__ void carve(char *base) {
     rec = reinterpret_cast<float4 *>(base);
     lshift = rec + (size_t)S * NREC;
-    lpack = reinterpret_cast<int *>(lshift + LC);
+    sph = lshift + LC;
+    chk = reinterpret_cast<int2 *>(sph + 32);
+    lpack = reinterpret_cast<int *>(chk + CCAP);
     act = lpack + LC;
     recj = act + LEAF_MAX_LIMIT;
     recc = reinterpret_cast<uint8_t *>(recj + S);
@@ -307,51 +332,116 @@ struct Stage {
   }
 };
 
+// Lane `lane` holds v_lane (lanes 0..n-1, ascending); returns, for this lane's
+// key t, the largest index c < n with v_c <= t (the segment holding t).
+__device__ __forceinline__ int seg_of(int v_lane, int n, int t) {
+  int lo = 0, hi = n - 1;
+#pragma unroll
+  for (int step = 0; step < 5; step++) {
+    const int mid = (lo + hi + 1) >> 1;
+    const int vm = __shfl_sync(FULL, v_lane, mid);
+    if (lo < hi) {
+      if (vm <= t) lo = mid;
+      else hi = mid - 1;
+    }
+  }
+  return lo;
+}
+
 // Lists, in cell-then-leaf order, the leaves of the 27 cells around the work
 // group that pass `leaf_ok` (in cells of more than CHUNK leaves, only those of
 // chunks passing `chunk_ok`): accepted leaves skip, skip + 1, ... up to LCAP
 // of them.  Returns how many were listed; `more` tells whether the list
-// stopped because it was full.
+// stopped because it was full.  The cells' chunks, then the accepted chunks'
+// leaves, are tested 32 at a time across all 27 cells, so the number of
+// dependent global-memory rounds does not grow with the cell count.
 template <class St, class LeafOk, class ChunkOk>
 __device__ __forceinline__ int search(const View &v, const CellFrame &F, St &st, LeafOk leaf_ok,
                                       ChunkOk chunk_ok, int skip, bool &more) {
   constexpr int LCAP = St::LCAP;
+  constexpr int CCAP = St::CCAP;
   const int lane = lane_id();
-  int seen = 0;
   more = false;
   const int limit = skip + LCAP;
-  for (int ci = 0; ci < 27; ci++) {
-    const int dxc = ci / 9 - 1, dyc = (ci / 3) % 3 - 1, dzc = ci % 3 - 1;
+  // phase 1: the 27 neighbour cells, one per lane
+  int g0 = 0, nch = 0, l0 = 0, l1 = 0;
+  if (lane < 27) {
+    const int dxc = lane / 9 - 1, dyc = (lane / 3) % 3 - 1, dzc = lane % 3 - 1;
     const int cj = (wrap_cell(F.cx + dxc, F.nc) * F.nc + wrap_cell(F.cy + dyc, F.nc)) * F.nc +
                    wrap_cell(F.cz + dzc, F.nc);
-    // grid-step offset of the neighbour cell's corner from the work group's corner
-    const int bx = dxc * (1 << MORTON_BITS) - F.kx;
-    const int by = dyc * (1 << MORTON_BITS) - F.ky;
-    const int bz = dzc * (1 << MORTON_BITS) - F.kz;
-    const int l0 = v.cell_leaf_start[cj], l1 = v.cell_leaf_start[cj + 1];
-    const int g0 = v.cell_chunk_start[cj], g1 = v.cell_chunk_start[cj + 1];
-    const bool chunked = l1 - l0 > CHUNK;
-    const float csx = dxc * F.wf, csy = dyc * F.wf, csz = dzc * F.wf;
-    // chunks of this cell, 32 at a time (a cell of <= CHUNK leaves is one chunk)
-    for (int gb = g0; gb < g1; gb += 32) {
-      const int g = gb + lane;
-      bool okc = g < g1;
-      if (chunked && okc) okc = chunk_ok(g, csx, csy, csz);
-      unsigned mc = __ballot_sync(FULL, okc);
-      while (mc) {
-        const int src = __ffs(mc) - 1;
-        mc &= mc - 1;
-        const int la = l0 + CHUNK * (gb + src - g0);
-        const int lb = min(la + CHUNK, l1);
-        const int l = la + lane;
+    g0 = v.cell_chunk_start[cj];
+    nch = v.cell_chunk_start[cj + 1] - g0;
+    l0 = v.cell_leaf_start[cj];
+    l1 = v.cell_leaf_start[cj + 1];
+  }
+  const int cstart = warp_incl_scan(nch) - nch;  // first flat chunk index of this lane's cell
+  const int T = __shfl_sync(FULL, cstart + nch, 26);
+  int seen = 0;  // accepted leaves so far
+  // phase 2: all chunks of the 27 cells, 32 per round; accepted chunks are
+  // gathered (in order) into st.chk, then phase 3 runs over their leaves
+  for (int tb = 0; tb < T; tb += 32 * 32) {
+    int nacc = 0;  // accepted chunks gathered in this segment
+    int tnext = T;
+    for (int t0 = tb; t0 < T; t0 += 32) {
+      const int t = t0 + lane;
+      const int ci = seg_of(cstart, 27, min(t, T - 1));
+      const int cg0 = __shfl_sync(FULL, g0, ci), cnch = __shfl_sync(FULL, nch, ci);
+      const int cl0 = __shfl_sync(FULL, l0, ci), cl1 = __shfl_sync(FULL, l1, ci);
+      const int cs = __shfl_sync(FULL, cstart, ci);
+      bool okc = false;
+      int la = 0, lb = 0;
+      if (t < T) {
+        const int k = t - cs;  // chunk number inside cell ci
+        la = cl0 + CHUNK * k;
+        lb = min(la + CHUNK, cl1);
+        okc = true;
+        if (cl1 - cl0 > CHUNK) {
+          const int dxc = ci / 9 - 1, dyc = (ci / 3) % 3 - 1, dzc = ci % 3 - 1;
+          okc = chunk_ok(cg0 + k, dxc * F.wf, dyc * F.wf, dzc * F.wf);
+        }
+        (void)cnch;
+      }
+      const unsigned mk = __ballot_sync(FULL, okc);
+      const int room = CCAP - nacc;
+      if (__popc(mk) > room) {  // this round does not fit: resume from it next segment
+        tnext = t0;
+        break;
+      }
+      if (okc) {
+        const int pos = nacc + __popc(mk & ((1u << lane) - 1u));
+        st.chk[pos] = make_int2(la, (lb - la) | (ci << 16));
+      }
+      nacc += __popc(mk);
+    }
+    __syncwarp();
+    // phase 3: leaves of the accepted chunks, 32 per round, in order
+    int lcount = 0;
+    if (lane < nacc) lcount = st.chk[lane].y & 0xffff;
+    // (at most 32 chunks per sub-round so that one lane holds each chunk)
+    for (int cb = 0; cb < nacc; cb += 32) {
+      const int cn = min(32, nacc - cb);
+      int2 ch = make_int2(0, 0);
+      if (lane < cn) ch = st.chk[cb + lane];
+      const int cnt_l = lane < cn ? (ch.y & 0xffff) : 0;
+      const int lst = warp_incl_scan(cnt_l) - cnt_l;
+      const int L = __shfl_sync(FULL, lst + cnt_l, 31);
+      for (int u0 = 0; u0 < L; u0 += 32) {
+        const int u = u0 + lane;
+        const int cc = seg_of(lst, cn, min(u, L - 1));
+        const int cla = __shfl_sync(FULL, ch.x, cc);
+        const int cy = __shfl_sync(FULL, ch.y, cc);
+        const int cls = __shfl_sync(FULL, lst, cc);
+        const int ci = cy >> 16;
         bool ok = false;
         int ja = 0, cnt = 0;
         float sx = 0.f, sy = 0.f, sz = 0.f;
-        if (l < lb) {
+        if (u < L) {
+          const int l = cla + (u - cls);
+          const int dxc = ci / 9 - 1, dyc = (ci / 3) % 3 - 1, dzc = ci % 3 - 1;
           const uint32_t kl = v.leaf_k[l];
-          sx = (float)(bx + leaf_kx(kl)) * F.wq;
-          sy = (float)(by + leaf_ky(kl)) * F.wq;
-          sz = (float)(bz + leaf_kz(kl)) * F.wq;
+          sx = (float)(dxc * (1 << MORTON_BITS) - F.kx + leaf_kx(kl)) * F.wq;
+          sy = (float)(dyc * (1 << MORTON_BITS) - F.ky + leaf_ky(kl)) * F.wq;
+          sz = (float)(dzc * (1 << MORTON_BITS) - F.kz + leaf_kz(kl)) * F.wq;
           ok = leaf_ok(l, sx, sy, sz);
           if (ok) {
             ja = v.leaf_start[l];
@@ -372,6 +462,10 @@ __device__ __forceinline__ int search(const View &v, const CellFrame &F, St &st,
         }
       }
     }
+    (void)lcount;
+    __syncwarp();
+    tb = tnext - 32 * 32;  // continue after the last gathered round
+    if (tnext >= T) break;
   }
   __syncwarp();
   return max(0, min(seen - skip, LCAP));
@@ -436,7 +530,7 @@ __device__ __forceinline__ void stage_list(const float4 *const *srcs, Stage<S, N
   }
 }
 
-using StageD = Stage<S_DENS, 1, 384>;
+using StageD = Stage<S_DENS, 1, 320>;
 using StageF = Stage<S_FORCE, 3, 256>;
 
 // ---------------------------------------------------------------------------
@@ -476,7 +570,8 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
     float h = v.h[i];
     double lo = 0.0, hi = INFINITY;
     bool done = !valid;
-    float Rs = 0.0f;      // radius of the leaf list in shared memory (0: none)
+    bool have_list = false;  // the leaf list in shared memory covers the round
+    float Ri = 0.0f;         // this particle's radius at the last search
     int nlist = 0;
     for (int it = 0; it < v.h_max_iter && !st.failed; it++) {
       const float H = GAMMA_K * h;
@@ -528,14 +623,21 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
           }
         }
       };
-      // the leaf list in shared memory is reused while it covers every support
-      // of the round; otherwise search again (in passes of LCAP leaves)
-      const bool reuse = Rs > 0.0f && Hs <= Rs;
-      const float R = reuse ? Rs : Hs * 1.05f;  // room for the next iterations to grow h
+      // the leaf list in shared memory is reused while every unconverged
+      // particle's support stays inside the radius it was searched with;
+      // otherwise search again (in passes of LCAP leaves)
+      const bool reuse = have_list && __all_sync(FULL, done || H <= Ri);
+      if (!reuse) {
+        Ri = done ? 0.0f : H * 1.05f;  // room for the next iterations to grow h
+        if (sub == 0) st.sph[grp] = make_float4(xi.x, xi.y, xi.z, Ri);
+        __syncwarp();
+      }
+      const float R = Hs * 1.05f;
       const float R2 = R * R * 1.0002f, Rc = R + ceps;
       auto leaf_ok = [&](int l, float sx, float sy, float sz) {
-        return box_gap2(W.lx, W.ly, W.lz, W.hx, W.hy, W.hz, v.leaf_lo[l], v.leaf_hi[l], sx, sy,
-                        sz) < R2;
+        const float4 lo = v.leaf_lo[l], hi = v.leaf_hi[l];
+        return box_gap2(W.lx, W.ly, W.lz, W.hx, W.hy, W.hz, lo, hi, sx, sy, sz) < R2 &&
+               spheres_reach(st.sph, P, lo, hi, sx, sy, sz, 0.0f);
       };
       auto chunk_ok = [&](int g, float sx, float sy, float sz) {
         return box_gap2(clx, cly, clz, chx, chy, chz, v.chunk_lo[g], v.chunk_hi[g], sx, sy, sz) <
@@ -551,7 +653,7 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
         stage_list(srcs, st, nlist, consume, wc);
         skip += nlist;
       } while (!reuse && more && !st.failed);
-      if (!reuse) Rs = complete ? R : 0.0f;
+      if (!reuse) have_list = complete;
       if (st.failed) break;
       fold(n_hi, n_lo, pn);
       fold(t_hi, t_lo, pt);
@@ -666,16 +768,18 @@ __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, co
     const float Hinv2 = hi4.w * hi4.w;
     const float nHi4 = KERNEL_NORM * Hinv2 * Hinv2;
     const float Hs = warp_max(valid ? xi.w : 0.0f);
+    if (sub == 0) st.sph[grp] = make_float4(xi.x, xi.y, xi.z, valid ? xi.w : 0.0f);
+    __syncwarp();
     float ax_hi = 0.f, ax_lo = 0.f, ay_hi = 0.f, ay_lo = 0.f, az_hi = 0.f, az_lo = 0.f;
     float ad_hi = 0.f, ad_lo = 0.f;
     float pax = 0.f, pay = 0.f, paz = 0.f, pad = 0.f;
     float vs = 2.0f * hi4.z;
     int cur = -1, cnt = 0;
     auto leaf_ok = [&](int l, float sx, float sy, float sz) {
-      const float4 loj = v.leaf_lo[l];
+      const float4 loj = v.leaf_lo[l], hij = v.leaf_hi[l];
       const float R = fmaxf(Hs, loj.w);
-      return box_gap2(W.lx, W.ly, W.lz, W.hx, W.hy, W.hz, loj, v.leaf_hi[l], sx, sy, sz) <
-             R * R * 1.0002f;
+      return box_gap2(W.lx, W.ly, W.lz, W.hx, W.hy, W.hz, loj, hij, sx, sy, sz) < R * R * 1.0002f &&
+             spheres_reach(st.sph, P, loj, hij, sx, sy, sz, loj.w);
     };
     auto chunk_ok = [&](int gg, float sx, float sy, float sz) {
       const float4 loc = v.chunk_lo[gg];
