@@ -19,7 +19,9 @@ e2e         the batched form through the C ABI with host buffers: each step
 roofline    the dominant pair-loop kernel: algorithmic FLOPs per useful pair
             (density 29, force 61) x useful pairs per launch / mean launch time
             (CUDA events in the library, on the launching stream), against the
-            FP32 peak 152 SMs x 128 lanes x 2 x 2.07 GHz;
+            FP32 peak 152 SMs x 128 lanes x 2 x 2.07 GHz; its `traffic` is the
+            DRAM bytes per launch from the kernel's ncu summary under profiles/,
+            reported only while that summary's source digest matches the sources;
 cpu_baseline  the FP64 oracle on a bounded sample of the same workload.
 
 --impl reference times the oracle alone (the CPU reference of this method).
@@ -31,6 +33,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -45,11 +48,41 @@ sys.path.insert(0, ROOT)
 METRIC = "active pair interactions/s (density+force) at 2.1M clustered; batched vs plain"
 UNIT = "pairs/s"
 WORKLOAD = "c3_clustered_2m"
-FLOP_DENSITY = 29   # per useful density pair
-FLOP_FORCE = 61     # per useful force pair
+# algorithmic FP32 operations per useful pair (FMA = 2; sqrt, rsqrt, divide = 1)
+FLOP_DENSITY = 29
+FLOP_FORCE = 61
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 DEFAULT_LAUNCH = dict(threads_per_particle=1, leaf_max=16, cell_margin=2.0)
 KNOBS = ("threads_per_particle", "leaf_max", "cell_margin")
+
+
+def kernel_source_digest() -> str:
+    """First 16 hex digits of the SHA-256 of the pair-kernel sources."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("sph_pairs.cu", "sph_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1807_01341_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of a pair kernel from its committed ncu summary,
+    or None when the summary is missing or was taken from other sources."""
+    path = os.path.join(ROOT, "profiles", f"k_{kernel}_{workload}.md")
+    try:
+        with open(path) as f:
+            text = f.read()
+    except OSError:
+        return None
+    fields = dict(re.findall(r"^(kernel_source_digest|traffic_bytes_per_launch):\s*(\S+)\s*$",
+                             text, flags=re.M))
+    if fields.get("kernel_source_digest") != kernel_source_digest():
+        return None
+    try:
+        return int(fields["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def _env_int(k, d):
@@ -386,7 +419,8 @@ def main():
                     "h2d_bytes_per_step": out["h2d"], "d2h_bytes_per_step": out["h2d"]},
             "roofline": {"bound": "alu", "kernel": rf["kernel"], "achieved": rf["achieved"],
                          "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": rf["achieved"] / FP32_PEAK_TFLOPS, "traffic": None,
+                         "frac": rf["achieved"] / FP32_PEAK_TFLOPS,
+                         "traffic": profiled_traffic(rf["kernel"], args.workload),
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived)",
                          "launch_ms": rf["per_launch_ms"], "density_ms": rf["density_ms"],
                          "force_ms": rf["force_ms"]},
