@@ -47,7 +47,7 @@ struct Buffers {
   unsigned long long *leaf_bin_mask = nullptr;
   int32_t *q_active = nullptr, *q_drift = nullptr, *q_bin = nullptr, *q_group = nullptr;
   // work groups of the pair loops
-  int32_t *pleaf = nullptr, *group_leaf0 = nullptr, *group_cell = nullptr;
+  int32_t *pleaf = nullptr, *group_leaf0 = nullptr, *group_cell = nullptr, *group_cost = nullptr;
   // records
   float4 *rec_xm = nullptr, *rec_xH = nullptr, *rec_v = nullptr, *rec_h = nullptr;
   // cells (grown on demand)
@@ -198,6 +198,7 @@ View make_view(const sph_ctx *ctx, const sph_particles *p) {
   v.pleaf = b.pleaf;
   v.group_leaf0 = b.group_leaf0;
   v.group_cell = b.group_cell;
+  v.group_cost = b.group_cost;
   v.q_act_cells = b.q_act_cells;
   v.q_drift = b.q_drift;
   v.q_bin = b.q_bin;
@@ -389,6 +390,8 @@ int build_cells(sph_ctx *ctx, sph_particles *p, cudaStream_t st) {
   SPH_CUDA(cudaMemsetAsync(SPH_DS_FIELD(b.ds, want_h_bits), 0, sizeof(unsigned int), st));
   SPH_CUDA(launch_bin_histogram(v, st));
   SPH_CUDA(launch_refresh_all(v, st));
+  // cost estimate of every work group (orders the active queue heavy-first)
+  SPH_CUDA(launch_group_cost(v, ctx->grid_dens, st));
   int nl = 0;
   SPH_CUDA(cudaMemcpyAsync(&nl, SPH_DS_FIELD(b.ds, n_leaves), sizeof(int), cudaMemcpyDeviceToHost, st));
   SPH_CUDA(cudaStreamSynchronize(st));
@@ -592,7 +595,7 @@ int sph_create(const sph_params *params, int64_t n_max, sph_ctx **out) {
         (r = dalloc(&b.leaf_min_bin, n)) || (r = dalloc(&b.leaf_bin_mask, n)) ||
         (r = dalloc(&b.q_active, n)) || (r = dalloc(&b.q_drift, n)) || (r = dalloc(&b.q_bin, n)) ||
         (r = dalloc(&b.q_group, n)) || (r = dalloc(&b.pleaf, n)) || (r = dalloc(&b.group_leaf0, n + 1)) ||
-        (r = dalloc(&b.group_cell, n)) ||
+        (r = dalloc(&b.group_cell, n)) || (r = dalloc(&b.group_cost, n)) ||
         (r = dalloc(&b.rec_xm, n)) || (r = dalloc(&b.rec_xH, n)) || (r = dalloc(&b.rec_v, n)) ||
         (r = dalloc(&b.rec_h, n)) || (r = dalloc(&b.ds, 1)) || (r = dalloc(&b.d_hmax, 1)))
       break;
@@ -635,7 +638,7 @@ int sph_destroy(sph_ctx *ctx) {
   dfree(b.chunk_cell); dfree(b.chunk_lo); dfree(b.chunk_hi); dfree(b.leaf_lo); dfree(b.leaf_hi);
   dfree(b.leaf_min_bin); dfree(b.leaf_bin_mask);
   dfree(b.q_active); dfree(b.q_drift); dfree(b.q_bin); dfree(b.q_group);
-  dfree(b.pleaf); dfree(b.group_leaf0); dfree(b.group_cell);
+  dfree(b.pleaf); dfree(b.group_leaf0); dfree(b.group_cell); dfree(b.group_cost);
   dfree(b.rec_xm); dfree(b.rec_xH); dfree(b.rec_v); dfree(b.rec_h);
   dfree(b.cell_start); dfree(b.cell_leaf_start); dfree(b.cell_stamp); dfree(b.cell_rel_stamp);
   dfree(b.q_act_cells); dfree(b.leaf_counts); dfree(b.leaf_offsets);

@@ -50,6 +50,7 @@ __global__ void k_begin_step(View v, long long ti_arg) {
   ds->n_drift_chunks = 0;
   ds->n_bin_groups = 0;
   ds->n_active_groups = 0;
+  ds->n_heavy_groups = 0;
   ds->head_density = ds->head_force = ds->head_drift = ds->head_kick = 0;
   ds->head_open = ds->head_bins = ds->head_misc = 0;
   ds->s_pairs_density = ds->s_pairs_force = 0ull;
@@ -72,14 +73,21 @@ __global__ void k_mark_leaves(View v) {
   }
 }
 
-// One thread per work group: queues the groups whose smallest bin is active.
+// One thread per work group: queues the groups whose smallest bin is active,
+// the heavy ones (estimated cost above HEAVY_FACTOR times the mean) apart so
+// that the pair loops start them first.
 __global__ void k_mark_groups(View v) {
   DevState *ds = v.ds;
   const int ng = ds->n_groups, m_act = ds->m_act;
+  const unsigned long long csum = ds->group_cost_sum;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
     int mb = 127;
     for (int l = v.group_leaf0[g]; l < v.group_leaf0[g + 1]; l++) mb = min(mb, (int)v.leaf_min_bin[l]);
-    if (mb <= m_act) v.q_group[atomicAdd(&ds->n_active_groups, 1)] = g;
+    if (mb > m_act) continue;
+    const bool heavy = (unsigned long long)v.group_cost[g] * (unsigned long long)ng >
+                       (unsigned long long)HEAVY_FACTOR * csum;
+    if (heavy) v.q_group[ng - 1 - atomicAdd(&ds->n_heavy_groups, 1)] = g;
+    else v.q_group[atomicAdd(&ds->n_active_groups, 1)] = g;
   }
 }
 
@@ -386,9 +394,9 @@ __global__ void k_next_time(View v, long long *out, int count_step) {
 
 __global__ void k_mark_bin(View v, int bin) {
   DevState *ds = v.ds;
-  const int nq = ds->n_active_groups;
+  const int nq = ds->n_active_groups + ds->n_heavy_groups;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nq; k += gridDim.x * blockDim.x) {
-    const int g = v.q_group[k];
+    const int g = active_group(v, ds, k);
     unsigned long long mask = 0ull;
     for (int l = v.group_leaf0[g]; l < v.group_leaf0[g + 1]; l++) mask |= v.leaf_bin_mask[l];
     if ((mask >> bin) & 1ull) v.q_bin[atomicAdd(&ds->n_bin_groups, 1)] = g;

@@ -37,7 +37,11 @@ struct DevState {
   int n_leaves;
   int n_chunks;          // groups of up to CHUNK consecutive leaves of one cell
   int n_groups;          // work groups: runs of consecutive leaves of one cell, <= WG_MAX particles
-  int n_active_groups;   // work groups holding active particles
+  int n_active_groups;   // work groups holding active particles (light ones from the front of
+                         // q_group, heavy ones from its back; see n_heavy_groups)
+  int n_heavy_groups;    // active work groups whose estimated cost is well above the mean
+  int pad1;
+  unsigned long long group_cost_sum;  // sum over work groups of group_cost (written at build)
   double w;              // cell width
   // queues (written by mark)
   int n_active_leaves;   // leaves holding active particles
@@ -100,6 +104,7 @@ struct View {
   int32_t *pleaf;            // [n] leaf of each particle
   int32_t *group_leaf0;      // [n_groups + 1] first leaf of each work group
   int32_t *group_cell;       // [n_groups] cell of each work group
+  int32_t *group_cost;       // [n_groups] estimated neighbour records of one search (at build)
   // FP32 records read by the pair loops (cell-relative positions)
   float4 *rec_xm;  // x, y, z, m
   float4 *rec_xH;  // x, y, z, H
@@ -109,7 +114,8 @@ struct View {
   int32_t *q_active;         // leaves holding active particles
   int32_t *q_act_cells;      // cells holding active particles
   int32_t *q_drift;          // chunks to drift (cells next to an active cell)
-  int32_t *q_group;          // work groups holding active particles
+  int32_t *q_group;          // work groups holding active particles: light ones at
+                             // [0, n_active_groups), heavy ones at n_groups - 1 - k
   int32_t *q_bin;            // plain form: active work groups holding particles of one bin
   DevState *ds;
   // parameters
@@ -149,6 +155,17 @@ __host__ __device__ __forceinline__ int leaf_kz(uint32_t k) { return (int)((k >>
 __device__ __forceinline__ int wrap_cell(int c, int nc) {
   return c < 0 ? c + nc : (c >= nc ? c - nc : c);
 }
+
+// k-th entry of the active work-group queue: the heavy groups first (they
+// start in the first wave of a persistent kernel), then the light ones.
+__device__ __forceinline__ int active_group(const View &v, const DevState *ds, int k) {
+  const int nh = ds->n_heavy_groups;
+  return k < nh ? v.q_group[ds->n_groups - 1 - k] : v.q_group[k - nh];
+}
+
+// Estimated cost above which a work group counts as heavy: HEAVY_FACTOR times
+// the mean estimate.
+constexpr int HEAVY_FACTOR = 4;
 
 // Number of integer bins active at tick ti: particles on bin b are active
 // when ti is a multiple of 2^b, i.e. b <= ctz(ti) (every bin at tick 0).
@@ -211,5 +228,6 @@ cudaError_t launch_force(const View &v, int bin_filter, bool persistent, int gri
                          cudaStream_t st);
 cudaError_t launch_entropy_from_u(const View &v, cudaStream_t st);
 int persistent_blocks_per_sm(int G, bool density);
+cudaError_t launch_group_cost(const View &v, int grid, cudaStream_t st);
 
 }  // namespace sph

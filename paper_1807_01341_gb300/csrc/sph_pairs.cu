@@ -932,8 +932,7 @@ __global__ void __launch_bounds__(PT, 2) k_density(View v, int flags, int bin_fi
   const float hcap = (float)((w - 2.0 * (double)exc) / GAMMA_K_D * (1.0 - 1e-6));
   const int m_act = ds->m_act;
   const long long ti = ds->ti;
-  const int *q = bin_filter >= 0 ? v.q_bin : v.q_group;
-  const int nq = bin_filter >= 0 ? ds->n_bin_groups : ds->n_active_groups;
+  const int nq = bin_filter >= 0 ? ds->n_bin_groups : ds->n_active_groups + ds->n_heavy_groups;
   WarpCounters wc = {0, 0, 0, 0, 0, 0};
   if (persistent) {
     for (;;) {
@@ -941,13 +940,13 @@ __global__ void __launch_bounds__(PT, 2) k_density(View v, int flags, int bin_fi
       if (lane == 0) item = atomicAdd(&ds->head_density, 1);
       item = __shfl_sync(FULL, item, 0);
       if (item >= nq || st.failed) break;
-      const int wg = q[item];
+      const int wg = bin_filter >= 0 ? v.q_bin[item] : active_group(v, ds, item);
       density_group<G>(v, wg, flags, bin_filter, m_act, frame_of(v, ds, wg), hcap, ti, st, wc);
     }
   } else {
     const int item = blockIdx.x * WARPS_PER_BLOCK + warp;
     if (item < nq) {
-      const int wg = q[item];
+      const int wg = bin_filter >= 0 ? v.q_bin[item] : active_group(v, ds, item);
       density_group<G>(v, wg, flags, bin_filter, m_act, frame_of(v, ds, wg), hcap, ti, st, wc);
     }
   }
@@ -962,8 +961,7 @@ __global__ void __launch_bounds__(PT, 2) k_force(View v, int bin_filter, int per
   StageF st;
   stage_init(st);
   const int m_act = ds->m_act;
-  const int *q = bin_filter >= 0 ? v.q_bin : v.q_group;
-  const int nq = bin_filter >= 0 ? ds->n_bin_groups : ds->n_active_groups;
+  const int nq = bin_filter >= 0 ? ds->n_bin_groups : ds->n_active_groups + ds->n_heavy_groups;
   WarpCounters wc = {0, 0, 0, 0, 0, 0};
   if (persistent) {
     for (;;) {
@@ -971,17 +969,68 @@ __global__ void __launch_bounds__(PT, 2) k_force(View v, int bin_filter, int per
       if (lane == 0) item = atomicAdd(&ds->head_force, 1);
       item = __shfl_sync(FULL, item, 0);
       if (item >= nq || st.failed) break;
-      const int wg = q[item];
+      const int wg = bin_filter >= 0 ? v.q_bin[item] : active_group(v, ds, item);
       force_group<G>(v, wg, bin_filter, m_act, frame_of(v, ds, wg), st, wc);
     }
   } else {
     const int item = blockIdx.x * WARPS_PER_BLOCK + warp;
     if (item < nq) {
-      const int wg = q[item];
+      const int wg = bin_filter >= 0 ? v.q_bin[item] : active_group(v, ds, item);
       force_group<G>(v, wg, bin_filter, m_act, frame_of(v, ds, wg), st, wc);
     }
   }
   flush_counters(ds, wc, false);
+}
+
+// Estimated cost of each work group: the particles in the leaves (in cells of
+// more than CHUNK leaves: in the leaf chunks) that a box around the group,
+// grown by the largest support among its particles, reaches.  One warp per
+// group; the search lists nothing, its tests only count.  The sum over all
+// groups goes to group_cost_sum (the mark kernel compares each group with the
+// mean).
+__global__ void __launch_bounds__(PT, 2) k_group_cost(View v) {
+  DevState *ds = v.ds;
+  StageD st;
+  stage_init(st);
+  const int lane = lane_id();
+  const int ng = ds->n_groups;
+  const int nwarps = gridDim.x * WARPS_PER_BLOCK;
+  for (int g = blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5); g < ng; g += nwarps) {
+    const CellFrame F = frame_of(v, ds, g);
+    const Group W = group_of(v, g, F);
+    const int i = W.a + lane;  // a work group holds at most 32 particles
+    const float Hl = i < W.b ? GAMMA_K * v.h[i] : 0.0f;
+    const float R = warp_max(Hl);
+    const float qox = F.kx * F.wq, qoy = F.ky * F.wq, qoz = F.kz * F.wq;
+    const float clx = W.lx + qox, cly = W.ly + qoy, clz = W.lz + qoz;
+    const float chx = W.hx + qox, chy = W.hy + qoy, chz = W.hz + qoz;
+    const float Rc = R + 1e-5f * F.wf;
+    long long count = 0;
+    auto leaf_ok = [&](int l, float sx, float sy, float sz) {
+      if (box_gap2(W.lx, W.ly, W.lz, W.hx, W.hy, W.hz, v.leaf_lo[l], v.leaf_hi[l], sx, sy, sz) <
+          R * R * 1.0002f)
+        count += v.leaf_start[l + 1] - v.leaf_start[l];
+      return false;
+    };
+    auto chunk_ok = [&](int c, float sx, float sy, float sz) {
+      if (box_gap2(clx, cly, clz, chx, chy, chz, v.chunk_lo[c], v.chunk_hi[c], sx, sy, sz) < Rc * Rc) {
+        const int cell = v.chunk_cell[c];
+        const int la = v.cell_leaf_start[cell] + CHUNK * (c - v.cell_chunk_start[cell]);
+        const int lb = min(la + CHUNK, v.cell_leaf_start[cell + 1]);
+        count += v.leaf_start[lb] - v.leaf_start[la];
+      }
+      return false;
+    };
+    bool more = false;
+    search(v, F, st, leaf_ok, chunk_ok, 0, more);
+    for (int o = 16; o; o >>= 1) count += __shfl_xor_sync(FULL, count, o);
+    if (lane == 0) {
+      const int c = (int)min(count, (long long)0x7fffffff);
+      v.group_cost[g] = c;
+      atomicAdd(&ds->group_cost_sum, (unsigned long long)c);
+    }
+    __syncwarp();
+  }
 }
 
 // Entropy from the initial internal energy (A holds u before the first
@@ -1079,6 +1128,17 @@ int persistent_blocks_per_sm(int G, bool density) {
     case 32: return blocks_per_sm_g<32>(density);
     default: return 0;
   }
+}
+
+cudaError_t launch_group_cost(const View &v, int grid, cudaStream_t st) {
+  note_launches(1);
+  cudaError_t e = cudaFuncSetAttribute(k_group_cost, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)DENS_SMEM);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(SPH_DS_FIELD(v.ds, group_cost_sum), 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  k_group_cost<<<grid, PT, DENS_SMEM, st>>>(v);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_entropy_from_u(const View &v, cudaStream_t st) {
