@@ -153,7 +153,10 @@ def force_active(pos, vpred, m, h, rho, f, P, c, act_idx, box, alpha, gamma):
     Q = f * P / (rho * rho)
     dv = vpred[It] - vpred[Jt]
     dvdr = (dv * d).sum(dim=1)
-    wij = torch.clamp(dvdr / r, max=0.0)
+    # the switch min(0, v.r / r) is not differentiable at v.r = 0 (e.g. every
+    # pair of a state at rest): its derivative is taken as 0 there, the
+    # receding side's
+    wij = torch.where(dvdr < 0.0, dvdr / r, torch.zeros_like(dvdr))
     vsig_ij = c[It] + c[Jt] - 3.0 * wij
     Pi = -0.5 * alpha * vsig_ij * wij / (0.5 * (rho[It] + rho[Jt]))
     dWbar = 0.5 * (dWi + dWj)
