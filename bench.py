@@ -60,7 +60,7 @@ def kernel_source_digest() -> str:
     """First 16 hex digits of the SHA-256 of the pair-kernel sources."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("sph_pairs.cu", "sph_internal.cuh"):
+    for f in ("sph_pairs.cu", "sph_pairloop.cuh", "sph_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1807_01341_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

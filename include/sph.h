@@ -267,6 +267,73 @@ int sph_reset_kernel_times(sph_ctx *ctx);
 int sph_cell_order_noalloc(const double *x, const double *y, const double *z, int64_t n,
                            double box, int n_cells_per_axis, int32_t *perm, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Differentiation.  The paper has no adjoint: these calls give the gradient
+ * of a loss on a later state of a run with respect to an earlier state (up to
+ * the initial positions, velocities and internal energies), by running the
+ * steps above (Sec. II-A integration, Eq. 1 and Eq. 2 bins, the Sec. III
+ * density and force loops) backwards.  Time bins, active sets and which pairs
+ * are neighbours are piecewise constant: the backward pass takes them from
+ * the forward run.  Pair arithmetic is FP32 as in the forward loops; every
+ * adjoint accumulator is FP64.
+ * ------------------------------------------------------------------------- */
+
+/* Adjoint of a particle state (caller-owned device arrays, FP64, length n, in
+ * the same particle order as the states handed to sph_step_bwd): the
+ * derivative of the loss with respect to each field of the state. */
+typedef struct {
+  int64_t n;
+  double *x, *y, *z;    /* positions */
+  double *vx, *vy, *vz; /* velocities (the half-step velocities of the state) */
+  double *ax, *ay, *az; /* accelerations */
+  double *A, *Adot;     /* entropic function and its rate; before the first step
+                           of a run (where A holds u) A is d loss / d u */
+  double *h, *rho, *f;  /* smoothing length, density, grad-h factor */
+} sph_adjoint;
+
+/* Copy every array of src into dst (both caller-owned, same n, asynchronous).
+ * to_input_order = 0: plain copy.  to_input_order = 1: src is the state ctx
+ * works on (sorted by its cell builds) and dst receives it in the order of
+ * the first sph_build_cells call (dst[sph_perm[k]] = src[k]); src and dst must
+ * not overlap.  NULL optional arrays (ngb_*) are skipped.  Used for checkpoints. */
+int sph_state_copy(const sph_ctx *ctx, const sph_particles *src, sph_particles *dst,
+                   int to_input_order, void *stream);
+
+/* Continue a run from a state held in p: the arrays of p are taken as a new
+ * input order (the next step rebuilds the cells and sph_perm restarts from the
+ * identity), the current tick becomes ti_current, and first = 1 makes the
+ * next step the initial one (p->A holds u), first = 0 a later one.  Clears
+ * the status.  A run resumed from a state saved (in input order) before some
+ * step, on a context with the same parameters, repeats that step and the
+ * following ones bit for bit when the saved run also resumed there and
+ * threads_per_particle is 1.  Synchronising. */
+int sph_resume(sph_ctx *ctx, sph_particles *p, int64_t ti_current, int first, void *stream);
+
+/* SPH density of a state sampled on the centres of an n_grid^3 grid of the
+ * periodic box (point (a, b, c) at ((a, b, c) + 1/2) box / n_grid, index
+ * a + n_grid (b + n_grid c)): rho_g = sum_j m_j W(|x_g - x_j|, h_j) with each
+ * particle's own h, every particle taken at tick ti (x + v (ti - ti_drift)
+ * dt_min).  rho_grid (device, FP64, n_grid^3) is overwritten.  Requires
+ * GAMMA_K h < box / 2.  FP64 arithmetic.  Errors: SPH_ERR_ARG. */
+int sph_grid_density(sph_ctx *ctx, const sph_particles *p, int n_grid, int64_t ti,
+                     double *rho_grid, void *stream);
+/* Its adjoint: given rho_grid_bar = d loss / d rho_g (device, FP64), adds
+ * d loss / d x, d h and (through the drift to ti) d v to adj. */
+int sph_grid_density_bwd(sph_ctx *ctx, const sph_particles *p, int n_grid, int64_t ti,
+                         const double *rho_grid_bar, sph_adjoint *adj, void *stream);
+
+/* One kick-drift-kick step backwards.  pre and post are the states before and
+ * after a step of sph_step at tick ti (the step's current tick), both in one
+ * particle order (e.g. saved with sph_state_copy(..., 1)); first = 1 for the
+ * initial step of a run.  On entry adj holds d loss / d post; on return
+ * d loss / d pre.  pre, post and adj are read-only apart from adj.  Uses a
+ * second internal context of ctx (its own cells over internal copies), so ctx
+ * may be the one that ran the forward steps.  Synchronising.  Errors:
+ * SPH_ERR_ARG, SPH_ERR_NOMEM, SPH_ERR_CUDA, SPH_ERR_TIMEOUT (a bounded wait in
+ * a pair kernel gave up). */
+int sph_step_bwd(sph_ctx *ctx, const sph_particles *pre, const sph_particles *post, int64_t ti,
+                 int first, sph_adjoint *adj, void *stream);
+
 const char *sph_strerror(int code);
 
 #ifdef __cplusplus

@@ -50,6 +50,13 @@ class sph_particles(ctypes.Structure):
     _fields_ = [("n", _i64)] + [(name, _vp) for name, _ in PARTICLE_FIELDS]
 
 
+ADJOINT_FIELDS = ["x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az", "A", "Adot", "h", "rho", "f"]
+
+
+class sph_adjoint(ctypes.Structure):
+    _fields_ = [("n", _i64)] + [(name, _vp) for name in ADJOINT_FIELDS]
+
+
 class sph_counters(ctypes.Structure):
     _fields_ = [(k, _i64) for k in ("pairs_density", "pairs_force", "cand_density", "cand_force",
                                     "iters_density", "active_particles", "steps", "rebuilds",
@@ -103,6 +110,12 @@ def load(path: str = LIB_PATH):
     L.sph_reset_kernel_times.argtypes = [_vp]
     L.sph_cell_order_noalloc.argtypes = [_vp, _vp, _vp, _i64, _d, _i, _vp, _vp]
     L.sph_cell_order_noalloc.restype = _i
+    L.sph_state_copy.argtypes = [_vp, P(sph_particles), P(sph_particles), _i, _vp]
+    L.sph_resume.argtypes = [_vp, P(sph_particles), _i64, _i, _vp]
+    L.sph_grid_density.argtypes = [_vp, P(sph_particles), _i, _i64, _vp, _vp]
+    L.sph_grid_density_bwd.argtypes = [_vp, P(sph_particles), _i, _i64, _vp, P(sph_adjoint), _vp]
+    L.sph_step_bwd.argtypes = [_vp, P(sph_particles), P(sph_particles), _i64, _i,
+                               P(sph_adjoint), _vp]
     L.sph_strerror.argtypes = [_i]
     L.sph_strerror.restype = ctypes.c_char_p
     for name in ("sph_create", "sph_destroy", "sph_build_cells", "sph_grid_info",
@@ -111,7 +124,8 @@ def load(path: str = LIB_PATH):
                  "sph_step", "sph_step_graph", "sph_get_time",
                  "sph_set_time", "sph_get_status", "sph_clear_status", "sph_get_counters",
                  "sph_reset_counters", "sph_set_profiling", "sph_get_kernel_times",
-                 "sph_reset_kernel_times"):
+                 "sph_reset_kernel_times", "sph_state_copy", "sph_resume", "sph_grid_density",
+                 "sph_grid_density_bwd", "sph_step_bwd"):
         getattr(L, name).restype = _i
     _lib = L
     return L
@@ -126,7 +140,8 @@ def exported_symbols():
             "sph_get_time", "sph_set_time", "sph_get_status", "sph_clear_status",
             "sph_get_counters", "sph_reset_counters", "sph_set_profiling",
             "sph_get_kernel_times", "sph_reset_kernel_times", "sph_cell_order_noalloc",
-            "sph_strerror"]
+            "sph_state_copy", "sph_resume", "sph_grid_density", "sph_grid_density_bwd",
+            "sph_step_bwd", "sph_strerror"]
 
 
 class SphError(RuntimeError):

@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsph_gb300.so")
-SOURCES = ["sph_cells.cu", "sph_integrate.cu", "sph_pairs.cu", "sph_api.cu", "sph_noalloc.cu"]
+SOURCES = ["sph_cells.cu", "sph_integrate.cu", "sph_pairs.cu", "sph_adjoint.cu", "sph_api.cu",
+           "sph_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]
@@ -35,7 +36,7 @@ def _stale(obj: str, deps) -> bool:
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
-    hdrs = [os.path.join(CSRC, "sph_internal.cuh"),
+    hdrs = [os.path.join(CSRC, "sph_internal.cuh"), os.path.join(CSRC, "sph_pairloop.cuh"),
             os.path.join(os.path.dirname(HERE), "include", "sph.h")]
     objs = []
     jobs = []

@@ -62,6 +62,21 @@ struct Buffers {
   DevState *h_ds = nullptr;  // pinned host mirror
 };
 
+// Reverse-mode scratch (allocated on the first sph_step_bwd): a second
+// context whose cells are built over internal copies of the step's particles,
+// those copies, and the FP64 work arrays.
+struct AdjBuffers {
+  sph_ctx *sub = nullptr;
+  double *x = nullptr, *y = nullptr, *z = nullptr;
+  float *f32 = nullptr;       // 15 float arrays of n_max
+  int8_t *bin = nullptr;
+  int64_t *ti = nullptr;      // ti_begin, ti_end, ti_drift
+  uint8_t *active = nullptr;
+  double *work = nullptr;     // ADJ_WORK_ARRAYS double arrays of n_max
+  int grid_pairs = 0;
+};
+constexpr int ADJ_WORK_ARRAYS = 20;
+
 }  // namespace
 
 struct sph_ctx {
@@ -96,6 +111,7 @@ struct sph_ctx {
   bool graph_profiled = false;
   int graph_kernels = 0;       // kernel nodes in the captured step
   sph_particles graph_p;
+  AdjBuffers *adj = nullptr;
 };
 
 namespace {
@@ -516,6 +532,76 @@ int capture_graph(sph_ctx *ctx, sph_particles *p) {
   return SPH_OK;
 }
 
+bool valid_adjoint(const sph_adjoint *a, long long n) {
+  if (!a || a->n != n) return false;
+  if (n == 0) return true;
+  const void *req[] = {a->x, a->y, a->z, a->vx, a->vy, a->vz, a->ax, a->ay, a->az,
+                       a->A, a->Adot, a->h, a->rho, a->f};
+  for (const void *q : req)
+    if (!q) return false;
+  return true;
+}
+
+void free_adj(AdjBuffers *a) {
+  if (a->sub) sph_destroy(a->sub);
+  dfree(a->x); dfree(a->y); dfree(a->z); dfree(a->f32); dfree(a->bin); dfree(a->ti);
+  dfree(a->active); dfree(a->work);
+  delete a;
+}
+
+int ensure_adj(sph_ctx *ctx) {
+  if (ctx->adj) return SPH_OK;
+  AdjBuffers *a = new (std::nothrow) AdjBuffers();
+  if (!a) return SPH_ERR_NOMEM;
+  const long long n = std::max<long long>(ctx->n_max, 1);
+  int r = sph_create(&ctx->prm, ctx->n_max, &a->sub);
+  if (r == SPH_OK &&
+      ((r = dalloc(&a->x, n)) || (r = dalloc(&a->y, n)) || (r = dalloc(&a->z, n)) ||
+       (r = dalloc(&a->f32, 15 * n)) || (r = dalloc(&a->bin, n)) || (r = dalloc(&a->ti, 3 * n)) ||
+       (r = dalloc(&a->active, n)) || (r = dalloc(&a->work, (long long)ADJ_WORK_ARRAYS * n)))) {
+  }
+  if (r == SPH_OK) {
+    const int nb = adj_blocks_per_sm();
+    if (nb <= 0) r = SPH_ERR_CUDA;
+    a->grid_pairs = ctx->num_sms * nb;
+  }
+  if (r != SPH_OK) {
+    free_adj(a);
+    return r;
+  }
+  ctx->adj = a;
+  return SPH_OK;
+}
+
+sph_particles adj_particles(const AdjBuffers &a, long long n_max, long long n) {
+  sph_particles W;
+  std::memset(&W, 0, sizeof(W));
+  W.n = n;
+  W.x = a.x; W.y = a.y; W.z = a.z;
+  float *f[15];
+  for (int k = 0; k < 15; k++) f[k] = a.f32 + (size_t)k * n_max;
+  W.vx = f[0]; W.vy = f[1]; W.vz = f[2]; W.ax = f[3]; W.ay = f[4]; W.az = f[5];
+  W.A = f[6]; W.Adot = f[7]; W.h = f[8]; W.rho = f[9]; W.f = f[10]; W.P = f[11];
+  W.c = f[12]; W.vsig = f[13]; W.m = f[14];
+  W.bin = a.bin;
+  W.ti_begin = a.ti; W.ti_end = a.ti + n_max; W.ti_drift = a.ti + 2 * n_max;
+  W.active = a.active;
+  return W;
+}
+
+AdjWork adj_work(const AdjBuffers &a, long long n_max, const int32_t *perm) {
+  AdjWork w;
+  double *d[ADJ_WORK_ARRAYS];
+  for (int k = 0; k < ADJ_WORK_ARRAYS; k++) d[k] = a.work + (size_t)k * n_max;
+  w.perm = perm;
+  w.xb = d[0]; w.yb = d[1]; w.zb = d[2];
+  w.vpxb = d[3]; w.vpyb = d[4]; w.vpzb = d[5];
+  w.hb = d[6]; w.rhob = d[7]; w.fb = d[8]; w.Qb = d[9]; w.cb = d[10];
+  w.axb = d[11]; w.ayb = d[12]; w.azb = d[13]; w.Adotb = d[14];
+  w.ka = d[15]; w.kb = d[16]; w.km = d[17];
+  return w;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -623,6 +709,10 @@ int sph_create(const sph_params *params, int64_t n_max, sph_ctx **out) {
 int sph_destroy(sph_ctx *ctx) {
   if (!ctx) return SPH_ERR_ARG;
   cudaDeviceSynchronize();
+  if (ctx->adj) {
+    free_adj(ctx->adj);
+    ctx->adj = nullptr;
+  }
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   for (auto &kind : ctx->prof_ev)
@@ -888,6 +978,78 @@ int sph_reset_kernel_times(sph_ctx *ctx) {
   ctx->prof_n[0] = ctx->prof_n[1] = 0;
   ctx->prof_ms[0] = ctx->prof_ms[1] = 0.0;
   ctx->prof_launches[0] = ctx->prof_launches[1] = 0;
+  return SPH_OK;
+}
+
+int sph_state_copy(const sph_ctx *ctx, const sph_particles *src, sph_particles *dst,
+                   int to_input_order, void *stream) {
+  if (!ctx || !valid_particles(ctx, src) || !valid_particles(ctx, dst) || src->n != dst->n)
+    return SPH_ERR_ARG;
+  const int32_t *perm = (to_input_order && ctx->built) ? ctx->b.perm : nullptr;
+  SPH_CUDA(launch_state_copy(*src, *dst, perm, S(stream)));
+  return SPH_OK;
+}
+
+int sph_resume(sph_ctx *ctx, sph_particles *p, int64_t ti_current, int first, void *stream) {
+  if (!ctx || !valid_particles(ctx, p) || ti_current < 0) return SPH_ERR_ARG;
+  SPH_TRY(sph_set_time(ctx, ti_current, stream));
+  SPH_TRY(sph_clear_status(ctx, stream));
+  SPH_CUDA(cudaStreamSynchronize(S(stream)));
+  ctx->built = false;  // a new input order: the next step rebuilds, the permutation restarts
+  ctx->entropy_ready = !first;
+  ctx->pending = 0;
+  ctx->init_pending = false;
+  return SPH_OK;
+}
+
+int sph_grid_density(sph_ctx *ctx, const sph_particles *p, int n_grid, int64_t ti,
+                     double *rho_grid, void *stream) {
+  if (!ctx || !valid_particles(ctx, p) || n_grid < 1 || n_grid > 1024 || !rho_grid || ti < 0)
+    return SPH_ERR_ARG;
+  const size_t ng3 = (size_t)n_grid * n_grid * n_grid;
+  SPH_CUDA(cudaMemsetAsync(rho_grid, 0, ng3 * sizeof(double), S(stream)));
+  SPH_CUDA(launch_grid_density(*p, n_grid, ti, ctx->prm.dt_min, ctx->prm.box, rho_grid, nullptr,
+                               nullptr, S(stream)));
+  return SPH_OK;
+}
+
+int sph_grid_density_bwd(sph_ctx *ctx, const sph_particles *p, int n_grid, int64_t ti,
+                         const double *rho_grid_bar, sph_adjoint *adj, void *stream) {
+  if (!ctx || !valid_particles(ctx, p) || n_grid < 1 || n_grid > 1024 || !rho_grid_bar ||
+      ti < 0 || !valid_adjoint(adj, p->n))
+    return SPH_ERR_ARG;
+  SPH_CUDA(launch_grid_density(*p, n_grid, ti, ctx->prm.dt_min, ctx->prm.box, nullptr,
+                               rho_grid_bar, adj, S(stream)));
+  return SPH_OK;
+}
+
+int sph_step_bwd(sph_ctx *ctx, const sph_particles *pre, const sph_particles *post, int64_t ti,
+                 int first, sph_adjoint *adj, void *stream) {
+  if (!ctx || !valid_particles(ctx, pre) || !valid_particles(ctx, post) || post->n != pre->n ||
+      !valid_adjoint(adj, pre->n) || ti < 0)
+    return SPH_ERR_ARG;
+  const long long n = pre->n;
+  if (n == 0) return SPH_OK;
+  SPH_TRY(ensure_adj(ctx));
+  AdjBuffers &a = *ctx->adj;
+  cudaStream_t st = S(stream);
+  sph_particles W = adj_particles(a, ctx->n_max, n);
+  SPH_CUDA(launch_adj_prepare(*pre, *post, W, *adj, ti, first, ctx->prm.dt_min, ctx->prm.box,
+                              ctx->prm.gamma, st));
+  sph_ctx *sub = a.sub;
+  sub->built = false;  // the permutation of this build starts from the caller's order
+  SPH_TRY(build_cells(sub, &W, st));
+  View v = make_view(sub, &W);
+  SPH_CUDA(launch_mark(v, 1, st));  // bin 0 (the step's active particles) is active at tick 1
+  const AdjWork w = adj_work(a, ctx->n_max, sub->b.perm);
+  SPH_CUDA(launch_adj_step(v, w, *pre, *post, *adj, ti, first, a.grid_pairs, st));
+  SPH_TRY(read_state(sub, st));
+  const DevState &h = *sub->b.h_ds;
+  if (h.halt || h.first_error) {
+    const int e = h.first_error ? h.first_error : SPH_ERR_CUDA;
+    SPH_TRY(sph_clear_status(sub, stream));
+    return e;
+  }
   return SPH_OK;
 }
 

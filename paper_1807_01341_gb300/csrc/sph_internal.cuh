@@ -124,6 +124,18 @@ struct View {
   int grid_util;             // blocks of the grid-stride utility kernels
 };
 
+// Reverse-mode work arrays of one step, in the order of the backward pass's
+// own cell build (FP64 accumulators; see sph_adjoint.cu).
+struct AdjWork {
+  const int32_t *perm;           // backward-build slot -> caller index
+  double *xb, *yb, *zb;          // d loss / d position at the step's tick
+  double *vpxb, *vpyb, *vpzb;    // d loss / d predicted velocity
+  double *hb, *rhob, *fb;        // d loss / d h, rho, f as the force loop saw them
+  double *Qb, *cb;               // d loss / d (f P / rho^2), d c; then d A_pred, d u
+  double *axb, *ayb, *azb, *Adotb;  // d loss / d a, Adot computed by this step
+  double *ka, *kb, *km;          // density-adjoint coefficients of the active particles
+};
+
 // address of a DevState field on the device, computed on the host
 #define SPH_DS_FIELD(ds, field) \
   (reinterpret_cast<decltype(&((DevState *)nullptr)->field)>( \
@@ -229,5 +241,19 @@ cudaError_t launch_force(const View &v, int bin_filter, bool persistent, int gri
 cudaError_t launch_entropy_from_u(const View &v, cudaStream_t st);
 int persistent_blocks_per_sm(int G, bool density);
 cudaError_t launch_group_cost(const View &v, int grid, cudaStream_t st);
+// sph_adjoint.cu
+cudaError_t launch_adj_prepare(const sph_particles &pre, const sph_particles &post,
+                               const sph_particles &W, const sph_adjoint &adj, long long ti,
+                               int first, double dt_min, double box, double gamma,
+                               cudaStream_t st);
+cudaError_t launch_adj_step(const View &v, const AdjWork &w, const sph_particles &pre,
+                            const sph_particles &post, const sph_adjoint &adj, long long ti,
+                            int first, int grid_pairs, cudaStream_t st);
+cudaError_t launch_grid_density(const sph_particles &p, int n_grid, long long ti, double dt_min,
+                                double box, double *rho_g, const double *rho_bar,
+                                const sph_adjoint *adj, cudaStream_t st);
+cudaError_t launch_state_copy(const sph_particles &src, const sph_particles &dst,
+                              const int32_t *perm, cudaStream_t st);
+int adj_blocks_per_sm();
 
 }  // namespace sph

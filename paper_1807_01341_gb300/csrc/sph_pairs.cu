@@ -27,511 +27,11 @@
 // by persistent warps pulling items from a device counter (batched form).
 #include <cstddef>
 
-#include "sph_internal.cuh"
+#include "sph_pairloop.cuh"
 
 namespace sph {
 
 namespace {
-
-constexpr unsigned FULL = 0xffffffffu;
-constexpr int PT = WARPS_PER_BLOCK * 32;
-constexpr int S_DENS = 256;   // staged candidate records per warp, density loop
-constexpr int S_FORCE = 128;  // staged candidates per warp, force loop (3 records each)
-constexpr long long WAIT_LIMIT = 1ll << 22;  // bounded mbarrier wait (iterations)
-
-__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
-
-// ---------------------------------------------------------------------------
-// mbarrier + bulk copy (inline PTX)
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-  asm volatile(
-      "{\n\t.reg .b64 st;\n\tmbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n\t}" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0u;
-}
-
-// bounded wait for the completion of the barrier phase with this parity
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-  for (long long k = 0; k < WAIT_LIMIT; k++) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (k > 16) __nanosleep(64);
-  }
-  return false;
-}
-
-// global -> shared bulk copy (TMA), bytes a multiple of 16, both ends 16-byte aligned
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// orders this thread's earlier shared-memory reads before later bulk writes
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// ---------------------------------------------------------------------------
-// small helpers
-// ---------------------------------------------------------------------------
-// compensated accumulation: hi + lo holds the sum of the parts
-__device__ __forceinline__ void fold(float &hi, float &lo, float part) {
-  float s = hi + part;
-  float bp = s - hi;
-  float err = (hi - (s - bp)) + (part - bp);
-  hi = s;
-  lo += err;
-}
-
-template <int G>
-__device__ __forceinline__ double group_sum(double x) {
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
-  return x;
-}
-
-template <int G>
-__device__ __forceinline__ int group_sum_i(int x) {
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
-  return x;
-}
-
-template <int G>
-__device__ __forceinline__ float group_max(float x) {
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(FULL, x, o));
-  return x;
-}
-
-__device__ __forceinline__ float warp_max(float x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(FULL, x, o));
-  return x;
-}
-
-__device__ __forceinline__ int warp_incl_scan(int x) {
-  const int lane = lane_id();
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(FULL, x, o);
-    if (lane >= o) x += y;
-  }
-  return x;
-}
-
-// Active particles of leaf [a, b) (bin <= m_act, and == bin_filter when that
-// is >= 0) written to s_act in particle order; returns their number.
-__device__ __forceinline__ int leaf_actives(const View &v, int a, int b, int m_act,
-                                            int bin_filter, int *s_act) {
-  const int lane = lane_id();
-  const unsigned lt = (1u << lane) - 1u;
-  int n = 0;
-  for (int base = a; base < b; base += 32) {
-    int i = base + lane;
-    bool ok = false;
-    if (i < b) {
-      int bi = v.bin[i];
-      ok = bi <= m_act && (bin_filter < 0 || bi == bin_filter);
-    }
-    unsigned mk = __ballot_sync(FULL, ok);
-    if (ok) s_act[n + __popc(mk & lt)] = i;
-    n += __popc(mk);
-  }
-  __syncwarp();
-  return n;
-}
-
-// squared gap between box i and box j shifted by s
-__device__ __forceinline__ float box_gap2(float lix, float liy, float liz, float hix, float hiy,
-                                          float hiz, const float4 &loj, const float4 &hij, float sx,
-                                          float sy, float sz) {
-  float gx = fmaxf(0.0f, fmaxf(loj.x + sx - hix, lix - (hij.x + sx)));
-  float gy = fmaxf(0.0f, fmaxf(loj.y + sy - hiy, liy - (hij.y + sy)));
-  float gz = fmaxf(0.0f, fmaxf(loj.z + sz - hiz, liz - (hij.z + sz)));
-  return gx * gx + gy * gy + gz * gz;
-}
-
-// Whether any of the n spheres (centre, radius in w; a radius <= 0 never
-// reaches) comes within its radius of box [lo, hi] (j's box shifted by s);
-// `grow` is the leaf's own support, a lower bound of every radius when > 0.
-__device__ __forceinline__ bool spheres_reach(const float4 *sph, int n, const float4 &lo,
-                                              const float4 &hi, float sx, float sy, float sz,
-                                              float grow) {
-  const float lx = lo.x + sx, ly = lo.y + sy, lz = lo.z + sz;
-  const float hx = hi.x + sx, hy = hi.y + sy, hz = hi.z + sz;
-  for (int p = 0; p < n; p++) {
-    const float4 c = sph[p];
-    const float R = fmaxf(c.w, grow);
-    if (c.w <= 0.0f) continue;
-    const float gx = fmaxf(0.0f, fmaxf(lx - c.x, c.x - hx));
-    const float gy = fmaxf(0.0f, fmaxf(ly - c.y, c.y - hy));
-    const float gz = fmaxf(0.0f, fmaxf(lz - c.z, c.z - hz));
-    if (gx * gx + gy * gy + gz * gz < R * R * 1.0002f) return true;
-  }
-  return false;
-}
-
-// Cubic spline: w(q) / (8/pi) and w'(q) / (8/pi), q in [0, 1)
-__device__ __forceinline__ void kernel_wd(float q, float &wq, float &dwq) {
-  const float s = 1.0f - q;
-  const float s2 = s * s;
-  const float q2 = q * q;
-  const float wa = fmaf(q2, fmaf(6.0f, q, -6.0f), 1.0f);  // 1 - 6q^2 + 6q^3
-  const float da = q * fmaf(18.0f, q, -12.0f);           // -12q + 18q^2
-  const float wb = 2.0f * s2 * s;                        // 2 (1-q)^3
-  const float db = -6.0f * s2;                           // -6 (1-q)^2
-  const bool inner = q < 0.5f;
-  wq = inner ? wa : wb;
-  dwq = inner ? da : db;
-}
-
-__device__ __forceinline__ float kernel_dw(float q) {
-  const float s = 1.0f - q;
-  const float da = q * fmaf(18.0f, q, -12.0f);
-  const float db = -6.0f * s * s;
-  return q < 0.5f ? da : db;
-}
-
-struct CellFrame {
-  int cx, cy, cz, nc;
-  float wq;        // Morton grid step w / 1024
-  float wf;        // cell width
-  int kx, ky, kz;  // the work leaf's corner on its cell's Morton grid
-};
-
-__device__ __forceinline__ CellFrame frame_of(const View &v, const DevState *ds, int grp) {
-  CellFrame F;
-  const int cell = v.group_cell[grp];
-  const uint32_t k = v.leaf_k[v.group_leaf0[grp]];
-  F.nc = ds->nc;
-  F.cx = cell / (F.nc * F.nc);
-  F.cy = (cell / F.nc) % F.nc;
-  F.cz = cell % F.nc;
-  F.wq = (float)(ds->w / (double)(1 << MORTON_BITS));
-  F.wf = (float)ds->w;
-  F.kx = leaf_kx(k);
-  F.ky = leaf_ky(k);
-  F.kz = leaf_kz(k);
-  return F;
-}
-
-struct WarpCounters {
-  unsigned long long pairs, cand, iters, noconv, overflow, timeout;
-};
-
-// A work group: particles [a, b) in leaves [L0, L1) of one cell, and the
-// group's bounding box in the frame of its first leaf's corner (all lanes).
-struct Group {
-  int a, b, L0, L1;
-  float lx, ly, lz, hx, hy, hz;
-};
-
-__device__ __forceinline__ Group group_of(const View &v, int g, const CellFrame &F) {
-  Group G;
-  G.L0 = v.group_leaf0[g];
-  G.L1 = v.group_leaf0[g + 1];
-  G.a = v.leaf_start[G.L0];
-  G.b = v.leaf_start[G.L1];
-  const int lane = lane_id();
-  float lx = INFINITY, ly = INFINITY, lz = INFINITY, hx = -INFINITY, hy = -INFINITY, hz = -INFINITY;
-  if (G.L0 + lane < G.L1) {
-    const int l = G.L0 + lane;
-    const uint32_t k = v.leaf_k[l];
-    const float ox = (float)(leaf_kx(k) - F.kx) * F.wq;
-    const float oy = (float)(leaf_ky(k) - F.ky) * F.wq;
-    const float oz = (float)(leaf_kz(k) - F.kz) * F.wq;
-    const float4 lo = v.leaf_lo[l], hi = v.leaf_hi[l];
-    lx = lo.x + ox; ly = lo.y + oy; lz = lo.z + oz;
-    hx = hi.x + ox; hy = hi.y + oy; hz = hi.z + oz;
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    lx = fminf(lx, __shfl_xor_sync(FULL, lx, o));
-    ly = fminf(ly, __shfl_xor_sync(FULL, ly, o));
-    lz = fminf(lz, __shfl_xor_sync(FULL, lz, o));
-    hx = fmaxf(hx, __shfl_xor_sync(FULL, hx, o));
-    hy = fmaxf(hy, __shfl_xor_sync(FULL, hy, o));
-    hz = fmaxf(hz, __shfl_xor_sync(FULL, hz, o));
-  }
-  G.lx = lx; G.ly = ly; G.lz = lz; G.hx = hx; G.hy = hy; G.hz = hz;
-  return G;
-}
-
-// offset of particle i's leaf corner from the group frame's corner
-__device__ __forceinline__ float3 leaf_offset(const View &v, int i, const CellFrame &F) {
-  const uint32_t k = v.leaf_k[v.pleaf[i]];
-  return make_float3((float)(leaf_kx(k) - F.kx) * F.wq, (float)(leaf_ky(k) - F.ky) * F.wq,
-                     (float)(leaf_kz(k) - F.kz) * F.wq);
-}
-
-// ---------------------------------------------------------------------------
-// per-warp staging area in dynamic shared memory
-// ---------------------------------------------------------------------------
-template <int S, int NREC, int LC>
-struct Stage {
-  static constexpr int LCAP = LC;  // accepted neighbour leaves listed per search pass
-  static constexpr int CCAP = 128; // accepted chunks gathered per search segment
-  float4 *rec;     // NREC arrays of S staged records, back to back (first: positions)
-  float4 *lshift;  // per listed leaf: offset of its corner (x, y, z), first particle (w bits)
-  int *lpack;      // per listed leaf: count | cell index << 16
-  int *act;        // active particles of the work group
-  int *recj;       // per staged record: particle index
-  uint8_t *recc;   // per staged record: neighbour-cell index (0..26)
-  float4 *sph;     // the round's particles: position (group frame), search radius
-  int2 *chk;       // accepted chunks of a search segment: first leaf, count | cell << 16
-  uint64_t *bar;
-  uint32_t phase;
-  bool failed;
-  static constexpr size_t bytes() {
-    return sizeof(float4) * ((size_t)S * NREC + LC + 32) + sizeof(int2) * CCAP +
-           sizeof(int) * (LC + LEAF_MAX_LIMIT + S) + (size_t)S + 16;
-  }
-  __device__ void carve(char *base) {
-    rec = reinterpret_cast<float4 *>(base);
-    lshift = rec + (size_t)S * NREC;
-    sph = lshift + LC;
-    chk = reinterpret_cast<int2 *>(sph + 32);
-    lpack = reinterpret_cast<int *>(chk + CCAP);
-    act = lpack + LC;
-    recj = act + LEAF_MAX_LIMIT;
-    recc = reinterpret_cast<uint8_t *>(recj + S);
-    bar = reinterpret_cast<uint64_t *>(recc + S);
-  }
-};
-
-// Lane `lane` holds v_lane (lanes 0..n-1, ascending); returns, for this lane's
-// key t, the largest index c < n with v_c <= t (the segment holding t).
-__device__ __forceinline__ int seg_of(int v_lane, int n, int t) {
-  int lo = 0, hi = n - 1;
-#pragma unroll
-  for (int step = 0; step < 5; step++) {
-    const int mid = (lo + hi + 1) >> 1;
-    const int vm = __shfl_sync(FULL, v_lane, mid);
-    if (lo < hi) {
-      if (vm <= t) lo = mid;
-      else hi = mid - 1;
-    }
-  }
-  return lo;
-}
-
-// Lists, in cell-then-leaf order, the leaves of the 27 cells around the work
-// group that pass `leaf_ok` (in cells of more than CHUNK leaves, only those of
-// chunks passing `chunk_ok`): accepted leaves skip, skip + 1, ... up to LCAP
-// of them.  Returns how many were listed; `more` tells whether the list
-// stopped because it was full.  The cells' chunks, then the accepted chunks'
-// leaves, are tested 32 at a time across all 27 cells, so the number of
-// dependent global-memory rounds does not grow with the cell count.
-template <class St, class LeafOk, class ChunkOk>
-__device__ __forceinline__ int search(const View &v, const CellFrame &F, St &st, LeafOk leaf_ok,
-                                      ChunkOk chunk_ok, int skip, bool &more) {
-  constexpr int LCAP = St::LCAP;
-  constexpr int CCAP = St::CCAP;
-  const int lane = lane_id();
-  more = false;
-  const int limit = skip + LCAP;
-  // phase 1: the 27 neighbour cells, one per lane
-  int g0 = 0, nch = 0, l0 = 0, l1 = 0;
-  if (lane < 27) {
-    const int dxc = lane / 9 - 1, dyc = (lane / 3) % 3 - 1, dzc = lane % 3 - 1;
-    const int cj = (wrap_cell(F.cx + dxc, F.nc) * F.nc + wrap_cell(F.cy + dyc, F.nc)) * F.nc +
-                   wrap_cell(F.cz + dzc, F.nc);
-    g0 = v.cell_chunk_start[cj];
-    nch = v.cell_chunk_start[cj + 1] - g0;
-    l0 = v.cell_leaf_start[cj];
-    l1 = v.cell_leaf_start[cj + 1];
-  }
-  const int cstart = warp_incl_scan(nch) - nch;  // first flat chunk index of this lane's cell
-  const int T = __shfl_sync(FULL, cstart + nch, 26);
-  int seen = 0;  // accepted leaves so far
-  // phase 2: all chunks of the 27 cells, 32 per round; accepted chunks are
-  // gathered (in order) into st.chk, then phase 3 runs over their leaves
-  for (int tb = 0; tb < T; tb += 32 * 32) {
-    int nacc = 0;  // accepted chunks gathered in this segment
-    int tnext = T;
-    for (int t0 = tb; t0 < T; t0 += 32) {
-      const int t = t0 + lane;
-      const int ci = seg_of(cstart, 27, min(t, T - 1));
-      const int cg0 = __shfl_sync(FULL, g0, ci), cnch = __shfl_sync(FULL, nch, ci);
-      const int cl0 = __shfl_sync(FULL, l0, ci), cl1 = __shfl_sync(FULL, l1, ci);
-      const int cs = __shfl_sync(FULL, cstart, ci);
-      bool okc = false;
-      int la = 0, lb = 0;
-      if (t < T) {
-        const int k = t - cs;  // chunk number inside cell ci
-        la = cl0 + CHUNK * k;
-        lb = min(la + CHUNK, cl1);
-        okc = true;
-        if (cl1 - cl0 > CHUNK) {
-          const int dxc = ci / 9 - 1, dyc = (ci / 3) % 3 - 1, dzc = ci % 3 - 1;
-          okc = chunk_ok(cg0 + k, dxc * F.wf, dyc * F.wf, dzc * F.wf);
-        }
-        (void)cnch;
-      }
-      const unsigned mk = __ballot_sync(FULL, okc);
-      const int room = CCAP - nacc;
-      if (__popc(mk) > room) {  // this round does not fit: resume from it next segment
-        tnext = t0;
-        break;
-      }
-      if (okc) {
-        const int pos = nacc + __popc(mk & ((1u << lane) - 1u));
-        st.chk[pos] = make_int2(la, (lb - la) | (ci << 16));
-      }
-      nacc += __popc(mk);
-    }
-    __syncwarp();
-    // phase 3: leaves of the accepted chunks, 32 per round, in order
-    int lcount = 0;
-    if (lane < nacc) lcount = st.chk[lane].y & 0xffff;
-    // (at most 32 chunks per sub-round so that one lane holds each chunk)
-    for (int cb = 0; cb < nacc; cb += 32) {
-      const int cn = min(32, nacc - cb);
-      int2 ch = make_int2(0, 0);
-      if (lane < cn) ch = st.chk[cb + lane];
-      const int cnt_l = lane < cn ? (ch.y & 0xffff) : 0;
-      const int lst = warp_incl_scan(cnt_l) - cnt_l;
-      const int L = __shfl_sync(FULL, lst + cnt_l, 31);
-      for (int u0 = 0; u0 < L; u0 += 32) {
-        const int u = u0 + lane;
-        const int cc = seg_of(lst, cn, min(u, L - 1));
-        const int cla = __shfl_sync(FULL, ch.x, cc);
-        const int cy = __shfl_sync(FULL, ch.y, cc);
-        const int cls = __shfl_sync(FULL, lst, cc);
-        const int ci = cy >> 16;
-        bool ok = false;
-        int ja = 0, cnt = 0;
-        float sx = 0.f, sy = 0.f, sz = 0.f;
-        if (u < L) {
-          const int l = cla + (u - cls);
-          const int dxc = ci / 9 - 1, dyc = (ci / 3) % 3 - 1, dzc = ci % 3 - 1;
-          const uint32_t kl = v.leaf_k[l];
-          sx = (float)(dxc * (1 << MORTON_BITS) - F.kx + leaf_kx(kl)) * F.wq;
-          sy = (float)(dyc * (1 << MORTON_BITS) - F.ky + leaf_ky(kl)) * F.wq;
-          sz = (float)(dzc * (1 << MORTON_BITS) - F.kz + leaf_kz(kl)) * F.wq;
-          ok = leaf_ok(l, sx, sy, sz);
-          if (ok) {
-            ja = v.leaf_start[l];
-            cnt = v.leaf_start[l + 1] - ja;
-          }
-        }
-        const unsigned mk = __ballot_sync(FULL, ok);
-        const int idx = seen + __popc(mk & ((1u << lane) - 1u));
-        if (ok && idx >= skip && idx < limit) {
-          st.lshift[idx - skip] = make_float4(sx, sy, sz, __int_as_float(ja));
-          st.lpack[idx - skip] = cnt | (ci << 16);
-        }
-        seen += __popc(mk);
-        if (seen > limit) {
-          more = true;
-          __syncwarp();
-          return LCAP;
-        }
-      }
-    }
-    (void)lcount;
-    __syncwarp();
-    tb = tnext - 32 * 32;  // continue after the last gathered round
-    if (tnext >= T) break;
-  }
-  __syncwarp();
-  return max(0, min(seen - skip, LCAP));
-}
-
-// Stages the records of listed leaves [0, nlist) into shared memory by bulk
-// copies, as many leaves per batch as fit S records.  When a batch has
-// landed, each position record is moved into the work group's frame (its
-// leaf's corner offset added) and tagged with its particle index and
-// neighbour-cell index; then consume(total) sees records 0 .. total-1.
-template <int S, int NREC, int LC, class Consume>
-__device__ __forceinline__ void stage_list(const float4 *const *srcs, Stage<S, NREC, LC> &st,
-                                           int nlist, Consume consume, WarpCounters &wc) {
-  const int lane = lane_id();
-  for (int e = 0; e < nlist && !st.failed;) {
-    const bool in = e + lane < nlist;
-    const int c = in ? (st.lpack[e + lane] & 0xffff) : 0;
-    const int incl = warp_incl_scan(c);
-    const unsigned take = __ballot_sync(FULL, in && incl <= S);  // a prefix; never empty
-    const int k = __popc(take);
-    const int total = __shfl_sync(FULL, incl, k - 1);
-    if (lane == 0) mbar_expect_tx(st.bar, (uint32_t)(total * NREC * (int)sizeof(float4)));
-    __syncwarp();
-    if ((take >> lane) & 1u) {
-      const int ja = __float_as_int(st.lshift[e + lane].w);
-      const int slot = incl - c;
-      for (int r = 0; r < NREC; r++)
-        bulk_g2s(st.rec + (size_t)r * S + slot, srcs[r] + ja, (uint32_t)(c * sizeof(float4)), st.bar);
-    }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(st.bar);
-    if (!mbar_wait(st.bar, st.phase)) {
-      st.failed = true;
-      wc.timeout++;
-    }
-    st.phase ^= 1u;
-    if (!st.failed) {
-      int base = 0;
-      for (int q = 0; q < k; q++) {
-        const float4 sh = st.lshift[e + q];
-        const int pk = st.lpack[e + q];
-        const int cq = pk & 0xffff;
-        const int ja = __float_as_int(sh.w);
-        for (int t = lane; t < cq; t += 32) {
-          float4 rr = st.rec[base + t];
-          rr.x += sh.x;
-          rr.y += sh.y;
-          rr.z += sh.z;
-          st.rec[base + t] = rr;
-          st.recj[base + t] = ja + t;
-          st.recc[base + t] = (uint8_t)(pk >> 16);
-        }
-        base += cq;
-      }
-      __syncwarp();
-      consume(total);
-    }
-    wc.cand += (unsigned long long)total;
-    __syncwarp();
-    fence_proxy_async();
-    e += k;
-  }
-}
-
-using StageD = Stage<S_DENS, 1, 320>;
-using StageF = Stage<S_FORCE, 3, 256>;
 
 // ---------------------------------------------------------------------------
 // density loop + smoothing-length iteration for the active particles of a group
@@ -899,19 +399,6 @@ __device__ __forceinline__ void flush_counters(DevState *ds, WarpCounters &wc, b
   }
 }
 
-template <class St>
-__device__ __forceinline__ void stage_init(St &st) {
-  extern __shared__ __align__(16) char smem_dyn[];
-  const int warp = threadIdx.x >> 5;
-  st.carve(smem_dyn + (size_t)warp * St::bytes());
-  st.phase = 0u;
-  st.failed = false;
-  if (lane_id() == 0) {
-    mbar_init(st.bar, 1);
-    fence_mbar_init();
-  }
-  __syncwarp();
-}
 
 template <int G>
 __global__ void __launch_bounds__(PT, 2) k_density(View v, int flags, int bin_filter, int persistent) {

@@ -111,6 +111,28 @@ class Particles:
                 if getattr(self, name) is not None}
 
 
+class Adjoint:
+    """Adjoint of a particle state: FP64 device arrays d loss / d field."""
+
+    def __init__(self, n: int, device="cuda"):
+        self.n = int(n)
+        for name in _lib.ADJOINT_FIELDS:
+            setattr(self, name, torch.zeros(self.n, dtype=torch.float64, device=device))
+
+    def struct(self) -> _lib.sph_adjoint:
+        s = _lib.sph_adjoint()
+        s.n = self.n
+        for name in _lib.ADJOINT_FIELDS:
+            setattr(s, name, getattr(self, name).data_ptr())
+        self._struct = s
+        return s
+
+    def zero_(self):
+        for name in _lib.ADJOINT_FIELDS:
+            getattr(self, name).zero_()
+        return self
+
+
 class _DevArray:
     def __init__(self, ptr, n, typestr):
         self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr,
@@ -228,6 +250,39 @@ class Context:
 
     def reset_kernel_times(self):
         check(self.L.sph_reset_kernel_times(self.h), "sph_reset_kernel_times")
+
+    # -- checkpoints and the reverse pass -----------------------------------
+    def state_copy(self, src: Particles, dst: Particles, to_input_order: bool, stream=None):
+        check(self.L.sph_state_copy(self.h, ctypes.byref(src.struct()), ctypes.byref(dst.struct()),
+                                    int(bool(to_input_order)), _stream_ptr(stream)),
+              "sph_state_copy")
+
+    def resume(self, p: Particles, ti: int, first: bool, stream=None):
+        check(self.L.sph_resume(self.h, ctypes.byref(p.struct()), int(ti), int(bool(first)),
+                                _stream_ptr(stream)), "sph_resume")
+
+    def grid_density(self, p: Particles, n_grid: int, ti: int, out: torch.Tensor | None = None,
+                     stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(n_grid ** 3, dtype=torch.float64, device=p.device)
+        check(self.L.sph_grid_density(self.h, ctypes.byref(p.struct()), int(n_grid), int(ti),
+                                      ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)),
+              "sph_grid_density")
+        return out
+
+    def grid_density_bwd(self, p: Particles, n_grid: int, ti: int, rho_bar: torch.Tensor,
+                         adj: Adjoint, stream=None):
+        rho_bar = rho_bar.contiguous()
+        check(self.L.sph_grid_density_bwd(self.h, ctypes.byref(p.struct()), int(n_grid), int(ti),
+                                          ctypes.c_void_p(rho_bar.data_ptr()),
+                                          ctypes.byref(adj.struct()), _stream_ptr(stream)),
+              "sph_grid_density_bwd")
+
+    def step_bwd(self, pre: Particles, post: Particles, ti: int, first: bool, adj: Adjoint,
+                 stream=None):
+        check(self.L.sph_step_bwd(self.h, ctypes.byref(pre.struct()), ctypes.byref(post.struct()),
+                                  int(ti), int(bool(first)), ctypes.byref(adj.struct()),
+                                  _stream_ptr(stream)), "sph_step_bwd")
 
     def reset_counters(self, stream=None):
         check(self.L.sph_reset_counters(self.h, _stream_ptr(stream)), "sph_reset_counters")

@@ -52,7 +52,8 @@ def test_struct_layouts_match_header(libpath, tmp_path):
     src = tmp_path / "layout.c"
     checks = []
     for cname, cls in (("sph_params", _lib.sph_params), ("sph_particles", _lib.sph_particles),
-                       ("sph_counters", _lib.sph_counters)):
+                       ("sph_counters", _lib.sph_counters), ("sph_adjoint", _lib.sph_adjoint),
+                       ("sph_kernel_times", _lib.sph_kernel_times)):
         checks.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
         for fname, _ in cls._fields_:
             checks.append(f'printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
@@ -66,7 +67,8 @@ def test_struct_layouts_match_header(libpath, tmp_path):
                subprocess.run([str(exe)], capture_output=True, text=True).stdout.split("\n")
                if line)
     for cname, cls in (("sph_params", _lib.sph_params), ("sph_particles", _lib.sph_particles),
-                       ("sph_counters", _lib.sph_counters)):
+                       ("sph_counters", _lib.sph_counters), ("sph_adjoint", _lib.sph_adjoint),
+                       ("sph_kernel_times", _lib.sph_kernel_times)):
         assert int(out[cname]) == ctypes.sizeof(cls)
         for fname, _ in cls._fields_:
             assert int(out[f"{cname}.{fname}"]) == getattr(cls, fname).offset, (cname, fname)
