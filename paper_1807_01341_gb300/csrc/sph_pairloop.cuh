@@ -163,6 +163,15 @@ __device__ __forceinline__ float box_gap2(float lix, float liy, float liz, float
   return gx * gx + gy * gy + gz * gz;
 }
 
+// Writes the spheres (centre, radius) of the lanes with `has` set to
+// sph[0..n) in lane order and returns n (all lanes of the warp call it).
+__device__ __forceinline__ int compact_spheres(float4 *sph, bool has, float4 s) {
+  const unsigned mk = __ballot_sync(FULL, has);
+  if (has) sph[__popc(mk & ((1u << lane_id()) - 1u))] = s;
+  __syncwarp();
+  return __popc(mk);
+}
+
 // Whether any of the n spheres (centre, radius in w; a radius <= 0 never
 // reaches) comes within its radius of box [lo, hi] (j's box shifted by s);
 // `grow` is the leaf's own support, a lower bound of every radius when > 0.
@@ -327,15 +336,28 @@ __device__ __forceinline__ int seg_of(int v_lane, int n, int t) {
   return lo;
 }
 
+// What a search may reach: the work group's box in its cell's frame and the
+// largest distance at which a leaf can still pass the caller's tests (every
+// leaf test implies box distance < R).  Neighbour cells farther than R from
+// the box -- their particles may lie up to `exc` outside the cell -- are
+// skipped without reading anything.
+struct Reach {
+  float lx, ly, lz, hx, hy, hz;  // group box, cell frame
+  float R;                       // reach
+  float exc;                     // largest excursion of a particle out of its cell
+};
+
 // Lists, in cell-then-leaf order, the leaves of the 27 cells around the work
 // group that pass `leaf_ok` (in cells of more than CHUNK leaves, only those of
-// chunks passing `chunk_ok`): accepted leaves skip, skip + 1, ... up to LCAP
-// of them.  Returns how many were listed; `more` tells whether the list
-// stopped because it was full.  The cells' chunks, then the accepted chunks'
-// leaves, are tested 32 at a time across all 27 cells, so the number of
-// dependent global-memory rounds does not grow with the cell count.
+// chunks passing `chunk_ok`; cells out of `reach` entirely skipped): accepted
+// leaves skip, skip + 1, ... up to LCAP of them.  Returns how many were
+// listed; `more` tells whether the list stopped because it was full.  The
+// cells' chunks, then the accepted chunks' leaves, are tested 32 at a time
+// across all 27 cells, so the number of dependent global-memory rounds does
+// not grow with the cell count.
 template <class St, class LeafOk, class ChunkOk>
-__device__ __forceinline__ int search(const View &v, const CellFrame &F, St &st, LeafOk leaf_ok,
+__device__ __forceinline__ int search(const View &v, const CellFrame &F, const Reach &reach,
+                                      St &st, LeafOk leaf_ok,
                                       ChunkOk chunk_ok, int skip, bool &more) {
   constexpr int LCAP = St::LCAP;
   constexpr int CCAP = St::CCAP;
@@ -346,12 +368,19 @@ __device__ __forceinline__ int search(const View &v, const CellFrame &F, St &st,
   int g0 = 0, nch = 0, l0 = 0, l1 = 0;
   if (lane < 27) {
     const int dxc = lane / 9 - 1, dyc = (lane / 3) % 3 - 1, dzc = lane % 3 - 1;
-    const int cj = (wrap_cell(F.cx + dxc, F.nc) * F.nc + wrap_cell(F.cy + dyc, F.nc)) * F.nc +
-                   wrap_cell(F.cz + dzc, F.nc);
-    g0 = v.cell_chunk_start[cj];
-    nch = v.cell_chunk_start[cj + 1] - g0;
-    l0 = v.cell_leaf_start[cj];
-    l1 = v.cell_leaf_start[cj + 1];
+    // gap between the group's box and the neighbour cell (grown by exc)
+    const float e = reach.exc;
+    const float gx = fmaxf(0.0f, fmaxf(dxc * F.wf - e - reach.hx, reach.lx - ((dxc + 1) * F.wf + e)));
+    const float gy = fmaxf(0.0f, fmaxf(dyc * F.wf - e - reach.hy, reach.ly - ((dyc + 1) * F.wf + e)));
+    const float gz = fmaxf(0.0f, fmaxf(dzc * F.wf - e - reach.hz, reach.lz - ((dzc + 1) * F.wf + e)));
+    if (gx * gx + gy * gy + gz * gz < reach.R * reach.R * 1.0002f) {
+      const int cj = (wrap_cell(F.cx + dxc, F.nc) * F.nc + wrap_cell(F.cy + dyc, F.nc)) * F.nc +
+                     wrap_cell(F.cz + dzc, F.nc);
+      g0 = v.cell_chunk_start[cj];
+      nch = v.cell_chunk_start[cj + 1] - g0;
+      l0 = v.cell_leaf_start[cj];
+      l1 = v.cell_leaf_start[cj + 1];
+    }
   }
   const int cstart = warp_incl_scan(nch) - nch;  // first flat chunk index of this lane's cell
   const int T = __shfl_sync(FULL, cstart + nch, 26);
@@ -417,14 +446,16 @@ __device__ __forceinline__ int search(const View &v, const CellFrame &F, St &st,
         if (u < L) {
           const int l = cla + (u - cls);
           const int dxc = ci / 9 - 1, dyc = (ci / 3) % 3 - 1, dzc = ci % 3 - 1;
+          // every load of the round depends only on l: one memory round trip
           const uint32_t kl = v.leaf_k[l];
+          const int la = v.leaf_start[l], lb = v.leaf_start[l + 1];
           sx = (float)(dxc * (1 << MORTON_BITS) - F.kx + leaf_kx(kl)) * F.wq;
           sy = (float)(dyc * (1 << MORTON_BITS) - F.ky + leaf_ky(kl)) * F.wq;
           sz = (float)(dzc * (1 << MORTON_BITS) - F.kz + leaf_kz(kl)) * F.wq;
           ok = leaf_ok(l, sx, sy, sz);
           if (ok) {
-            ja = v.leaf_start[l];
-            cnt = v.leaf_start[l + 1] - ja;
+            ja = la;
+            cnt = lb - la;
           }
         }
         const unsigned mk = __ballot_sync(FULL, ok);
@@ -455,10 +486,13 @@ __device__ __forceinline__ int search(const View &v, const CellFrame &F, St &st,
 // landed, each position record is moved into the work group's frame (its
 // leaf's corner offset added) and tagged with its particle index and
 // neighbour-cell index; then consume(total) sees records 0 .. total-1.
+// Returns the record count when the whole list fitted one batch (the records
+// then stay resident until the next staging), else -1.
 template <int S, int NREC, int LC, class Consume>
-__device__ __forceinline__ void stage_list(const float4 *const *srcs, Stage<S, NREC, LC> &st,
-                                           int nlist, Consume consume, WarpCounters &wc) {
+__device__ __forceinline__ int stage_list(const float4 *const *srcs, Stage<S, NREC, LC> &st,
+                                          int nlist, Consume consume, WarpCounters &wc) {
   const int lane = lane_id();
+  int batches = 0, last_total = 0;
   for (int e = 0; e < nlist && !st.failed;) {
     const bool in = e + lane < nlist;
     const int c = in ? (st.lpack[e + lane] & 0xffff) : 0;
@@ -506,7 +540,10 @@ __device__ __forceinline__ void stage_list(const float4 *const *srcs, Stage<S, N
     __syncwarp();
     fence_proxy_async();
     e += k;
+    batches++;
+    last_total = total;
   }
+  return (batches == 1 && !st.failed) ? last_total : (nlist == 0 ? 0 : -1);
 }
 
 using StageD = Stage<S_DENS, 1, 320>;

@@ -42,7 +42,7 @@ namespace {
 // S_w = sum w(q), S_t = sum (3 w + q w').
 template <int G>
 __device__ void density_group(const View &v, int wg, int flags, int bin_filter, int m_act,
-                              const CellFrame &F, float hcap, long long ti,
+                              const CellFrame &F, float hcap, float exc, long long ti,
                               StageD &st, WarpCounters &wc) {
   const int lane = lane_id();
   const Group W = group_of(v, wg, F);
@@ -71,8 +71,10 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
     double lo = 0.0, hi = INFINITY;
     bool done = !valid;
     bool have_list = false;  // the leaf list in shared memory covers the round
+    int nsph = 0;            // support spheres of the round's unconverged particles
     float Ri = 0.0f;         // this particle's radius at the last search
     int nlist = 0;
+    int resident = -1;       // staged records still in shared memory (whole list), or -1
     for (int it = 0; it < v.h_max_iter && !st.failed; it++) {
       const float H = GAMMA_K * h;
       const float Hs = warp_max(done ? 0.0f : H);
@@ -129,31 +131,41 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
       const bool reuse = have_list && __all_sync(FULL, done || H <= Ri);
       if (!reuse) {
         Ri = done ? 0.0f : H * 1.05f;  // room for the next iterations to grow h
-        if (sub == 0) st.sph[grp] = make_float4(xi.x, xi.y, xi.z, Ri);
-        __syncwarp();
+        nsph = compact_spheres(st.sph, sub == 0 && Ri > 0.0f, make_float4(xi.x, xi.y, xi.z, Ri));
       }
       const float R = Hs * 1.05f;
       const float R2 = R * R * 1.0002f, Rc = R + ceps;
       auto leaf_ok = [&](int l, float sx, float sy, float sz) {
         const float4 lo = v.leaf_lo[l], hi = v.leaf_hi[l];
         return box_gap2(W.lx, W.ly, W.lz, W.hx, W.hy, W.hz, lo, hi, sx, sy, sz) < R2 &&
-               spheres_reach(st.sph, P, lo, hi, sx, sy, sz, 0.0f);
+               spheres_reach(st.sph, nsph, lo, hi, sx, sy, sz, 0.0f);
       };
       auto chunk_ok = [&](int g, float sx, float sy, float sz) {
         return box_gap2(clx, cly, clz, chx, chy, chz, v.chunk_lo[g], v.chunk_hi[g], sx, sy, sz) <
                Rc * Rc;
       };
-      int skip = 0;
-      bool more = false, complete = true;
-      do {
-        if (!reuse) {
-          nlist = search(v, F, st, leaf_ok, chunk_ok, skip, more);
-          complete = complete && !more;
-        }
-        stage_list(srcs, st, nlist, consume, wc);
-        skip += nlist;
-      } while (!reuse && more && !st.failed);
-      if (!reuse) have_list = complete;
+      const Reach reach = {clx, cly, clz, chx, chy, chz, Rc, exc};
+      if (reuse && resident >= 0) {
+        // the whole list is still staged: evaluate it again at the new h
+        consume(resident);
+        wc.cand += (unsigned long long)resident;
+        __syncwarp();
+        fence_proxy_async();
+      } else {
+        int skip = 0, passes = 0, staged = -1;
+        bool more = false, complete = true;
+        do {
+          if (!reuse) {
+            nlist = search(v, F, reach, st, leaf_ok, chunk_ok, skip, more);
+            complete = complete && !more;
+          }
+          staged = stage_list(srcs, st, nlist, consume, wc);
+          passes++;
+          skip += nlist;
+        } while (!reuse && more && !st.failed);
+        if (!reuse) have_list = complete;
+        resident = passes == 1 ? staged : -1;
+      }
       if (st.failed) break;
       fold(n_hi, n_lo, pn);
       fold(t_hi, t_lo, pt);
@@ -238,7 +250,7 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
 // ---------------------------------------------------------------------------
 template <int G>
 __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, const CellFrame &F,
-                            StageF &st, WarpCounters &wc) {
+                            float Hmax, float exc, StageF &st, WarpCounters &wc) {
   const int lane = lane_id();
   const Group W = group_of(v, wg, F);
   const int a = W.a, b = W.b;
@@ -268,8 +280,7 @@ __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, co
     const float Hinv2 = hi4.w * hi4.w;
     const float nHi4 = KERNEL_NORM * Hinv2 * Hinv2;
     const float Hs = warp_max(valid ? xi.w : 0.0f);
-    if (sub == 0) st.sph[grp] = make_float4(xi.x, xi.y, xi.z, valid ? xi.w : 0.0f);
-    __syncwarp();
+    const int nsph = compact_spheres(st.sph, sub == 0 && valid, make_float4(xi.x, xi.y, xi.z, xi.w));
     float ax_hi = 0.f, ax_lo = 0.f, ay_hi = 0.f, ay_lo = 0.f, az_hi = 0.f, az_lo = 0.f;
     float ad_hi = 0.f, ad_lo = 0.f;
     float pax = 0.f, pay = 0.f, paz = 0.f, pad = 0.f;
@@ -279,7 +290,7 @@ __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, co
       const float4 loj = v.leaf_lo[l], hij = v.leaf_hi[l];
       const float R = fmaxf(Hs, loj.w);
       return box_gap2(W.lx, W.ly, W.lz, W.hx, W.hy, W.hz, loj, hij, sx, sy, sz) < R * R * 1.0002f &&
-             spheres_reach(st.sph, P, loj, hij, sx, sy, sz, loj.w);
+             spheres_reach(st.sph, nsph, loj, hij, sx, sy, sz, loj.w);
     };
     auto chunk_ok = [&](int gg, float sx, float sy, float sz) {
       const float4 loc = v.chunk_lo[gg];
@@ -341,10 +352,12 @@ __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, co
         }
       }
     };
+    // a leaf passes only within max(Hs, its own largest H) <= max(Hs, Hmax)
+    const Reach reach = {clx, cly, clz, chx, chy, chz, fmaxf(Hs, Hmax) + ceps, exc};
     int skip = 0, nlist = 0;
     bool more = false;
     do {
-      nlist = search(v, F, st, leaf_ok, chunk_ok, skip, more);
+      nlist = search(v, F, reach, st, leaf_ok, chunk_ok, skip, more);
       stage_list(srcs, st, nlist, consume, wc);
       skip += nlist;
     } while (more && !st.failed);
@@ -428,13 +441,13 @@ __global__ void __launch_bounds__(PT, 2) k_density(View v, int flags, int bin_fi
       item = __shfl_sync(FULL, item, 0);
       if (item >= nq || st.failed) break;
       const int wg = bin_filter >= 0 ? v.q_bin[item] : active_group(v, ds, item);
-      density_group<G>(v, wg, flags, bin_filter, m_act, frame_of(v, ds, wg), hcap, ti, st, wc);
+      density_group<G>(v, wg, flags, bin_filter, m_act, frame_of(v, ds, wg), hcap, exc, ti, st, wc);
     }
   } else {
     const int item = blockIdx.x * WARPS_PER_BLOCK + warp;
     if (item < nq) {
       const int wg = bin_filter >= 0 ? v.q_bin[item] : active_group(v, ds, item);
-      density_group<G>(v, wg, flags, bin_filter, m_act, frame_of(v, ds, wg), hcap, ti, st, wc);
+      density_group<G>(v, wg, flags, bin_filter, m_act, frame_of(v, ds, wg), hcap, exc, ti, st, wc);
     }
   }
   flush_counters(ds, wc, true);
@@ -448,6 +461,8 @@ __global__ void __launch_bounds__(PT, 2) k_force(View v, int bin_filter, int per
   StageF st;
   stage_init(st);
   const int m_act = ds->m_act;
+  const float Hmax = __uint_as_float(ds->Hmax_bits);
+  const float exc = __uint_as_float(ds->excursion_bits);
   const int nq = bin_filter >= 0 ? ds->n_bin_groups : ds->n_active_groups + ds->n_heavy_groups;
   WarpCounters wc = {0, 0, 0, 0, 0, 0};
   if (persistent) {
@@ -457,13 +472,13 @@ __global__ void __launch_bounds__(PT, 2) k_force(View v, int bin_filter, int per
       item = __shfl_sync(FULL, item, 0);
       if (item >= nq || st.failed) break;
       const int wg = bin_filter >= 0 ? v.q_bin[item] : active_group(v, ds, item);
-      force_group<G>(v, wg, bin_filter, m_act, frame_of(v, ds, wg), st, wc);
+      force_group<G>(v, wg, bin_filter, m_act, frame_of(v, ds, wg), Hmax, exc, st, wc);
     }
   } else {
     const int item = blockIdx.x * WARPS_PER_BLOCK + warp;
     if (item < nq) {
       const int wg = bin_filter >= 0 ? v.q_bin[item] : active_group(v, ds, item);
-      force_group<G>(v, wg, bin_filter, m_act, frame_of(v, ds, wg), st, wc);
+      force_group<G>(v, wg, bin_filter, m_act, frame_of(v, ds, wg), Hmax, exc, st, wc);
     }
   }
   flush_counters(ds, wc, false);
@@ -509,7 +524,8 @@ __global__ void __launch_bounds__(PT, 2) k_group_cost(View v) {
       return false;
     };
     bool more = false;
-    search(v, F, st, leaf_ok, chunk_ok, 0, more);
+    const Reach reach = {clx, cly, clz, chx, chy, chz, Rc, __uint_as_float(ds->excursion_bits)};
+    search(v, F, reach, st, leaf_ok, chunk_ok, 0, more);
     for (int o = 16; o; o >>= 1) count += __shfl_xor_sync(FULL, count, o);
     if (lane == 0) {
       const int c = (int)min(count, (long long)0x7fffffff);
