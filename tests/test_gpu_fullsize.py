@@ -1,0 +1,149 @@
+"""Parity at the full sizes of the workloads, in the launch configuration the
+benchmark times (batched persistent kernels + CUDA graph, one lane per
+particle, leaf_max 16, cell margin 2), on sampled outputs the oracle computes
+one by one.
+
+* 2,097,152-particle clustered set: the first step (every particle active):
+  h and rho of a seeded sample against the oracle's density solve from the
+  same initial guesses; accelerations, dA/dt and v_sig of the sample against
+  the oracle's force loop on the GPU's own density state; time bins exact
+  (except where Delta t / t_min is within 2e-5 of a power of two).
+* 16,777,216-particle Zel'dovich set: the same checks on its first step.
+* 262,144-particle Sedov blast: three steps, then one more step of the GPU
+  against one oracle step from the GPU's state (the active particles of that
+  step are checked in full).
+Tolerances as for the small cases: h, rho rel 1e-5; a, dA/dt within 1e-4 of
+the sample's rms; v_sig rel 1e-5.
+"""
+import numpy as np
+import pytest
+
+import sph_ics
+from sph_ics import workloads
+
+pytestmark = pytest.mark.gpu
+
+LAUNCH = dict(threads_per_particle=1, leaf_max=16, cell_margin=2.0)
+
+
+@pytest.fixture(scope="module")
+def sim():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1807_01341_gb300 import build
+    build.build()
+    from paper_1807_01341_gb300 import sim as S
+    return S
+
+
+def _f64(a):
+    return np.asarray(a, dtype=np.float64)
+
+
+def _sample(h0_sorted, n_sample, seed):
+    """Half of the sample among the smallest initial h (clumps, filaments),
+    half uniform."""
+    rng = np.random.default_rng(seed)
+    n = h0_sorted.shape[0]
+    small = np.nonzero(h0_sorted < np.quantile(h0_sorted, 0.1))[0]
+    a = rng.choice(small, size=min(n_sample // 2, small.size), replace=False)
+    b = rng.choice(n, size=n_sample - a.size, replace=False)
+    return np.unique(np.concatenate([a, b]))
+
+
+def _first_step_parity(sim, orc, name, n_sample=512, seed=0):
+    from paper_1807_01341_gb300 import _lib
+    ic = workloads.make(name)
+    n = ic["pos"].shape[0]
+    params = sim.Params(**workloads.PARAMS[name], **LAUNCH)
+    ctx = sim.Context(params, n)
+    p = sim.Particles.from_ics(ic, with_counts=False)
+    ctx.build_cells(p)
+    ctx.begin_run()
+    ctx.step(p, _lib.SPH_FORM_BATCHED)
+    assert ctx.status()[0] == 0
+    perm = ctx.perm_tensor(n).cpu().numpy()
+    g = p.numpy()
+    h0 = _f64(np.float32(ic["h0"]))[perm]
+    pos = np.stack([g["x"], g["y"], g["z"]], axis=1)
+    idx = _sample(h0, n_sample, seed)
+    mask = np.zeros(n, np.uint8)
+    mask[idx] = 1
+    # density: the oracle's solve from the same guesses, for the sample only
+    ref = orc.density(pos, _f64(g["m"]), h0, mask)
+    assert ref["n_unconverged"] == 0
+    assert np.max(np.abs(g["h"][idx] / ref["h"][idx] - 1)) < 1e-5
+    assert np.max(np.abs(g["rho"][idx] / ref["rho"][idx] - 1)) < 1e-5
+    # force on the GPU's density state (inputs as the first step's force loop
+    # saw them: the initial velocities, P and c from the new entropy)
+    vel0 = _f64(ic["vel"])[perm]
+    fr = orc.force(pos, vel0, _f64(g["m"]), _f64(g["h"]), _f64(g["rho"]), _f64(g["f"]),
+                   _f64(g["P"]), _f64(g["c"]), mask)
+    a = np.stack([g["ax"], g["ay"], g["az"]], 1)[idx]
+    a_ref = fr["a"][idx]
+    a_rms = np.sqrt((a_ref ** 2).sum(1).mean())
+    assert np.max(np.abs(a - a_ref)) < 1e-4 * a_rms
+    ad_ref = fr["Adot"][idx]
+    ad_rms = np.sqrt((ad_ref ** 2).mean())
+    if ad_rms > 0:
+        assert np.max(np.abs(g["Adot"][idx] - ad_ref)) < 1e-4 * ad_rms
+    assert np.max(np.abs(g["vsig"][idx] / fr["vsig"][idx] - 1)) < 1e-5
+    # bins of the sample from the GPU's own h and v_sig (exact)
+    kw = workloads.PARAMS[name]
+    tb = orc.timestep_bins(_f64(g["h"]), _f64(g["vsig"]), mask, kw["cfl"], kw["dt_min"],
+                           kw["bin_cap"], 0, np.zeros(n, np.int8))
+    q = kw["cfl"] * _f64(g["h"][idx]) / _f64(g["vsig"][idx]) / kw["dt_min"]
+    near = np.abs(np.log2(q) - np.round(np.log2(q))) < 3e-5
+    same = tb["bin"][idx] == g["bin"][idx]
+    assert np.all(same | near)
+    ctx.close()
+
+
+def test_clustered_2m_first_step_sampled(sim, orc):
+    _first_step_parity(sim, orc, "c3_clustered_2m")
+
+
+def test_zeldovich_16m_first_step_sampled(sim, orc):
+    _first_step_parity(sim, orc, "c5_zeldovich_16m", seed=1)
+
+
+def test_sedov_262k_later_step_against_oracle_step(sim, orc):
+    """Three GPU steps of the Sedov blast, then the fourth step on the GPU and
+    on the oracle from the GPU's state: the active particles' h, rho and
+    accelerations, and the new bins."""
+    from paper_1807_01341_gb300 import _lib
+    from oracle.kdk import OracleSim
+    name = "c2_sedov_262k"
+    ic = workloads.make(name)
+    n = ic["pos"].shape[0]
+    kw = workloads.PARAMS[name]
+    params = sim.Params(**kw, **LAUNCH)
+    ctx = sim.Context(params, n)
+    p = sim.Particles.from_ics(ic, with_counts=False)
+    ctx.build_cells(p)
+    ctx.begin_run()
+    for _ in range(3):
+        ctx.step(p, _lib.SPH_FORM_BATCHED)
+    assert ctx.status()[0] == 0
+    ti = ctx.get_time()[1]
+    st = {k: v for k, v in p.numpy().items()}
+    orc_sim = OracleSim.from_state(st, ti=ti, cfl=kw["cfl"], dt_min=kw["dt_min"],
+                                   bin_cap=kw["bin_cap"], h_tol=1e-12)
+    act = orc_sim.step()
+    ctx.step(p, _lib.SPH_FORM_BATCHED)
+    assert ctx.status()[0] == 0
+    g = p.numpy()
+    assert np.array_equal(g["active"].astype(bool), act)
+    idx = np.nonzero(act)[0]
+    assert idx.size > 0
+    assert np.max(np.abs(g["h"][idx] / orc_sim.h[idx] - 1)) < 1e-5
+    assert np.max(np.abs(g["rho"][idx] / orc_sim.rho[idx] - 1)) < 1e-5
+    a = np.stack([g["ax"], g["ay"], g["az"]], 1)[idx]
+    a_ref = orc_sim.acc[idx]
+    a_rms = np.sqrt((a_ref ** 2).sum(1).mean())
+    assert np.max(np.abs(a - a_ref)) < 1e-4 * a_rms
+    q = kw["cfl"] * orc_sim.h[idx] / orc_sim.vsig[idx] / kw["dt_min"]
+    near = np.abs(np.log2(q) - np.round(np.log2(q))) < 3e-5
+    assert np.all((g["bin"][idx] == orc_sim.bin[idx]) | near)
+    ctx.close()
