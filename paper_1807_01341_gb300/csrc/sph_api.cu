@@ -157,6 +157,7 @@ bool valid_params(const sph_params *p) {
   int G = p->threads_per_particle;
   if (G != 1 && G != 2 && G != 4 && G != 8 && G != 16 && G != 32) return false;
   if (p->n_cells_override < 0 || p->n_cells_override > NC_MAX) return false;
+  if (std::isnan(p->heavy_factor)) return false;
   return true;
 }
 
@@ -227,6 +228,7 @@ View make_view(const sph_ctx *ctx, const sph_particles *p) {
   v.cfl = q.cfl;
   v.h_tol = q.h_tol;
   v.dt_min = q.dt_min;
+  v.heavy_factor = q.heavy_factor;
   v.h_max_iter = q.h_max_iter;
   v.bin_cap = q.bin_cap;
   v.leaf_max = q.leaf_max;
@@ -448,23 +450,25 @@ int plain_body(sph_ctx *ctx, const View &v, int flags, cudaStream_t st) {
   // one density launch per active bin, the grid sized from the bin's queue
   for (int k = 0; k < nb; k++) {
     SPH_CUDA(launch_mark_bin(v, bins[k], st));
-    int nq = 0;
-    SPH_CUDA(cudaMemcpyAsync(&nq, SPH_DS_FIELD(v.ds, n_bin_groups), sizeof(int),
+    int nq[2] = {0, 0};  // groups taken one per warp, heavy groups taken one per block
+    SPH_CUDA(cudaMemcpyAsync(nq, SPH_DS_FIELD(v.ds, n_bin_groups), 2 * sizeof(int),
                              cudaMemcpyDeviceToHost, st));
     SPH_CUDA(cudaStreamSynchronize(st));
     prof_begin(ctx, 0, st);
-    SPH_CUDA(launch_density(v, flags, bins[k], false, (nq + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK, st));
+    SPH_CUDA(launch_density(v, flags, bins[k], false,
+                            nq[1] + (nq[0] + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK, st));
     prof_end(ctx, 0, st);
   }
   if (flags & SPH_DENSITY_INIT_ENTROPY) SPH_CUDA(launch_entropy_from_u(v, st));
   for (int k = 0; k < nb; k++) {
     SPH_CUDA(launch_mark_bin(v, bins[k], st));
-    int nq = 0;
-    SPH_CUDA(cudaMemcpyAsync(&nq, SPH_DS_FIELD(v.ds, n_bin_groups), sizeof(int),
+    int nq[2] = {0, 0};
+    SPH_CUDA(cudaMemcpyAsync(nq, SPH_DS_FIELD(v.ds, n_bin_groups), 2 * sizeof(int),
                              cudaMemcpyDeviceToHost, st));
     SPH_CUDA(cudaStreamSynchronize(st));
     prof_begin(ctx, 1, st);
-    SPH_CUDA(launch_force(v, bins[k], false, (nq + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK, st));
+    SPH_CUDA(launch_force(v, bins[k], false,
+                          nq[1] + (nq[0] + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK, st));
     prof_end(ctx, 1, st);
   }
   SPH_CUDA(launch_kick(v, SPH_KICK_CLOSE, st));
@@ -627,6 +631,7 @@ void sph_default_params(sph_params *p) {
   p->threads_per_particle = 1;
   p->drift_all = 0;
   p->n_cells_override = 0;
+  p->heavy_factor = 0.0;
 }
 
 const char *sph_strerror(int code) {

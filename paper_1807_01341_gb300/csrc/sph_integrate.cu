@@ -53,6 +53,7 @@ __global__ void k_begin_step(View v, long long ti_arg) {
   ds->n_heavy_groups = 0;
   ds->head_density = ds->head_force = ds->head_drift = ds->head_kick = 0;
   ds->head_open = ds->head_bins = ds->head_misc = 0;
+  ds->head_coop_density = ds->head_coop_force = 0;
   ds->s_pairs_density = ds->s_pairs_force = 0ull;
   ds->s_cand_density = ds->s_cand_force = 0ull;
   ds->s_iters_density = ds->s_active_particles = 0ull;
@@ -74,7 +75,7 @@ __global__ void k_mark_leaves(View v) {
 }
 
 // One thread per work group: queues the groups whose smallest bin is active,
-// the heavy ones (estimated cost above HEAVY_FACTOR times the mean) apart so
+// the heavy ones (estimated cost above heavy_factor times the mean) apart so
 // that the pair loops start them first.
 __global__ void k_mark_groups(View v) {
   DevState *ds = v.ds;
@@ -84,8 +85,8 @@ __global__ void k_mark_groups(View v) {
     int mb = 127;
     for (int l = v.group_leaf0[g]; l < v.group_leaf0[g + 1]; l++) mb = min(mb, (int)v.leaf_min_bin[l]);
     if (mb > m_act) continue;
-    const bool heavy = (unsigned long long)v.group_cost[g] * (unsigned long long)ng >
-                       (unsigned long long)HEAVY_FACTOR * csum;
+    const bool heavy = v.heavy_factor > 0.0 &&
+                       (double)v.group_cost[g] * (double)ng > v.heavy_factor * (double)csum;
     if (heavy) v.q_group[ng - 1 - atomicAdd(&ds->n_heavy_groups, 1)] = g;
     else v.q_group[atomicAdd(&ds->n_active_groups, 1)] = g;
   }
@@ -392,14 +393,20 @@ __global__ void k_next_time(View v, long long *out, int count_step) {
   if (count_step) ds->steps += 1ull;
 }
 
+// One thread per active work group: queues the groups holding particles of
+// one bin; with one lane per particle the heavy ones go to the back of the
+// queue (blocks process them cooperatively, as in the batched form).
 __global__ void k_mark_bin(View v, int bin) {
   DevState *ds = v.ds;
-  const int nq = ds->n_active_groups + ds->n_heavy_groups;
+  const int nh = ds->n_heavy_groups, ng = ds->n_groups;
+  const int nq = ds->n_active_groups + nh;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nq; k += gridDim.x * blockDim.x) {
     const int g = active_group(v, ds, k);
     unsigned long long mask = 0ull;
     for (int l = v.group_leaf0[g]; l < v.group_leaf0[g + 1]; l++) mask |= v.leaf_bin_mask[l];
-    if ((mask >> bin) & 1ull) v.q_bin[atomicAdd(&ds->n_bin_groups, 1)] = g;
+    if (!((mask >> bin) & 1ull)) continue;
+    if (v.G == 1 && k < nh) v.q_bin[ng - 1 - atomicAdd(&ds->n_bin_coop, 1)] = g;
+    else v.q_bin[atomicAdd(&ds->n_bin_groups, 1)] = g;
   }
 }
 
@@ -446,7 +453,7 @@ cudaError_t launch_bins(const View &v, long long *ti_next_out, int count_step, c
 
 cudaError_t launch_mark_bin(const View &v, int bin, cudaStream_t st) {
   note_launches(1);
-  cudaError_t e = cudaMemsetAsync(SPH_DS_FIELD(v.ds, n_bin_groups), 0, sizeof(int), st);
+  cudaError_t e = cudaMemsetAsync(SPH_DS_FIELD(v.ds, n_bin_groups), 0, 2 * sizeof(int), st);
   if (e != cudaSuccess) return e;
   k_mark_bin<<<v.grid_util, UT, 0, st>>>(v, bin);
   return cudaGetLastError();

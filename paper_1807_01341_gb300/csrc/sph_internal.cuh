@@ -48,9 +48,11 @@ struct DevState {
   int n_active_cells;    // cells holding active particles
   int n_drift_chunks;    // leaf chunks of the cells within one cell of an active cell
   int n_bin_groups;      // plain form: active work groups holding particles of one bin
+  int n_bin_coop;        // plain form: the heavy ones among them (back of q_bin)
   // persistent-kernel work heads
   int head_density, head_force, head_drift, head_kick;
-  int head_open, head_bins, head_misc, pad2;
+  int head_open, head_bins, head_misc, head_coop_density;
+  int head_coop_force, pad2;
   // errors
   unsigned int halt;      // a step-invalidating error happened: kernels return
   int first_error;        // first SPH_ERR_* code recorded
@@ -117,9 +119,11 @@ struct View {
   int32_t *q_group;          // work groups holding active particles: light ones at
                              // [0, n_active_groups), heavy ones at n_groups - 1 - k
   int32_t *q_bin;            // plain form: active work groups holding particles of one bin
+                             // (light ones at [0, n_bin_groups), heavy ones from the back)
   DevState *ds;
   // parameters
   double box, eta, gamma, alpha, cfl, h_tol, dt_min;
+  double heavy_factor;       // heavy work group: estimated cost > heavy_factor x mean
   int h_max_iter, bin_cap, leaf_max, G, drift_all;
   int grid_util;             // blocks of the grid-stride utility kernels
 };
@@ -174,10 +178,6 @@ __device__ __forceinline__ int active_group(const View &v, const DevState *ds, i
   const int nh = ds->n_heavy_groups;
   return k < nh ? v.q_group[ds->n_groups - 1 - k] : v.q_group[k - nh];
 }
-
-// Estimated cost above which a work group counts as heavy: HEAVY_FACTOR times
-// the mean estimate.
-constexpr int HEAVY_FACTOR = 4;
 
 // Number of integer bins active at tick ti: particles on bin b are active
 // when ti is a multiple of 2^b, i.e. b <= ctz(ti) (every bin at tick 0).

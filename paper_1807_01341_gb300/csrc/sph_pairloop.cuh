@@ -349,7 +349,8 @@ struct Reach {
 
 // Lists, in cell-then-leaf order, the leaves of the 27 cells around the work
 // group that pass `leaf_ok` (in cells of more than CHUNK leaves, only those of
-// chunks passing `chunk_ok`; cells out of `reach` entirely skipped): accepted
+// chunks passing `chunk_ok`; cells out of `reach` entirely skipped; with
+// part >= 0 only chunks with index = part modulo WARPS_PER_BLOCK): accepted
 // leaves skip, skip + 1, ... up to LCAP of them.  Returns how many were
 // listed; `more` tells whether the list stopped because it was full.  The
 // cells' chunks, then the accepted chunks' leaves, are tested 32 at a time
@@ -358,7 +359,7 @@ struct Reach {
 template <class St, class LeafOk, class ChunkOk>
 __device__ __forceinline__ int search(const View &v, const CellFrame &F, const Reach &reach,
                                       St &st, LeafOk leaf_ok,
-                                      ChunkOk chunk_ok, int skip, bool &more) {
+                                      ChunkOk chunk_ok, int skip, bool &more, int part = -1) {
   constexpr int LCAP = St::LCAP;
   constexpr int CCAP = St::CCAP;
   const int lane = lane_id();
@@ -402,8 +403,10 @@ __device__ __forceinline__ int search(const View &v, const CellFrame &F, const R
         const int k = t - cs;  // chunk number inside cell ci
         la = cl0 + CHUNK * k;
         lb = min(la + CHUNK, cl1);
-        okc = true;
-        if (cl1 - cl0 > CHUNK) {
+        // part >= 0: a warp of a cooperating block takes only the chunks
+        // whose index is its warp number modulo WARPS_PER_BLOCK
+        okc = part < 0 || ((cg0 + k) & (WARPS_PER_BLOCK - 1)) == part;
+        if (okc && cl1 - cl0 > CHUNK) {
           const int dxc = ci / 9 - 1, dyc = (ci / 3) % 3 - 1, dzc = ci % 3 - 1;
           okc = chunk_ok(cg0 + k, dxc * F.wf, dyc * F.wf, dzc * F.wf);
         }

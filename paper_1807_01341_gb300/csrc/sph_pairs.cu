@@ -33,6 +33,18 @@ namespace sph {
 
 namespace {
 
+// Cooperative processing of a heavy work group: the 8 warps of a block share
+// it, each taking the neighbour chunks with its warp number modulo 8 (so the
+// partial sums of a particle depend only on the particle), and combine their
+// per-lane partial sums through shared memory in warp order.  The reduction
+// area of a warp is the start of its own staging buffer (free between
+// stagings).
+template <class St>
+__device__ __forceinline__ float *red_area(int warp) {
+  extern __shared__ __align__(16) char smem_dyn[];
+  return reinterpret_cast<float *>(smem_dyn + (size_t)warp * St::bytes());
+}
+
 // ---------------------------------------------------------------------------
 // density loop + smoothing-length iteration for the active particles of a group
 // ---------------------------------------------------------------------------
@@ -40,11 +52,15 @@ namespace {
 // h^3 n = (8/pi) S_w / GAMMA_K^3 and h dF/dh = 3 h^3 n + h^4 dn/dh, so
 // dh / h = -(S_w - C) / (3 S_w - S_t), C = eta^3 GAMMA_K^3 / (8/pi),
 // S_w = sum w(q), S_t = sum (3 w + q w').
-template <int G>
+template <int G, bool COOP>
 __device__ void density_group(const View &v, int wg, int flags, int bin_filter, int m_act,
                               const CellFrame &F, float hcap, float exc, long long ti,
                               StageD &st, WarpCounters &wc) {
+  static_assert(!COOP || G == 1, "cooperative groups use one lane per particle");
   const int lane = lane_id();
+  const int warp = threadIdx.x >> 5;
+  const int part = COOP ? warp : -1;
+  const bool writer = !COOP || warp == 0;  // the warp that writes results
   const Group W = group_of(v, wg, F);
   const int a = W.a, b = W.b;
   const int nact = leaf_actives(v, a, b, m_act, bin_filter, st.act);
@@ -156,7 +172,7 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
         bool more = false, complete = true;
         do {
           if (!reuse) {
-            nlist = search(v, F, reach, st, leaf_ok, chunk_ok, skip, more);
+            nlist = search(v, F, reach, st, leaf_ok, chunk_ok, skip, more, part);
             complete = complete && !more;
           }
           staged = stage_list(srcs, st, nlist, consume, wc);
@@ -166,16 +182,52 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
         if (!reuse) have_list = complete;
         resident = passes == 1 ? staged : -1;
       }
-      if (st.failed) break;
+      if (!COOP && st.failed) break;
       fold(n_hi, n_lo, pn);
       fold(t_hi, t_lo, pt);
       fold(r_hi, r_lo, pr);
       fold(rt_hi, rt_lo, prt);
-      const double sn = group_sum<G>((double)n_hi + (double)n_lo);
-      const double stt = group_sum<G>((double)t_hi + (double)t_lo);
-      const float sr = (float)group_sum<G>((double)r_hi + (double)r_lo);
-      const float srt = (float)group_sum<G>((double)rt_hi + (double)rt_lo);
-      cnt = group_sum_i<G>(cnt);
+      double sn, stt;
+      float sr, srt;
+      if constexpr (COOP) {
+        // combine the 8 warps' partial sums, in warp order
+        float *mine = red_area<StageD>(warp);
+        mine[0 * 32 + lane] = n_hi; mine[1 * 32 + lane] = n_lo;
+        mine[2 * 32 + lane] = t_hi; mine[3 * 32 + lane] = t_lo;
+        mine[4 * 32 + lane] = r_hi; mine[5 * 32 + lane] = r_lo;
+        mine[6 * 32 + lane] = rt_hi; mine[7 * 32 + lane] = rt_lo;
+        reinterpret_cast<int *>(mine)[8 * 32 + lane] = cnt;
+        reinterpret_cast<int *>(mine)[9 * 32 + lane] = st.failed ? 1 : 0;
+        __syncthreads();
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int c = 0, fl = 0;
+        for (int w = 0; w < WARPS_PER_BLOCK; w++) {
+          const float *rw = red_area<StageD>(w);
+          a0 += (double)rw[0 * 32 + lane] + (double)rw[1 * 32 + lane];
+          a1 += (double)rw[2 * 32 + lane] + (double)rw[3 * 32 + lane];
+          a2 += (double)rw[4 * 32 + lane] + (double)rw[5 * 32 + lane];
+          a3 += (double)rw[6 * 32 + lane] + (double)rw[7 * 32 + lane];
+          c += reinterpret_cast<const int *>(rw)[8 * 32 + lane];
+          fl |= reinterpret_cast<const int *>(rw)[9 * 32 + lane];
+        }
+        fl = __any_sync(FULL, fl != 0) ? 1 : 0;
+        __syncthreads();
+        fence_proxy_async();
+        resident = -1;  // the reduction overwrote the start of the staged records
+        if (fl) st.failed = true;
+        if (st.failed) break;  // the same decision in every warp
+        sn = a0;
+        stt = a1;
+        sr = (float)a2;
+        srt = (float)a3;
+        cnt = c;
+      } else {
+        sn = group_sum<G>((double)n_hi + (double)n_lo);
+        stt = group_sum<G>((double)t_hi + (double)t_lo);
+        sr = (float)group_sum<G>((double)r_hi + (double)r_lo);
+        srt = (float)group_sum<G>((double)rt_hi + (double)rt_lo);
+        cnt = group_sum_i<G>(cnt);
+      }
       if (!done) {
         // Newton step in FP64, kept inside the bracket [lo, hi] (F grows with h)
         const double hd = (double)h;
@@ -194,7 +246,7 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
         const bool last = it == v.h_max_iter - 1;
         if (conv || over || last) {
           done = true;
-          if (sub == 0) {
+          if (sub == 0 && writer) {
             wc.pairs += (unsigned long long)cnt;
             wc.iters += (unsigned long long)(it + 1);
             if (over) {
@@ -232,7 +284,7 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
   }
   // largest support of each leaf after the update; the chunk's keeps a bound
   __syncwarp();
-  if (W.L0 + lane < W.L1) {
+  if (writer && W.L0 + lane < W.L1) {
     const int leaf = W.L0 + lane;
     float Hm = 0.0f;
     for (int k = v.leaf_start[leaf]; k < v.leaf_start[leaf + 1]; k++) Hm = fmaxf(Hm, v.rec_xH[k].w);
@@ -248,10 +300,14 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
 // ---------------------------------------------------------------------------
 // force loop for the active particles of a group
 // ---------------------------------------------------------------------------
-template <int G>
+template <int G, bool COOP>
 __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, const CellFrame &F,
                             float Hmax, float exc, StageF &st, WarpCounters &wc) {
+  static_assert(!COOP || G == 1, "cooperative groups use one lane per particle");
   const int lane = lane_id();
+  const int warp = threadIdx.x >> 5;
+  const int part = COOP ? warp : -1;
+  const bool writer = !COOP || warp == 0;
   const Group W = group_of(v, wg, F);
   const int a = W.a, b = W.b;
   const int nact = leaf_actives(v, a, b, m_act, bin_filter, st.act);
@@ -357,22 +413,60 @@ __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, co
     int skip = 0, nlist = 0;
     bool more = false;
     do {
-      nlist = search(v, F, reach, st, leaf_ok, chunk_ok, skip, more);
+      nlist = search(v, F, reach, st, leaf_ok, chunk_ok, skip, more, part);
       stage_list(srcs, st, nlist, consume, wc);
       skip += nlist;
     } while (more && !st.failed);
-    if (st.failed) break;
+    if (!COOP && st.failed) break;
     fold(ax_hi, ax_lo, pax);
     fold(ay_hi, ay_lo, pay);
     fold(az_hi, az_lo, paz);
     fold(ad_hi, ad_lo, pad);
-    const double sax = group_sum<G>((double)ax_hi + (double)ax_lo);
-    const double say = group_sum<G>((double)ay_hi + (double)ay_lo);
-    const double saz = group_sum<G>((double)az_hi + (double)az_lo);
-    const double sad = group_sum<G>((double)ad_hi + (double)ad_lo);
-    cnt = group_sum_i<G>(cnt);
-    vs = group_max<G>(vs);
-    if (valid && sub == 0) {
+    double sax, say, saz, sad;
+    if constexpr (COOP) {
+      // combine the 8 warps' partial sums, in warp order
+      float *mine = red_area<StageF>(warp);
+      mine[0 * 32 + lane] = ax_hi; mine[1 * 32 + lane] = ax_lo;
+      mine[2 * 32 + lane] = ay_hi; mine[3 * 32 + lane] = ay_lo;
+      mine[4 * 32 + lane] = az_hi; mine[5 * 32 + lane] = az_lo;
+      mine[6 * 32 + lane] = ad_hi; mine[7 * 32 + lane] = ad_lo;
+      mine[8 * 32 + lane] = vs;
+      reinterpret_cast<int *>(mine)[9 * 32 + lane] = cnt;
+      reinterpret_cast<int *>(mine)[10 * 32 + lane] = st.failed ? 1 : 0;
+      __syncthreads();
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      float vm = 0.0f;
+      int c = 0, fl = 0;
+      for (int w = 0; w < WARPS_PER_BLOCK; w++) {
+        const float *rw = red_area<StageF>(w);
+        a0 += (double)rw[0 * 32 + lane] + (double)rw[1 * 32 + lane];
+        a1 += (double)rw[2 * 32 + lane] + (double)rw[3 * 32 + lane];
+        a2 += (double)rw[4 * 32 + lane] + (double)rw[5 * 32 + lane];
+        a3 += (double)rw[6 * 32 + lane] + (double)rw[7 * 32 + lane];
+        vm = fmaxf(vm, rw[8 * 32 + lane]);
+        c += reinterpret_cast<const int *>(rw)[9 * 32 + lane];
+        fl |= reinterpret_cast<const int *>(rw)[10 * 32 + lane];
+      }
+      fl = __any_sync(FULL, fl != 0) ? 1 : 0;
+      __syncthreads();
+      fence_proxy_async();
+      if (fl) st.failed = true;
+      if (st.failed) break;  // the same decision in every warp
+      sax = a0;
+      say = a1;
+      saz = a2;
+      sad = a3;
+      vs = vm;
+      cnt = c;
+    } else {
+      sax = group_sum<G>((double)ax_hi + (double)ax_lo);
+      say = group_sum<G>((double)ay_hi + (double)ay_lo);
+      saz = group_sum<G>((double)az_hi + (double)az_lo);
+      sad = group_sum<G>((double)ad_hi + (double)ad_lo);
+      cnt = group_sum_i<G>(cnt);
+      vs = group_max<G>(vs);
+    }
+    if (valid && sub == 0 && writer) {
       wc.pairs += (unsigned long long)cnt;
       v.ax[i] = (float)sax;
       v.ay[i] = (float)say;
@@ -387,6 +481,30 @@ __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, co
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
+// The work of a pair-loop launch: `ncoop` heavy work groups processed by
+// whole blocks (one lane per particle only), then `nwarp` groups one warp each.
+// Batched form: the step's active groups (heavy ones from the back of
+// q_group); plain form: the groups of one bin (q_bin, same layout).
+struct Queues {
+  int ncoop, nwarp;
+};
+
+template <int G>
+__device__ __forceinline__ Queues queues(const DevState *ds, int bin_filter) {
+  if (bin_filter >= 0) return {ds->n_bin_coop, ds->n_bin_groups};
+  if (G == 1) return {ds->n_heavy_groups, ds->n_active_groups};
+  return {0, ds->n_active_groups + ds->n_heavy_groups};
+}
+
+__device__ __forceinline__ int coop_group(const View &v, const DevState *ds, int bin_filter, int k) {
+  return (bin_filter >= 0 ? v.q_bin : v.q_group)[ds->n_groups - 1 - k];
+}
+
+template <int G>
+__device__ __forceinline__ int warp_group(const View &v, const DevState *ds, int bin_filter, int k) {
+  if (bin_filter >= 0) return v.q_bin[k];
+  return G == 1 ? v.q_group[k] : active_group(v, ds, k);
+}
 __device__ __forceinline__ void flush_counters(DevState *ds, WarpCounters &wc, bool density) {
   // pairs and iterations are held by group leaders; sum over the warp
   unsigned long long p = wc.pairs, it = wc.iters, nc = wc.noconv, ov = wc.overflow;
@@ -416,38 +534,71 @@ __device__ __forceinline__ void flush_counters(DevState *ds, WarpCounters &wc, b
 template <int G>
 __global__ void __launch_bounds__(PT, 2) k_density(View v, int flags, int bin_filter, int persistent) {
   DevState *ds = v.ds;
-  if (ds->halt) return;
   const int warp = threadIdx.x >> 5, lane = lane_id();
   // every support must stay inside the 27 cells around its particle's cell:
-  // H + 2 (largest excursion of a particle out of its cell) <= cell width
+  // H + 2 (largest excursion of a particle out of its cell) <= cell width.
+  // Thread 0 reads the device state once for the block, so that every warp
+  // of a block takes the same decisions (its warps meet at block barriers).
+  __shared__ int s_go;
+  __shared__ float s_exc;
   const double w = ds->w;
-  const float exc = __uint_as_float(ds->excursion_bits);
-  const float Hmax = __uint_as_float(ds->Hmax_bits);
-  if ((double)Hmax + 2.0 * (double)exc > w) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) record_error(ds, SPH_ERR_CELL_OVERFLOW, 1, true);
-    return;
+  if (threadIdx.x == 0) {
+    const float exc0 = __uint_as_float(ds->excursion_bits);
+    const float Hmax0 = __uint_as_float(ds->Hmax_bits);
+    int go = ds->halt ? 0 : 1;
+    if (go && (double)Hmax0 + 2.0 * (double)exc0 > w) {
+      record_error(ds, SPH_ERR_CELL_OVERFLOW, 1, true);
+      go = 0;
+    }
+    s_go = go;
+    s_exc = exc0;
   }
+  __syncthreads();
+  if (!s_go) return;
+  const float exc = s_exc;
   StageD st;
   stage_init(st);
   const float hcap = (float)((w - 2.0 * (double)exc) / GAMMA_K_D * (1.0 - 1e-6));
   const int m_act = ds->m_act;
   const long long ti = ds->ti;
-  const int nq = bin_filter >= 0 ? ds->n_bin_groups : ds->n_active_groups + ds->n_heavy_groups;
+  const Queues qs = queues<G>(ds, bin_filter);
   WarpCounters wc = {0, 0, 0, 0, 0, 0};
   if (persistent) {
+    if constexpr (G == 1) {
+      // heavy groups first, a block each
+      __shared__ int s_item;
+      for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(&ds->head_coop_density, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= qs.ncoop || st.failed) break;
+        const int wg = coop_group(v, ds, bin_filter, item);
+        density_group<1, true>(v, wg, flags, bin_filter, m_act, frame_of(v, ds, wg), hcap, exc, ti,
+                               st, wc);
+      }
+    }
     for (;;) {
       int item = 0;
       if (lane == 0) item = atomicAdd(&ds->head_density, 1);
       item = __shfl_sync(FULL, item, 0);
-      if (item >= nq || st.failed) break;
-      const int wg = bin_filter >= 0 ? v.q_bin[item] : active_group(v, ds, item);
-      density_group<G>(v, wg, flags, bin_filter, m_act, frame_of(v, ds, wg), hcap, exc, ti, st, wc);
+      if (item >= qs.nwarp || st.failed) break;
+      const int wg = warp_group<G>(v, ds, bin_filter, item);
+      density_group<G, false>(v, wg, flags, bin_filter, m_act, frame_of(v, ds, wg), hcap, exc, ti,
+                              st, wc);
+    }
+  } else if (G == 1 && (int)blockIdx.x < qs.ncoop) {
+    if constexpr (G == 1) {
+      const int wg = coop_group(v, ds, bin_filter, blockIdx.x);
+      density_group<1, true>(v, wg, flags, bin_filter, m_act, frame_of(v, ds, wg), hcap, exc, ti,
+                             st, wc);
     }
   } else {
-    const int item = blockIdx.x * WARPS_PER_BLOCK + warp;
-    if (item < nq) {
-      const int wg = bin_filter >= 0 ? v.q_bin[item] : active_group(v, ds, item);
-      density_group<G>(v, wg, flags, bin_filter, m_act, frame_of(v, ds, wg), hcap, exc, ti, st, wc);
+    const int item = (blockIdx.x - (G == 1 ? qs.ncoop : 0)) * WARPS_PER_BLOCK + warp;
+    if (item < qs.nwarp) {
+      const int wg = warp_group<G>(v, ds, bin_filter, item);
+      density_group<G, false>(v, wg, flags, bin_filter, m_act, frame_of(v, ds, wg), hcap, exc, ti,
+                              st, wc);
     }
   }
   flush_counters(ds, wc, true);
@@ -456,29 +607,55 @@ __global__ void __launch_bounds__(PT, 2) k_density(View v, int flags, int bin_fi
 template <int G>
 __global__ void __launch_bounds__(PT, 2) k_force(View v, int bin_filter, int persistent) {
   DevState *ds = v.ds;
-  if (ds->halt) return;
   const int warp = threadIdx.x >> 5, lane = lane_id();
+  // one read of the device state per block (its warps meet at block barriers)
+  __shared__ int s_go;
+  __shared__ float s_Hmax, s_exc;
+  if (threadIdx.x == 0) {
+    s_go = ds->halt ? 0 : 1;
+    s_Hmax = __uint_as_float(ds->Hmax_bits);
+    s_exc = __uint_as_float(ds->excursion_bits);
+  }
+  __syncthreads();
+  if (!s_go) return;
   StageF st;
   stage_init(st);
   const int m_act = ds->m_act;
-  const float Hmax = __uint_as_float(ds->Hmax_bits);
-  const float exc = __uint_as_float(ds->excursion_bits);
-  const int nq = bin_filter >= 0 ? ds->n_bin_groups : ds->n_active_groups + ds->n_heavy_groups;
+  const float Hmax = s_Hmax;
+  const float exc = s_exc;
+  const Queues qs = queues<G>(ds, bin_filter);
   WarpCounters wc = {0, 0, 0, 0, 0, 0};
   if (persistent) {
+    if constexpr (G == 1) {
+      __shared__ int s_item;
+      for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(&ds->head_coop_force, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= qs.ncoop || st.failed) break;
+        const int wg = coop_group(v, ds, bin_filter, item);
+        force_group<1, true>(v, wg, bin_filter, m_act, frame_of(v, ds, wg), Hmax, exc, st, wc);
+      }
+    }
     for (;;) {
       int item = 0;
       if (lane == 0) item = atomicAdd(&ds->head_force, 1);
       item = __shfl_sync(FULL, item, 0);
-      if (item >= nq || st.failed) break;
-      const int wg = bin_filter >= 0 ? v.q_bin[item] : active_group(v, ds, item);
-      force_group<G>(v, wg, bin_filter, m_act, frame_of(v, ds, wg), Hmax, exc, st, wc);
+      if (item >= qs.nwarp || st.failed) break;
+      const int wg = warp_group<G>(v, ds, bin_filter, item);
+      force_group<G, false>(v, wg, bin_filter, m_act, frame_of(v, ds, wg), Hmax, exc, st, wc);
+    }
+  } else if (G == 1 && (int)blockIdx.x < qs.ncoop) {
+    if constexpr (G == 1) {
+      const int wg = coop_group(v, ds, bin_filter, blockIdx.x);
+      force_group<1, true>(v, wg, bin_filter, m_act, frame_of(v, ds, wg), Hmax, exc, st, wc);
     }
   } else {
-    const int item = blockIdx.x * WARPS_PER_BLOCK + warp;
-    if (item < nq) {
-      const int wg = bin_filter >= 0 ? v.q_bin[item] : active_group(v, ds, item);
-      force_group<G>(v, wg, bin_filter, m_act, frame_of(v, ds, wg), Hmax, exc, st, wc);
+    const int item = (blockIdx.x - (G == 1 ? qs.ncoop : 0)) * WARPS_PER_BLOCK + warp;
+    if (item < qs.nwarp) {
+      const int wg = warp_group<G>(v, ds, bin_filter, item);
+      force_group<G, false>(v, wg, bin_filter, m_act, frame_of(v, ds, wg), Hmax, exc, st, wc);
     }
   }
   flush_counters(ds, wc, false);

@@ -39,6 +39,7 @@ class Params:
     threads_per_particle: int = 1
     drift_all: int = 0
     n_cells_override: int = 0
+    heavy_factor: float = 0.0
 
     def to_c(self) -> _lib.sph_params:
         p = _lib.sph_params()

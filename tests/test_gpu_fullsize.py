@@ -108,6 +108,44 @@ def test_zeldovich_16m_first_step_sampled(sim, orc):
     _first_step_parity(sim, orc, "c5_zeldovich_16m", seed=1)
 
 
+def test_clustered_2m_later_steps_against_oracle_step(sim, orc):
+    """Twelve steps of the clustered set (individual bins, relevant-only
+    drift, leaf lists resident across Newton iterations), then one more GPU
+    step against one oracle step from the GPU's state: every active particle
+    checked."""
+    from paper_1807_01341_gb300 import _lib
+    from oracle.kdk import OracleSim
+    name = "c3_clustered_2m"
+    ic = workloads.make(name)
+    n = ic["pos"].shape[0]
+    kw = workloads.PARAMS[name]
+    ctx = sim.Context(sim.Params(**kw, **LAUNCH), n)
+    p = sim.Particles.from_ics(ic, with_counts=False)
+    ctx.build_cells(p)
+    ctx.begin_run()
+    for _ in range(12):
+        ctx.step(p, _lib.SPH_FORM_BATCHED)
+        assert ctx.status()[0] == 0
+    ti = ctx.get_time()[1]
+    st = p.numpy()
+    osim = OracleSim.from_state(st, ti=ti, cfl=kw["cfl"], dt_min=kw["dt_min"],
+                                bin_cap=kw["bin_cap"], h_tol=1e-12)
+    act = osim.step()
+    ctx.step(p, _lib.SPH_FORM_BATCHED)
+    assert ctx.status()[0] == 0
+    g = p.numpy()
+    assert np.array_equal(g["active"].astype(bool), act)
+    idx = np.nonzero(act)[0]
+    assert idx.size > 0
+    assert np.max(np.abs(g["h"][idx] / osim.h[idx] - 1)) < 1e-5
+    assert np.max(np.abs(g["rho"][idx] / osim.rho[idx] - 1)) < 1e-5
+    a = np.stack([g["ax"], g["ay"], g["az"]], 1)[idx]
+    a_ref = osim.acc[idx]
+    a_rms = np.sqrt((a_ref ** 2).sum(1).mean())
+    assert np.max(np.abs(a - a_ref)) < 1e-4 * a_rms
+    ctx.close()
+
+
 def test_sedov_262k_later_step_against_oracle_step(sim, orc):
     """Three GPU steps of the Sedov blast, then the fourth step on the GPU and
     on the oracle from the GPU's state: the active particles' h, rho and

@@ -38,14 +38,16 @@ def _ic_step(seed=13, nside=12):
 STEP_PARAMS = dict(dt_min=1e-6, bin_cap=14, cfl=0.1)
 
 
-def test_step_parity_each_step_from_same_state(sim, orc):
+@pytest.mark.parametrize("heavy_factor", [0.0, 1e-9])
+def test_step_parity_each_step_from_same_state(sim, orc, heavy_factor):
     """Before every GPU step the oracle integrator is loaded with the GPU's
     state and advanced one step: active sets and bins must agree exactly
     (bins up to dt values within 2e-5 of a power of two), and the floating
-    point state within the hot-path tolerances."""
+    point state within the hot-path tolerances.  heavy_factor 1e-9 sends every
+    work group through the block-cooperative path."""
     ic = _ic_step()
     n = ic["pos"].shape[0]
-    ctx, p = gpu_setup(ic, sim.Params(**STEP_PARAMS))
+    ctx, p = gpu_setup(ic, sim.Params(**STEP_PARAMS, heavy_factor=heavy_factor))
     L = _lib()
     n_partial = 0
     for k in range(10):
@@ -100,10 +102,14 @@ def _run_form(sim, ic, form, steps, params):
     return p.numpy(), ctx.counters(), ctx.get_time()
 
 
-def test_plain_batched_graph_bitwise_identical(sim):
-    """One lane per particle: every sum's order depends on the particle only."""
+@pytest.mark.parametrize("heavy_factor", [0.0, 1.0, 1e-9])
+def test_plain_batched_graph_bitwise_identical(sim, heavy_factor):
+    """One lane per particle: every sum's order depends on the particle only,
+    also when heavy work groups are shared by the warps of a block (factor 1:
+    some groups, factor 1e-9: all)."""
     ic = _ic_step(seed=17)
-    res = {f: _run_form(sim, ic, f, 12, STEP_PARAMS) for f in ("plain", "batched", "graph")}
+    params = dict(STEP_PARAMS, heavy_factor=heavy_factor)
+    res = {f: _run_form(sim, ic, f, 12, params) for f in ("plain", "batched", "graph")}
     ref, cref, tref = res["batched"]
     for f in ("plain", "graph"):
         st, c, t = res[f]
