@@ -163,6 +163,14 @@ __device__ __forceinline__ float box_gap2(float lix, float liy, float liz, float
   return gx * gx + gy * gy + gz * gz;
 }
 
+// Candidate test of a staged block of 32 records with the records across the
+// lanes: one ballot per live particle (tst[0..ntst), lane order) gives that
+// particle's accept mask, which lands on the lane whose rank among the live
+// lanes is the particle's.  Each (particle, record) test is the very
+// expression of the per-lane test, so the masks are the same bits; for few
+// live particles it costs ntst votes instead of 32 serial tests per lane.
+constexpr int TRANSPOSE_MAX = 24;
+
 // Writes the spheres (centre, radius) of the lanes with `has` set to
 // sph[0..n) in lane order and returns n (all lanes of the warp call it).
 __device__ __forceinline__ int compact_spheres(float4 *sph, bool has, float4 s) {
@@ -299,19 +307,21 @@ struct Stage {
   int *recj;       // per staged record: particle index
   uint8_t *recc;   // per staged record: neighbour-cell index (0..26)
   float4 *sph;     // the round's particles: position (group frame), search radius
+  float4 *tst;     // the round's live particles: position (group frame), squared support
   int2 *chk;       // accepted chunks of a search segment: first leaf, count | cell << 16
   uint64_t *bar;
   uint32_t phase;
   bool failed;
   static constexpr size_t bytes() {
-    return sizeof(float4) * ((size_t)S * NREC + LC + 32) + sizeof(int2) * CCAP +
+    return sizeof(float4) * ((size_t)S * NREC + LC + 64) + sizeof(int2) * CCAP +
            sizeof(int) * (LC + LEAF_MAX_LIMIT + S) + (size_t)S + 16;
   }
   __device__ void carve(char *base) {
     rec = reinterpret_cast<float4 *>(base);
     lshift = rec + (size_t)S * NREC;
     sph = lshift + LC;
-    chk = reinterpret_cast<int2 *>(sph + 32);
+    tst = sph + 32;
+    chk = reinterpret_cast<int2 *>(tst + 32);
     lpack = reinterpret_cast<int *>(chk + CCAP);
     act = lpack + LC;
     recj = act + LEAF_MAX_LIMIT;

@@ -102,15 +102,36 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
       int cur = -1, cnt = 0;
       // test 32 staged records per pass without branching, then evaluate the
       // accepted ones; partial sums are folded at neighbour-cell boundaries
+      // the live particles of the round, for the transposed candidate test
+      int ntst = 32 + 1, my_rank = 0;
+      if constexpr (G == 1) {
+        const unsigned vm = __ballot_sync(FULL, !done);
+        ntst = __popc(vm);
+        my_rank = __popc(vm & ((1u << lane) - 1u));
+        if (!done) st.tst[my_rank] = make_float4(xi.x, xi.y, xi.z, H2);
+        __syncwarp();
+      }
       auto consume = [&](int total) {
         for (int k0 = 0; k0 < total; k0 += 32) {
           unsigned mask = 0u;
+          if (G == 1 && ntst <= TRANSPOSE_MAX) {
+            const bool in = k0 + lane < total;
+            const float4 pj = st.rec[min(k0 + lane, S_DENS - 1)];
+            for (int q = 0; q < ntst; q++) {
+              const float4 t = st.tst[q];
+              const float dx = t.x - pj.x, dy = t.y - pj.y, dz = t.z - pj.z;
+              const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+              const unsigned m = __ballot_sync(FULL, in && r2 < t.w);
+              if (q == my_rank) mask = m;
+            }
+          } else {
 #pragma unroll
-          for (int u = sub; u < 32; u += G) {
-            const float4 pj = st.rec[min(k0 + u, S_DENS - 1)];
-            const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            mask |= (k0 + u < total && r2 < H2) ? (1u << u) : 0u;
+            for (int u = sub; u < 32; u += G) {
+              const float4 pj = st.rec[min(k0 + u, S_DENS - 1)];
+              const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
+              const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+              mask |= (k0 + u < total && r2 < H2) ? (1u << u) : 0u;
+            }
           }
           if (done) mask = 0u;
           while (mask) {
@@ -353,15 +374,37 @@ __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, co
       const float R = fmaxf(Hs, loc.w) + ceps;
       return box_gap2(clx, cly, clz, chx, chy, chz, loc, v.chunk_hi[gg], sx, sy, sz) < R * R;
     };
+    // the valid particles of the round, for the transposed candidate test
+    int ntst = 32 + 1, my_rank = 0;
+    if constexpr (G == 1) {
+      const unsigned vm = __ballot_sync(FULL, valid);
+      ntst = __popc(vm);
+      my_rank = __popc(vm & ((1u << lane) - 1u));
+      if (valid) st.tst[my_rank] = make_float4(xi.x, xi.y, xi.z, Hi2);
+      __syncwarp();
+    }
     auto consume = [&](int total) {
       for (int k0 = 0; k0 < total; k0 += 32) {
         unsigned mask = 0u;
+        if (G == 1 && ntst <= TRANSPOSE_MAX) {
+          const bool in = k0 + lane < total;
+          const float4 pj = sx_rec[min(k0 + lane, S_FORCE - 1)];
+          const float Hj2 = pj.w * pj.w;
+          for (int q = 0; q < ntst; q++) {
+            const float4 t = st.tst[q];
+            const float dx = t.x - pj.x, dy = t.y - pj.y, dz = t.z - pj.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const unsigned m = __ballot_sync(FULL, in && (r2 < t.w || r2 < Hj2));
+            if (q == my_rank) mask = m;
+          }
+        } else {
 #pragma unroll
-        for (int u = sub; u < 32; u += G) {
-          const float4 pj = sx_rec[min(k0 + u, S_FORCE - 1)];
-          const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
-          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          mask |= (k0 + u < total && (r2 < Hi2 || r2 < pj.w * pj.w)) ? (1u << u) : 0u;
+          for (int u = sub; u < 32; u += G) {
+            const float4 pj = sx_rec[min(k0 + u, S_FORCE - 1)];
+            const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            mask |= (k0 + u < total && (r2 < Hi2 || r2 < pj.w * pj.w)) ? (1u << u) : 0u;
+          }
         }
         if (!valid) mask = 0u;
         while (mask) {
