@@ -165,7 +165,7 @@ int sph_kick_drift(sph_ctx *ctx, sph_particles *p, int phase, void *stream);
 enum { SPH_DENSITY_INIT_ENTROPY = 1 }; /* p->A holds u on input; set A from u and rho */
 /* Density loop with the smoothing-length iteration ("ghost", Sec. III-B) for
  * the active particles: solves h^3 n(h) = eta^3 by a bracket-safeguarded
- * Newton iteration (each iteration one pass over the neighbour leaves), then
+ * Halley iteration (each iteration one pass over the neighbour leaves), then
  * writes h, rho, f (grad-h factor), P and c (from the predicted entropy).
  * Cubic-spline kernel with support H = 1.825742 h.  FP32 pair arithmetic on
  * cell-relative coordinates, compensated accumulation, FP64 convergence test. */

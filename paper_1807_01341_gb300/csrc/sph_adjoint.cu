@@ -39,11 +39,6 @@ namespace {
 
 constexpr double KN_D = 2.5464790894703255;  // 8 / pi
 
-__device__ __forceinline__ float kernel_d2w(float q) {
-  // w''(q) / (8/pi): -12 + 36 q (q < 1/2), 12 (1 - q) (q < 1)
-  return q < 0.5f ? fmaf(36.0f, q, -12.0f) : 12.0f * (1.0f - q);
-}
-
 __device__ __forceinline__ double wrap_box(double x, double box) {
   if (x < 0.0) x += box;
   if (x >= box) x -= box;

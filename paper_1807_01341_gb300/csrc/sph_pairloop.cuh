@@ -214,6 +214,11 @@ __device__ __forceinline__ void kernel_wd(float q, float &wq, float &dwq) {
   dwq = inner ? da : db;
 }
 
+// w''(q) / (8/pi): -12 + 36 q (q < 1/2), 12 (1 - q) (q < 1)
+__device__ __forceinline__ float kernel_d2w(float q) {
+  return q < 0.5f ? fmaf(36.0f, q, -12.0f) : 12.0f * (1.0f - q);
+}
+
 __device__ __forceinline__ float kernel_dw(float q) {
   const float s = 1.0f - q;
   const float da = q * fmaf(18.0f, q, -12.0f);

@@ -99,6 +99,7 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
       float n_hi = 0.f, n_lo = 0.f, t_hi = 0.f, t_lo = 0.f;
       float r_hi = 0.f, r_lo = 0.f, rt_hi = 0.f, rt_lo = 0.f;
       float pn = 0.f, pt = 0.f, pr = 0.f, prt = 0.f;
+      float p2 = 0.f;  // sum q^2 w'' (the second derivative of the h equation)
       int cur = -1, cnt = 0;
       // test 32 staged records per pass without branching, then evaluate the
       // accepted ones; partial sums are folded at neighbour-cell boundaries
@@ -154,6 +155,7 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
             float wq, dwq;
             kernel_wd(qq, wq, dwq);
             const float tt = fmaf(qq, dwq, 3.0f * wq);
+            p2 = fmaf(qq * qq, kernel_d2w(qq), p2);
             pn += wq;
             pt += tt;
             pr = fmaf(pj.w, wq, pr);
@@ -208,7 +210,7 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
       fold(t_hi, t_lo, pt);
       fold(r_hi, r_lo, pr);
       fold(rt_hi, rt_lo, prt);
-      double sn, stt;
+      double sn, stt, s2;
       float sr, srt;
       if constexpr (COOP) {
         // combine the 8 warps' partial sums, in warp order
@@ -219,8 +221,9 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
         mine[6 * 32 + lane] = rt_hi; mine[7 * 32 + lane] = rt_lo;
         reinterpret_cast<int *>(mine)[8 * 32 + lane] = cnt;
         reinterpret_cast<int *>(mine)[9 * 32 + lane] = st.failed ? 1 : 0;
+        mine[10 * 32 + lane] = p2;
         __syncthreads();
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, a4 = 0.0;
         int c = 0, fl = 0;
         for (int w = 0; w < WARPS_PER_BLOCK; w++) {
           const float *rw = red_area<StageD>(w);
@@ -230,6 +233,7 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
           a3 += (double)rw[6 * 32 + lane] + (double)rw[7 * 32 + lane];
           c += reinterpret_cast<const int *>(rw)[8 * 32 + lane];
           fl |= reinterpret_cast<const int *>(rw)[9 * 32 + lane];
+          a4 += (double)rw[10 * 32 + lane];
         }
         fl = __any_sync(FULL, fl != 0) ? 1 : 0;
         __syncthreads();
@@ -241,25 +245,35 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
         stt = a1;
         sr = (float)a2;
         srt = (float)a3;
+        s2 = a4;
         cnt = c;
       } else {
         sn = group_sum<G>((double)n_hi + (double)n_lo);
         stt = group_sum<G>((double)t_hi + (double)t_lo);
         sr = (float)group_sum<G>((double)r_hi + (double)r_lo);
         srt = (float)group_sum<G>((double)rt_hi + (double)rt_lo);
+        s2 = group_sum<G>((double)p2);
         cnt = group_sum_i<G>(cnt);
       }
       if (!done) {
-        // Newton step in FP64, kept inside the bracket [lo, hi] (F grows with h)
+        // Halley step in FP64 (Newton where its denominator is not positive),
+        // kept inside the bracket [lo, hi] (F grows with h).  With
+        // g = S_w - C: a = h g' = 3 S_w - S_t, b = h^2 g'' = sum q^2 w'' - 2 a,
+        // dh / h = -2 g a / (2 a^2 - g b)
         const double hd = (double)h;
-        const double Fr = sn - Cw;              // sign of F(h)
-        const double dFr = 3.0 * sn - stt;      // h dF/dh, same scale
+        const double Fr = sn - Cw;              // g, the sign of F(h)
+        const double dFr = 3.0 * sn - stt;      // a
         if (Fr < 0.0) lo = hd;
         else hi = hd;
         double hn;
-        if (Fr == 0.0) hn = hd;
-        else if (dFr > 0.0) hn = hd - hd * (Fr / dFr);
-        else hn = NAN;
+        if (Fr == 0.0) {
+          hn = hd;
+        } else if (dFr > 0.0) {
+          const double den = 2.0 * dFr * dFr - Fr * (s2 - 2.0 * dFr);
+          hn = den > 0.0 ? hd - hd * (2.0 * Fr * dFr / den) : hd - hd * (Fr / dFr);
+        } else {
+          hn = NAN;
+        }
         if (!(hn >= lo && hn <= hi)) hn = isinf(hi) ? 2.0 * hd : 0.5 * (lo + hi);
         hn = fmin(fmax(hn, 0.5 * hd), 2.0 * hd);
         const bool conv = fabs(hn - hd) <= v.h_tol * hd;
