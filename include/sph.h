@@ -50,7 +50,8 @@ enum sph_status_code {
 /* Parameters.  Defaults (sph_default_params): eta 1.2348, gamma 5/3,
  * alpha_visc 0.8, cfl 0.1, h_tol 1e-6, h_max_iter 30, bin_cap 20,
  * dt_min 1e-6, t_begin 0, box 1, cell_margin 2.0, leaf_max 8,
- * threads_per_particle 1, drift_all 0, n_cells_override 0, heavy_factor 0.
+ * threads_per_particle 1, drift_all 0, n_cells_override 0, heavy_factor 0,
+ * coop_max_groups -1.
  * With threads_per_particle = 1 every sum of a particle is taken in an order
  * that depends on the particle alone, so SPH_FORM_PLAIN and SPH_FORM_BATCHED
  * give bit-identical results; with more lanes per particle they agree to
@@ -76,6 +77,9 @@ typedef struct {
                            heavy_factor times the mean is started first and, with one
                            lane per particle, shared by the 8 warps of a block; <= 0: no
                            group is treated so */
+  int coop_max_groups;  /* with one lane per particle: a step with at most this many
+                           active work groups hands every one to the 8 warps of a block
+                           (0: never; -1: twice the persistent grid's block count) */
 } sph_params;
 
 /* Particle state, structure of arrays, all device pointers of length n.

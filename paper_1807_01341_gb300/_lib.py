@@ -36,7 +36,7 @@ class sph_params(ctypes.Structure):
                 ("h_tol", _d), ("h_max_iter", _i), ("bin_cap", _i), ("dt_min", _d),
                 ("t_begin", _d), ("cell_margin", _d), ("leaf_max", _i),
                 ("threads_per_particle", _i), ("drift_all", _i), ("n_cells_override", _i),
-                ("heavy_factor", _d)]
+                ("heavy_factor", _d), ("coop_max_groups", _i)]
 
 
 PARTICLE_FIELDS = [("x", "f8"), ("y", "f8"), ("z", "f8"), ("vx", "f4"), ("vy", "f4"),

@@ -394,8 +394,9 @@ __global__ void k_next_time(View v, long long *out, int count_step) {
 }
 
 // One thread per active work group: queues the groups holding particles of
-// one bin; with one lane per particle the heavy ones go to the back of the
-// queue (blocks process them cooperatively, as in the batched form).
+// one bin; with one lane per particle the heavy ones (all of them in a step
+// with few active groups) go to the back of the queue (blocks process them
+// cooperatively, as in the batched form).
 __global__ void k_mark_bin(View v, int bin) {
   DevState *ds = v.ds;
   const int nh = ds->n_heavy_groups, ng = ds->n_groups;
@@ -405,7 +406,7 @@ __global__ void k_mark_bin(View v, int bin) {
     unsigned long long mask = 0ull;
     for (int l = v.group_leaf0[g]; l < v.group_leaf0[g + 1]; l++) mask |= v.leaf_bin_mask[l];
     if (!((mask >> bin) & 1ull)) continue;
-    if (v.G == 1 && k < nh) v.q_bin[ng - 1 - atomicAdd(&ds->n_bin_coop, 1)] = g;
+    if (v.G == 1 && (k < nh || all_coop(v, ds))) v.q_bin[ng - 1 - atomicAdd(&ds->n_bin_coop, 1)] = g;
     else v.q_bin[atomicAdd(&ds->n_bin_groups, 1)] = g;
   }
 }

@@ -124,6 +124,7 @@ struct View {
   // parameters
   double box, eta, gamma, alpha, cfl, h_tol, dt_min;
   double heavy_factor;       // heavy work group: estimated cost > heavy_factor x mean
+  int coop_max_groups;       // steps with at most this many active groups: all cooperative
   int h_max_iter, bin_cap, leaf_max, G, drift_all;
   int grid_util;             // blocks of the grid-stride utility kernels
 };
@@ -177,6 +178,12 @@ __device__ __forceinline__ int wrap_cell(int c, int nc) {
 __device__ __forceinline__ int active_group(const View &v, const DevState *ds, int k) {
   const int nh = ds->n_heavy_groups;
   return k < nh ? v.q_group[ds->n_groups - 1 - k] : v.q_group[k - nh];
+}
+
+// Whether this step hands every active work group to a whole block (one lane
+// per particle, few active groups: warps would otherwise idle).
+__device__ __forceinline__ bool all_coop(const View &v, const DevState *ds) {
+  return v.G == 1 && ds->n_active_groups + ds->n_heavy_groups <= v.coop_max_groups;
 }
 
 // Number of integer bins active at tick ti: particles on bin b are active

@@ -547,14 +547,16 @@ struct Queues {
 };
 
 template <int G>
-__device__ __forceinline__ Queues queues(const DevState *ds, int bin_filter) {
+__device__ __forceinline__ Queues queues(const View &v, const DevState *ds, int bin_filter) {
   if (bin_filter >= 0) return {ds->n_bin_coop, ds->n_bin_groups};
+  if (G == 1 && all_coop(v, ds)) return {ds->n_active_groups + ds->n_heavy_groups, 0};
   if (G == 1) return {ds->n_heavy_groups, ds->n_active_groups};
   return {0, ds->n_active_groups + ds->n_heavy_groups};
 }
 
 __device__ __forceinline__ int coop_group(const View &v, const DevState *ds, int bin_filter, int k) {
-  return (bin_filter >= 0 ? v.q_bin : v.q_group)[ds->n_groups - 1 - k];
+  if (bin_filter >= 0) return v.q_bin[ds->n_groups - 1 - k];
+  return all_coop(v, ds) ? active_group(v, ds, k) : v.q_group[ds->n_groups - 1 - k];
 }
 
 template <int G>
@@ -618,7 +620,7 @@ __global__ void __launch_bounds__(PT, 2) k_density(View v, int flags, int bin_fi
   const float hcap = (float)((w - 2.0 * (double)exc) / GAMMA_K_D * (1.0 - 1e-6));
   const int m_act = ds->m_act;
   const long long ti = ds->ti;
-  const Queues qs = queues<G>(ds, bin_filter);
+  const Queues qs = queues<G>(v, ds, bin_filter);
   WarpCounters wc = {0, 0, 0, 0, 0, 0};
   if (persistent) {
     if constexpr (G == 1) {
@@ -680,7 +682,7 @@ __global__ void __launch_bounds__(PT, 2) k_force(View v, int bin_filter, int per
   const int m_act = ds->m_act;
   const float Hmax = s_Hmax;
   const float exc = s_exc;
-  const Queues qs = queues<G>(ds, bin_filter);
+  const Queues qs = queues<G>(v, ds, bin_filter);
   WarpCounters wc = {0, 0, 0, 0, 0, 0};
   if (persistent) {
     if constexpr (G == 1) {

@@ -40,6 +40,7 @@ class Params:
     drift_all: int = 0
     n_cells_override: int = 0
     heavy_factor: float = 0.0
+    coop_max_groups: int = -1
 
     def to_c(self) -> _lib.sph_params:
         p = _lib.sph_params()

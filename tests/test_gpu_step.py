@@ -102,13 +102,14 @@ def _run_form(sim, ic, form, steps, params):
     return p.numpy(), ctx.counters(), ctx.get_time()
 
 
-@pytest.mark.parametrize("heavy_factor", [0.0, 1.0, 1e-9])
-def test_plain_batched_graph_bitwise_identical(sim, heavy_factor):
+@pytest.mark.parametrize("heavy_factor,coop_max_groups", [(0.0, 0), (1.0, 0), (1e-9, 0),
+                                                           (0.0, 1 << 30)])
+def test_plain_batched_graph_bitwise_identical(sim, heavy_factor, coop_max_groups):
     """One lane per particle: every sum's order depends on the particle only,
-    also when heavy work groups are shared by the warps of a block (factor 1:
-    some groups, factor 1e-9: all)."""
+    also when work groups are shared by the warps of a block (heavy factor 1:
+    some groups, 1e-9: all; coop_max_groups: every group of every step)."""
     ic = _ic_step(seed=17)
-    params = dict(STEP_PARAMS, heavy_factor=heavy_factor)
+    params = dict(STEP_PARAMS, heavy_factor=heavy_factor, coop_max_groups=coop_max_groups)
     res = {f: _run_form(sim, ic, f, 12, params) for f in ("plain", "batched", "graph")}
     ref, cref, tref = res["batched"]
     for f in ("plain", "graph"):
