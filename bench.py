@@ -233,12 +233,12 @@ def run_ours(args, rank, world):
     pairs = res["counters"]["pairs_density"] + res["counters"]["pairs_force"]
     total_ms = sum(res["ms"])
 
-    # e2e: the same steps through the C ABI from host buffers
-    host = {k: torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for k, t in p.arrays().items()}
+    # e2e: the same steps through the C ABI from a host copy of the state (one
+    # pinned buffer holding every particle array, as the device state does)
+    host = torch.empty(p.storage.shape, dtype=torch.uint8, pin_memory=True)
     restore()
-    for k, t in p.arrays().items():
-        host[k].copy_(t)
-    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    host.copy_(p.storage)
+    h2d = host.numel()  # bytes moved each way per step
     ctx.reset_counters(stream)
     torch.cuda.synchronize()
     e2e_ms = []
@@ -251,11 +251,9 @@ def run_ours(args, rank, world):
             ev1 = torch.cuda.Event(enable_timing=True)
             with torch.cuda.stream(stream):
                 ev0.record(stream)
-                for k, t in p.arrays().items():
-                    t.copy_(host[k], non_blocking=True)
+                p.storage.copy_(host, non_blocking=True)
                 ctx.step_async(p, _lib.SPH_FORM_BATCHED, stream)
-                for k, t in p.arrays().items():
-                    host[k].copy_(t, non_blocking=True)
+                host.copy_(p.storage, non_blocking=True)
                 ev1.record(stream)
             done = ctx.step_sync(p, stream)
             t_step += ev0.elapsed_time(ev1)
@@ -263,8 +261,7 @@ def run_ours(args, rank, world):
                 break
             # the cells were rebuilt on the device: fetch the reordered state
             tw = time.perf_counter()
-            for k, t in p.arrays().items():
-                host[k].copy_(t)
+            host.copy_(p.storage)
             torch.cuda.synchronize()
             t_step += (time.perf_counter() - tw) * 1e3
         e2e_ms.append(t_step)

@@ -55,16 +55,32 @@ def _stream_ptr(stream=None):
 
 
 class Particles:
-    """Structure-of-arrays particle state on one CUDA device (caller-owned)."""
+    """Structure-of-arrays particle state on one CUDA device (caller-owned).
+
+    All arrays are views into one contiguous byte buffer (`storage`, each
+    array 256-byte aligned), so a whole state moves between host and device
+    with a single copy."""
+
+    ALIGN = 256
 
     def __init__(self, n: int, device="cuda", with_counts: bool = True):
         self.n = int(n)
         self.device = torch.device(device)
+        fields = [(name, dt) for name, dt in _lib.PARTICLE_FIELDS
+                  if with_counts or name not in ("ngb_density", "ngb_force")]
+        offs, total = {}, 0
+        for name, dt in fields:
+            offs[name] = total
+            nbytes = self.n * np.dtype(_NP[dt]).itemsize
+            total += (nbytes + self.ALIGN - 1) // self.ALIGN * self.ALIGN
+        self.storage = torch.zeros(max(total, self.ALIGN), dtype=torch.uint8, device=self.device)
         for name, dt in _lib.PARTICLE_FIELDS:
-            if name in ("ngb_density", "ngb_force") and not with_counts:
+            if name not in offs:
                 setattr(self, name, None)
                 continue
-            setattr(self, name, torch.zeros(self.n, dtype=_TORCH[dt], device=self.device))
+            nbytes = self.n * np.dtype(_NP[dt]).itemsize
+            view = self.storage[offs[name]:offs[name] + nbytes].view(_TORCH[dt])
+            setattr(self, name, view)
         self._struct = None
 
     @classmethod
