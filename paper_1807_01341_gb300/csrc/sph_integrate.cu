@@ -144,14 +144,17 @@ __device__ __forceinline__ double wrap_pos(double x, double box) {
   return x;
 }
 
-// One warp per chunk (up to CHUNK leaves of one cell, contiguous particles):
-// drifts (when do_drift) its particles to the current tick, predicts v and A
-// at that tick, refreshes the FP32 records the pair loops read (positions
-// relative to each particle's leaf corner), gives inactive particles P and c
-// from their frozen density and predicted entropy; then recomputes, one leaf
-// per lane, each leaf's bounding box and largest support (and, when do_bins,
-// its smallest bin and bin mask), and the chunk's box in the cell frame.
+// One block per chunk (up to CHUNK leaves of one cell, contiguous particles):
+// its threads drift (when do_drift) the chunk's particles to the current tick,
+// predict v and A at that tick, refresh the FP32 records the pair loops read
+// (positions relative to each particle's leaf corner) and give inactive
+// particles P and c from their frozen density and predicted entropy -- a
+// chunk of a dense clump holds up to 512 particles, two rounds of the block;
+// then the first warp recomputes, one leaf per lane, each leaf's bounding box
+// and largest support (and, when do_bins, its smallest bin and bin mask), and
+// the chunk's box in the cell frame.  Called by every thread of the block.
 __device__ void chunk_update(const View &v, int g, bool do_drift, bool do_bins) {
+  __shared__ float s_exc[UT / 32];
   const DevState *ds = v.ds;
   const int lane = lane_id();
   const int cell = v.chunk_cell[g];
@@ -167,7 +170,7 @@ __device__ void chunk_update(const View &v, int g, bool do_drift, bool do_bins) 
   const float g_ = (float)v.gamma;
   float exc = 0.0f;
   // phase 1: particles, coalesced
-  for (int i = pa + lane; i < pb; i += 32) {
+  for (int i = pa + (int)threadIdx.x; i < pb; i += (int)blockDim.x) {
     double x = v.x[i], y = v.y[i], z = v.z[i];
     if (do_drift) {
       const long long td = v.ti_drift[i];
@@ -216,7 +219,11 @@ __device__ void chunk_update(const View &v, int g, bool do_drift, bool do_bins) 
     }
     v.rec_h[i] = make_float4(rho, fP, c, 1.0f / H);
   }
-  __syncwarp();
+  for (int o = 16; o; o >>= 1) exc = fmaxf(exc, __shfl_xor_sync(0xffffffffu, exc, o));
+  if (lane == 0) s_exc[threadIdx.x >> 5] = exc;
+  __syncthreads();  // the records of phase 1 are visible to the first warp
+  if (threadIdx.x < 32) {
+  for (int k = 0; k < (int)(blockDim.x >> 5); k++) exc = fmaxf(exc, s_exc[k]);
   // phase 2: one leaf per lane
   float lx = INFINITY, ly = INFINITY, lz = INFINITY;
   float hx = -INFINITY, hy = -INFINITY, hz = -INFINITY, Hm = 0.0f;
@@ -266,17 +273,19 @@ __device__ void chunk_update(const View &v, int g, bool do_drift, bool do_bins) 
     atomic_max_float_pos(&v.ds->excursion_bits, exc);
     atomic_max_float_pos(&v.ds->Hmax_bits, Hm);
   }
+  }
+  __syncthreads();  // s_exc is reused by the block's next chunk
 }
 
-__global__ void k_refresh(View v) {
+__global__ void __launch_bounds__(UT) k_refresh(View v) {
   const int ng = v.ds->n_chunks;
-  for (int g = gwarp(); g < ng; g += nwarps()) chunk_update(v, g, false, true);
+  for (int g = blockIdx.x; g < ng; g += gridDim.x) chunk_update(v, g, false, true);
 }
 
-__global__ void k_drift(View v) {
+__global__ void __launch_bounds__(UT) k_drift(View v) {
   const DevState *ds = v.ds;
   const int nq = v.drift_all ? ds->n_chunks : ds->n_drift_chunks;
-  for (int k = gwarp(); k < nq; k += nwarps()) {
+  for (int k = blockIdx.x; k < nq; k += gridDim.x) {
     const int g = v.drift_all ? k : v.q_drift[k];
     chunk_update(v, g, true, false);
   }
@@ -418,7 +427,7 @@ __global__ void k_mark_bin(View v, int bin) {
 // ---------------------------------------------------------------------------
 cudaError_t launch_refresh_all(const View &v, cudaStream_t st) {
   note_launches(1);
-  k_refresh<<<v.grid_util, UT, 0, st>>>(v);
+  k_refresh<<<2 * v.grid_util, UT, 0, st>>>(v);
   return cudaGetLastError();
 }
 
@@ -435,7 +444,7 @@ cudaError_t launch_mark(const View &v, long long ti_or_neg, cudaStream_t st) {
 
 cudaError_t launch_drift(const View &v, cudaStream_t st) {
   note_launches(1);
-  k_drift<<<v.grid_util, UT, 0, st>>>(v);
+  k_drift<<<2 * v.grid_util, UT, 0, st>>>(v);
   return cudaGetLastError();
 }
 
