@@ -163,7 +163,7 @@ def run_ours(args, rank, world):
     tuned = dict(DEFAULT_LAUNCH)
     tune_info = None
     if not args.no_autotune:
-        t = autotune.tune(ic, base, args.workload, steps=4)
+        t = autotune.tune(ic, base, args.workload, steps=12)
         tuned = {k: t[k] for k in KNOBS}
         tune_info = {"cached": t.get("cached"),
                      "trials": [dict(r["cand"], pairs_per_s=r["rate"]) for r in t.get("trials", [])]}

@@ -21,12 +21,12 @@ from . import _lib
 from .sim import Context, Params, Particles
 
 DEFAULT_CANDIDATES = [
-    dict(threads_per_particle=1, leaf_max=8, cell_margin=2.0),
     dict(threads_per_particle=1, leaf_max=16, cell_margin=2.0),
-    dict(threads_per_particle=1, leaf_max=8, cell_margin=1.5),
-    dict(threads_per_particle=1, leaf_max=4, cell_margin=2.0),
-    dict(threads_per_particle=2, leaf_max=8, cell_margin=2.0),
-    dict(threads_per_particle=1, leaf_max=8, cell_margin=2.5),
+    dict(threads_per_particle=1, leaf_max=24, cell_margin=2.5),
+    dict(threads_per_particle=1, leaf_max=32, cell_margin=2.5),
+    dict(threads_per_particle=1, leaf_max=12, cell_margin=2.0),
+    dict(threads_per_particle=1, leaf_max=16, cell_margin=1.5),
+    dict(threads_per_particle=2, leaf_max=16, cell_margin=2.0),
 ]
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
