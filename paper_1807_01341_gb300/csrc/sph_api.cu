@@ -436,9 +436,7 @@ int batched_body(sph_ctx *ctx, const View &v, int flags, cudaStream_t st) {
   prof_begin(ctx, 1, st);
   SPH_CUDA(launch_force(v, -1, true, ctx->grid_force, st));
   prof_end(ctx, 1, st);
-  SPH_CUDA(launch_kick(v, SPH_KICK_CLOSE, st));
-  SPH_CUDA(launch_bins(v, nullptr, 1, st));
-  SPH_CUDA(launch_kick(v, SPH_KICK_OPEN, st));
+  SPH_CUDA(launch_close_step(v, st));
   return SPH_OK;
 }
 
@@ -474,9 +472,7 @@ int plain_body(sph_ctx *ctx, const View &v, int flags, cudaStream_t st) {
                           nq[1] + (nq[0] + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK, st));
     prof_end(ctx, 1, st);
   }
-  SPH_CUDA(launch_kick(v, SPH_KICK_CLOSE, st));
-  SPH_CUDA(launch_bins(v, nullptr, 1, st));
-  SPH_CUDA(launch_kick(v, SPH_KICK_OPEN, st));
+  SPH_CUDA(launch_close_step(v, st));
   return SPH_OK;
 }
 

@@ -77,11 +77,13 @@ __global__ void k_mark_leaves(View v) {
 // One thread per work group: queues the groups whose smallest bin is active,
 // the heavy ones (estimated cost above heavy_factor times the mean) apart so
 // that the pair loops start them first.
-__global__ void k_mark_groups(View v) {
+// (blocks [b0, b0 + nb) of the launch take this task)
+__device__ void mark_groups_part(View &v, int b0, int nb) {
   DevState *ds = v.ds;
   const int ng = ds->n_groups, m_act = ds->m_act;
   const unsigned long long csum = ds->group_cost_sum;
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+  const int t0 = ((int)blockIdx.x - b0) * blockDim.x + threadIdx.x, nt = nb * blockDim.x;
+  for (int g = t0; g < ng; g += nt) {
     int mb = 127;
     for (int l = v.group_leaf0[g]; l < v.group_leaf0[g + 1]; l++) mb = min(mb, (int)v.leaf_min_bin[l]);
     if (mb > m_act) continue;
@@ -93,10 +95,12 @@ __global__ void k_mark_groups(View v) {
 }
 
 // One warp per active leaf: writes `active` for its particles.
-__global__ void k_mark_particles(View v) {
+__device__ void mark_particles_part(View &v, int b0, int nb) {
   DevState *ds = v.ds;
   const int nq = ds->n_active_leaves, m_act = ds->m_act;
-  for (int k = gwarp(); k < nq; k += nwarps()) {
+  const int w0 = (((int)blockIdx.x - b0) * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (nb * blockDim.x) >> 5;
+  for (int k = w0; k < nq; k += nw) {
     int leaf = v.q_active[k];
     int a = v.leaf_start[leaf], b = v.leaf_start[leaf + 1];
     int cnt = 0;
@@ -112,11 +116,12 @@ __global__ void k_mark_particles(View v) {
 // One thread per (active cell, neighbour offset): queues the leaf chunks of
 // every cell next to an active cell that is not queued yet (Sec. III-D: only
 // these particles can be neighbours of an active particle and need drifting).
-__global__ void k_relevant(View v) {
+__device__ void relevant_part(View &v, int b0, int nb) {
   DevState *ds = v.ds;
   const int nq = ds->n_active_cells * 27, nc = ds->nc;
   const unsigned int epoch = ds->epoch;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nq; k += gridDim.x * blockDim.x) {
+  const int t0 = ((int)blockIdx.x - b0) * blockDim.x + threadIdx.x, nt = nb * blockDim.x;
+  for (int k = t0; k < nq; k += nt) {
     const int c = v.q_act_cells[k / 27], o = k % 27;
     const int dx = o / 9 - 1, dy = (o / 3) % 3 - 1, dz = o % 3 - 1;
     const int cx = c / (nc * nc), cy = (c / nc) % nc, cz = c % nc;
@@ -377,9 +382,8 @@ __global__ void k_bins(View v) {
 // Next tick: a particle on bin b ends its step at the next multiple of 2^b
 // after the current tick, so the earliest end over all particles is the
 // smallest such multiple over the occupied bins.
-__global__ void k_next_time(View v, long long *out, int count_step) {
+__device__ void next_time(View &v, long long *out, int count_step) {
   DevState *ds = v.ds;
-  if (ds->halt) return;
   const long long ti = ds->ti;
   long long tn = LLONG_MAX;
   for (int b = 0; b < MAX_BINS; b++)
@@ -400,6 +404,112 @@ __global__ void k_next_time(View v, long long *out, int count_step) {
   ds->s_cand_density = ds->s_cand_force = 0ull;
   ds->s_iters_density = ds->s_active_particles = 0ull;
   if (count_step) ds->steps += 1ull;
+}
+
+__global__ void k_next_time(View v, long long *out, int count_step) {
+  if (v.ds->halt) return;
+  next_time(v, out, count_step);
+}
+
+// The end of a step in one launch: for every active particle (one warp per
+// active leaf) the closing half-kick of its old step, its new bin (as
+// k_bins), the opening half-kick of the new step -- the same arithmetic as
+// k_kick and k_bins in the same order -- then, in the last block to finish,
+// the next tick and the step's counters (as k_next_time).
+__global__ void __launch_bounds__(UT) k_close_step(View v) {
+  DevState *ds = v.ds;
+  __shared__ int delta[MAX_BINS];
+  __shared__ unsigned int too_small;
+  __shared__ int s_go, s_last;
+  if (threadIdx.x == 0) {
+    s_go = ds->halt ? 0 : 1;
+    too_small = 0u;
+  }
+  for (int t = threadIdx.x; t < MAX_BINS; t += blockDim.x) delta[t] = 0;
+  __syncthreads();
+  if (!s_go) return;  // the whole block (a halted step changes nothing)
+  const int nq = ds->n_active_leaves, m_act = ds->m_act;
+  const long long ti = ds->ti;
+  for (int k = gwarp(); k < nq; k += nwarps()) {
+    const int leaf = v.q_active[k];
+    const int a = v.leaf_start[leaf], b = v.leaf_start[leaf + 1];
+    int minb = 127;
+    unsigned long long mask = 0ull;
+    for (int i = a + lane_id(); i < b; i += 32) {
+      const int old = v.bin[i];
+      int nb = old;
+      if (old <= m_act) {
+        // closing half-kick of the old step
+        double half = 0.5 * (double)(v.ti_end[i] - v.ti_begin[i]) * v.dt_min;
+        float hf = (float)half;
+        v.vx[i] += v.ax[i] * hf;
+        v.vy[i] += v.ay[i] * hf;
+        v.vz[i] += v.az[i] * hf;
+        v.A[i] = (float)((double)v.A[i] + (double)v.Adot[i] * half);
+        // Eq. 1 and Eq. 2, increases only on a multiple of the new step
+        double dt = __ddiv_rn(__dmul_rn(v.cfl, (double)v.h[i]), (double)v.vsig[i]);
+        double q = __ddiv_rn(dt, v.dt_min);
+        if (!(q >= 1.0)) {
+          atomicAdd(&too_small, 1u);
+          nb = 0;
+        } else {
+          int e;
+          frexp(q, &e);
+          nb = e - 1;
+          if (nb > v.bin_cap) nb = v.bin_cap;
+        }
+        while (nb > old && (ti & ((1ll << nb) - 1)) != 0) nb--;
+        v.bin[i] = (int8_t)nb;
+        v.ti_begin[i] = ti;
+        v.ti_end[i] = ti + (1ll << nb);
+        if (nb != old) {
+          atomicSub(&delta[old], 1);
+          atomicAdd(&delta[nb], 1);
+        }
+        // opening half-kick of the new step
+        half = 0.5 * (double)(v.ti_end[i] - v.ti_begin[i]) * v.dt_min;
+        hf = (float)half;
+        v.vx[i] += v.ax[i] * hf;
+        v.vy[i] += v.ay[i] * hf;
+        v.vz[i] += v.az[i] * hf;
+        v.A[i] = (float)((double)v.A[i] + (double)v.Adot[i] * half);
+      }
+      minb = min(minb, nb);
+      mask |= 1ull << nb;
+    }
+    for (int o = 16; o; o >>= 1) {
+      minb = min(minb, __shfl_xor_sync(0xffffffffu, minb, o));
+      mask |= __shfl_xor_sync(0xffffffffu, mask, o);
+    }
+    if (lane_id() == 0) {
+      v.leaf_min_bin[leaf] = (uint8_t)minb;
+      v.leaf_bin_mask[leaf] = mask;
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < MAX_BINS; t += blockDim.x)
+    if (delta[t]) atomicAdd(&ds->bin_count[t], delta[t]);
+  if (threadIdx.x == 0 && too_small) record_error(ds, SPH_ERR_DT_TOO_SMALL, too_small, false);
+  // the last block to finish sees every block's bin counts
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&ds->blocks_done, 1u) == gridDim.x - 1u;
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
+    __threadfence();
+    ds->blocks_done = 0u;
+    next_time(v, nullptr, 1);
+  }
+}
+
+// Active work groups, active particles and the cells to drift, in one launch
+// (the three read only what k_mark_leaves wrote): the blocks of the grid are
+// split into three ranges, one per task.
+__global__ void __launch_bounds__(UT) k_mark_rest(View v) {
+  const int third = gridDim.x / 3;
+  if ((int)blockIdx.x < third) mark_groups_part(v, 0, third);
+  else if ((int)blockIdx.x < 2 * third) mark_particles_part(v, third, third);
+  else if (!v.drift_all) relevant_part(v, 2 * third, gridDim.x - 2 * third);
 }
 
 // One thread per active work group: queues the groups holding particles of
@@ -432,13 +542,17 @@ cudaError_t launch_refresh_all(const View &v, cudaStream_t st) {
 }
 
 cudaError_t launch_mark(const View &v, long long ti_or_neg, cudaStream_t st) {
-  note_launches(v.drift_all ? 5 : 6);
+  note_launches(4);
   k_mark_clear<<<v.grid_util, UT, 0, st>>>(v);
   k_begin_step<<<1, 1, 0, st>>>(v, ti_or_neg);
   k_mark_leaves<<<v.grid_util, UT, 0, st>>>(v);
-  k_mark_groups<<<v.grid_util, UT, 0, st>>>(v);
-  k_mark_particles<<<v.grid_util, UT, 0, st>>>(v);
-  if (!v.drift_all) k_relevant<<<v.grid_util, UT, 0, st>>>(v);
+  k_mark_rest<<<3 * (v.grid_util / 3 > 0 ? v.grid_util / 3 : 1), UT, 0, st>>>(v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_close_step(const View &v, cudaStream_t st) {
+  note_launches(1);
+  k_close_step<<<v.grid_util, UT, 0, st>>>(v);
   return cudaGetLastError();
 }
 

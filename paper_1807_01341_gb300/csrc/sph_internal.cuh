@@ -52,7 +52,8 @@ struct DevState {
   // persistent-kernel work heads
   int head_density, head_force, head_drift, head_kick;
   int head_open, head_bins, head_misc, head_coop_density;
-  int head_coop_force, pad2;
+  int head_coop_force;
+  unsigned int blocks_done;   // blocks of the closing kernel of a step that have finished
   // errors
   unsigned int halt;      // a step-invalidating error happened: kernels return
   int first_error;        // first SPH_ERR_* code recorded
@@ -240,6 +241,8 @@ cudaError_t launch_drift(const View &v, cudaStream_t st);
 cudaError_t launch_kick(const View &v, int phase, cudaStream_t st);
 cudaError_t launch_bins(const View &v, long long *ti_next_out, int count_step, cudaStream_t st);
 cudaError_t launch_mark_bin(const View &v, int bin, cudaStream_t st);
+// closing kick, new bins, opening kick and the next tick of a step, one launch
+cudaError_t launch_close_step(const View &v, cudaStream_t st);
 // sph_pairs.cu
 cudaError_t launch_density(const View &v, int flags, int bin_filter, bool persistent,
                            int grid, cudaStream_t st);
