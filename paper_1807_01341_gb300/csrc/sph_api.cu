@@ -411,8 +411,8 @@ int build_cells(sph_ctx *ctx, sph_particles *p, cudaStream_t st) {
   SPH_CUDA(cudaMemsetAsync(SPH_DS_FIELD(b.ds, want_h_bits), 0, sizeof(unsigned int), st));
   SPH_CUDA(launch_bin_histogram(v, st));
   SPH_CUDA(launch_refresh_all(v, st));
-  // cost estimate of every work group (orders the active queue heavy-first)
-  SPH_CUDA(launch_group_cost(v, ctx->grid_dens, st));
+  // cost estimate of every work group (only heavy-group scheduling uses it)
+  if (ctx->prm.heavy_factor > 0.0) SPH_CUDA(launch_group_cost(v, ctx->grid_dens, st));
   int nl = 0;
   SPH_CUDA(cudaMemcpyAsync(&nl, SPH_DS_FIELD(b.ds, n_leaves), sizeof(int), cudaMemcpyDeviceToHost, st));
   SPH_CUDA(cudaStreamSynchronize(st));
