@@ -451,7 +451,8 @@ __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, co
             // Monaghan signal-velocity viscosity, beta = 3 (as in Eq. 1)
             const float wij = fminf(0.0f, dvdr * rinv);
             const float vsij = hi4.z + hj.z - 3.0f * wij;
-            const float Pi = -alpha * vsij * wij / (hi4.x + hj.x);
+            // (fast division: 2 ulp, the pair term's only divide)
+            const float Pi = __fdividef(-alpha * vsij * wij, hi4.x + hj.x);
             const float dWb = 0.5f * (dwi + dwj);
             const float sc = vj.w * fmaf(hi4.y, dwi, fmaf(hj.y, dwj, Pi * dWb)) * rinv;
             pax = fmaf(-sc, dx, pax);
