@@ -160,7 +160,7 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
             pt += tt;
             pr = fmaf(pj.w, wq, pr);
             prt = fmaf(pj.w, tt, prt);
-            cnt += (st.recj[k] != i);
+            cnt++;  // (the particle itself is among the accepted records: one subtracted below)
           }
         }
       };
@@ -246,14 +246,14 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
         sr = (float)a2;
         srt = (float)a3;
         s2 = a4;
-        cnt = c;
+        cnt = c - 1;
       } else {
         sn = group_sum<G>((double)n_hi + (double)n_lo);
         stt = group_sum<G>((double)t_hi + (double)t_lo);
         sr = (float)group_sum<G>((double)r_hi + (double)r_lo);
         srt = (float)group_sum<G>((double)rt_hi + (double)rt_lo);
         s2 = group_sum<G>((double)p2);
-        cnt = group_sum_i<G>(cnt);
+        cnt = group_sum_i<G>(cnt) - 1;
       }
       if (!done) {
         // Halley step in FP64 (Newton where its denominator is not positive),
@@ -422,9 +422,10 @@ __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, co
         }
         if (!valid) mask = 0u;
         while (mask) {
+          // (the particle itself is accepted too: r = 0, it adds nothing but
+          // the signal velocity 2 c_i, the start value; one count subtracted below)
           const int k = k0 + __ffs(mask) - 1;
           mask &= mask - 1;
-          if (st.recj[k] == i) continue;
           const int ci = st.recc[k];
           if (ci != cur) {
             fold(ax_hi, ax_lo, pax);
@@ -515,13 +516,13 @@ __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, co
       saz = a2;
       sad = a3;
       vs = vm;
-      cnt = c;
+      cnt = c - 1;
     } else {
       sax = group_sum<G>((double)ax_hi + (double)ax_lo);
       say = group_sum<G>((double)ay_hi + (double)ay_lo);
       saz = group_sum<G>((double)az_hi + (double)az_lo);
       sad = group_sum<G>((double)ad_hi + (double)ad_lo);
-      cnt = group_sum_i<G>(cnt);
+      cnt = group_sum_i<G>(cnt) - 1;
       vs = group_max<G>(vs);
     }
     if (valid && sub == 0 && writer) {
