@@ -379,14 +379,17 @@ int build_cells(sph_ctx *ctx, sph_particles *p, cudaStream_t st) {
   }
   // cells and leaves
   SPH_CUDA(launch_cell_start(skeys, n, (int)n_cells, b.cell_start, b.pcell, st));
-  SPH_CUDA(launch_leaf_count(skeys, b.cell_start, (int)n_cells, ctx->prm.leaf_max, b.leaf_counts, st));
-  SPH_CUDA(exclusive_scan_u32(b.leaf_counts, b.leaf_offsets, (int)n_cells + 1, b.scan_tmp, st));
-  SPH_CUDA(launch_leaf_write(skeys, b.cell_start, (int)n_cells, ctx->prm.leaf_max, b.leaf_offsets,
-                             b.leaf_start, b.leaf_cell, b.leaf_k, b.cell_leaf_start, n, st));
-  SPH_CUDA(cudaMemcpyAsync(SPH_DS_FIELD(b.ds, n_leaves), b.leaf_offsets + n_cells, sizeof(int),
+  // (scratch: the marks in b.scratch, the node lists in the sort's spare key
+  // buffer, the counters in the histogram)
+  const unsigned int *d_n_leaves = nullptr;
+  SPH_CUDA(launch_leaves(skeys, b.cell_start, (int)n_cells, n, ctx->prm.leaf_max,
+                         (uint8_t *)b.scratch, (int2 *)(alt ? b.keys[0] : b.keys[1]), b.hist,
+                         b.scan_tmp, b.leaf_start, b.leaf_cell, b.leaf_k, b.cell_leaf_start,
+                         2 * ctx->grid_util, &d_n_leaves, st));
+  SPH_CUDA(cudaMemcpyAsync(SPH_DS_FIELD(b.ds, n_leaves), d_n_leaves, sizeof(int),
                            cudaMemcpyDeviceToDevice, st));
   int n_leaves_h = 0;
-  SPH_CUDA(cudaMemcpyAsync(&n_leaves_h, b.leaf_offsets + n_cells, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SPH_CUDA(cudaMemcpyAsync(&n_leaves_h, d_n_leaves, sizeof(int), cudaMemcpyDeviceToHost, st));
   SPH_CUDA(cudaStreamSynchronize(st));
   // work groups and the leaf of each particle
   SPH_CUDA(launch_groups(b.cell_leaf_start, b.leaf_start, (int)n_cells, (int)n, b.leaf_counts,

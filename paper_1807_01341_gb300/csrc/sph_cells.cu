@@ -270,129 +270,154 @@ __device__ __forceinline__ uint32_t corner_of(unsigned long long key, int level)
   return compact3(t >> 2) | (compact3(t >> 1) << 10) | (compact3(t) << 20);
 }
 
-// Walks the octree of one cell's Morton-ordered particles depth first and
-// emits its leaves in particle order.  A node holding more than leaf_max
-// particles is split into its 8 children; consecutive children that hold at
-// most leaf_max particles between them are merged into one leaf (siblings, so
-// the leaf stays inside the parent node), and larger children are split in
-// turn.  At the deepest level a node is cut into chunks of leaf_max.  Each
-// leaf records the corner of the node it lies in.  Returns the leaf count.
-__device__ int split_cell(const unsigned long long *__restrict__ keys, int a0, int b0,
-                          int leaf_max, int32_t *leaf_start, int32_t *leaf_cell,
-                          uint32_t *leaf_k, int cell, int out_base) {
-  // stack entries: [a, b) and level; a negative level -(L+1) marks a merged
-  // run of children of a node at level L, emitted as one leaf
-  int sa[8 * MORTON_BITS + 8], sb[8 * MORTON_BITS + 8];
-  signed char sl[8 * MORTON_BITS + 8];
-  int top = 0, count = 0;
-  auto emit = [&](int a, int b, int level) {
-    for (int s = a; s < b; s += leaf_max) {
-      if (leaf_start) {
-        leaf_start[out_base + count] = s;
-        leaf_cell[out_base + count] = cell;
-        leaf_k[out_base + count] = corner_of(keys[a], level);
-      }
-      count++;
-    }
-  };
-  if (b0 <= a0) return 0;
-  sa[0] = a0;
-  sb[0] = b0;
-  sl[0] = 0;
-  top = 1;
-  while (top > 0) {
-    top--;
-    const int a = sa[top], b = sb[top], L = sl[top];
-    if (L < 0) {  // merged siblings
-      emit(a, b, -L - 1);
-      continue;
-    }
-    const int cnt = b - a;
-    if (cnt <= leaf_max || L == MORTON_BITS) {
-      emit(a, b, L);
-      continue;
-    }
-    const int shift = 3 * (MORTON_BITS - 1 - L);
-    int bnd[9];
-    bnd[0] = a;
-    bnd[8] = b;
-    for (int k = 1; k < 8; k++) {
-      // first index in [bnd[k-1], b) whose child digit is >= k
-      int lo = bnd[k - 1], hi = b;
+// Leaves: the octree of each cell's Morton-ordered particles, split level by
+// level.  A node holding more than leaf_max particles is split into its 8
+// children; consecutive children that hold at most leaf_max particles between
+// them are merged into one leaf (siblings, so the leaf stays inside the parent
+// node), and larger children are split at the next level.  At the deepest
+// level a node is cut into runs of leaf_max.  Every leaf is marked at its
+// first particle by lead[s] = 1 + the level of the node it lies in; the marks,
+// compacted in particle order, give the leaves cell by cell in the order of a
+// depth-first walk.  All particles of a leaf share the Morton prefix of that
+// level, so its corner follows from the first particle's code.
+
+// Level 0: each cell is one node; a cell of at most leaf_max particles is a leaf.
+__global__ void k_leaf_cells(const int32_t *__restrict__ cell_start, int n_cells, int leaf_max,
+                             uint8_t *__restrict__ lead, int2 *__restrict__ nodes,
+                             unsigned int *__restrict__ n_nodes, unsigned int cap) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_cells) return;
+  const int a = cell_start[c], b = cell_start[c + 1];
+  if (b <= a) return;
+  if (b - a <= leaf_max) {
+    lead[a] = 1;
+    return;
+  }
+  const unsigned int slot = atomicAdd(n_nodes, 1u);
+  if (slot < cap) nodes[slot] = make_int2(a, b);  // nodes of >= 2 particles: cap = n/2 suffices
+}
+
+// One level: 8 lanes per node.  Lane k (1..7) finds the first particle of
+// child k by binary search; lane 0 merges runs of small siblings, marks their
+// leaves and queues the large children for the next level.
+__global__ void __launch_bounds__(256)
+k_leaf_level(const unsigned long long *__restrict__ keys, int level, int leaf_max,
+             const int2 *__restrict__ nodes, const unsigned int *__restrict__ n_nodes,
+             int2 *__restrict__ next, unsigned int *__restrict__ n_next, unsigned int cap,
+             uint8_t *__restrict__ lead) {
+  const unsigned int cnt = *n_nodes;
+  const int lane = threadIdx.x & 31, k = lane & 7;
+  const unsigned int gmask = 0xFFu << (lane & 24);
+  const int shift = 3 * (MORTON_BITS - 1 - level);
+  const unsigned int stride = (gridDim.x * blockDim.x) >> 3;
+  for (unsigned int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 3; i < min(cnt, cap);
+       i += stride) {
+    const int2 nd = nodes[i];
+    int lo = nd.x, hi = nd.y;
+    if (k > 0) {
+      // first index in [a, b) whose child digit is >= k
       while (lo < hi) {
         const int mid = (lo + hi) >> 1;
         if (child_of(keys[mid], shift) < (unsigned int)k) lo = mid + 1;
         else hi = mid;
       }
-      bnd[k] = lo;
     }
-    // entries in child order: big children to split, runs of small ones
-    int ea[8], eb[8];
-    signed char el[8];
-    int ne = 0;
-    for (int k = 0; k < 8;) {
-      const int c = bnd[k + 1] - bnd[k];
+    int bnd[9];
+#pragma unroll
+    for (int j = 0; j < 8; j++) bnd[j] = __shfl_sync(gmask, lo, j, 8);
+    bnd[0] = nd.x;
+    bnd[8] = nd.y;
+    if (k != 0) continue;
+    for (int j = 0; j < 8;) {
+      const int c = bnd[j + 1] - bnd[j];
       if (c == 0) {
-        k++;
+        j++;
         continue;
       }
       if (c > leaf_max) {
-        ea[ne] = bnd[k];
-        eb[ne] = bnd[k + 1];
-        el[ne] = (signed char)(L + 1);
-        ne++;
-        k++;
+        if (level + 1 == MORTON_BITS) {
+          for (int s = bnd[j]; s < bnd[j + 1]; s += leaf_max) lead[s] = (uint8_t)(MORTON_BITS + 1);
+        } else {
+          const unsigned int slot = atomicAdd(n_next, 1u);
+          if (slot < cap) next[slot] = make_int2(bnd[j], bnd[j + 1]);
+        }
+        j++;
         continue;
       }
-      int k2 = k + 1, sum = c;
-      while (k2 < 8 && sum + (bnd[k2 + 1] - bnd[k2]) <= leaf_max) {
-        sum += bnd[k2 + 1] - bnd[k2];
-        k2++;
+      int j2 = j + 1, sum = c;
+      while (j2 < 8 && sum + (bnd[j2 + 1] - bnd[j2]) <= leaf_max) {
+        sum += bnd[j2 + 1] - bnd[j2];
+        j2++;
       }
-      ea[ne] = bnd[k];
-      eb[ne] = bnd[k2];
-      el[ne] = (signed char)(-(L + 1));
-      ne++;
-      k = k2;
-    }
-    for (int e = ne - 1; e >= 0; e--) {
-      sa[top] = ea[e];
-      sb[top] = eb[e];
-      sl[top] = el[e];
-      top++;
+      lead[bnd[j]] = (uint8_t)(level + 1);
+      j = j2;
     }
   }
-  return count;
 }
 
-__global__ void k_leaf_count(const unsigned long long *__restrict__ keys,
-                             const int32_t *__restrict__ cell_start, int n_cells, int leaf_max,
-                             unsigned int *__restrict__ counts) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c > n_cells) return;
-  if (c == n_cells) {
-    counts[c] = 0;
-    return;
+__device__ __forceinline__ void load_lead(const uint8_t *__restrict__ lead, long long base,
+                                          long long n, uint8_t l[SCAN_ITEMS]) {
+  if (base + SCAN_ITEMS <= n) {
+    const uchar4 q = *reinterpret_cast<const uchar4 *>(lead + base);
+    l[0] = q.x; l[1] = q.y; l[2] = q.z; l[3] = q.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; k++) l[k] = base + k < n ? lead[base + k] : (uint8_t)0;
   }
-  counts[c] = (unsigned int)split_cell(keys, cell_start[c], cell_start[c + 1], leaf_max, nullptr,
-                                       nullptr, nullptr, c, 0);
 }
 
-__global__ void k_leaf_write(const unsigned long long *__restrict__ keys,
-                             const int32_t *__restrict__ cell_start, int n_cells, int leaf_max,
-                             const unsigned int *__restrict__ offsets,
-                             int32_t *__restrict__ leaf_start, int32_t *__restrict__ leaf_cell,
-                             uint32_t *__restrict__ leaf_k, int32_t *__restrict__ cell_leaf_start,
-                             long long n) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c > n_cells) return;
-  cell_leaf_start[c] = (int32_t)offsets[c];
-  if (c == n_cells) {
-    leaf_start[offsets[c]] = (int32_t)n;
-    return;
+// leaves per tile of SCAN_TILE particles; tile_cnt[n_tiles] = 0 closes the scan
+__global__ void __launch_bounds__(SCAN_THREADS)
+k_leaf_tiles(const uint8_t *__restrict__ lead, long long n, unsigned int *__restrict__ tile_cnt,
+             int n_tiles) {
+  static_assert(SCAN_ITEMS == 4, "lead bytes are read as uchar4");
+  uint8_t l[SCAN_ITEMS];
+  load_lead(lead, (long long)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS, n, l);
+  unsigned int s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; k++) s += l[k] != 0;
+  unsigned int tot;
+  block_exclusive_scan(s, &tot);
+  if (threadIdx.x == 0) {
+    tile_cnt[blockIdx.x] = tot;
+    if (blockIdx.x == 0) tile_cnt[n_tiles] = 0u;
   }
-  split_cell(keys, cell_start[c], cell_start[c + 1], leaf_max, leaf_start, leaf_cell, leaf_k, c,
-             (int)offsets[c]);
+}
+
+// compaction of the marks: leaf records, first leaf of every cell, closing entry
+__global__ void __launch_bounds__(SCAN_THREADS)
+k_leaf_emit(const unsigned long long *__restrict__ keys, const uint8_t *__restrict__ lead,
+            long long n, int n_cells, const unsigned int *__restrict__ tile_off,
+            int32_t *__restrict__ leaf_start, int32_t *__restrict__ leaf_cell,
+            uint32_t *__restrict__ leaf_k, int32_t *__restrict__ cell_leaf_start) {
+  const long long base = (long long)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+  uint8_t l[SCAN_ITEMS];
+  load_lead(lead, base, n, l);
+  unsigned int s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; k++) s += l[k] != 0;
+  unsigned int off = block_exclusive_scan(s, nullptr) + tile_off[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; k++) {
+    const long long i = base + k;
+    if (i >= n) break;
+    if (l[k]) {
+      const unsigned long long key = keys[i];
+      const int c = (int)(key >> KEY_MORTON_BITS);
+      leaf_start[off] = (int32_t)i;
+      leaf_cell[off] = c;
+      leaf_k[off] = corner_of(key, l[k] - 1);
+      // the first particle of a cell always starts a leaf
+      const int cp = i > 0 ? (int)(keys[i - 1] >> KEY_MORTON_BITS) : -1;
+      for (int cc = cp + 1; cc <= c; cc++) cell_leaf_start[cc] = (int32_t)off;
+      off++;
+    }
+    if (i == n - 1) {
+      for (int cc = (int)(keys[i] >> KEY_MORTON_BITS) + 1; cc <= n_cells; cc++)
+        cell_leaf_start[cc] = (int32_t)off;
+      leaf_start[off] = (int32_t)n;
+    }
+  }
 }
 
 __global__ void k_bin_hist(const int8_t *__restrict__ bin, long long n, int *__restrict__ out) {
@@ -563,22 +588,40 @@ cudaError_t launch_cell_start(const unsigned long long *sorted_keys, long long n
   return cudaGetLastError();
 }
 
-cudaError_t launch_leaf_count(const unsigned long long *sorted_keys, const int32_t *cell_start,
-                              int n_cells, int leaf_max, unsigned int *counts, cudaStream_t st) {
-  note_launches(1);
-  k_leaf_count<<<blocks_for(n_cells + 1, 128), 128, 0, st>>>(sorted_keys, cell_start, n_cells,
-                                                              leaf_max, counts);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_leaf_write(const unsigned long long *sorted_keys, const int32_t *cell_start,
-                              int n_cells, int leaf_max, const unsigned int *offsets,
-                              int32_t *leaf_start, int32_t *leaf_cell, uint32_t *leaf_k,
-                              int32_t *cell_leaf_start, long long n, cudaStream_t st) {
-  note_launches(1);
-  k_leaf_write<<<blocks_for(n_cells + 1, 128), 128, 0, st>>>(
-      sorted_keys, cell_start, n_cells, leaf_max, offsets, leaf_start, leaf_cell, leaf_k,
-      cell_leaf_start, n);
+cudaError_t launch_leaves(const unsigned long long *sorted_keys, const int32_t *cell_start,
+                          int n_cells, long long n, int leaf_max, uint8_t *lead, int2 *nodes,
+                          unsigned int *work, unsigned int *scan_tmp, int32_t *leaf_start,
+                          int32_t *leaf_cell, uint32_t *leaf_k, int32_t *cell_leaf_start,
+                          int grid, const unsigned int **n_leaves, cudaStream_t st) {
+  const long long n_tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  unsigned int *tile_cnt = work, *n_nodes = work + n_tiles + 1;
+  *n_leaves = tile_cnt + n_tiles;
+  if (n == 0) {
+    cudaError_t e = cudaMemsetAsync(cell_leaf_start, 0, sizeof(int32_t) * (n_cells + 1), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(leaf_start, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tile_cnt, 0, sizeof(unsigned int), st);
+    return e;
+  }
+  if (n_tiles > SCAN_TILE) return cudaErrorInvalidValue;
+  const unsigned int cap = (unsigned int)(n / 2);
+  int2 *list[2] = {nodes, nodes + cap};
+  cudaError_t e = cudaMemsetAsync(lead, 0, (size_t)n, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(n_nodes, 0, sizeof(unsigned int) * MORTON_BITS, st);
+  if (e != cudaSuccess) return e;
+  note_launches(1 + MORTON_BITS + 2);
+  k_leaf_cells<<<blocks_for(n_cells, 128), 128, 0, st>>>(cell_start, n_cells, leaf_max, lead,
+                                                          list[0], n_nodes, cap);
+  for (int L = 0; L < MORTON_BITS; L++) {
+    unsigned int *n_next = L + 1 < MORTON_BITS ? n_nodes + L + 1 : n_nodes;  // unused at the last level
+    k_leaf_level<<<grid, 256, 0, st>>>(sorted_keys, L, leaf_max, list[L & 1], n_nodes + L,
+                                        list[(L + 1) & 1], n_next, cap, lead);
+  }
+  k_leaf_tiles<<<(int)n_tiles, SCAN_THREADS, 0, st>>>(lead, n, tile_cnt, (int)n_tiles);
+  e = exclusive_scan_u32(tile_cnt, tile_cnt, (int)n_tiles + 1, scan_tmp, st);
+  if (e != cudaSuccess) return e;
+  k_leaf_emit<<<(int)n_tiles, SCAN_THREADS, 0, st>>>(sorted_keys, lead, n, n_cells, tile_cnt,
+                                                     leaf_start, leaf_cell, leaf_k,
+                                                     cell_leaf_start);
   return cudaGetLastError();
 }
 

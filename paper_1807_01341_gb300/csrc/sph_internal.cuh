@@ -219,13 +219,15 @@ cudaError_t launch_gather(void *dst, const void *src, const unsigned int *idx, l
                           int elem_bytes, cudaStream_t st);
 cudaError_t launch_cell_start(const unsigned long long *sorted_keys, long long n, int n_cells,
                               int32_t *cell_start, int32_t *pcell, cudaStream_t st);
-cudaError_t launch_leaf_count(const unsigned long long *sorted_keys, const int32_t *cell_start,
-                              int n_cells, int leaf_max, unsigned int *counts,
-                              cudaStream_t st);
-cudaError_t launch_leaf_write(const unsigned long long *sorted_keys, const int32_t *cell_start,
-                              int n_cells, int leaf_max, const unsigned int *offsets,
-                              int32_t *leaf_start, int32_t *leaf_cell, uint32_t *leaf_k,
-                              int32_t *cell_leaf_start, long long n, cudaStream_t st);
+// Leaves of every cell in particle order (leaf_start[n_leaves] = n), their
+// cells and corners, and the first leaf of every cell (cell_leaf_start[n_cells]
+// = n_leaves).  Scratch: lead (n bytes), nodes (n int2), work (n/4096 + 12
+// words); *n_leaves points at the device count.
+cudaError_t launch_leaves(const unsigned long long *sorted_keys, const int32_t *cell_start,
+                          int n_cells, long long n, int leaf_max, uint8_t *lead, int2 *nodes,
+                          unsigned int *work, unsigned int *scan_tmp, int32_t *leaf_start,
+                          int32_t *leaf_cell, uint32_t *leaf_k, int32_t *cell_leaf_start,
+                          int grid, const unsigned int **n_leaves, cudaStream_t st);
 cudaError_t launch_bin_histogram(const View &v, cudaStream_t st);
 cudaError_t launch_groups(const int32_t *cell_leaf_start, const int32_t *leaf_start, int n_cells,
                           int n_leaves_max, unsigned int *counts, unsigned int *offsets,
