@@ -423,6 +423,11 @@ def main():
                          "force_ms": rf["force_ms"]},
             "cpu_baseline": cpu,
             "gpu_launches": b["launches"],
+            # useful pairs / tested (record, particle) pairs; the density loop's
+            # tests include every h iteration, its useful pairs the final one
+            "candidate_efficiency": {
+                "density": c["pairs_density"] / max(c["cand_density"], 1),
+                "force": c["pairs_force"] / max(c["cand_force"], 1)},
             "counters": {k: c[k] for k in ("pairs_density", "pairs_force", "cand_density",
                                            "cand_force", "iters_density", "active_particles",
                                            "steps", "rebuilds", "redone_steps")},

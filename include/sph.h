@@ -111,8 +111,9 @@ typedef struct sph_ctx sph_ctx;
 typedef struct {
   int64_t pairs_density;   /* useful density pairs: i active, j != i, r_ij < H_i (final h) */
   int64_t pairs_force;     /* useful force pairs: i active, j != i, r_ij < max(H_i, H_j) */
-  int64_t cand_density;    /* candidate pairs evaluated in the density loop (all iterations) */
-  int64_t cand_force;      /* candidate pairs evaluated in the force loop */
+  int64_t cand_density;    /* candidate pairs tested in the density loop: staged records x
+                              unconverged particles of the round, all iterations */
+  int64_t cand_force;      /* candidate pairs tested in the force loop (records x particles) */
   int64_t iters_density;   /* sum over active particles of h iterations */
   int64_t active_particles;/* sum over steps of the active particle count */
   int64_t steps;           /* completed sph_step / sph_step_graph steps */

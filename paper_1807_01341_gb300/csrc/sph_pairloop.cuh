@@ -115,6 +115,17 @@ __device__ __forceinline__ float group_max(float x) {
   return x;
 }
 
+// Squared distances of two pairs at once, a - b per component, with packed
+// FP32 instructions; each component is rounded exactly as the scalar
+// fmaf(dx, dx, fmaf(dy, dy, dz * dz)) with dx = a.x - b.x.
+__device__ __forceinline__ float2 dist2_x2(float2 ax, float2 ay, float2 az, float2 bx, float2 by,
+                                           float2 bz) {
+  const float2 dx = __fadd2_rn(ax, make_float2(-bx.x, -bx.y));
+  const float2 dy = __fadd2_rn(ay, make_float2(-by.x, -by.y));
+  const float2 dz = __fadd2_rn(az, make_float2(-bz.x, -bz.y));
+  return __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+}
+
 __device__ __forceinline__ float warp_max(float x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(FULL, x, o));
@@ -554,7 +565,6 @@ __device__ __forceinline__ int stage_list(const float4 *const *srcs, Stage<S, NR
       __syncwarp();
       consume(total);
     }
-    wc.cand += (unsigned long long)total;
     __syncwarp();
     fence_proxy_async();
     e += k;
