@@ -197,12 +197,12 @@ __device__ void force_adj_group(const View &v, const AdjWork &w, int wg, const C
   const int nsph = compact_spheres(st.sph, live, make_float4(xi.x, xi.y, xi.z, xi.w));
   double dxi = 0.0, dyi = 0.0, dzi = 0.0, dvxi = 0.0, dvyi = 0.0, dvzi = 0.0;
   double Hbi = 0.0, Qbi = 0.0, cbi = 0.0, rbi = 0.0;
-  auto leaf_ok = [&](int l, float sx, float sy, float sz) {
+  auto leaf_ok = [&](int l, float sx, float sy, float sz, LeafBox &lb) {
     const float4 loj = v.leaf_lo[l], hij = v.leaf_hi[l];
     const float R = fmaxf(Hs, loj.w);
+    lb = leaf_box(loj, hij, sx, sy, sz, loj.w);
     return box_gap2(Wg.lx, Wg.ly, Wg.lz, Wg.hx, Wg.hy, Wg.hz, loj, hij, sx, sy, sz) <
-               R * R * 1.0002f &&
-           spheres_reach(st.sph, nsph, loj, hij, sx, sy, sz, loj.w);
+           R * R * 1.0002f;
   };
   auto chunk_ok = [&](int gg, float sx, float sy, float sz) {
     const float4 loc = v.chunk_lo[gg];
@@ -295,7 +295,7 @@ __device__ void force_adj_group(const View &v, const AdjWork &w, int wg, const C
   };
   const Reach reach = {clx, cly, clz, chx, chy, chz,
                        fmaxf(Hs, __uint_as_float(v.ds->Hmax_bits)) + ceps,
-                       __uint_as_float(v.ds->excursion_bits)};
+                       __uint_as_float(v.ds->excursion_bits), st.sph, nsph};
   int skip = 0, nlist = 0;
   bool more = false;
   do {
@@ -428,10 +428,10 @@ __device__ void density_adj_group(const View &v, const AdjWork &w, int wg, const
   double sr = 0.0, srt = 0.0, s1 = 0.0, s2 = 0.0;
   double dxi = 0.0, dyi = 0.0, dzi = 0.0;
   const float R2 = Hs * Hs * 1.0002f, Rc = Hs + ceps;
-  auto leaf_ok = [&](int l, float sx, float sy, float sz) {
+  auto leaf_ok = [&](int l, float sx, float sy, float sz, LeafBox &lb) {
     const float4 lo = v.leaf_lo[l], hi = v.leaf_hi[l];
-    return box_gap2(Wg.lx, Wg.ly, Wg.lz, Wg.hx, Wg.hy, Wg.hz, lo, hi, sx, sy, sz) < R2 &&
-           spheres_reach(st.sph, nsph, lo, hi, sx, sy, sz, 0.0f);
+    lb = leaf_box(lo, hi, sx, sy, sz, 0.0f);
+    return box_gap2(Wg.lx, Wg.ly, Wg.lz, Wg.hx, Wg.hy, Wg.hz, lo, hi, sx, sy, sz) < R2;
   };
   auto chunk_ok = [&](int gg, float sx, float sy, float sz) {
     return box_gap2(clx, cly, clz, chx, chy, chz, v.chunk_lo[gg], v.chunk_hi[gg], sx, sy, sz) <
@@ -480,7 +480,8 @@ __device__ void density_adj_group(const View &v, const AdjWork &w, int wg, const
   };
   int skip = 0, nlist = 0;
   bool more = false;
-  const Reach reach = {clx, cly, clz, chx, chy, chz, Rc, __uint_as_float(v.ds->excursion_bits)};
+  const Reach reach = {clx, cly, clz, chx, chy, chz, Rc, __uint_as_float(v.ds->excursion_bits),
+                       st.sph, nsph};
   if (Hs > 0.0f) {
     do {
       nlist = search(v, F, reach, st, leaf_ok, chunk_ok, skip, more);

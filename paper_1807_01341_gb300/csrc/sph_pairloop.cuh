@@ -191,24 +191,59 @@ __device__ __forceinline__ int compact_spheres(float4 *sph, bool has, float4 s) 
   return __popc(mk);
 }
 
-// Whether any of the n spheres (centre, radius in w; a radius <= 0 never
-// reaches) comes within its radius of box [lo, hi] (j's box shifted by s);
-// `grow` is the leaf's own support, a lower bound of every radius when > 0.
-__device__ __forceinline__ bool spheres_reach(const float4 *sph, int n, const float4 &lo,
-                                              const float4 &hi, float sx, float sy, float sz,
-                                              float grow) {
-  const float lx = lo.x + sx, ly = lo.y + sy, lz = lo.z + sz;
-  const float hx = hi.x + sx, hy = hi.y + sy, hz = hi.z + sz;
-  for (int p = 0; p < n; p++) {
-    const float4 c = sph[p];
-    const float R = fmaxf(c.w, grow);
-    if (c.w <= 0.0f) continue;
-    const float gx = fmaxf(0.0f, fmaxf(lx - c.x, c.x - hx));
-    const float gy = fmaxf(0.0f, fmaxf(ly - c.y, c.y - hy));
-    const float gz = fmaxf(0.0f, fmaxf(lz - c.z, c.z - hz));
-    if (gx * gx + gy * gy + gz * gz < R * R * 1.0002f) return true;
+// Whether sphere c (centre, radius in w; a radius <= 0 never reaches) comes
+// within max(radius, grow) of the box [l, h]; `grow` is the leaf's own
+// support, a lower bound of every radius when > 0.
+__device__ __forceinline__ bool sphere_reaches(const float4 &c, float grow, float lx, float ly,
+                                               float lz, float hx, float hy, float hz) {
+  const float R = fmaxf(c.w, grow);
+  const float gx = fmaxf(0.0f, fmaxf(lx - c.x, c.x - hx));
+  const float gy = fmaxf(0.0f, fmaxf(ly - c.y, c.y - hy));
+  const float gz = fmaxf(0.0f, fmaxf(lz - c.z, c.z - hz));
+  return c.w > 0.0f && gx * gx + gy * gy + gz * gz < R * R * 1.0002f;
+}
+
+// A leaf that passed a search's box test, for the support-sphere test after
+// it: its box shifted into the group's frame and its own support.
+struct LeafBox {
+  float lx, ly, lz, hx, hy, hz, grow;
+};
+
+__device__ __forceinline__ LeafBox leaf_box(const float4 &lo, const float4 &hi, float sx, float sy,
+                                            float sz, float grow) {
+  return LeafBox{lo.x + sx, lo.y + sy, lo.z + sz, hi.x + sx, hi.y + sy, hi.z + sz, grow};
+}
+
+// For the lanes with `ok` set, whether any of the n spheres sph[0..n)
+// reaches the lane's leaf box (all lanes of the warp call it).  With many
+// boxes (or lanes_only) each lane loops over the spheres; with few, the
+// spheres go across the lanes (lane p holds sphere p) and each box is
+// broadcast and tested by one vote -- the same expression either way.
+__device__ __forceinline__ bool spheres_reach_any(const float4 *sph, int n, bool ok,
+                                                  const LeafBox &b, bool lanes_only) {
+  const unsigned pend0 = __ballot_sync(FULL, ok);
+  const int nb = __popc(pend0);
+  if (lanes_only || nb * 4 >= n * 3) {
+    if (!ok) return false;
+    for (int p = 0; p < n; p++)
+      if (sphere_reaches(sph[p], b.grow, b.lx, b.ly, b.lz, b.hx, b.hy, b.hz)) return true;
+    return false;
   }
-  return false;
+  const int lane = lane_id();
+  const float4 c = sph[min(lane, n - 1)];  // n > 0 here
+  unsigned hit = 0u, pend = pend0;
+  while (pend) {
+    const int s = __ffs(pend) - 1;
+    pend &= pend - 1;
+    const float lx = __shfl_sync(FULL, b.lx, s), ly = __shfl_sync(FULL, b.ly, s),
+                lz = __shfl_sync(FULL, b.lz, s);
+    const float hx = __shfl_sync(FULL, b.hx, s), hy = __shfl_sync(FULL, b.hy, s),
+                hz = __shfl_sync(FULL, b.hz, s);
+    const float g = __shfl_sync(FULL, b.grow, s);
+    const bool r = lane < n && sphere_reaches(c, g, lx, ly, lz, hx, hy, hz);
+    if (__any_sync(FULL, r)) hit |= 1u << s;
+  }
+  return (hit >> lane) & 1u;
 }
 
 // Cubic spline: w(q) / (8/pi) and w'(q) / (8/pi), q in [0, 1)
@@ -371,10 +406,14 @@ struct Reach {
   float lx, ly, lz, hx, hy, hz;  // group box, cell frame
   float R;                       // reach
   float exc;                     // largest excursion of a particle out of its cell
+  const float4 *sph;             // support spheres a leaf must also meet (or nullptr)
+  int nsph;
+  bool lanes_only = false;       // sphere test per lane only (fewer registers)
 };
 
 // Lists, in cell-then-leaf order, the leaves of the 27 cells around the work
-// group that pass `leaf_ok` (in cells of more than CHUNK leaves, only those of
+// group that pass `leaf_ok` (a box test; then, with reach.sph set, one of the
+// support spheres must reach the leaf box leaf_ok returned) (in cells of more than CHUNK leaves, only those of
 // chunks passing `chunk_ok`; cells out of `reach` entirely skipped; with
 // part >= 0 only chunks with index = part modulo WARPS_PER_BLOCK): accepted
 // leaves skip, skip + 1, ... up to LCAP of them.  Returns how many were
@@ -472,6 +511,7 @@ __device__ __forceinline__ int search(const View &v, const CellFrame &F, const R
         bool ok = false;
         int ja = 0, cnt = 0;
         float sx = 0.f, sy = 0.f, sz = 0.f;
+        LeafBox lbox = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (u < L) {
           const int l = cla + (u - cls);
           const int dxc = ci / 9 - 1, dyc = (ci / 3) % 3 - 1, dzc = ci % 3 - 1;
@@ -481,12 +521,13 @@ __device__ __forceinline__ int search(const View &v, const CellFrame &F, const R
           sx = (float)(dxc * (1 << MORTON_BITS) - F.kx + leaf_kx(kl)) * F.wq;
           sy = (float)(dyc * (1 << MORTON_BITS) - F.ky + leaf_ky(kl)) * F.wq;
           sz = (float)(dzc * (1 << MORTON_BITS) - F.kz + leaf_kz(kl)) * F.wq;
-          ok = leaf_ok(l, sx, sy, sz);
+          ok = leaf_ok(l, sx, sy, sz, lbox);
           if (ok) {
             ja = la;
             cnt = lb - la;
           }
         }
+        if (reach.sph) ok = spheres_reach_any(reach.sph, reach.nsph, ok, lbox, reach.lanes_only);
         const unsigned mk = __ballot_sync(FULL, ok);
         const int idx = seen + __popc(mk & ((1u << lane) - 1u));
         if (ok && idx >= skip && idx < limit) {

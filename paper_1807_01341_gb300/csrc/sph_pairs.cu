@@ -201,16 +201,18 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
       }
       const float R = Hs * 1.05f;
       const float R2 = R * R * 1.0002f, Rc = R + ceps;
-      auto leaf_ok = [&](int l, float sx, float sy, float sz) {
+      auto leaf_ok = [&](int l, float sx, float sy, float sz, LeafBox &lb) {
         const float4 lo = v.leaf_lo[l], hi = v.leaf_hi[l];
-        return box_gap2(W.lx, W.ly, W.lz, W.hx, W.hy, W.hz, lo, hi, sx, sy, sz) < R2 &&
-               spheres_reach(st.sph, nsph, lo, hi, sx, sy, sz, 0.0f);
+        lb = leaf_box(lo, hi, sx, sy, sz, 0.0f);
+        return box_gap2(W.lx, W.ly, W.lz, W.hx, W.hy, W.hz, lo, hi, sx, sy, sz) < R2;
       };
       auto chunk_ok = [&](int g, float sx, float sy, float sz) {
         return box_gap2(clx, cly, clz, chx, chy, chz, v.chunk_lo[g], v.chunk_hi[g], sx, sy, sz) <
                Rc * Rc;
       };
-      const Reach reach = {clx, cly, clz, chx, chy, chz, Rc, exc};
+      // (the density loop keeps the per-lane sphere test: at its register
+      // limit the transposed form costs more in spills than it saves)
+      const Reach reach = {clx, cly, clz, chx, chy, chz, Rc, exc, st.sph, nsph, true};
       if (reuse && resident >= 0) {
         // the whole list is still staged: evaluate it again at the new h
         consume(resident);
@@ -403,11 +405,11 @@ __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, co
     float pax = 0.f, pay = 0.f, paz = 0.f, pad = 0.f;
     float vs = 2.0f * hi4.z;
     int cur = -1, cnt = 0;
-    auto leaf_ok = [&](int l, float sx, float sy, float sz) {
+    auto leaf_ok = [&](int l, float sx, float sy, float sz, LeafBox &lb) {
       const float4 loj = v.leaf_lo[l], hij = v.leaf_hi[l];
       const float R = fmaxf(Hs, loj.w);
-      return box_gap2(W.lx, W.ly, W.lz, W.hx, W.hy, W.hz, loj, hij, sx, sy, sz) < R * R * 1.0002f &&
-             spheres_reach(st.sph, nsph, loj, hij, sx, sy, sz, loj.w);
+      lb = leaf_box(loj, hij, sx, sy, sz, loj.w);
+      return box_gap2(W.lx, W.ly, W.lz, W.hx, W.hy, W.hz, loj, hij, sx, sy, sz) < R * R * 1.0002f;
     };
     auto chunk_ok = [&](int gg, float sx, float sy, float sz) {
       const float4 loc = v.chunk_lo[gg];
@@ -520,7 +522,7 @@ __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, co
       }
     };
     // a leaf passes only within max(Hs, its own largest H) <= max(Hs, Hmax)
-    const Reach reach = {clx, cly, clz, chx, chy, chz, fmaxf(Hs, Hmax) + ceps, exc};
+    const Reach reach = {clx, cly, clz, chx, chy, chz, fmaxf(Hs, Hmax) + ceps, exc, st.sph, nsph};
     int skip = 0, nlist = 0;
     bool more = false;
     do {
@@ -798,7 +800,7 @@ __global__ void __launch_bounds__(PT, 2) k_group_cost(View v) {
     const float chx = W.hx + qox, chy = W.hy + qoy, chz = W.hz + qoz;
     const float Rc = R + 1e-5f * F.wf;
     long long count = 0;
-    auto leaf_ok = [&](int l, float sx, float sy, float sz) {
+    auto leaf_ok = [&](int l, float sx, float sy, float sz, LeafBox &) {
       if (box_gap2(W.lx, W.ly, W.lz, W.hx, W.hy, W.hz, v.leaf_lo[l], v.leaf_hi[l], sx, sy, sz) <
           R * R * 1.0002f)
         count += v.leaf_start[l + 1] - v.leaf_start[l];
@@ -814,7 +816,8 @@ __global__ void __launch_bounds__(PT, 2) k_group_cost(View v) {
       return false;
     };
     bool more = false;
-    const Reach reach = {clx, cly, clz, chx, chy, chz, Rc, __uint_as_float(ds->excursion_bits)};
+    const Reach reach = {clx, cly, clz, chx, chy, chz, Rc, __uint_as_float(ds->excursion_bits),
+                         nullptr, 0};
     search(v, F, reach, st, leaf_ok, chunk_ok, 0, more);
     for (int o = 16; o; o >>= 1) count += __shfl_xor_sync(FULL, count, o);
     if (lane == 0) {
