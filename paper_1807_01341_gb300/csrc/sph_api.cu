@@ -39,7 +39,7 @@ struct Buffers {
   // leaves (at most one per particle)
   int32_t *leaf_start = nullptr, *leaf_cell = nullptr;
   uint32_t *leaf_k = nullptr;
-  // chunks of 32 leaves (at most one per particle)
+  // chunks of CHUNK leaves (at most one per particle)
   int32_t *chunk_cell = nullptr;
   float4 *chunk_lo = nullptr, *chunk_hi = nullptr;
   float4 *leaf_lo = nullptr, *leaf_hi = nullptr;

@@ -19,7 +19,7 @@ constexpr int KEY_MORTON_BITS = 3 * MORTON_BITS;
 constexpr int MAX_BINS = 64;
 constexpr int WARPS_PER_BLOCK = 8;
 constexpr int LEAF_MAX_LIMIT = 64;
-constexpr int CHUNK = 32;          // leaves per chunk (one warp ballot)
+constexpr int CHUNK = 16;          // leaves per chunk (at most 32: one warp ballot)
 constexpr int WG_MAX = 32;         // particles per work group of the pair loops (one per lane)
 
 // Device-resident state of the context: the integer timeline, the sizes of

@@ -7,8 +7,8 @@
 // by one warp.  The warp splits into groups of G lanes;
 // each group owns one active particle i, and its lanes stride over the
 // candidate particles j.  Candidates come from the 27 top-level cells around
-// the leaf's cell: cells holding more than 32 leaves are first pruned by
-// chunk (32 consecutive leaves) bounding boxes, then leaves by their own
+// the leaf's cell: cells holding more than CHUNK leaves are first pruned by
+// chunk (CHUNK consecutive leaves) bounding boxes, then leaves by their own
 // boxes, 32 boxes per warp ballot.  The records of the accepted leaves
 // (contiguous in memory) are staged into shared memory by cp.async.bulk
 // (TMA bulk copies) completing on a per-warp mbarrier, a batch at a time, and
