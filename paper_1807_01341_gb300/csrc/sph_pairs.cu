@@ -114,53 +114,58 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
       }
       // candidate pairs tested: every staged record against every live particle
       const unsigned nlive = __popc(__ballot_sync(FULL, !done && sub == 0));
+      // accept mask of the staged records kb .. kb+31 for this lane's particle
+      auto test_block = [&](int total, int kb) -> unsigned {
+        unsigned mask = 0u;
+        if (G == 1 && ntst <= TRANSPOSE_MAX) {
+          const bool in = kb + lane < total;
+          const float4 pj = st.rec[min(kb + lane, S_DENS - 1)];
+          const float2 px = make_float2(pj.x, pj.x), py = make_float2(pj.y, pj.y),
+                       pz = make_float2(pj.z, pj.z);
+          int q = 0;
+          for (; q + 1 < ntst; q += 2) {  // two live particles per packed test
+            const float4 t0 = st.tst[q], t1 = st.tst[q + 1];
+            const float2 r2 = dist2_x2(make_float2(t0.x, t1.x), make_float2(t0.y, t1.y),
+                                       make_float2(t0.z, t1.z), px, py, pz);
+            const unsigned m0 = __ballot_sync(FULL, in && r2.x < t0.w);
+            const unsigned m1 = __ballot_sync(FULL, in && r2.y < t1.w);
+            if (q == my_rank) mask = m0;
+            if (q + 1 == my_rank) mask = m1;
+          }
+          if (q < ntst) {
+            const float4 t = st.tst[q];
+            const float dx = t.x - pj.x, dy = t.y - pj.y, dz = t.z - pj.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const unsigned m = __ballot_sync(FULL, in && r2 < t.w);
+            if (q == my_rank) mask = m;
+          }
+        } else if (G == 1) {
+          const float2 xx = make_float2(xi.x, xi.x), yy = make_float2(xi.y, xi.y),
+                       zz = make_float2(xi.z, xi.z);
+#pragma unroll
+          for (int u = 0; u < 32; u += 2) {  // two records per packed test
+            const float4 p0 = st.rec[min(kb + u, S_DENS - 1)];
+            const float4 p1 = st.rec[min(kb + u + 1, S_DENS - 1)];
+            const float2 r2 = dist2_x2(xx, yy, zz, make_float2(p0.x, p1.x),
+                                       make_float2(p0.y, p1.y), make_float2(p0.z, p1.z));
+            mask |= (kb + u < total && r2.x < H2) ? (1u << u) : 0u;
+            mask |= (kb + u + 1 < total && r2.y < H2) ? (2u << u) : 0u;
+          }
+        } else {
+#pragma unroll
+          for (int u = sub; u < 32; u += G) {
+            const float4 pj = st.rec[min(kb + u, S_DENS - 1)];
+            const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            mask |= (kb + u < total && r2 < H2) ? (1u << u) : 0u;
+          }
+        }
+        return mask;
+      };
       auto consume = [&](int total) {
         wc.cand += (unsigned long long)total * nlive;
         for (int k0 = 0; k0 < total; k0 += 32) {
-          unsigned mask = 0u;
-          if (G == 1 && ntst <= TRANSPOSE_MAX) {
-            const bool in = k0 + lane < total;
-            const float4 pj = st.rec[min(k0 + lane, S_DENS - 1)];
-            const float2 px = make_float2(pj.x, pj.x), py = make_float2(pj.y, pj.y),
-                         pz = make_float2(pj.z, pj.z);
-            int q = 0;
-            for (; q + 1 < ntst; q += 2) {  // two live particles per packed test
-              const float4 t0 = st.tst[q], t1 = st.tst[q + 1];
-              const float2 r2 = dist2_x2(make_float2(t0.x, t1.x), make_float2(t0.y, t1.y),
-                                         make_float2(t0.z, t1.z), px, py, pz);
-              const unsigned m0 = __ballot_sync(FULL, in && r2.x < t0.w);
-              const unsigned m1 = __ballot_sync(FULL, in && r2.y < t1.w);
-              if (q == my_rank) mask = m0;
-              if (q + 1 == my_rank) mask = m1;
-            }
-            if (q < ntst) {
-              const float4 t = st.tst[q];
-              const float dx = t.x - pj.x, dy = t.y - pj.y, dz = t.z - pj.z;
-              const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-              const unsigned m = __ballot_sync(FULL, in && r2 < t.w);
-              if (q == my_rank) mask = m;
-            }
-          } else if (G == 1) {
-            const float2 xx = make_float2(xi.x, xi.x), yy = make_float2(xi.y, xi.y),
-                         zz = make_float2(xi.z, xi.z);
-#pragma unroll
-            for (int u = 0; u < 32; u += 2) {  // two records per packed test
-              const float4 p0 = st.rec[min(k0 + u, S_DENS - 1)];
-              const float4 p1 = st.rec[min(k0 + u + 1, S_DENS - 1)];
-              const float2 r2 = dist2_x2(xx, yy, zz, make_float2(p0.x, p1.x),
-                                         make_float2(p0.y, p1.y), make_float2(p0.z, p1.z));
-              mask |= (k0 + u < total && r2.x < H2) ? (1u << u) : 0u;
-              mask |= (k0 + u + 1 < total && r2.y < H2) ? (2u << u) : 0u;
-            }
-          } else {
-#pragma unroll
-            for (int u = sub; u < 32; u += G) {
-              const float4 pj = st.rec[min(k0 + u, S_DENS - 1)];
-              const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
-              const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-              mask |= (k0 + u < total && r2 < H2) ? (1u << u) : 0u;
-            }
-          }
+          unsigned mask = test_block(total, k0);  // (every lane: the test votes)
           if (done) mask = 0u;
           while (mask) {
             const int k = k0 + __ffs(mask) - 1;
@@ -426,59 +431,70 @@ __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, co
       __syncwarp();
     }
     const unsigned nlive = __popc(__ballot_sync(FULL, valid && sub == 0));
+    // accept mask of the staged records kb .. kb+31 for this lane's particle
+    auto test_block = [&](int total, int kb) -> unsigned {
+      unsigned mask = 0u;
+      if (G == 1 && ntst <= TRANSPOSE_MAX) {
+        const bool in = kb + lane < total;
+        const float4 pj = sx_rec[min(kb + lane, S_FORCE - 1)];
+        const float Hj2 = pj.w * pj.w;
+        const float2 px = make_float2(pj.x, pj.x), py = make_float2(pj.y, pj.y),
+                     pz = make_float2(pj.z, pj.z);
+        int q = 0;
+        for (; q + 1 < ntst; q += 2) {  // two valid particles per packed test
+          const float4 t0 = st.tst[q], t1 = st.tst[q + 1];
+          const float2 r2 = dist2_x2(make_float2(t0.x, t1.x), make_float2(t0.y, t1.y),
+                                     make_float2(t0.z, t1.z), px, py, pz);
+          const unsigned m0 = __ballot_sync(FULL, in && (r2.x < t0.w || r2.x < Hj2));
+          const unsigned m1 = __ballot_sync(FULL, in && (r2.y < t1.w || r2.y < Hj2));
+          if (q == my_rank) mask = m0;
+          if (q + 1 == my_rank) mask = m1;
+        }
+        if (q < ntst) {
+          const float4 t = st.tst[q];
+          const float dx = t.x - pj.x, dy = t.y - pj.y, dz = t.z - pj.z;
+          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          const unsigned m = __ballot_sync(FULL, in && (r2 < t.w || r2 < Hj2));
+          if (q == my_rank) mask = m;
+        }
+      } else if (G == 1) {
+        const float2 xx = make_float2(xi.x, xi.x), yy = make_float2(xi.y, xi.y),
+                     zz = make_float2(xi.z, xi.z);
+#pragma unroll
+        for (int u = 0; u < 32; u += 2) {  // two records per packed test
+          const float4 p0 = sx_rec[min(kb + u, S_FORCE - 1)];
+          const float4 p1 = sx_rec[min(kb + u + 1, S_FORCE - 1)];
+          const float2 r2 = dist2_x2(xx, yy, zz, make_float2(p0.x, p1.x),
+                                     make_float2(p0.y, p1.y), make_float2(p0.z, p1.z));
+          mask |= (kb + u < total && (r2.x < Hi2 || r2.x < p0.w * p0.w)) ? (1u << u) : 0u;
+          mask |= (kb + u + 1 < total && (r2.y < Hi2 || r2.y < p1.w * p1.w)) ? (2u << u) : 0u;
+        }
+      } else {
+#pragma unroll
+        for (int u = sub; u < 32; u += G) {
+          const float4 pj = sx_rec[min(kb + u, S_FORCE - 1)];
+          const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
+          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+          mask |= (kb + u < total && (r2 < Hi2 || r2 < pj.w * pj.w)) ? (1u << u) : 0u;
+        }
+      }
+      return mask;
+    };
     auto consume = [&](int total) {
       wc.cand += (unsigned long long)total * nlive;
-      for (int k0 = 0; k0 < total; k0 += 32) {
-        unsigned mask = 0u;
-        if (G == 1 && ntst <= TRANSPOSE_MAX) {
-          const bool in = k0 + lane < total;
-          const float4 pj = sx_rec[min(k0 + lane, S_FORCE - 1)];
-          const float Hj2 = pj.w * pj.w;
-          const float2 px = make_float2(pj.x, pj.x), py = make_float2(pj.y, pj.y),
-                       pz = make_float2(pj.z, pj.z);
-          int q = 0;
-          for (; q + 1 < ntst; q += 2) {  // two valid particles per packed test
-            const float4 t0 = st.tst[q], t1 = st.tst[q + 1];
-            const float2 r2 = dist2_x2(make_float2(t0.x, t1.x), make_float2(t0.y, t1.y),
-                                       make_float2(t0.z, t1.z), px, py, pz);
-            const unsigned m0 = __ballot_sync(FULL, in && (r2.x < t0.w || r2.x < Hj2));
-            const unsigned m1 = __ballot_sync(FULL, in && (r2.y < t1.w || r2.y < Hj2));
-            if (q == my_rank) mask = m0;
-            if (q + 1 == my_rank) mask = m1;
-          }
-          if (q < ntst) {
-            const float4 t = st.tst[q];
-            const float dx = t.x - pj.x, dy = t.y - pj.y, dz = t.z - pj.z;
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const unsigned m = __ballot_sync(FULL, in && (r2 < t.w || r2 < Hj2));
-            if (q == my_rank) mask = m;
-          }
-        } else if (G == 1) {
-          const float2 xx = make_float2(xi.x, xi.x), yy = make_float2(xi.y, xi.y),
-                       zz = make_float2(xi.z, xi.z);
-#pragma unroll
-          for (int u = 0; u < 32; u += 2) {  // two records per packed test
-            const float4 p0 = sx_rec[min(k0 + u, S_FORCE - 1)];
-            const float4 p1 = sx_rec[min(k0 + u + 1, S_FORCE - 1)];
-            const float2 r2 = dist2_x2(xx, yy, zz, make_float2(p0.x, p1.x),
-                                       make_float2(p0.y, p1.y), make_float2(p0.z, p1.z));
-            mask |= (k0 + u < total && (r2.x < Hi2 || r2.x < p0.w * p0.w)) ? (1u << u) : 0u;
-            mask |= (k0 + u + 1 < total && (r2.y < Hi2 || r2.y < p1.w * p1.w)) ? (2u << u) : 0u;
-          }
-        } else {
-#pragma unroll
-          for (int u = sub; u < 32; u += G) {
-            const float4 pj = sx_rec[min(k0 + u, S_FORCE - 1)];
-            const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            mask |= (k0 + u < total && (r2 < Hi2 || r2 < pj.w * pj.w)) ? (1u << u) : 0u;
-          }
-        }
-        if (!valid) mask = 0u;
+      // two blocks of 32 records per evaluation round: the lanes' accepted
+      // counts even out over 64 records (records still in index order; the
+      // density loop, at its register limit, keeps rounds of 32)
+      for (int k0 = 0; k0 < total; k0 += 64) {
+        // (every lane calls the test, which votes; the second call's
+        // condition is the same in all lanes)
+        const unsigned m0 = test_block(total, k0);
+        const unsigned m1 = k0 + 32 < total ? test_block(total, k0 + 32) : 0u;
+        unsigned long long mask = valid ? ((unsigned long long)m1 << 32) | m0 : 0ull;
         while (mask) {
           // (the particle itself is accepted too: r = 0, it adds nothing but
           // the signal velocity 2 c_i, the start value; one count subtracted below)
-          const int k = k0 + __ffs(mask) - 1;
+          const int k = k0 + __ffsll(mask) - 1;
           mask &= mask - 1;
           const int ci = st.recc[k];
           if (ci != cur) {
