@@ -25,6 +25,8 @@ roofline    the dominant pair-loop kernel: algorithmic FLOPs per useful pair
 cpu_baseline  the FP64 oracle on a bounded sample of the same workload.
 
 --impl reference times the oracle alone (the CPU reference of this method).
+--ablation prints, instead, the cost per unit simulated time of relevant-only
+drift, drift-all and one global time step (Sec. III-D).
 Under torchrun every rank runs its own replica (the method does not shard
 across GPUs here); value sums the ranks' pairs over the slowest rank's time.
 """
@@ -288,6 +290,89 @@ def run_ours(args, rank, world):
 
 
 # ---------------------------------------------------------------------------
+# --ablation: the time-stepping schemes of Sec. III-D compared (Fig. 2 analogue)
+# ---------------------------------------------------------------------------
+def run_ablation(args):
+    """K steps from the initial conditions under three schemes, each timed
+    with CUDA events (after one warm-up step and a restore):
+    relevant-only drift (the default), drift of every particle each step, and
+    one global time step (every particle active every step).  The individual
+    schemes advance the tick by what their bins allow; the global scheme's
+    time step is the smallest particle step of the initial bins (the
+    Gadget-2-style global step), so its cost per unit simulated time is its
+    cost per all-active step over that step."""
+    import torch
+    from paper_1807_01341_gb300 import _lib, sim
+    from sph_ics import workloads
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ic = workloads.make(args.workload)
+    n = ic["pos"].shape[0]
+    base = dict(workloads.PARAMS[args.workload])
+    stream = torch.cuda.Stream()
+    schemes = {"relevant_only_drift": dict(drift_all=0),
+               "drift_all": dict(drift_all=1),
+               "global_step": dict(drift_all=0, bin_cap=0)}
+    out, b_min = {}, None
+    for name, kw in schemes.items():
+        prm = dict(base, **DEFAULT_LAUNCH)
+        prm.update(kw)
+        ctx = sim.Context(sim.Params(**prm), n)
+        p = sim.Particles.from_ics(ic, with_counts=False)
+        snap = {k: t.clone() for k, t in p.arrays().items()}
+
+        def restore():
+            for k, t in p.arrays().items():
+                t.copy_(snap[k])
+            torch.cuda.synchronize()
+            ctx.build_cells(p, stream)
+            ctx.begin_run(stream)
+        restore()
+        ctx.step_async(p, _lib.SPH_FORM_BATCHED, stream)
+        ctx.step_sync(p, stream)
+        if name == "relevant_only_drift":
+            b_min = int(p.numpy()["bin"].min())  # the initial bins (from step 0)
+        restore()
+        ctx.reset_counters(stream)
+        ti0 = ctx.get_time()[0]
+        ms = 0.0
+        for _ in range(args.steps):
+            while True:
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                with torch.cuda.stream(stream):
+                    ev0.record(stream)
+                    ctx.step_async(p, _lib.SPH_FORM_BATCHED, stream)
+                    ev1.record(stream)
+                done = ctx.step_sync(p, stream)
+                ms += ev0.elapsed_time(ev1)
+                if done:
+                    break
+        ti1 = ctx.get_time()[1]  # the tick the next step would start at
+        c = ctx.counters()
+        sim_t = (ti1 - ti0) * base["dt_min"]
+        out[name] = {"gpu_ms": ms, "ms_per_step": ms / args.steps,
+                     "active_per_step": c["active_particles"] / args.steps,
+                     "pairs": c["pairs_density"] + c["pairs_force"],
+                     "sim_time": sim_t, "ms_per_sim_time": ms / sim_t if sim_t > 0 else None,
+                     "rebuilds": c["rebuilds"]}
+        ctx.close()
+        del p, snap
+        torch.cuda.empty_cache()
+    # the global scheme at the Gadget-2 global step: the smallest initial bin
+    g = out["global_step"]
+    g["global_dt"] = (2 ** b_min) * base["dt_min"]
+    g["ms_per_sim_time"] = g["ms_per_step"] / g["global_dt"]
+    ref = out["relevant_only_drift"]["ms_per_sim_time"]
+    line = {"experiment": "time-to-solution of the time-stepping schemes (Sec. III-D, Fig. 2)",
+            "workload": args.workload, "n_particles": n, "steps": args.steps,
+            "data": "synthetic", "schemes": out,
+            "speedup_vs_global_step": g["ms_per_sim_time"] / ref if ref else None,
+            "speedup_vs_drift_all": out["drift_all"]["ms_per_sim_time"] / ref if ref else None}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # oracle on a bounded sample (cpu_baseline and --impl reference)
 # ---------------------------------------------------------------------------
 def oracle_sample(ic, sample=2048, seed=0):
@@ -353,6 +438,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=2048)
     ap.add_argument("--cpu-sample", type=int, default=2048)
+    ap.add_argument("--ablation", action="store_true",
+                    help="instead of the benchmark line, print the comparison of "
+                         "relevant-only drift, drift-all and one global step")
     args = ap.parse_args()
     world = _env_int("WORLD_SIZE", 1)
     rank = _env_int("RANK", 0)
@@ -364,6 +452,10 @@ def main():
             run_reference(args, rank, world)
         return
 
+    if args.ablation:
+        if rank == 0:
+            run_ablation(args)
+        return
     import torch
     if world > 1:
         torch.distributed.init_process_group("nccl")
