@@ -68,18 +68,26 @@ def kernel_source_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel: str, workload: str):
+def launch_key(launch: dict) -> str:
+    return " ".join(f"{k}={launch[k]}" for k in KNOBS)
+
+
+def profiled_traffic(kernel: str, workload: str, launch: dict):
     """DRAM bytes per launch of a pair kernel from its committed ncu summary,
-    or None when the summary is missing or was taken from other sources."""
+    or None when the summary is missing or was taken from other sources or
+    another launch configuration."""
     path = os.path.join(ROOT, "profiles", f"k_{kernel}_{workload}.md")
     try:
         with open(path) as f:
             text = f.read()
     except OSError:
         return None
-    fields = dict(re.findall(r"^(kernel_source_digest|traffic_bytes_per_launch):\s*(\S+)\s*$",
-                             text, flags=re.M))
+    fields = dict(re.findall(
+        r"^(kernel_source_digest|traffic_bytes_per_launch|launch_config):\s*(\S.*?)\s*$",
+        text, flags=re.M))
     if fields.get("kernel_source_digest") != kernel_source_digest():
+        return None
+    if fields.get("launch_config") != launch_key(launch):
         return None
     try:
         return int(fields["traffic_bytes_per_launch"])
@@ -164,8 +172,10 @@ def run_ours(args, rank, world):
     base = workloads.PARAMS[args.workload]
     tuned = dict(DEFAULT_LAUNCH)
     tune_info = None
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
     if not args.no_autotune:
-        t = autotune.tune(ic, base, args.workload, steps=12)
+        # trials time the benchmark's own step count, L2 flushed between steps
+        t = autotune.tune(ic, base, args.workload, steps=args.steps, flush=flush.zero_)
         tuned = {k: t[k] for k in KNOBS}
         tune_info = {"cached": t.get("cached"),
                      "trials": [dict(r["cand"], pairs_per_s=r["rate"]) for r in t.get("trials", [])]}
@@ -175,7 +185,6 @@ def run_ours(args, rank, world):
     ctx.build_cells(p)
     snapshot = {k: t.clone() for k, t in p.arrays().items()}
     stream = torch.cuda.Stream()
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
 
     def restore():
         for k, t in p.arrays().items():
@@ -509,7 +518,7 @@ def main():
             "roofline": {"bound": "alu", "kernel": rf["kernel"], "achieved": rf["achieved"],
                          "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": rf["achieved"] / FP32_PEAK_TFLOPS,
-                         "traffic": profiled_traffic(rf["kernel"], args.workload),
+                         "traffic": profiled_traffic(rf["kernel"], args.workload, out["tuned"]),
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived)",
                          "launch_ms": rf["per_launch_ms"], "density_ms": rf["density_ms"],
                          "force_ms": rf["force_ms"]},
