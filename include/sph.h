@@ -225,6 +225,18 @@ int sph_step(sph_ctx *ctx, sph_particles *p, int form, void *stream);
  * synchronisation at the end (plus one per recovery). */
 int sph_step_graph(sph_ctx *ctx, sph_particles *p, int n_steps, void *stream);
 
+/* Diagnostics (FP64): the state's total energy and momentum at tick ti
+ * (ti < 0: the current tick), with each particle's velocity and entropy
+ * predicted from its half-step state, v = v_half + a (t - t_mid) and
+ * A + Adot (t - t_mid) (the KDK state of Sec. II-A), and its internal energy
+ * u = A rho^(gamma-1) / (gamma-1) from its last density.  At a tick where
+ * every particle's step ends this is the synchronised energy.  out (host,
+ * 8 doubles): kinetic energy, thermal energy, momentum x, y, z, mass, the
+ * number of particles without a density (rho <= 0, no thermal term), 0.
+ * Summed in a fixed order (reproducible).  Synchronising.
+ * Errors: SPH_ERR_ARG, SPH_ERR_CUDA. */
+int sph_diagnostics(sph_ctx *ctx, const sph_particles *p, int64_t ti, double *out, void *stream);
+
 /* Current and next tick of the device-resident timeline (synchronising). */
 int sph_get_time(sph_ctx *ctx, int64_t *ti_current, int64_t *ti_next);
 /* Set the device-resident current tick (asynchronous). */

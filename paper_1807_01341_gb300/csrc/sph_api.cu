@@ -59,6 +59,7 @@ struct Buffers {
   // state
   DevState *ds = nullptr;
   float *d_hmax = nullptr;
+  double *diag = nullptr;  // diagnostics: block partials, then the result
   DevState *h_ds = nullptr;  // pinned host mirror
 };
 
@@ -691,7 +692,8 @@ int sph_create(const sph_params *params, int64_t n_max, sph_ctx **out) {
         (r = dalloc(&b.q_group, n)) || (r = dalloc(&b.pleaf, n)) || (r = dalloc(&b.group_leaf0, n + 1)) ||
         (r = dalloc(&b.group_cell, n)) || (r = dalloc(&b.group_cost, n)) ||
         (r = dalloc(&b.rec_xm, n)) || (r = dalloc(&b.rec_xH, n)) || (r = dalloc(&b.rec_v, n)) ||
-        (r = dalloc(&b.rec_h, n)) || (r = dalloc(&b.ds, 1)) || (r = dalloc(&b.d_hmax, 1)))
+        (r = dalloc(&b.rec_h, n)) || (r = dalloc(&b.ds, 1)) || (r = dalloc(&b.d_hmax, 1)) ||
+        (r = dalloc(&b.diag, (long long)(DIAG_BLOCKS + 1) * DIAG_FIELDS)))
       break;
     if (cudaMallocHost((void **)&b.h_ds, sizeof(DevState)) != cudaSuccess) {
       r = SPH_ERR_NOMEM;
@@ -740,7 +742,7 @@ int sph_destroy(sph_ctx *ctx) {
   dfree(b.rec_xm); dfree(b.rec_xH); dfree(b.rec_v); dfree(b.rec_h);
   dfree(b.cell_start); dfree(b.cell_leaf_start); dfree(b.cell_stamp); dfree(b.cell_rel_stamp);
   dfree(b.q_act_cells); dfree(b.leaf_counts); dfree(b.leaf_offsets);
-  dfree(b.ds); dfree(b.d_hmax);
+  dfree(b.ds); dfree(b.d_hmax); dfree(b.diag);
   if (b.h_ds) cudaFreeHost(b.h_ds);
   delete ctx;
   return SPH_OK;
@@ -1007,6 +1009,22 @@ int sph_resume(sph_ctx *ctx, sph_particles *p, int64_t ti_current, int first, vo
   ctx->entropy_ready = !first;
   ctx->pending = 0;
   ctx->init_pending = false;
+  return SPH_OK;
+}
+
+int sph_diagnostics(sph_ctx *ctx, const sph_particles *p, int64_t ti, double *out,
+                    void *stream) {
+  if (!ctx || !valid_particles(ctx, p) || !out) return SPH_ERR_ARG;
+  cudaStream_t st = S(stream);
+  long long t = ti;
+  if (t < 0) {
+    SPH_TRY(read_state(ctx, st));
+    t = ctx->b.h_ds->ti;
+  }
+  double *dout = ctx->b.diag + (size_t)DIAG_BLOCKS * DIAG_FIELDS;
+  SPH_CUDA(launch_diagnostics(*p, t, ctx->prm.dt_min, ctx->prm.gamma, ctx->b.diag, dout, st));
+  SPH_CUDA(cudaMemcpyAsync(out, dout, sizeof(double) * DIAG_FIELDS, cudaMemcpyDeviceToHost, st));
+  SPH_CUDA(cudaStreamSynchronize(st));
   return SPH_OK;
 }
 

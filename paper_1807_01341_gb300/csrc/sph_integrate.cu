@@ -530,6 +530,58 @@ __global__ void k_mark_bin(View v, int bin) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// diagnostics: total energy and momentum in FP64
+// ---------------------------------------------------------------------------
+// Per particle, the velocity and entropy at tick ti predicted from the
+// half-step state (v_half + a (t - t_mid), A + Adot (t - t_mid), Sec. II-A),
+// u = A rho^(gamma-1) / (gamma-1) from the last density; summed per block in
+// a fixed order (each thread a fixed stride of particles, then a tree in
+// shared memory), so the result does not depend on scheduling.
+__global__ void __launch_bounds__(DIAG_THREADS)
+k_diag(const sph_particles p, long long ti, double dt_min, double gamma, double *partials) {
+  __shared__ double s[DIAG_FIELDS][DIAG_THREADS];
+  double acc[DIAG_FIELDS];
+#pragma unroll
+  for (int k = 0; k < DIAG_FIELDS; k++) acc[k] = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
+    const int bi = p.bin[i] & (MAX_BINS - 1);
+    const double dtp = ((double)(ti - p.ti_begin[i]) - 0.5 * (double)(1ll << bi)) * dt_min;
+    const double m = (double)p.m[i];
+    const double vx = (double)p.vx[i] + (double)p.ax[i] * dtp;
+    const double vy = (double)p.vy[i] + (double)p.ay[i] * dtp;
+    const double vz = (double)p.vz[i] + (double)p.az[i] * dtp;
+    const double A = (double)p.A[i] + (double)p.Adot[i] * dtp;
+    const double rho = (double)p.rho[i];
+    acc[0] += 0.5 * m * (vx * vx + vy * vy + vz * vz);
+    if (rho > 0.0) acc[1] += m * A * pow(rho, gamma - 1.0) / (gamma - 1.0);
+    else acc[6] += 1.0;
+    acc[2] += m * vx;
+    acc[3] += m * vy;
+    acc[4] += m * vz;
+    acc[5] += m;
+  }
+#pragma unroll
+  for (int k = 0; k < DIAG_FIELDS; k++) s[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int w = DIAG_THREADS / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+#pragma unroll
+      for (int k = 0; k < DIAG_FIELDS; k++) s[k][threadIdx.x] += s[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < DIAG_FIELDS) partials[blockIdx.x * DIAG_FIELDS + threadIdx.x] = s[threadIdx.x][0];
+}
+
+// the block partials summed in block order
+__global__ void k_diag_final(const double *partials, int nblocks, double *out) {
+  if (threadIdx.x >= DIAG_FIELDS) return;
+  double t = 0.0;
+  for (int b = 0; b < nblocks; b++) t += partials[b * DIAG_FIELDS + threadIdx.x];
+  out[threadIdx.x] = t;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -572,6 +624,14 @@ cudaError_t launch_bins(const View &v, long long *ti_next_out, int count_step, c
   note_launches(2);
   k_bins<<<v.grid_util, UT, 0, st>>>(v);
   k_next_time<<<1, 1, 0, st>>>(v, ti_next_out, count_step);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diagnostics(const sph_particles &p, long long ti, double dt_min, double gamma,
+                               double *partials, double *out, cudaStream_t st) {
+  note_launches(2);
+  k_diag<<<DIAG_BLOCKS, DIAG_THREADS, 0, st>>>(p, ti, dt_min, gamma, partials);
+  k_diag_final<<<1, 32, 0, st>>>(partials, DIAG_BLOCKS, out);
   return cudaGetLastError();
 }
 

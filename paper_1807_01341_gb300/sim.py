@@ -245,6 +245,16 @@ class Context:
     def set_time(self, ti: int, stream=None):
         check(self.L.sph_set_time(self.h, int(ti), _stream_ptr(stream)), "sph_set_time")
 
+    def diagnostics(self, p: Particles, ti: int = -1, stream=None) -> dict:
+        """FP64 kinetic and thermal energy, momentum and mass of the state at
+        tick ti (default: the current tick); see sph_diagnostics."""
+        out = (ctypes.c_double * 8)()
+        check(self.L.sph_diagnostics(self.h, ctypes.byref(p.struct()), int(ti), out,
+                                     _stream_ptr(stream)), "sph_diagnostics")
+        return {"E_kin": out[0], "E_therm": out[1], "E": out[0] + out[1],
+                "momentum": (out[2], out[3], out[4]), "mass": out[5],
+                "no_density": int(out[6])}
+
     def status(self):
         s, d = ctypes.c_int(), ctypes.c_int64()
         check(self.L.sph_get_status(self.h, ctypes.byref(s), ctypes.byref(d)), "sph_get_status")

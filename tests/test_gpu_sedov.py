@@ -1,0 +1,102 @@
+"""The Sedov blast on the GPU against the self-similar Sedov-Taylor solution:
+the shock radius R = XI0 (E t^2 / rho_0)^(1/5) (XI0 = 0.4936^(-1/5) for
+gamma = 5/3), measured as the mass-weighted radius of the compressed shell
+(rho > 1.2 rho_0) and as the peak of the binned radial density, and the total
+energy from the FP64 diagnostics.  The oracle's own run of the small case is
+pinned to the same solution in tests/test_oracle_pins.py."""
+import numpy as np
+import pytest
+
+import sph_ics
+from sph_ics import workloads
+
+pytestmark = pytest.mark.gpu
+
+XI0 = 0.4936 ** -0.2
+
+
+@pytest.fixture(scope="module")
+def sim():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1807_01341_gb300 import build
+    build.build()
+    from paper_1807_01341_gb300 import sim as S
+    return S
+
+
+def _advance(ctx, p, n_steps=None, t_until=None, dt_min=None):
+    """Steps (rebuilding the cells when the library asks for it)."""
+    from paper_1807_01341_gb300 import _lib
+    k = 0
+    while True:
+        if n_steps is not None and k >= n_steps:
+            return
+        if t_until is not None and ctx.get_time()[1] * dt_min > t_until:
+            return
+        ctx.step_async(p, _lib.SPH_FORM_BATCHED)
+        while not ctx.step_sync(p):
+            ctx.step_async(p, _lib.SPH_FORM_BATCHED)
+        assert ctx.status()[0] == 0
+        k += 1
+
+
+def _measure(ctx, p, E0, dt_min):
+    t = ctx.get_time()[0] * dt_min
+    st = p.numpy()
+    r = np.linalg.norm(np.stack([st["x"], st["y"], st["z"]], 1) - 0.5, axis=1)
+    rho, m = st["rho"].astype(np.float64), st["m"].astype(np.float64)
+    R_st = XI0 * (E0 * t * t) ** 0.2
+    sh = rho > 1.2
+    R_shell = float((m[sh] * r[sh]).sum() / m[sh].sum())
+    edges = np.arange(0.0, 0.45, 0.005)
+    k = np.digitize(r, edges) - 1
+    nb = len(edges) - 1
+    prof = np.bincount(k, weights=rho, minlength=nb + 1)[:nb] / \
+        np.maximum(np.bincount(k, minlength=nb + 1)[:nb], 1)
+    j = int(np.argmax(prof))
+    R_peak = 0.5 * (edges[j] + edges[j + 1])
+    E = ctx.diagnostics(p)["E"]
+    return t, R_shell / R_st, R_peak / R_st, E / E0
+
+
+def test_sedov_small_follows_sedov_taylor(sim):
+    """The oracle pin's case (24^3, unit energy in 32 particles, bins up to
+    2^3 t_min) on the GPU: at t = 0.0075, 0.015, 0.03 the shell radius is
+    within 5 % of R, the density peak 0-12 % behind it, and the energy within
+    1e-3 of its initial value."""
+    ic = sph_ics.sedov(24, seed=2)
+    E0 = float((ic["m"] * ic["u"]).sum())
+    params = sim.Params(cfl=0.1, dt_min=2.0 ** -15, bin_cap=3)
+    ctx = sim.Context(params, ic["pos"].shape[0])
+    p = sim.Particles.from_ics(ic)
+    ctx.build_cells(p)
+    ctx.begin_run()
+    for t_want in (0.0075, 0.015, 0.03):
+        _advance(ctx, p, t_until=t_want, dt_min=params.dt_min)
+        t, shell, peak, e = _measure(ctx, p, E0, params.dt_min)
+        assert abs(shell - 1.0) < 0.05, (t, shell)
+        assert 0.88 < peak <= 1.0, (t, peak)
+        assert abs(e - 1.0) < 1e-3, (t, e)
+    ctx.close()
+
+
+def test_sedov_262k_follows_sedov_taylor(sim):
+    """The 262,144-particle Sedov workload, its 100 steps (bins up to 2^10
+    t_min): shell radius within 5 % of R, density peak 0-12 % behind it,
+    energy within 1 %."""
+    name = "c2_sedov_262k"
+    ic = workloads.make(name)
+    E0 = float((ic["m"] * ic["u"]).sum())
+    params = sim.Params(**workloads.PARAMS[name])
+    ctx = sim.Context(params, ic["pos"].shape[0])
+    p = sim.Particles.from_ics(ic, with_counts=False)
+    ctx.build_cells(p)
+    ctx.begin_run()
+    _advance(ctx, p, n_steps=workloads.STEPS[name])
+    t, shell, peak, e = _measure(ctx, p, E0, params.dt_min)
+    assert abs(shell - 1.0) < 0.05, (t, shell)
+    assert 0.88 < peak <= 1.0, (t, peak)
+    assert abs(e - 1.0) < 0.01, (t, e)
+    ctx.close()
