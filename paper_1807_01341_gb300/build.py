@@ -37,6 +37,7 @@ def _stale(obj: str, deps) -> bool:
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
     hdrs = [os.path.join(CSRC, "sph_internal.cuh"), os.path.join(CSRC, "sph_pairloop.cuh"),
+            os.path.join(CSRC, "sph_diag.cuh"),
             os.path.join(os.path.dirname(HERE), "include", "sph.h")]
     objs = []
     jobs = []

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "sph_internal.cuh"
+#include "sph_diag.cuh"
 
 #include <atomic>
 

@@ -11,6 +11,7 @@
 #include <cstddef>
 
 #include "sph_internal.cuh"
+#include "sph_diag.cuh"
 
 namespace sph {
 

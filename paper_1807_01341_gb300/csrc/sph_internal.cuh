@@ -245,11 +245,6 @@ cudaError_t launch_bins(const View &v, long long *ti_next_out, int count_step, c
 cudaError_t launch_mark_bin(const View &v, int bin, cudaStream_t st);
 // closing kick, new bins, opening kick and the next tick of a step, one launch
 cudaError_t launch_close_step(const View &v, cudaStream_t st);
-// FP64 energy and momentum of the state at tick ti (partials: DIAG_BLOCKS x
-// DIAG_FIELDS doubles of scratch; out: DIAG_FIELDS doubles, device)
-constexpr int DIAG_FIELDS = 8, DIAG_BLOCKS = 304, DIAG_THREADS = 256;
-cudaError_t launch_diagnostics(const sph_particles &p, long long ti, double dt_min, double gamma,
-                               double *partials, double *out, cudaStream_t st);
 // sph_pairs.cu
 cudaError_t launch_density(const View &v, int flags, int bin_filter, bool persistent,
                            int grid, cudaStream_t st);
