@@ -249,6 +249,11 @@ int sph_get_status(sph_ctx *ctx, int *status, int64_t *detail);
 int sph_clear_status(sph_ctx *ctx, void *stream);
 int sph_get_counters(sph_ctx *ctx, sph_counters *out);
 int sph_reset_counters(sph_ctx *ctx, void *stream);
+/* Occupancy of the time bins (Eq. 2): counts[b] = the number of particles on
+ * bin b, b < n_bins (at most 64), as of the last step or cell build (the
+ * histogram of Fig. 1).  Synchronising: waits for the work queued on stream.
+ * Errors: SPH_ERR_ARG, SPH_ERR_CUDA. */
+int sph_get_bin_counts(sph_ctx *ctx, int64_t *counts, int n_bins, void *stream);
 
 /* Device time of the pair-loop launches, measured with CUDA events recorded
  * on the launching stream around every density and force launch (inside the

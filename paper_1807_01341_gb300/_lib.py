@@ -115,6 +115,7 @@ def load(path: str = LIB_PATH):
     L.sph_resume.argtypes = [_vp, P(sph_particles), _i64, _i, _vp]
     L.sph_grid_density.argtypes = [_vp, P(sph_particles), _i, _i64, _vp, _vp]
     L.sph_diagnostics.argtypes = [_vp, P(sph_particles), _i64, P(_d), _vp]
+    L.sph_get_bin_counts.argtypes = [_vp, P(_i64), _i, _vp]
     L.sph_grid_density_bwd.argtypes = [_vp, P(sph_particles), _i, _i64, _vp, P(sph_adjoint), _vp]
     L.sph_step_bwd.argtypes = [_vp, P(sph_particles), P(sph_particles), _i64, _i,
                                P(sph_adjoint), _vp]
@@ -127,7 +128,8 @@ def load(path: str = LIB_PATH):
                  "sph_set_time", "sph_get_status", "sph_clear_status", "sph_get_counters",
                  "sph_reset_counters", "sph_set_profiling", "sph_get_kernel_times",
                  "sph_reset_kernel_times", "sph_state_copy", "sph_resume", "sph_grid_density",
-                 "sph_grid_density_bwd", "sph_step_bwd", "sph_diagnostics"):
+                 "sph_grid_density_bwd", "sph_step_bwd", "sph_diagnostics",
+                 "sph_get_bin_counts"):
         getattr(L, name).restype = _i
     _lib = L
     return L
@@ -143,7 +145,7 @@ def exported_symbols():
             "sph_get_counters", "sph_reset_counters", "sph_set_profiling",
             "sph_get_kernel_times", "sph_reset_kernel_times", "sph_cell_order_noalloc",
             "sph_state_copy", "sph_resume", "sph_grid_density", "sph_grid_density_bwd",
-            "sph_step_bwd", "sph_diagnostics", "sph_strerror"]
+            "sph_step_bwd", "sph_diagnostics", "sph_get_bin_counts", "sph_strerror"]
 
 
 class SphError(RuntimeError):

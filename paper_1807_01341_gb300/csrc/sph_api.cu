@@ -948,6 +948,13 @@ int sph_get_counters(sph_ctx *ctx, sph_counters *out) {
   return SPH_OK;
 }
 
+int sph_get_bin_counts(sph_ctx *ctx, int64_t *counts, int n_bins, void *stream) {
+  if (!ctx || !counts || n_bins < 1 || n_bins > MAX_BINS) return SPH_ERR_ARG;
+  SPH_TRY(read_state(ctx, S(stream)));
+  for (int b = 0; b < n_bins; b++) counts[b] = (int64_t)ctx->b.h_ds->bin_count[b];
+  return SPH_OK;
+}
+
 int sph_reset_counters(sph_ctx *ctx, void *stream) {
   if (!ctx) return SPH_ERR_ARG;
   cudaStream_t st = S(stream);

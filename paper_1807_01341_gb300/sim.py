@@ -245,6 +245,13 @@ class Context:
     def set_time(self, ti: int, stream=None):
         check(self.L.sph_set_time(self.h, int(ti), _stream_ptr(stream)), "sph_set_time")
 
+    def bin_counts(self, n_bins: int = 64, stream=None) -> list:
+        """Particles per time bin (Eq. 2) as of the last step or cell build."""
+        out = (ctypes.c_int64 * n_bins)()
+        check(self.L.sph_get_bin_counts(self.h, out, int(n_bins), _stream_ptr(stream)),
+              "sph_get_bin_counts")
+        return list(out)
+
     def diagnostics(self, p: Particles, ti: int = -1, stream=None) -> dict:
         """FP64 kinetic and thermal energy, momentum and mass of the state at
         tick ti (default: the current tick); see sph_diagnostics."""
