@@ -61,6 +61,7 @@ struct Buffers {
   DevState *ds = nullptr;
   float *d_hmax = nullptr;
   double *diag = nullptr;  // diagnostics: block partials, then the result
+  unsigned int *d_bad = nullptr;  // invalid-input count of the last cell build
   DevState *h_ds = nullptr;  // pinned host mirror
 };
 
@@ -353,7 +354,15 @@ int build_cells(sph_ctx *ctx, sph_particles *p, cudaStream_t st) {
   v = make_view(ctx, p);
   const double w = ctx->prm.box / (double)nc;
   // keys, stable radix sort, permutation of every particle array
-  SPH_CUDA(launch_cell_keys(v, nc, w, b.keys[0], b.vals[0], st));
+  SPH_CUDA(cudaMemsetAsync(b.d_bad, 0, sizeof(unsigned int), st));
+  SPH_CUDA(launch_cell_keys(v, nc, w, b.keys[0], b.vals[0], b.d_bad, st));
+  if (n > 0) {
+    // non-finite positions or h: rejected before anything is reordered
+    unsigned int bad = 0;
+    SPH_CUDA(cudaMemcpyAsync(&bad, b.d_bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+    SPH_CUDA(cudaStreamSynchronize(st));
+    if (bad) return SPH_ERR_ARG;
+  }
   int cell_bits = 1;
   while ((1LL << cell_bits) < n_cells) cell_bits++;
   bool alt = false;
@@ -694,7 +703,8 @@ int sph_create(const sph_params *params, int64_t n_max, sph_ctx **out) {
         (r = dalloc(&b.group_cell, n)) || (r = dalloc(&b.group_cost, n)) ||
         (r = dalloc(&b.rec_xm, n)) || (r = dalloc(&b.rec_xH, n)) || (r = dalloc(&b.rec_v, n)) ||
         (r = dalloc(&b.rec_h, n)) || (r = dalloc(&b.ds, 1)) || (r = dalloc(&b.d_hmax, 1)) ||
-        (r = dalloc(&b.diag, (long long)(DIAG_BLOCKS + 1) * DIAG_FIELDS)))
+        (r = dalloc(&b.diag, (long long)(DIAG_BLOCKS + 1) * DIAG_FIELDS)) ||
+        (r = dalloc(&b.d_bad, 1)))
       break;
     if (cudaMallocHost((void **)&b.h_ds, sizeof(DevState)) != cudaSuccess) {
       r = SPH_ERR_NOMEM;
@@ -743,7 +753,7 @@ int sph_destroy(sph_ctx *ctx) {
   dfree(b.rec_xm); dfree(b.rec_xH); dfree(b.rec_v); dfree(b.rec_h);
   dfree(b.cell_start); dfree(b.cell_leaf_start); dfree(b.cell_stamp); dfree(b.cell_rel_stamp);
   dfree(b.q_act_cells); dfree(b.leaf_counts); dfree(b.leaf_offsets);
-  dfree(b.ds); dfree(b.d_hmax); dfree(b.diag);
+  dfree(b.ds); dfree(b.d_hmax); dfree(b.diag); dfree(b.d_bad);
   if (b.h_ds) cudaFreeHost(b.h_ds);
   delete ctx;
   return SPH_OK;

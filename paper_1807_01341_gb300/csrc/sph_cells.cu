@@ -69,10 +69,15 @@ __device__ __forceinline__ unsigned long long spread3(unsigned long long v) {
   return r;
 }
 
+// (also counts in *bad the particles whose position is not finite or whose h
+// is not a positive finite number: the caller rejects such input)
 __global__ void k_cell_keys(View v, int nc, double w, unsigned long long *__restrict__ keys,
-                            unsigned int *__restrict__ vals) {
+                            unsigned int *__restrict__ vals, unsigned int *__restrict__ bad) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= v.n) return;
+  const float hi = v.h[i];
+  if (!(isfinite(v.x[i]) && isfinite(v.y[i]) && isfinite(v.z[i]) && hi > 0.0f && isfinite(hi)))
+    atomicAdd(bad, 1u);
   double x = wrap_box(v.x[i], v.box), y = wrap_box(v.y[i], v.box), z = wrap_box(v.z[i], v.box);
   v.x[i] = x;
   v.y[i] = y;
@@ -523,10 +528,10 @@ cudaError_t launch_reduce_hmax(const View &v, float *out_max, cudaStream_t st) {
 }
 
 cudaError_t launch_cell_keys(const View &v, int nc, double w, unsigned long long *keys,
-                             unsigned int *vals, cudaStream_t st) {
+                             unsigned int *vals, unsigned int *bad, cudaStream_t st) {
   note_launches(1);
   if (v.n == 0) return cudaSuccess;
-  k_cell_keys<<<blocks_for(v.n, 256), 256, 0, st>>>(v, nc, w, keys, vals);
+  k_cell_keys<<<blocks_for(v.n, 256), 256, 0, st>>>(v, nc, w, keys, vals, bad);
   return cudaGetLastError();
 }
 

@@ -207,8 +207,10 @@ void note_launches(int n);
 // ---------------------------------------------------------------------------
 // sph_cells.cu
 cudaError_t launch_reduce_hmax(const View &v, float *out_max, cudaStream_t st);
+// (bad: a device counter, incremented per particle with a non-finite position
+// or an h that is not a positive finite number)
 cudaError_t launch_cell_keys(const View &v, int nc, double w, unsigned long long *keys,
-                             unsigned int *vals, cudaStream_t st);
+                             unsigned int *vals, unsigned int *bad, cudaStream_t st);
 cudaError_t radix_sort_pairs(unsigned long long *keys, unsigned int *vals,
                              unsigned long long *keys_alt, unsigned int *vals_alt, int n,
                              int nbits, unsigned int *hist, unsigned int *scan_tmp,

@@ -205,3 +205,61 @@ def test_h_growth_triggers_rebuild_and_redo(sim, orc):
     ref = orc.density(pos, st["m"].astype(np.float64),
                       np.float32(ic["h0"])[perm].astype(np.float64), np.ones(n, np.uint8))
     assert np.max(np.abs(st["h"] / ref["h"] - 1)) < 1e-5
+
+
+def test_invalid_input_is_rejected(sim):
+    """A non-finite position or h (NaN, inf, h <= 0): the cell build returns
+    SPH_ERR_ARG before reordering anything; the context stays usable."""
+    import torch
+    L = _lib()
+    ic = sph_ics.lattice(8, 0.1, seed=5)
+    for field, value in (("x", float("nan")), ("z", float("inf")), ("h", float("nan")),
+                         ("h", 0.0), ("h", -1.0)):
+        ctx = sim.Context(sim.Params(**STEP_PARAMS), ic["pos"].shape[0])
+        p = sim.Particles.from_ics(ic)
+        getattr(p, field)[7] = value
+        before = p.numpy()["y"].copy()
+        with pytest.raises(L.SphError) as e:
+            ctx.build_cells(p)
+        assert e.value.code == L.SPH_ERR_ARG, (field, value)
+        assert np.array_equal(p.numpy()["y"], before)  # not reordered
+        # the same context builds and steps once the input is repaired
+        p2 = sim.Particles.from_ics(ic)
+        ctx.build_cells(p2)
+        ctx.step(p2, L.SPH_FORM_BATCHED)
+        assert ctx.status()[0] == 0
+        ctx.close()
+    torch.cuda.synchronize()
+
+
+def test_h_nonconvergence_is_reported(sim):
+    """h_max_iter = 1: the smoothing lengths cannot converge; the step
+    completes and the status word reports SPH_ERR_H_NOCONV with the number
+    of particles concerned (no halt, finite state)."""
+    L = _lib()
+    ic = _ic_step(seed=37)
+    n = ic["pos"].shape[0]
+    ctx, p = gpu_setup(ic, sim.Params(**STEP_PARAMS, h_max_iter=1))
+    ctx.step(p, L.SPH_FORM_BATCHED)
+    code, detail = ctx.status()
+    assert code == L.SPH_ERR_H_NOCONV and 0 < detail <= n
+    st = p.numpy()
+    assert np.all(np.isfinite(st["rho"])) and np.all(np.isfinite(st["ax"]))
+    ctx.clear_status()
+    assert ctx.status()[0] == 0
+    ctx.close()
+
+
+def test_dt_below_t_min_is_reported(sim):
+    """t_min larger than every CFL step: the step completes, the particles go
+    to bin 0 and the status word reports SPH_ERR_DT_TOO_SMALL for all of
+    them."""
+    L = _lib()
+    ic = _ic_step(seed=41)
+    n = ic["pos"].shape[0]
+    ctx, p = gpu_setup(ic, sim.Params(**dict(STEP_PARAMS, dt_min=10.0)))
+    ctx.step(p, L.SPH_FORM_BATCHED)
+    code, detail = ctx.status()
+    assert code == L.SPH_ERR_DT_TOO_SMALL and detail == n
+    assert np.all(p.numpy()["bin"] == 0)
+    ctx.close()
