@@ -155,14 +155,23 @@ __device__ __forceinline__ double wrap_pos(double x, double box) {
 // predict v and A at that tick, refresh the FP32 records the pair loops read
 // (positions relative to each particle's leaf corner) and give inactive
 // particles P and c from their frozen density and predicted entropy -- a
-// chunk of a dense clump holds up to 512 particles, two rounds of the block;
-// then the first warp recomputes, one leaf per lane, each leaf's bounding box
-// and largest support (and, when do_bins, its smallest bin and bin mask), and
-// the chunk's box in the cell frame.  Called by every thread of the block.
+// chunk of a dense clump holds up to CHUNK * leaf_max particles, a few rounds
+// of the block -- keeping each particle's position record and bin in shared
+// memory; then each warp reduces whole leaves (one particle per lane) to the
+// leaf's bounding box and largest support (and, when do_bins, its smallest
+// bin and bin mask), and the first warp combines the leaves into the chunk's
+// box in the cell frame.  Min and max are exact, so the boxes do not depend
+// on the order of the reduction.  Called by every thread of the block.
+constexpr int CHUNK_PARTICLES = CHUNK * WG_MAX;  // leaf_max <= WG_MAX
+static_assert(WG_MAX == 32, "one lane per particle of a leaf");
+
 __device__ void chunk_update(const View &v, int g, bool do_drift, bool do_bins) {
   __shared__ float s_exc[UT / 32];
+  __shared__ float4 s_rec[CHUNK_PARTICLES];  // leaf-frame position and support
+  __shared__ uint8_t s_bin[CHUNK_PARTICLES];
+  __shared__ float4 s_lo[CHUNK], s_hi[CHUNK];  // leaf boxes in the cell frame (w: largest H)
   const DevState *ds = v.ds;
-  const int lane = lane_id();
+  const int lane = lane_id(), warp = threadIdx.x >> 5;
   const int cell = v.chunk_cell[g];
   const int l0 = v.cell_leaf_start[cell] + CHUNK * (g - v.cell_chunk_start[cell]);
   const int l1 = min(l0 + CHUNK, v.cell_leaf_start[cell + 1]);
@@ -214,6 +223,8 @@ __device__ void chunk_update(const View &v, int g, bool do_drift, bool do_bins) 
     v.rec_xm[i] = make_float4(fx, fy, fz, m);
     v.rec_xH[i] = make_float4(fx, fy, fz, H);
     v.rec_v[i] = make_float4(vpx, vpy, vpz, m);
+    s_rec[i - pa] = make_float4(fx, fy, fz, H);
+    s_bin[i - pa] = (uint8_t)bi;
     const float rho = v.rho[i];
     float fP = 0.0f, c = 0.0f;
     if (rho > 0.0f) {
@@ -226,61 +237,82 @@ __device__ void chunk_update(const View &v, int g, bool do_drift, bool do_bins) 
     v.rec_h[i] = make_float4(rho, fP, c, 1.0f / H);
   }
   for (int o = 16; o; o >>= 1) exc = fmaxf(exc, __shfl_xor_sync(0xffffffffu, exc, o));
-  if (lane == 0) s_exc[threadIdx.x >> 5] = exc;
-  __syncthreads();  // the records of phase 1 are visible to the first warp
-  if (threadIdx.x < 32) {
-  for (int k = 0; k < (int)(blockDim.x >> 5); k++) exc = fmaxf(exc, s_exc[k]);
-  // phase 2: one leaf per lane
-  float lx = INFINITY, ly = INFINITY, lz = INFINITY;
-  float hx = -INFINITY, hy = -INFINITY, hz = -INFINITY, Hm = 0.0f;
-  if (l0 + lane < l1) {
-    const int leaf = l0 + lane;
-    const int a = v.leaf_start[leaf], b = v.leaf_start[leaf + 1];
+  if (lane == 0) s_exc[warp] = exc;
+  __syncthreads();  // the chunk's records are in shared memory
+  // phase 2: one leaf per warp, one particle per lane
+  const float wqf = (float)wq;
+  for (int q = warp; q < l1 - l0; q += (int)(blockDim.x >> 5)) {
+    const int leaf = l0 + q;
+    const int a = v.leaf_start[leaf], cnt = v.leaf_start[leaf + 1] - a;
     float bx = INFINITY, by = INFINITY, bz = INFINITY, tx = -INFINITY, ty = -INFINITY, tz = -INFINITY;
+    float Hm = 0.0f;
     int minb = 127;
     unsigned long long mask = 0ull;
-#pragma unroll 4
-    for (int k = a; k < b; k++) {
-      const float4 r = v.rec_xH[k];
-      bx = fminf(bx, r.x); by = fminf(by, r.y); bz = fminf(bz, r.z);
-      tx = fmaxf(tx, r.x); ty = fmaxf(ty, r.y); tz = fmaxf(tz, r.z);
-      Hm = fmaxf(Hm, r.w);
+    if (lane < cnt) {
+      const float4 r = s_rec[a - pa + lane];
+      bx = tx = r.x;
+      by = ty = r.y;
+      bz = tz = r.z;
+      Hm = r.w;
       if (do_bins) {
-        const int bk = v.bin[k] & (MAX_BINS - 1);
-        minb = min(minb, bk);
-        mask |= 1ull << bk;
+        minb = s_bin[a - pa + lane];
+        mask = 1ull << minb;
       }
     }
-    v.leaf_lo[leaf] = make_float4(bx, by, bz, Hm);
-    v.leaf_hi[leaf] = make_float4(tx, ty, tz, 0.0f);
-    if (do_bins) {
-      v.leaf_min_bin[leaf] = (uint8_t)minb;
-      v.leaf_bin_mask[leaf] = mask;
+    for (int o = 16; o; o >>= 1) {
+      bx = fminf(bx, __shfl_xor_sync(0xffffffffu, bx, o));
+      by = fminf(by, __shfl_xor_sync(0xffffffffu, by, o));
+      bz = fminf(bz, __shfl_xor_sync(0xffffffffu, bz, o));
+      tx = fmaxf(tx, __shfl_xor_sync(0xffffffffu, tx, o));
+      ty = fmaxf(ty, __shfl_xor_sync(0xffffffffu, ty, o));
+      tz = fmaxf(tz, __shfl_xor_sync(0xffffffffu, tz, o));
+      Hm = fmaxf(Hm, __shfl_xor_sync(0xffffffffu, Hm, o));
+      if (do_bins) {
+        minb = min(minb, __shfl_xor_sync(0xffffffffu, minb, o));
+        mask |= __shfl_xor_sync(0xffffffffu, mask, o);
+      }
     }
-    const uint32_t k = v.leaf_k[leaf];
-    const float wqf = (float)wq;
-    const float sx = leaf_kx(k) * wqf, sy = leaf_ky(k) * wqf, sz = leaf_kz(k) * wqf;
-    lx = bx + sx; ly = by + sy; lz = bz + sz;
-    hx = tx + sx; hy = ty + sy; hz = tz + sz;
+    if (lane == 0) {
+      v.leaf_lo[leaf] = make_float4(bx, by, bz, Hm);
+      v.leaf_hi[leaf] = make_float4(tx, ty, tz, 0.0f);
+      if (do_bins) {
+        v.leaf_min_bin[leaf] = (uint8_t)minb;
+        v.leaf_bin_mask[leaf] = mask;
+      }
+      const uint32_t k = v.leaf_k[leaf];
+      const float sx = leaf_kx(k) * wqf, sy = leaf_ky(k) * wqf, sz = leaf_kz(k) * wqf;
+      s_lo[q] = make_float4(bx + sx, by + sy, bz + sz, Hm);
+      s_hi[q] = make_float4(tx + sx, ty + sy, tz + sz, 0.0f);
+    }
   }
-  for (int o = 16; o; o >>= 1) {
-    lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
-    ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
-    lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
-    hx = fmaxf(hx, __shfl_xor_sync(0xffffffffu, hx, o));
-    hy = fmaxf(hy, __shfl_xor_sync(0xffffffffu, hy, o));
-    hz = fmaxf(hz, __shfl_xor_sync(0xffffffffu, hz, o));
-    Hm = fmaxf(Hm, __shfl_xor_sync(0xffffffffu, Hm, o));
-    exc = fmaxf(exc, __shfl_xor_sync(0xffffffffu, exc, o));
+  __syncthreads();
+  // phase 3: the chunk's box from its leaves (first warp)
+  if (warp == 0) {
+    for (int k = 0; k < (int)(blockDim.x >> 5); k++) exc = fmaxf(exc, s_exc[k]);
+    float lx = INFINITY, ly = INFINITY, lz = INFINITY;
+    float hx = -INFINITY, hy = -INFINITY, hz = -INFINITY, Hm = 0.0f;
+    if (lane < l1 - l0) {
+      const float4 lo = s_lo[lane], hi = s_hi[lane];
+      lx = lo.x; ly = lo.y; lz = lo.z; Hm = lo.w;
+      hx = hi.x; hy = hi.y; hz = hi.z;
+    }
+    for (int o = 16; o; o >>= 1) {
+      lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
+      ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
+      lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
+      hx = fmaxf(hx, __shfl_xor_sync(0xffffffffu, hx, o));
+      hy = fmaxf(hy, __shfl_xor_sync(0xffffffffu, hy, o));
+      hz = fmaxf(hz, __shfl_xor_sync(0xffffffffu, hz, o));
+      Hm = fmaxf(Hm, __shfl_xor_sync(0xffffffffu, Hm, o));
+    }
+    if (lane == 0) {
+      v.chunk_lo[g] = make_float4(lx, ly, lz, Hm);
+      v.chunk_hi[g] = make_float4(hx, hy, hz, 0.0f);
+      atomic_max_float_pos(&v.ds->excursion_bits, exc);
+      atomic_max_float_pos(&v.ds->Hmax_bits, Hm);
+    }
   }
-  if (lane == 0) {
-    v.chunk_lo[g] = make_float4(lx, ly, lz, Hm);
-    v.chunk_hi[g] = make_float4(hx, hy, hz, 0.0f);
-    atomic_max_float_pos(&v.ds->excursion_bits, exc);
-    atomic_max_float_pos(&v.ds->Hmax_bits, Hm);
-  }
-  }
-  __syncthreads();  // s_exc is reused by the block's next chunk
+  __syncthreads();  // the shared arrays are reused by the block's next chunk
 }
 
 __global__ void __launch_bounds__(UT) k_refresh(View v) {
