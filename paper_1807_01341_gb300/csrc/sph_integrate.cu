@@ -84,14 +84,31 @@ __device__ void mark_groups_part(View &v, int b0, int nb) {
   const int ng = ds->n_groups, m_act = ds->m_act;
   const unsigned long long csum = ds->group_cost_sum;
   const int t0 = ((int)blockIdx.x - b0) * blockDim.x + threadIdx.x, nt = nb * blockDim.x;
-  for (int g = t0; g < ng; g += nt) {
-    int mb = 127;
-    for (int l = v.group_leaf0[g]; l < v.group_leaf0[g + 1]; l++) mb = min(mb, (int)v.leaf_min_bin[l]);
-    if (mb > m_act) continue;
-    const bool heavy = v.heavy_factor > 0.0 &&
-                       (double)v.group_cost[g] * (double)ng > v.heavy_factor * (double)csum;
-    if (heavy) v.q_group[ng - 1 - atomicAdd(&ds->n_heavy_groups, 1)] = g;
-    else v.q_group[atomicAdd(&ds->n_active_groups, 1)] = g;
+  const int lane = lane_id();
+  const unsigned below = (1u << lane) - 1u;
+  // (the same trip count in every lane of a warp: one queue atomic per warp)
+  for (int gb = t0 - lane; gb < ng; gb += nt) {
+    const int g = gb + lane;
+    bool act = false, heavy = false;
+    if (g < ng) {
+      int mb = 127;
+      for (int l = v.group_leaf0[g]; l < v.group_leaf0[g + 1]; l++)
+        mb = min(mb, (int)v.leaf_min_bin[l]);
+      act = mb <= m_act;
+      heavy = act && v.heavy_factor > 0.0 &&
+              (double)v.group_cost[g] * (double)ng > v.heavy_factor * (double)csum;
+    }
+    const unsigned mh = __ballot_sync(0xffffffffu, heavy);
+    const unsigned mw = __ballot_sync(0xffffffffu, act && !heavy);
+    int bh = 0, bw = 0;
+    if (lane == 0) {
+      if (mh) bh = atomicAdd(&ds->n_heavy_groups, __popc(mh));
+      if (mw) bw = atomicAdd(&ds->n_active_groups, __popc(mw));
+    }
+    bh = __shfl_sync(0xffffffffu, bh, 0);
+    bw = __shfl_sync(0xffffffffu, bw, 0);
+    if (heavy) v.q_group[ng - 1 - (bh + __popc(mh & below))] = g;
+    else if (act) v.q_group[bw + __popc(mw & below)] = g;
   }
 }
 
@@ -332,6 +349,18 @@ __global__ void __launch_bounds__(UT) k_drift(View v) {
 // ---------------------------------------------------------------------------
 // kicks and time bins (one warp per active leaf)
 // ---------------------------------------------------------------------------
+// Bin-occupancy change of the lanes in `changed` (old -> nb), one shared
+// atomic per distinct bin of the warp instead of one per particle.
+__device__ __forceinline__ void count_bin_change(int *delta, bool changed, int old, int nb) {
+  const unsigned cm = __ballot_sync(0xffffffffu, changed);
+  if (!changed) return;
+  const int lane = lane_id();
+  const unsigned same_old = __match_any_sync(cm, old);
+  if (lane == __ffs(same_old) - 1) atomicSub(&delta[old], __popc(same_old));
+  const unsigned same_new = __match_any_sync(cm, nb);
+  if (lane == __ffs(same_new) - 1) atomicAdd(&delta[nb], __popc(same_new));
+}
+
 __global__ void k_kick(View v, int phase) {
   DevState *ds = v.ds;
   if (ds->halt) return;
@@ -368,10 +397,14 @@ __global__ void k_bins(View v) {
     int a = v.leaf_start[leaf], b = v.leaf_start[leaf + 1];
     int minb = 127;
     unsigned long long mask = 0ull;
-    for (int i = a + lane_id(); i < b; i += 32) {
-      int old = v.bin[i];
-      int nb = old;
-      if (old <= m_act) {
+    for (int base = a; base < b; base += 32) {  // (the same trip count in every lane)
+      const int i = base + lane_id();
+      int old = 0, nb = 0;
+      if (i < b) {
+        old = v.bin[i];
+        nb = old;
+      }
+      if (i < b && old <= m_act) {
         // Eq. 1: dt = C h / v_sig; Eq. 2: largest n with dt >= 2^n dt_min
         double dt = __ddiv_rn(__dmul_rn(v.cfl, (double)v.h[i]), (double)v.vsig[i]);
         double q = __ddiv_rn(dt, v.dt_min);
@@ -389,13 +422,12 @@ __global__ void k_bins(View v) {
         v.bin[i] = (int8_t)nb;
         v.ti_begin[i] = ti;
         v.ti_end[i] = ti + (1ll << nb);
-        if (nb != old) {
-          atomicSub(&delta[old], 1);
-          atomicAdd(&delta[nb], 1);
-        }
       }
-      minb = min(minb, nb);
-      mask |= 1ull << nb;
+      count_bin_change(delta, i < b && nb != old, old, nb);
+      if (i < b) {
+        minb = min(minb, nb);
+        mask |= 1ull << nb;
+      }
     }
     for (int o = 16; o; o >>= 1) {
       minb = min(minb, __shfl_xor_sync(0xffffffffu, minb, o));
@@ -468,10 +500,11 @@ __global__ void __launch_bounds__(UT) k_close_step(View v) {
     const int a = v.leaf_start[leaf], b = v.leaf_start[leaf + 1];
     int minb = 127;
     unsigned long long mask = 0ull;
-    for (int i = a + lane_id(); i < b; i += 32) {
-      const int old = v.bin[i];
+    for (int base = a; base < b; base += 32) {  // (the same trip count in every lane)
+      const int i = base + lane_id();
+      const int old = i < b ? (int)v.bin[i] : 0;
       int nb = old;
-      if (old <= m_act) {
+      if (i < b && old <= m_act) {
         // closing half-kick of the old step
         double half = 0.5 * (double)(v.ti_end[i] - v.ti_begin[i]) * v.dt_min;
         float hf = (float)half;
@@ -495,10 +528,6 @@ __global__ void __launch_bounds__(UT) k_close_step(View v) {
         v.bin[i] = (int8_t)nb;
         v.ti_begin[i] = ti;
         v.ti_end[i] = ti + (1ll << nb);
-        if (nb != old) {
-          atomicSub(&delta[old], 1);
-          atomicAdd(&delta[nb], 1);
-        }
         // opening half-kick of the new step
         half = 0.5 * (double)(v.ti_end[i] - v.ti_begin[i]) * v.dt_min;
         hf = (float)half;
@@ -507,8 +536,11 @@ __global__ void __launch_bounds__(UT) k_close_step(View v) {
         v.vz[i] += v.az[i] * hf;
         v.A[i] = (float)((double)v.A[i] + (double)v.Adot[i] * half);
       }
-      minb = min(minb, nb);
-      mask |= 1ull << nb;
+      count_bin_change(delta, i < b && nb != old, old, nb);
+      if (i < b) {
+        minb = min(minb, nb);
+        mask |= 1ull << nb;
+      }
     }
     for (int o = 16; o; o >>= 1) {
       minb = min(minb, __shfl_xor_sync(0xffffffffu, minb, o));
