@@ -26,7 +26,8 @@ cpu_baseline  the FP64 oracle on a bounded sample of the same workload.
 
 --impl reference times the oracle alone (the CPU reference of this method).
 --ablation prints, instead, the cost per unit simulated time of relevant-only
-drift, drift-all and one global time step (Sec. III-D).
+drift, drift-all and one global time step (Sec. III-D); --adjoint the times
+of the forward and reverse pass of the differentiation workload.
 Under torchrun every rank runs its own replica (the method does not shard
 across GPUs here); value sums the ranks' pairs over the slowest rank's time.
 """
@@ -382,6 +383,68 @@ def run_ablation(args):
 
 
 # ---------------------------------------------------------------------------
+# --adjoint: the differentiation workload (forward and reverse pass timed)
+# ---------------------------------------------------------------------------
+def run_adjoint(args):
+    """The 32,768-particle clumpy set, 20 steps, loss = sum of squared
+    differences of the final density on a 32^3 grid against the same run from
+    perturbed initial conditions (positions + N(0, 0.05 spacing), energies
+    x (1 + N(0, 0.05)), seed 5; computed on the GPU).  Times, with CUDA events
+    after W warm-up repetitions, K repetitions of the forward run (checkpoints
+    every 5 steps, grid density) and of the backward pass (the grid-density
+    adjoint, then per segment the recomputed steps and sph_step_bwd over
+    them), and reports the gradient evaluations per second."""
+    import torch
+    from paper_1807_01341_gb300 import adjoint, build, sim
+    from sph_ics import workloads
+    build.build()
+    torch.cuda.set_device(0)
+    name = "c4_clumpy_32k"
+    ic = workloads.make(name)
+    n = ic["pos"].shape[0]
+    n_steps, n_grid, k = workloads.STEPS[name], 32, 5
+    params = sim.Params(**workloads.PARAMS[name], **DEFAULT_LAUNCH)
+    run = adjoint.Run(params, ic["m"], ic["h0"], n_steps, n_grid, checkpoint_every=k)
+    dev = torch.device("cuda")
+    pos0 = torch.as_tensor(ic["pos"], dtype=torch.float64, device=dev)
+    vel0 = torch.as_tensor(ic["vel"], dtype=torch.float32, device=dev)
+    u0 = torch.as_tensor(np.broadcast_to(np.asarray(ic["u"], np.float64), (n,)).copy(),
+                         dtype=torch.float32, device=dev)
+    rng = np.random.default_rng(5)
+    posp = torch.as_tensor((ic["pos"] + rng.normal(0.0, 0.05 / 32, size=ic["pos"].shape)) % 1.0,
+                           dtype=torch.float64, device=dev)
+    up = u0 * torch.as_tensor(1.0 + 0.05 * rng.normal(size=n), dtype=torch.float32, device=dev)
+    target = run.forward(posp, vel0, up).clone()
+    fwd, bwd = [], []
+    loss = grad_rms = None
+    for rep in range(args.warmup + args.steps):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize()
+        e[0].record()
+        rho = run.forward(pos0, vel0, u0)
+        diff = rho - target
+        e[1].record()
+        gpos, gvel, gu = run.backward(2.0 * diff)
+        e[2].record()
+        torch.cuda.synchronize()
+        if rep >= args.warmup:
+            fwd.append(e[0].elapsed_time(e[1]))
+            bwd.append(e[1].elapsed_time(e[2]))
+        loss = float((diff * diff).sum())
+        grad_rms = float(gpos.pow(2).mean().sqrt())
+    run.close()
+    f, b = statistics.median(fwd), statistics.median(bwd)
+    line = {"experiment": "reverse pass of the differentiation workload (checkpoint-and-recompute)",
+            "workload": name, "n_particles": n, "steps": n_steps, "grid": n_grid,
+            "checkpoint_every": k, "repetitions": args.steps, "warmup": args.warmup,
+            "data": "synthetic", "forward_ms": f, "backward_ms": b, "backward_over_forward": b / f,
+            "gradients_per_s": 1e3 / (f + b), "loss": loss, "grad_pos_rms": grad_rms,
+            "timing": "CUDA events, median over repetitions; the backward includes the "
+                      "recomputation of every segment"}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # oracle on a bounded sample (cpu_baseline and --impl reference)
 # ---------------------------------------------------------------------------
 def oracle_sample(ic, sample=2048, seed=0):
@@ -447,6 +510,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=2048)
     ap.add_argument("--cpu-sample", type=int, default=2048)
+    ap.add_argument("--adjoint", action="store_true",
+                    help="instead of the benchmark line, time the forward and reverse pass "
+                         "of the differentiation workload")
     ap.add_argument("--ablation", action="store_true",
                     help="instead of the benchmark line, print the comparison of "
                          "relevant-only drift, drift-all and one global step")
@@ -464,6 +530,10 @@ def main():
     if args.ablation:
         if rank == 0:
             run_ablation(args)
+        return
+    if args.adjoint:
+        if rank == 0:
+            run_adjoint(args)
         return
     import torch
     if world > 1:

@@ -195,8 +195,19 @@ __device__ void force_adj_group(const View &v, const AdjWork &w, int wg, const C
                          : 0.0f;
   const bool live = valid && (abx != 0.0f || aby != 0.0f || abz != 0.0f || Bi != 0.0f);
   const int nsph = compact_spheres(st.sph, live, make_float4(xi.x, xi.y, xi.z, xi.w));
+  // the particle's own adjoint sums: FP32 partial sums per neighbour cell,
+  // folded into FP64 where the cell changes (FP64 arithmetic is scarce)
   double dxi = 0.0, dyi = 0.0, dzi = 0.0, dvxi = 0.0, dvyi = 0.0, dvzi = 0.0;
   double Hbi = 0.0, Qbi = 0.0, cbi = 0.0, rbi = 0.0;
+  float pdx = 0.f, pdy = 0.f, pdz = 0.f, pvx = 0.f, pvy = 0.f, pvz = 0.f;
+  float pH = 0.f, pQ = 0.f, pc = 0.f, pr = 0.f;
+  int cur = -1;
+  auto fold_cell = [&]() {
+    dxi += (double)pdx; dyi += (double)pdy; dzi += (double)pdz;
+    dvxi += (double)pvx; dvyi += (double)pvy; dvzi += (double)pvz;
+    Hbi += (double)pH; Qbi += (double)pQ; cbi += (double)pc; rbi += (double)pr;
+    pdx = pdy = pdz = pvx = pvy = pvz = pH = pQ = pc = pr = 0.f;
+  };
   auto leaf_ok = [&](int l, float sx, float sy, float sz, LeafBox &lb) {
     const float4 loj = v.leaf_lo[l], hij = v.leaf_hi[l];
     const float R = fmaxf(Hs, loj.w);
@@ -225,6 +236,11 @@ __device__ void force_adj_group(const View &v, const AdjWork &w, int wg, const C
         mask &= mask - 1;
         const int j = st.recj[k];
         if (j == i) continue;
+        const int ci = st.recc[k];
+        if (ci != cur) {
+          fold_cell();
+          cur = ci;
+        }
         const float4 pj = sx_rec[k];
         const float4 vj = sv_rec[k];
         const float4 hj = sh_rec[k];
@@ -274,12 +290,12 @@ __device__ void force_adj_group(const View &v, const AdjWork &w, int wg, const C
         const float by = fmaf(gK, aby, fmaf(ub * rinv, dvy, rb * ey));
         const float bz = fmaf(gK, abz, fmaf(ub * rinv, dvz, rb * ez));
         const float vbx = ub * ex, vby = ub * ey, vbz = ub * ez;
-        dxi += bx; dyi += by; dzi += bz;
-        dvxi += vbx; dvyi += vby; dvzi += vbz;
-        Hbi += Hib;
-        Qbi += Kb * dWi;
-        cbi += cpart;
-        rbi += rpart;
+        pdx += bx; pdy += by; pdz += bz;
+        pvx += vbx; pvy += vby; pvz += vbz;
+        pH += Hib;
+        pQ += Kb * dWi;
+        pc += cpart;
+        pr += rpart;
         atomicAdd(&w.xb[j], -(double)bx);
         atomicAdd(&w.yb[j], -(double)by);
         atomicAdd(&w.zb[j], -(double)bz);
@@ -303,6 +319,7 @@ __device__ void force_adj_group(const View &v, const AdjWork &w, int wg, const C
     stage_list(srcs, st, nlist, consume, wc);
     skip += nlist;
   } while (more && !st.failed);
+  fold_cell();
   if (live) {
     atomicAdd(&w.xb[i], dxi);
     atomicAdd(&w.yb[i], dyi);
