@@ -159,11 +159,23 @@ __global__ void k_adj_gather(View v, AdjWork w, sph_adjoint adj, double gamma) {
 }
 
 // ---------------------------------------------------------------------------
-// 3. force adjoint: one warp per active work group, one lane per particle
+// 3. force adjoint: one warp per active work group, one lane per particle;
+//    with COOP the 8 warps of a block share a group (each takes the neighbour
+//    chunks with its index modulo 8) and combine the particle's own sums in
+//    warp order through the start of their staging buffers
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ double *adj_red_area(int warp) {
+  extern __shared__ __align__(16) char smem_dyn[];
+  static_assert(StageF::bytes() % 16 == 0 && S_FORCE * 3 * 16 >= 11 * 32 * 8,
+                "the reduction area fits the start of a staging buffer");
+  return reinterpret_cast<double *>(smem_dyn + (size_t)warp * StageF::bytes());
+}
+
+template <bool COOP>
 __device__ void force_adj_group(const View &v, const AdjWork &w, int wg, const CellFrame &F,
                                 StageF &st, WarpCounters &wc) {
   const int lane = lane_id();
+  const int warp = threadIdx.x >> 5;
   const Group Wg = group_of(v, wg, F);
   const int a = Wg.a, b = Wg.b;
   const int nact = leaf_actives(v, a, b, 0, -1, st.act);
@@ -315,12 +327,34 @@ __device__ void force_adj_group(const View &v, const AdjWork &w, int wg, const C
   int skip = 0, nlist = 0;
   bool more = false;
   do {
-    nlist = search(v, F, reach, st, leaf_ok, chunk_ok, skip, more);
+    nlist = search(v, F, reach, st, leaf_ok, chunk_ok, skip, more, COOP ? warp : -1);
     stage_list(srcs, st, nlist, consume, wc);
     skip += nlist;
   } while (more && !st.failed);
   fold_cell();
-  if (live) {
+  if constexpr (COOP) {
+    double *mine = adj_red_area(warp);
+    const double part[10] = {dxi, dyi, dzi, dvxi, dvyi, dvzi, Hbi, Qbi, cbi, rbi};
+#pragma unroll
+    for (int k = 0; k < 10; k++) mine[k * 32 + lane] = part[k];
+    mine[10 * 32 + lane] = st.failed ? 1.0 : 0.0;
+    __syncthreads();
+    double sum[10] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    bool failed = false;
+    for (int q = 0; q < WARPS_PER_BLOCK; q++) {
+      const double *rw = adj_red_area(q);
+#pragma unroll
+      for (int k = 0; k < 10; k++) sum[k] += rw[k * 32 + lane];
+      failed = failed || rw[10 * 32 + lane] != 0.0;
+    }
+    __syncthreads();
+    fence_proxy_async();  // the staging buffers take bulk copies again
+    if (__any_sync(FULL, failed)) st.failed = true;  // the same in every warp
+    dxi = sum[0]; dyi = sum[1]; dzi = sum[2];
+    dvxi = sum[3]; dvyi = sum[4]; dvzi = sum[5];
+    Hbi = sum[6]; Qbi = sum[7]; cbi = sum[8]; rbi = sum[9];
+  }
+  if (live && (!COOP || warp == 0)) {
     atomicAdd(&w.xb[i], dxi);
     atomicAdd(&w.yb[i], dyi);
     atomicAdd(&w.zb[i], dzi);
@@ -335,21 +369,41 @@ __device__ void force_adj_group(const View &v, const AdjWork &w, int wg, const C
   __syncwarp();
 }
 
+// A step with at most two groups per block gives each group a whole block
+// (its time is otherwise the latency of single warps on the largest groups).
 __global__ void __launch_bounds__(PT, 1) k_adj_force(View v, AdjWork w) {
   DevState *ds = v.ds;
-  if (ds->halt) return;
+  __shared__ int s_go, s_nq, s_item;
+  if (threadIdx.x == 0) {
+    s_go = ds->halt ? 0 : 1;
+    s_nq = ds->n_active_groups + ds->n_heavy_groups;
+  }
+  __syncthreads();
+  if (!s_go) return;  // the whole block
   StageF st;
   stage_init(st);
   const int lane = lane_id();
-  const int nq = ds->n_active_groups + ds->n_heavy_groups;
+  const int nq = s_nq;
   WarpCounters wc = {0, 0, 0, 0, 0, 0};
-  for (;;) {
-    int item = 0;
-    if (lane == 0) item = atomicAdd(&ds->head_force, 1);
-    item = __shfl_sync(FULL, item, 0);
-    if (item >= nq || st.failed) break;
-    const int wg = active_group(v, ds, item);
-    force_adj_group(v, w, wg, frame_of(v, ds, wg), st, wc);
+  if (nq <= 2 * (int)gridDim.x) {
+    for (;;) {
+      if (threadIdx.x == 0) s_item = atomicAdd(&ds->head_force, 1);
+      __syncthreads();
+      const int item = s_item;
+      __syncthreads();
+      if (item >= nq || st.failed) break;  // (st.failed is the same in every warp)
+      const int wg = active_group(v, ds, item);
+      force_adj_group<true>(v, w, wg, frame_of(v, ds, wg), st, wc);
+    }
+  } else {
+    for (;;) {
+      int item = 0;
+      if (lane == 0) item = atomicAdd(&ds->head_force, 1);
+      item = __shfl_sync(FULL, item, 0);
+      if (item >= nq || st.failed) break;
+      const int wg = active_group(v, ds, item);
+      force_adj_group<false>(v, w, wg, frame_of(v, ds, wg), st, wc);
+    }
   }
   if (lane == 0 && wc.timeout) record_error(ds, SPH_ERR_TIMEOUT, wc.timeout, true);
 }
