@@ -96,6 +96,19 @@ def profiled_traffic(kernel: str, workload: str, launch: dict):
         return None
 
 
+def reduce_over_ranks(max_values, sum_values, device):
+    """Across the ranks of the process group: the largest of each time-like
+    value (the job takes as long as its slowest rank) and the sum of each
+    count (the work of the whole job)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(max_values, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    s = torch.tensor(sum_values, dtype=torch.float64, device=device)
+    dist.all_reduce(s)
+    return [float(x) for x in t.tolist()], [float(x) for x in s.tolist()]
+
+
 def _env_int(k, d):
     try:
         return int(os.environ.get(k, d))
@@ -543,13 +556,8 @@ def main():
     pairs = out["pairs"]
     e2e_ms = out["e2e_ms"]
     if world > 1:
-        t = torch.tensor([total_ms, e2e_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        s = torch.tensor([float(pairs), float(out["e2e_pairs"])], device="cuda",
-                         dtype=torch.float64)
-        torch.distributed.all_reduce(s)
-        total_ms, e2e_ms = float(t[0]), float(t[1])
-        pairs_all, e2e_pairs = float(s[0]), float(s[1])
+        (total_ms, e2e_ms), (pairs_all, e2e_pairs) = reduce_over_ranks(
+            [total_ms, e2e_ms], [float(pairs), float(out["e2e_pairs"])], "cuda")
     else:
         pairs_all, e2e_pairs = float(pairs), float(out["e2e_pairs"])
     if rank == 0:
