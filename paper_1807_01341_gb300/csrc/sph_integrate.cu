@@ -10,6 +10,8 @@
 #include <climits>
 #include <cstddef>
 
+#include <cfloat>
+
 #include "sph_internal.cuh"
 #include "sph_diag.cuh"
 
@@ -349,6 +351,37 @@ __global__ void __launch_bounds__(UT) k_drift(View v) {
 // ---------------------------------------------------------------------------
 // kicks and time bins (one warp per active leaf)
 // ---------------------------------------------------------------------------
+// Eq. 1 and Eq. 2: the bin of a particle, the largest n with
+// dt >= 2^n dt_min for dt = C h / v_sig, i.e. the binary exponent of the FP64
+// quotient q = (C h / v_sig) / dt_min (capped at bin_cap); q < 1 sets *small
+// and gives bin 0.  An FP32 estimate of q (five roundings: relative error below
+// 4e-7) decides whenever it lies more than 2e-6 (relative) away from a power of
+// two, where the FP64 quotient necessarily has the same exponent; near a power
+// of two, below 2 or when not finite, q is computed in FP64 as defined.
+__device__ __forceinline__ int bin_of(const View &v, float h, float vsig, bool &small) {
+  // (every intermediate normal, so each rounding is relative)
+  const float t1 = (float)v.cfl * h, t2 = t1 / vsig, q32 = t2 / (float)v.dt_min;
+  int e32;
+  const float m32 = frexpf(q32, &e32);  // q32 = m32 2^e32, m32 in [0.5, 1)
+  int nb;
+  small = false;
+  if (t1 >= FLT_MIN && t2 >= FLT_MIN && isfinite(q32) && q32 >= 2.0f && m32 > 0.500001f &&
+      m32 < 0.999998f) {
+    nb = e32 - 1;
+  } else {
+    const double dt = __ddiv_rn(__dmul_rn(v.cfl, (double)h), (double)vsig);
+    const double q = __ddiv_rn(dt, v.dt_min);
+    if (!(q >= 1.0)) {
+      small = true;
+      return 0;
+    }
+    int e;
+    frexp(q, &e);
+    nb = e - 1;
+  }
+  return nb > v.bin_cap ? v.bin_cap : nb;
+}
+
 // Bin-occupancy change of the lanes in `changed` (old -> nb), one shared
 // atomic per distinct bin of the warp instead of one per particle.
 __device__ __forceinline__ void count_bin_change(int *delta, bool changed, int old, int nb) {
@@ -406,17 +439,9 @@ __global__ void k_bins(View v) {
       }
       if (i < b && old <= m_act) {
         // Eq. 1: dt = C h / v_sig; Eq. 2: largest n with dt >= 2^n dt_min
-        double dt = __ddiv_rn(__dmul_rn(v.cfl, (double)v.h[i]), (double)v.vsig[i]);
-        double q = __ddiv_rn(dt, v.dt_min);
-        if (!(q >= 1.0)) {
-          atomicAdd(&too_small, 1u);
-          nb = 0;
-        } else {
-          int e;
-          frexp(q, &e);
-          nb = e - 1;
-          if (nb > v.bin_cap) nb = v.bin_cap;
-        }
+        bool small;
+        nb = bin_of(v, v.h[i], v.vsig[i], small);
+        if (small) atomicAdd(&too_small, 1u);
         // a longer step only when the current tick is a multiple of it
         while (nb > old && (ti & ((1ll << nb) - 1)) != 0) nb--;
         v.bin[i] = (int8_t)nb;
@@ -513,17 +538,9 @@ __global__ void __launch_bounds__(UT) k_close_step(View v) {
         v.vz[i] += v.az[i] * hf;
         v.A[i] = (float)((double)v.A[i] + (double)v.Adot[i] * half);
         // Eq. 1 and Eq. 2, increases only on a multiple of the new step
-        double dt = __ddiv_rn(__dmul_rn(v.cfl, (double)v.h[i]), (double)v.vsig[i]);
-        double q = __ddiv_rn(dt, v.dt_min);
-        if (!(q >= 1.0)) {
-          atomicAdd(&too_small, 1u);
-          nb = 0;
-        } else {
-          int e;
-          frexp(q, &e);
-          nb = e - 1;
-          if (nb > v.bin_cap) nb = v.bin_cap;
-        }
+        bool small;
+        nb = bin_of(v, v.h[i], v.vsig[i], small);
+        if (small) atomicAdd(&too_small, 1u);
         while (nb > old && (ti & ((1ll << nb) - 1)) != 0) nb--;
         v.bin[i] = (int8_t)nb;
         v.ti_begin[i] = ti;
