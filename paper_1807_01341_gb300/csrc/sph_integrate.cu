@@ -32,13 +32,14 @@ __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 // Clears `active` for the previous step's active leaves (their queue is still
 // in place), then starts the step: current tick, largest active bin, epoch,
 // empty queues.
+// (one thread per leaf: a leaf holds at most 32 particles)
 __global__ void k_mark_clear(View v) {
   DevState *ds = v.ds;
-  int nq = ds->n_active_leaves;
-  for (int k = gwarp(); k < nq; k += nwarps()) {
-    int leaf = v.q_active[k];
-    int a = v.leaf_start[leaf], b = v.leaf_start[leaf + 1];
-    for (int i = a + lane_id(); i < b; i += 32) v.active[i] = 0;
+  const int nq = ds->n_active_leaves;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nq; k += gridDim.x * blockDim.x) {
+    const int leaf = v.q_active[k];
+    const int a = v.leaf_start[leaf], b = v.leaf_start[leaf + 1];
+    for (int i = a; i < b; i++) v.active[i] = 0;
   }
 }
 
@@ -114,23 +115,24 @@ __device__ void mark_groups_part(View &v, int b0, int nb) {
   }
 }
 
-// One warp per active leaf: writes `active` for its particles.
+// One thread per active leaf (at most 32 particles): writes `active` for its
+// particles; the active count goes to the device state once per warp.
 __device__ void mark_particles_part(View &v, int b0, int nb) {
   DevState *ds = v.ds;
   const int nq = ds->n_active_leaves, m_act = ds->m_act;
-  const int w0 = (((int)blockIdx.x - b0) * blockDim.x + threadIdx.x) >> 5;
-  const int nw = (nb * blockDim.x) >> 5;
-  for (int k = w0; k < nq; k += nw) {
-    int leaf = v.q_active[k];
-    int a = v.leaf_start[leaf], b = v.leaf_start[leaf + 1];
-    int cnt = 0;
-    for (int i = a + lane_id(); i < b; i += 32) {
-      bool act = (int)v.bin[i] <= m_act;
+  const int t0 = ((int)blockIdx.x - b0) * blockDim.x + threadIdx.x, nt = nb * blockDim.x;
+  unsigned long long cnt = 0;
+  for (int k = t0; k < nq; k += nt) {
+    const int leaf = v.q_active[k];
+    const int a = v.leaf_start[leaf], b = v.leaf_start[leaf + 1];
+    for (int i = a; i < b; i++) {
+      const bool act = (int)v.bin[i] <= m_act;
       v.active[i] = act ? 1 : 0;
-      cnt += __popc(__ballot_sync(__activemask(), act));
+      cnt += act ? 1ull : 0ull;
     }
-    if (lane_id() == 0 && cnt) atomicAdd(&ds->s_active_particles, (unsigned long long)cnt);
   }
+  for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if (lane_id() == 0 && cnt) atomicAdd(&ds->s_active_particles, cnt);
 }
 
 // One thread per (active cell, neighbour offset): queues the leaf chunks of
