@@ -164,11 +164,38 @@ __global__ void k_adj_gather(View v, AdjWork w, sph_adjoint adj, double gamma) {
 //    chunks with its index modulo 8) and combine the particle's own sums in
 //    warp order through the start of their staging buffers
 // ---------------------------------------------------------------------------
+template <class St = StageF>
 __device__ __forceinline__ double *adj_red_area(int warp) {
   extern __shared__ __align__(16) char smem_dyn[];
-  static_assert(StageF::bytes() % 16 == 0 && S_FORCE * 3 * 16 >= 11 * 32 * 8,
-                "the reduction area fits the start of a staging buffer");
-  return reinterpret_cast<double *>(smem_dyn + (size_t)warp * StageF::bytes());
+  static_assert(StageF::bytes() % 16 == 0 && S_FORCE * 3 * 16 >= 11 * 32 * 8 &&
+                    StageD::bytes() % 16 == 0 && S_DENS * 16 >= 5 * 32 * 8,
+                "the reduction areas fit the start of a staging buffer");
+  return reinterpret_cast<double *>(smem_dyn + (size_t)warp * St::bytes());
+}
+
+// The COOP reduction: the 8 warps' per-lane partial sums part[0..N) added in
+// warp order, the result in every warp; a failure in any warp becomes every
+// warp's (so that all take the same branches).
+template <class St, int N>
+__device__ __forceinline__ void coop_reduce(double (&part)[N], bool &failed) {
+  const int lane = lane_id(), warp = threadIdx.x >> 5;
+  double *mine = adj_red_area<St>(warp);
+#pragma unroll
+  for (int k = 0; k < N; k++) mine[k * 32 + lane] = part[k];
+  mine[N * 32 + lane] = failed ? 1.0 : 0.0;
+  __syncthreads();
+  bool any = false;
+#pragma unroll
+  for (int k = 0; k < N; k++) part[k] = 0.0;
+  for (int q = 0; q < WARPS_PER_BLOCK; q++) {
+    const double *rw = adj_red_area<St>(q);
+#pragma unroll
+    for (int k = 0; k < N; k++) part[k] += rw[k * 32 + lane];
+    any = any || rw[N * 32 + lane] != 0.0;
+  }
+  __syncthreads();
+  fence_proxy_async();  // the staging buffers take bulk copies again
+  failed = __any_sync(FULL, any);
 }
 
 template <bool COOP>
@@ -333,23 +360,10 @@ __device__ void force_adj_group(const View &v, const AdjWork &w, int wg, const C
   } while (more && !st.failed);
   fold_cell();
   if constexpr (COOP) {
-    double *mine = adj_red_area(warp);
-    const double part[10] = {dxi, dyi, dzi, dvxi, dvyi, dvzi, Hbi, Qbi, cbi, rbi};
-#pragma unroll
-    for (int k = 0; k < 10; k++) mine[k * 32 + lane] = part[k];
-    mine[10 * 32 + lane] = st.failed ? 1.0 : 0.0;
-    __syncthreads();
-    double sum[10] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    bool failed = false;
-    for (int q = 0; q < WARPS_PER_BLOCK; q++) {
-      const double *rw = adj_red_area(q);
-#pragma unroll
-      for (int k = 0; k < 10; k++) sum[k] += rw[k * 32 + lane];
-      failed = failed || rw[10 * 32 + lane] != 0.0;
-    }
-    __syncthreads();
-    fence_proxy_async();  // the staging buffers take bulk copies again
-    if (__any_sync(FULL, failed)) st.failed = true;  // the same in every warp
+    double sum[10] = {dxi, dyi, dzi, dvxi, dvyi, dvzi, Hbi, Qbi, cbi, rbi};
+    bool failed = st.failed;
+    coop_reduce<StageF, 10>(sum, failed);
+    st.failed = failed;  // the same in every warp
     dxi = sum[0]; dyi = sum[1]; dzi = sum[2];
     dvxi = sum[3]; dvyi = sum[4]; dvzi = sum[5];
     Hbi = sum[6]; Qbi = sum[7]; cbi = sum[8]; rbi = sum[9];
@@ -461,10 +475,11 @@ __global__ void k_adj_eos(View v, AdjWork w, sph_adjoint adj, int first) {
 //   hbt = h_bar + rho_bar d rho/dh + f_bar d f/dh   (explicit h-dependence)
 // and the implicit solve turns it into lambda = -hbt / F_h, F_h = -(8/pi)/GAMMA_K^3 s1 / h.
 // Pass 2: every pair's r-derivative r_bar = (ka m_j w' + kb m_j (4 w' + q w'') + km w') / H.
-template <int PASS>
+template <int PASS, bool COOP>
 __device__ void density_adj_group(const View &v, const AdjWork &w, int wg, const CellFrame &F,
                                   StageD &st, WarpCounters &wc) {
   const int lane = lane_id();
+  const int warp = threadIdx.x >> 5;
   const Group Wg = group_of(v, wg, F);
   const int a = Wg.a, b = Wg.b;
   const int nact = leaf_actives(v, a, b, 0, -1, st.act);
@@ -496,8 +511,19 @@ __device__ void density_adj_group(const View &v, const AdjWork &w, int wg, const
   }
   const float Hs = warp_max(live ? H : 0.0f);
   const int nsph = compact_spheres(st.sph, live, make_float4(xi.x, xi.y, xi.z, H));
+  // FP32 partial sums per neighbour cell, folded into FP64 where the cell changes
   double sr = 0.0, srt = 0.0, s1 = 0.0, s2 = 0.0;
   double dxi = 0.0, dyi = 0.0, dzi = 0.0;
+  float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+  int cur = -1;
+  auto fold_cell = [&]() {
+    if (PASS == 1) {
+      sr += (double)p0; srt += (double)p1; s1 += (double)p2; s2 += (double)p3;
+    } else {
+      dxi += (double)p0; dyi += (double)p1; dzi += (double)p2;
+    }
+    p0 = p1 = p2 = p3 = 0.f;
+  };
   const float R2 = Hs * Hs * 1.0002f, Rc = Hs + ceps;
   auto leaf_ok = [&](int l, float sx, float sy, float sz, LeafBox &lb) {
     const float4 lo = v.leaf_lo[l], hi = v.leaf_hi[l];
@@ -523,6 +549,11 @@ __device__ void density_adj_group(const View &v, const AdjWork &w, int wg, const
         const int k = k0 + __ffs(mask) - 1;
         mask &= mask - 1;
         const int j = st.recj[k];
+        const int ci = st.recc[k];
+        if (ci != cur) {
+          fold_cell();
+          cur = ci;
+        }
         const float4 pj = st.rec[k];
         const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
@@ -532,16 +563,16 @@ __device__ void density_adj_group(const View &v, const AdjWork &w, int wg, const
         kernel_wd(q, wq, dwq);
         const float d2 = kernel_d2w(q);
         if (PASS == 1) {
-          sr += (double)(pj.w * wq);
-          srt += (double)(pj.w * fmaf(q, dwq, 3.0f * wq));
-          s1 += (double)(q * dwq);
-          s2 += (double)(pj.w * q * fmaf(q, d2, 4.0f * dwq));
+          p0 += pj.w * wq;
+          p1 += pj.w * fmaf(q, dwq, 3.0f * wq);
+          p2 += q * dwq;
+          p3 += pj.w * q * fmaf(q, d2, 4.0f * dwq);
         } else {
           if (j == i || !(r2 > 0.0f)) continue;
           const float rbar = (ka * pj.w * dwq + kb * pj.w * fmaf(q, d2, 4.0f * dwq) + km * dwq) * Hinv;
           const float rinv = rsqrtf(r2);
           const float bx = rbar * dx * rinv, by = rbar * dy * rinv, bz = rbar * dz * rinv;
-          dxi += bx; dyi += by; dzi += bz;
+          p0 += bx; p1 += by; p2 += bz;
           atomicAdd(&w.xb[j], -(double)bx);
           atomicAdd(&w.yb[j], -(double)by);
           atomicAdd(&w.zb[j], -(double)bz);
@@ -555,10 +586,23 @@ __device__ void density_adj_group(const View &v, const AdjWork &w, int wg, const
                        st.sph, nsph};
   if (Hs > 0.0f) {
     do {
-      nlist = search(v, F, reach, st, leaf_ok, chunk_ok, skip, more);
+      nlist = search(v, F, reach, st, leaf_ok, chunk_ok, skip, more, COOP ? warp : -1);
       stage_list(srcs, st, nlist, consume, wc);
       skip += nlist;
     } while (more && !st.failed);
+  }
+  fold_cell();
+  if constexpr (COOP) {
+    double sum[4] = {PASS == 1 ? sr : dxi, PASS == 1 ? srt : dyi, PASS == 1 ? s1 : dzi, s2};
+    bool failed = st.failed;
+    coop_reduce<StageD, 4>(sum, failed);
+    st.failed = failed;  // the same in every warp
+    if (PASS == 1) {
+      sr = sum[0]; srt = sum[1]; s1 = sum[2]; s2 = sum[3];
+    } else {
+      dxi = sum[0]; dyi = sum[1]; dzi = sum[2];
+    }
+    if (warp != 0) return;  // the first warp writes the results
   }
   if (PASS == 1 && valid && !live) {
     // nothing flows back through this particle's density
@@ -595,23 +639,42 @@ __device__ void density_adj_group(const View &v, const AdjWork &w, int wg, const
   __syncwarp();
 }
 
+// (as k_adj_force: a whole block per group in steps with few groups)
 template <int PASS>
 __global__ void __launch_bounds__(PT, 1) k_adj_density(View v, AdjWork w) {
   DevState *ds = v.ds;
-  if (ds->halt) return;
+  __shared__ int s_go, s_nq, s_item;
+  if (threadIdx.x == 0) {
+    s_go = ds->halt ? 0 : 1;
+    s_nq = ds->n_active_groups + ds->n_heavy_groups;
+  }
+  __syncthreads();
+  if (!s_go) return;  // the whole block
   StageD st;
   stage_init(st);
   const int lane = lane_id();
-  const int nq = ds->n_active_groups + ds->n_heavy_groups;
+  const int nq = s_nq;
   int *head = PASS == 1 ? &ds->head_density : &ds->head_misc;
   WarpCounters wc = {0, 0, 0, 0, 0, 0};
-  for (;;) {
-    int item = 0;
-    if (lane == 0) item = atomicAdd(head, 1);
-    item = __shfl_sync(FULL, item, 0);
-    if (item >= nq || st.failed) break;
-    const int wg = active_group(v, ds, item);
-    density_adj_group<PASS>(v, w, wg, frame_of(v, ds, wg), st, wc);
+  if (nq <= 2 * (int)gridDim.x) {
+    for (;;) {
+      if (threadIdx.x == 0) s_item = atomicAdd(head, 1);
+      __syncthreads();
+      const int item = s_item;
+      __syncthreads();
+      if (item >= nq || st.failed) break;  // (st.failed is the same in every warp)
+      const int wg = active_group(v, ds, item);
+      density_adj_group<PASS, true>(v, w, wg, frame_of(v, ds, wg), st, wc);
+    }
+  } else {
+    for (;;) {
+      int item = 0;
+      if (lane == 0) item = atomicAdd(head, 1);
+      item = __shfl_sync(FULL, item, 0);
+      if (item >= nq || st.failed) break;
+      const int wg = active_group(v, ds, item);
+      density_adj_group<PASS, false>(v, w, wg, frame_of(v, ds, wg), st, wc);
+    }
   }
   if (lane == 0 && wc.timeout) record_error(ds, SPH_ERR_TIMEOUT, wc.timeout, true);
 }

@@ -171,6 +171,24 @@ __global__ void k_scan_down(const unsigned int *in, unsigned int *out, int n,
   }
 }
 
+// one block: exclusive scan of n <= SCAN_TILE values (in and out may coincide)
+__global__ void k_scan_one(const unsigned int *in, unsigned int *out, int n) {
+  const int base = threadIdx.x * SCAN_ITEMS;
+  unsigned int v[SCAN_ITEMS];
+  unsigned int s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; k++) {
+    v[k] = (base + k < n) ? in[base + k] : 0u;
+    s += v[k];
+  }
+  unsigned int pre = block_exclusive_scan(s, nullptr);
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; k++) {
+    if (base + k < n) out[base + k] = pre;
+    pre += v[k];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // stable LSD radix sort, 8-bit digits
 // ---------------------------------------------------------------------------
@@ -537,10 +555,15 @@ cudaError_t launch_cell_keys(const View &v, int nc, double w, unsigned long long
 
 cudaError_t exclusive_scan_u32(const unsigned int *in, unsigned int *out, int n,
                                unsigned int *tmp, cudaStream_t st) {
-  note_launches(3);
   if (n <= 0) return cudaSuccess;
   int nb = (n + SCAN_TILE - 1) / SCAN_TILE;
   if (nb > SCAN_TILE) return cudaErrorInvalidValue;
+  if (nb == 1) {  // one tile: a single launch
+    note_launches(1);
+    k_scan_one<<<1, SCAN_THREADS, 0, st>>>(in, out, n);
+    return cudaGetLastError();
+  }
+  note_launches(3);
   k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(in, n, tmp);
   k_scan_tops<<<1, SCAN_THREADS, 0, st>>>(tmp, nb);
   k_scan_down<<<nb, SCAN_THREADS, 0, st>>>(in, out, n, tmp);
