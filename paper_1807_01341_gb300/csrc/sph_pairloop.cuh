@@ -367,6 +367,11 @@ struct Stage {
     return sizeof(float4) * ((size_t)S * NREC + LC + 64) + sizeof(int2) * CCAP +
            sizeof(int) * (LC + LEAF_MAX_LIMIT + S) + (size_t)S + 16;
   }
+  // sph, tst and chk back to back: free between one round's last consume and
+  // the next search, they serve a block's cross-warp reductions (the staged
+  // records and the leaf list stay in place)
+  static constexpr size_t red_offset() { return sizeof(float4) * ((size_t)S * NREC + LC); }
+  static constexpr size_t red_bytes() { return sizeof(float4) * 64 + sizeof(int2) * CCAP; }
   __device__ void carve(char *base) {
     rec = reinterpret_cast<float4 *>(base);
     lshift = rec + (size_t)S * NREC;

@@ -37,12 +37,14 @@ namespace {
 // it, each taking the neighbour chunks with its warp number modulo 8 (so the
 // partial sums of a particle depend only on the particle), and combine their
 // per-lane partial sums through shared memory in warp order.  The reduction
-// area of a warp is the start of its own staging buffer (free between
-// stagings).
+// area of a warp is the part of its staging buffer that is free between a
+// round's last consume and the next search (Stage::red_offset), so the staged
+// records stay resident for the next h iteration.
 template <class St>
 __device__ __forceinline__ float *red_area(int warp) {
   extern __shared__ __align__(16) char smem_dyn[];
-  return reinterpret_cast<float *>(smem_dyn + (size_t)warp * St::bytes());
+  static_assert(St::red_bytes() >= 11 * 32 * sizeof(float), "the reduction area holds 11 words");
+  return reinterpret_cast<float *>(smem_dyn + (size_t)warp * St::bytes() + St::red_offset());
 }
 
 // ---------------------------------------------------------------------------
@@ -271,7 +273,6 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
         fl = __any_sync(FULL, fl != 0) ? 1 : 0;
         __syncthreads();
         fence_proxy_async();
-        resident = -1;  // the reduction overwrote the start of the staged records
         if (fl) st.failed = true;
         if (st.failed) break;  // the same decision in every warp
         sn = a0;
