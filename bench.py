@@ -73,11 +73,11 @@ def launch_key(launch: dict) -> str:
     return " ".join(f"{k}={launch[k]}" for k in KNOBS)
 
 
-def profiled_traffic(kernel: str, workload: str, launch: dict):
+def profiled_traffic(kernel: str, workload: str, launch: dict, profiles_dir: str | None = None):
     """DRAM bytes per launch of a pair kernel from its committed ncu summary,
     or None when the summary is missing or was taken from other sources or
     another launch configuration."""
-    path = os.path.join(ROOT, "profiles", f"k_{kernel}_{workload}.md")
+    path = os.path.join(profiles_dir or os.path.join(ROOT, "profiles"), f"k_{kernel}_{workload}.md")
     try:
         with open(path) as f:
             text = f.read()
