@@ -54,6 +54,9 @@ def _stream_ptr(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+_FIELD_NAMES = frozenset(name for name, _ in _lib.PARTICLE_FIELDS)
+
+
 class Particles:
     """Structure-of-arrays particle state on one CUDA device (caller-owned).
 
@@ -99,13 +102,23 @@ class Particles:
         p.h.copy_(torch.as_tensor(ic["h0"], dtype=torch.float32))
         return p
 
+    def __setattr__(self, name, value):
+        # a replaced array (or count) invalidates the cached C structure
+        if name == "n" or name in _FIELD_NAMES:
+            self.__dict__["_struct"] = None
+        super().__setattr__(name, value)
+
     def struct(self) -> _lib.sph_particles:
-        s = _lib.sph_particles()
-        s.n = self.n
-        for name, _ in _lib.PARTICLE_FIELDS:
-            t = getattr(self, name)
-            setattr(s, name, None if t is None else t.data_ptr())
-        self._struct = s
+        """The sph_particles of this state (built once; rebuilt after an array
+        is replaced), so a step's submission does not rebuild it."""
+        s = self.__dict__.get("_struct")
+        if s is None:
+            s = _lib.sph_particles()
+            s.n = self.n
+            for name, _ in _lib.PARTICLE_FIELDS:
+                t = getattr(self, name)
+                setattr(s, name, None if t is None else t.data_ptr())
+            self.__dict__["_struct"] = s
         return s
 
     def numpy(self, perm=None) -> dict:
