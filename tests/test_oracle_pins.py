@@ -234,6 +234,76 @@ def test_force_pairwise_conservation_and_heating(orc):
     assert np.array_equal(fa["count"], f0["count"])
 
 
+def _visc_case(orc, alpha=0.8):
+    """Three particles in a box of side 10, no pressure (P = 0), so every
+    acceleration and entropy rate comes from the artificial viscosity alone.
+
+    i  at (5, 5, 5), v = (1, 0, 0), H = 1, rho = 8, c = 1
+    j1 at (5.75, 5, 5), v = (-1, 0, 0), H = 1, rho = 4, c = 1 (approaching i)
+    j2 at (5, 5.6, 5), v = (0, 1, 0), H = 1.2, rho = 1, c = 20 (receding from i)
+    masses 1.  H = 1.825742 h is the kernel support."""
+    pos = np.array([[5.0, 5.0, 5.0], [5.75, 5.0, 5.0], [5.0, 5.6, 5.0]])
+    vel = np.array([[1.0, 0.0, 0.0], [-1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+    H = np.array([1.0, 1.0, 1.2])
+    rho = np.array([8.0, 4.0, 1.0])
+    c = np.array([1.0, 1.0, 20.0])
+    n = 3
+    return orc.force(pos, vel, np.ones(n), H / orc.GAMMA_K, rho, np.ones(n), np.zeros(n), c,
+                     np.ones(n, np.uint8), box=10.0, alpha=alpha, gamma=GAMMA, use_cells=False)
+
+
+def test_force_viscosity_hand_computed(orc):
+    """Pins the signal-velocity viscosity (Monaghan 1997, beta = 3 as inside
+    Eq. 1) with numbers worked out by hand.
+
+    Pair (i, j1): r_ij = x_i - x_j1 = (-0.75, 0, 0), r = 0.75, v_ij = (2, 0, 0),
+    v_ij . r_ij / r = -2, so w = min(0, -2) = -2 and v_sig,ij = c_i + c_j - 3w
+    = 8.  Mean density (8 + 4) / 2 = 6, so Pi = -(alpha/2) v_sig w / rho_bar
+    = -0.4 * 8 * (-2) / 6 = 16/15.  Both supports are 1, q = 0.75, and
+    w'(q) = -(8/pi) 6 (1 - q)^2 = -3/pi, so grad_i Wbar = (r_ij / r) dW/dr
+    = (3/pi, 0, 0).  a_i = -m Pi grad_i Wbar = (-16/(5 pi), 0, 0): the
+    approaching pair is braked.  dA_i/dt = (gamma - 1)/2 rho_i^(1 - gamma)
+    m Pi v_ij . grad_i Wbar = (1/3)(1/4)(16/15)(6/pi) = 8/(15 pi).
+
+    Pair (i, j2): v_ij . r_ij = (1, -1, 0) . (0, -0.6, 0) = 0.6 > 0, receding:
+    w = 0, no viscous force or heating, v_sig,ij = c_i + c_j2 = 21.  So
+    v_sig,i = max(2 c_i, 8, 21) = 21.  With P = 0 the pair adds nothing else.
+
+    j1 and j2 approach each other too (v . r = -0.15 at r = 0.96), so only
+    the total momentum is checked for them: every pair term is antisymmetric,
+    sum_k m_k a_k = 0."""
+    fr = _visc_case(orc)
+    a_i = fr["a"][0]
+    assert abs(a_i[0] - (-16.0 / (5.0 * math.pi))) < 1e-12
+    assert abs(a_i[1]) < 1e-15 and abs(a_i[2]) < 1e-15
+    assert abs(fr["Adot"][0] - 8.0 / (15.0 * math.pi)) < 1e-12
+    assert fr["vsig"][0] == 21.0
+    assert fr["count"][0] == 2
+    assert np.abs(fr["a"].sum(0)).max() < 1e-14
+    # no viscosity: the same configuration moves nothing (P = 0)
+    f0 = _visc_case(orc, alpha=0.0)
+    assert np.all(f0["a"] == 0.0) and np.all(f0["Adot"] == 0.0)
+    # Pi is linear in alpha: a_i(alpha = 1.6) = 2 a_i(0.8)
+    f2 = _visc_case(orc, alpha=1.6)
+    assert abs(f2["a"][0, 0] - 2.0 * a_i[0]) < 1e-12
+
+
+def test_force_viscosity_plausible_slips_are_distinguishable():
+    """The hand-computed case above separates the plausible slips in the
+    viscosity: each gives a value of a_i,x or v_sig,i that is off by far more
+    than the 1e-12 tolerance of the pin (values worked out by hand)."""
+    right = -16.0 / (5.0 * math.pi)
+    slips = {
+        "alpha for alpha/2": -32.0 / (5.0 * math.pi),          # Pi = 32/15
+        "rho_i for the mean density": -2.4 / math.pi,          # Pi = 0.8
+        "-w for -3w in v_sig": -1.6 / math.pi,                 # v_sig 4, Pi = 8/15
+        "max(0, .) for min(0, .)": 0.0,                        # no approach seen
+        "rho_j for the mean density": -4.8 / math.pi,          # Pi = 1.6
+    }
+    for name, val in slips.items():
+        assert abs(val - right) > 0.1, name
+
+
 def test_force_search_modes_agree(orc):
     ic = sph_ics.clumpy_lattice(nside=12, n_clumps=2, per_clump=200, seed=3)
     n = ic["pos"].shape[0]
