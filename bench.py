@@ -55,8 +55,10 @@ WORKLOAD = "c3_clustered_2m"
 FLOP_DENSITY = 29
 FLOP_FORCE = 61
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-DEFAULT_LAUNCH = dict(threads_per_particle=1, leaf_max=16, cell_margin=2.0)
-KNOBS = ("threads_per_particle", "leaf_max", "cell_margin")
+DEFAULT_LAUNCH = dict(threads_per_particle=1, leaf_max=16, cell_margin=2.0, list_cap=256,
+                      search_margin=1.02, staging_depth=1, heavy_factor=0.0)
+KNOBS = ("threads_per_particle", "leaf_max", "cell_margin", "list_cap", "search_margin",
+         "staging_depth", "heavy_factor")
 
 
 def kernel_source_digest() -> str:
@@ -94,6 +96,21 @@ def profiled_traffic(kernel: str, workload: str, launch: dict, profiles_dir: str
         return int(fields["traffic_bytes_per_launch"])
     except (KeyError, ValueError):
         return None
+
+
+def parse_launch(text: str | None) -> dict:
+    """--launch "knob=value,knob=value" (knobs of KNOBS) as a dict."""
+    out = {}
+    for item in (text or "").split(","):
+        if not item.strip():
+            continue
+        k, v = item.split("=", 1)
+        k = k.strip()
+        if k not in KNOBS:
+            raise SystemExit(f"--launch: unknown knob {k!r} (one of {', '.join(KNOBS)})")
+        out[k] = type(DEFAULT_LAUNCH[k])(float(v)) if isinstance(DEFAULT_LAUNCH[k], int) \
+            else float(v)
+    return out
 
 
 def reduce_over_ranks(max_values, sum_values, device):
@@ -185,6 +202,7 @@ def run_ours(args, rank, world):
     n = ic["pos"].shape[0]
     base = workloads.PARAMS[args.workload]
     tuned = dict(DEFAULT_LAUNCH)
+    tuned.update(parse_launch(args.launch))
     tune_info = None
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
     if not args.no_autotune:
@@ -523,6 +541,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=2048)
     ap.add_argument("--cpu-sample", type=int, default=2048)
+    ap.add_argument("--launch", default=None,
+                    help="launch knobs, e.g. 'list_cap=128,staging_depth=2' (with "
+                         "--no-autotune: used as given; otherwise the autotuner's start)")
     ap.add_argument("--adjoint", action="store_true",
                     help="instead of the benchmark line, time the forward and reverse pass "
                          "of the differentiation workload")
@@ -608,7 +629,8 @@ def main():
                 "density": c["pairs_density"] / max(c["cand_density"], 1),
                 "force": c["pairs_force"] / max(c["cand_force"], 1)},
             "counters": {k: c[k] for k in ("pairs_density", "pairs_force", "cand_density",
-                                           "cand_force", "iters_density", "active_particles",
+                                           "cand_force", "iters_density", "gathers_density",
+                                           "list_overflows", "active_particles",
                                            "steps", "rebuilds", "redone_steps")},
             "clocks": b["clocks"],
         }

@@ -51,7 +51,8 @@ enum sph_status_code {
  * alpha_visc 0.8, cfl 0.1, h_tol 1e-6, h_max_iter 30, bin_cap 20,
  * dt_min 1e-6, t_begin 0, box 1, cell_margin 2.0, leaf_max 8,
  * threads_per_particle 1, drift_all 0, n_cells_override 0, heavy_factor 0,
- * coop_max_groups -1.
+ * coop_max_groups -1, list_cap 256, search_margin 1.02, staging_depth 1,
+ * wait_limit 0, test_stall 0.
  * With threads_per_particle = 1 every sum of a particle is taken in an order
  * that depends on the particle alone, so SPH_FORM_PLAIN and SPH_FORM_BATCHED
  * give bit-identical results; with more lanes per particle they agree to
@@ -80,6 +81,25 @@ typedef struct {
   int coop_max_groups;  /* with one lane per particle: a step with at most this many
                            active work groups hands every one to the 8 warps of a block
                            (0: never; -1: twice the persistent grid's block count) */
+  int list_cap;         /* density loop: entries of each active particle's neighbour list
+                           (squared distance and mass of every candidate within
+                           search_margin x its support, kept across the h iterations;
+                           a gather that finds more runs in passes of list_cap); 32..4096.
+                           The library holds 8 x list_cap bytes per particle for them.
+                           Results do not depend on it. */
+  double search_margin; /* density loop: a particle's candidates are gathered within
+                           search_margin x its support H, and gathered again only once
+                           its H outgrows that radius; 1..2.  Results do not depend on it. */
+  int staging_depth;    /* pair loops: staging buffers per warp (1, 2 or 3); with d > 1
+                           the bulk copies of the next d - 1 batches of neighbour records
+                           are in flight while a batch is evaluated.  Results do not
+                           depend on it. */
+  int wait_limit;       /* polls of every bounded device wait (0: 2^22, about half a
+                           second); a wait that gives up records SPH_ERR_TIMEOUT */
+  int test_stall;       /* testing only, 0 in normal use: the first test_stall density
+                           launches make one warp wait on a staging barrier that no copy
+                           completes, so that the wait gives up after wait_limit polls and
+                           the step stops with SPH_ERR_TIMEOUT */
 } sph_params;
 
 /* Particle state, structure of arrays, all device pointers of length n.
@@ -121,6 +141,10 @@ typedef struct {
   int64_t redone_steps;    /* steps redone after a cell overflow */
   int64_t kernel_launches; /* kernels this process launched through the library so far
                               (graph replays count their kernel nodes) */
+  int64_t gathers_density; /* density loop: particle gathers (a particle counted once in
+                              every staging pass over its candidates) */
+  int64_t list_overflows;  /* density loop: gathers whose neighbour list filled up (that
+                              particle then took its sums while staging) */
 } sph_counters;
 
 void sph_default_params(sph_params *p);

@@ -36,7 +36,9 @@ class sph_params(ctypes.Structure):
                 ("h_tol", _d), ("h_max_iter", _i), ("bin_cap", _i), ("dt_min", _d),
                 ("t_begin", _d), ("cell_margin", _d), ("leaf_max", _i),
                 ("threads_per_particle", _i), ("drift_all", _i), ("n_cells_override", _i),
-                ("heavy_factor", _d), ("coop_max_groups", _i)]
+                ("heavy_factor", _d), ("coop_max_groups", _i), ("list_cap", _i),
+                ("search_margin", _d), ("staging_depth", _i), ("wait_limit", _i),
+                ("test_stall", _i)]
 
 
 PARTICLE_FIELDS = [("x", "f8"), ("y", "f8"), ("z", "f8"), ("vx", "f4"), ("vy", "f4"),
@@ -61,7 +63,8 @@ class sph_adjoint(ctypes.Structure):
 class sph_counters(ctypes.Structure):
     _fields_ = [(k, _i64) for k in ("pairs_density", "pairs_force", "cand_density", "cand_force",
                                     "iters_density", "active_particles", "steps", "rebuilds",
-                                    "redone_steps", "kernel_launches")]
+                                    "redone_steps", "kernel_launches", "gathers_density",
+                                    "list_overflows")]
 
 
 class sph_kernel_times(ctypes.Structure):

@@ -7,6 +7,10 @@ fastest in useful pairs per second:
   cell_margin           top-level cell width / largest kernel support (cell size)
   leaf_max              particles per leaf: the pruning and staging granularity
   threads_per_particle  lanes sharing one active particle
+  staging_depth         staging buffers per warp (bulk copies in flight)
+  search_margin         how far beyond its support a particle's candidates are
+                        gathered (larger: fewer gathers, longer lists)
+  list_cap              neighbour-list entries per particle (more: fewer overflow passes)
 
 Each trial starts from the same initial state (its own context and a copy of
 the particles), so the trials do not influence one another; it runs one
@@ -25,13 +29,17 @@ import os
 from . import _lib
 from .sim import Context, Params, Particles
 
+_BASE = dict(threads_per_particle=1, leaf_max=16, cell_margin=2.0, list_cap=256,
+             search_margin=1.02, staging_depth=1)
 DEFAULT_CANDIDATES = [
-    dict(threads_per_particle=1, leaf_max=16, cell_margin=2.0),
-    dict(threads_per_particle=1, leaf_max=24, cell_margin=2.5),
-    dict(threads_per_particle=1, leaf_max=32, cell_margin=2.5),
-    dict(threads_per_particle=1, leaf_max=12, cell_margin=2.0),
-    dict(threads_per_particle=1, leaf_max=16, cell_margin=1.5),
-    dict(threads_per_particle=2, leaf_max=16, cell_margin=2.0),
+    _BASE,
+    dict(_BASE, staging_depth=2),
+    dict(_BASE, staging_depth=3),
+    dict(_BASE, search_margin=1.05),
+    dict(_BASE, list_cap=128),
+    dict(_BASE, leaf_max=12),
+    dict(_BASE, leaf_max=24, cell_margin=2.5),
+    dict(_BASE, threads_per_particle=2),
 ]
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
@@ -92,11 +100,13 @@ def tune(ic: dict, base: dict, key: str, steps: int = 4, candidates=None,
     """Returns the fastest candidate configuration for this particle set (the
     first candidate unless another beats it by more than `margin`)."""
     n = ic["pos"].shape[0]
-    ckey = f"{key}:n={n}:steps={steps}"
+    cands = candidates or DEFAULT_CANDIDATES
+    # (the knobs tuned are part of the key: a cache from another candidate set is not reused)
+    ckey = f"{key}:n={n}:steps={steps}:knobs=" + ",".join(sorted(cands[0]))
     cache = _load(cache_path)
     if use_cache and ckey in cache:
         return dict(cache[ckey]["best"], cached=True)
-    results = [trial(ic, base, c, steps, flush) for c in (candidates or DEFAULT_CANDIDATES)]
+    results = [trial(ic, base, c, steps, flush) for c in cands]
     best = max(results, key=lambda r: r["rate"])
     if best["rate"] <= results[0]["rate"] * (1.0 + margin):
         best = results[0]

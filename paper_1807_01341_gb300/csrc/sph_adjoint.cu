@@ -259,15 +259,16 @@ __device__ void force_adj_group(const View &v, const AdjWork &w, int wg, const C
     const float R = fmaxf(Hs, loc.w) + ceps;
     return box_gap2(clx, cly, clz, chx, chy, chz, loc, v.chunk_hi[gg], sx, sy, sz) < R * R;
   };
-  auto consume = [&](int total) {
-    for (int k0 = 0; k0 < total; k0 += 32) {
+  auto consume = [&](int base, int total) {
+    const int end = base + total;
+    for (int k0 = base; k0 < end; k0 += 32) {
       unsigned mask = 0u;
 #pragma unroll
       for (int u = 0; u < 32; u++) {
         const float4 pj = sx_rec[min(k0 + u, S_FORCE - 1)];
         const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        mask |= (k0 + u < total && (r2 < Hi2 || r2 < pj.w * pj.w)) ? (1u << u) : 0u;
+        mask |= (k0 + u < end && (r2 < Hi2 || r2 < pj.w * pj.w)) ? (1u << u) : 0u;
       }
       if (!live) mask = 0u;
       while (mask) {
@@ -534,15 +535,16 @@ __device__ void density_adj_group(const View &v, const AdjWork &w, int wg, const
     return box_gap2(clx, cly, clz, chx, chy, chz, v.chunk_lo[gg], v.chunk_hi[gg], sx, sy, sz) <
            Rc * Rc;
   };
-  auto consume = [&](int total) {
-    for (int k0 = 0; k0 < total; k0 += 32) {
+  auto consume = [&](int base, int total) {
+    const int end = base + total;
+    for (int k0 = base; k0 < end; k0 += 32) {
       unsigned mask = 0u;
 #pragma unroll
       for (int u = 0; u < 32; u++) {
         const float4 pj = st.rec[min(k0 + u, S_DENS - 1)];
         const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        mask |= (k0 + u < total && r2 < H2) ? (1u << u) : 0u;
+        mask |= (k0 + u < end && r2 < H2) ? (1u << u) : 0u;
       }
       if (!live) mask = 0u;
       while (mask) {

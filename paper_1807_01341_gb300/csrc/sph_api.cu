@@ -19,7 +19,12 @@ using namespace sph;
 
 namespace sph {
 static std::atomic<unsigned long long> g_launches{0};
-void note_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+// set while this thread captures a step into a graph: its launches are graph
+// nodes, counted when the graph is replayed, not launches
+static thread_local bool t_capturing = false;
+void note_launches(int n) {
+  if (!t_capturing) g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed);
+}
 }  // namespace sph
 
 namespace {
@@ -57,6 +62,9 @@ struct Buffers {
   unsigned int *cell_stamp = nullptr, *cell_rel_stamp = nullptr;
   int32_t *q_act_cells = nullptr;
   unsigned int *leaf_counts = nullptr, *leaf_offsets = nullptr;
+  // neighbour lists of the density loop (list_cap entries per particle, and
+  // per warp of the first coop_slots blocks)
+  float2 *nbr = nullptr, *nbr_coop = nullptr;
   // state
   DevState *ds = nullptr;
   float *d_hmax = nullptr;
@@ -89,6 +97,7 @@ struct sph_ctx {
   int num_sms = 0;
   int grid_util = 0;
   int grid_dens = 0, grid_force = 0;
+  int coop_slots = 0;  // blocks of a density launch with neighbour lists for shared groups
   Buffers b;
   bool built = false;
   bool entropy_ready = false;  // the first density pass has converted u to A
@@ -161,6 +170,10 @@ bool valid_params(const sph_params *p) {
   if (G != 1 && G != 2 && G != 4 && G != 8 && G != 16 && G != 32) return false;
   if (p->n_cells_override < 0 || p->n_cells_override > NC_MAX) return false;
   if (std::isnan(p->heavy_factor) || p->coop_max_groups < -1) return false;
+  if (p->list_cap < 32 || p->list_cap > 4096) return false;
+  if (!(p->search_margin >= 1.0 && p->search_margin <= 2.0)) return false;
+  if (p->staging_depth < 1 || p->staging_depth > 3) return false;
+  if (p->wait_limit < 0 || p->test_stall < 0) return false;
   return true;
 }
 
@@ -241,6 +254,13 @@ View make_view(const sph_ctx *ctx, const sph_particles *p) {
   v.G = q.threads_per_particle;
   v.drift_all = q.drift_all;
   v.grid_util = ctx->grid_util;
+  v.nbr = b.nbr;
+  v.nbr_coop = b.nbr_coop;
+  v.list_cap = q.list_cap;
+  v.coop_slots = ctx->coop_slots;
+  v.search_margin = (float)q.search_margin;
+  v.stage_depth = q.staging_depth;
+  v.wait_limit = q.wait_limit;
   return v;
 }
 
@@ -469,9 +489,12 @@ int plain_body(sph_ctx *ctx, const View &v, int flags, cudaStream_t st) {
     SPH_CUDA(cudaMemcpyAsync(nq, SPH_DS_FIELD(v.ds, n_bin_groups), 2 * sizeof(int),
                              cudaMemcpyDeviceToHost, st));
     SPH_CUDA(cudaStreamSynchronize(st));
+    // blocks for the shared groups (at most one per neighbour-list slot), then
+    // one warp per group
+    const int ncb = std::min(nq[1], ctx->coop_slots);
     prof_begin(ctx, 0, st);
     SPH_CUDA(launch_density(v, flags, bins[k], false,
-                            nq[1] + (nq[0] + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK, st));
+                            ncb + (nq[0] + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK, st));
     prof_end(ctx, 0, st);
   }
   if (flags & SPH_DENSITY_INIT_ENTROPY) SPH_CUDA(launch_entropy_from_u(v, st));
@@ -481,9 +504,10 @@ int plain_body(sph_ctx *ctx, const View &v, int flags, cudaStream_t st) {
     SPH_CUDA(cudaMemcpyAsync(nq, SPH_DS_FIELD(v.ds, n_bin_groups), 2 * sizeof(int),
                              cudaMemcpyDeviceToHost, st));
     SPH_CUDA(cudaStreamSynchronize(st));
+    const int ncb = std::min(nq[1], ctx->coop_slots);
     prof_begin(ctx, 1, st);
     SPH_CUDA(launch_force(v, bins[k], false,
-                          nq[1] + (nq[0] + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK, st));
+                          ncb + (nq[0] + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK, st));
     prof_end(ctx, 1, st);
   }
   SPH_CUDA(launch_close_step(v, st));
@@ -528,11 +552,23 @@ int capture_graph(sph_ctx *ctx, sph_particles *p) {
   const int saved_n[2] = {ctx->prof_n[0], ctx->prof_n[1]};
   ctx->prof_n[0] = ctx->prof_n[1] = 0;  // the graph records into slot 0 of each kind
   SPH_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
-  const unsigned long long before = g_launches.load();
+  t_capturing = true;
   int r = batched_body(ctx, v, 0, ctx->cap_stream);
-  ctx->graph_kernels = (int)(g_launches.load() - before);
-  g_launches.fetch_sub((unsigned long long)ctx->graph_kernels);  // captured, not launched
+  t_capturing = false;
   cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+  // the kernels of one replay: the graph's kernel nodes
+  ctx->graph_kernels = 0;
+  size_t n_nodes = 0;
+  if (e == cudaSuccess && r == SPH_OK && cudaGraphGetNodes(g, nullptr, &n_nodes) == cudaSuccess) {
+    std::vector<cudaGraphNode_t> nodes(n_nodes);
+    if (n_nodes && cudaGraphGetNodes(g, nodes.data(), &n_nodes) == cudaSuccess) {
+      for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+          ctx->graph_kernels++;
+      }
+    }
+  }
   ctx->prof_n[0] = saved_n[0];
   ctx->prof_n[1] = saved_n[1];
   ctx->graph_profiled = ctx->prof_on;
@@ -646,6 +682,11 @@ void sph_default_params(sph_params *p) {
   p->n_cells_override = 0;
   p->heavy_factor = 0.0;
   p->coop_max_groups = -1;
+  p->list_cap = 256;
+  p->search_margin = 1.02;
+  p->staging_depth = 1;
+  p->wait_limit = 0;
+  p->test_stall = 0;
 }
 
 const char *sph_strerror(int code) {
@@ -710,10 +751,21 @@ int sph_create(const sph_params *params, int64_t n_max, sph_ctx **out) {
       r = SPH_ERR_NOMEM;
       break;
     }
-    if (cudaMemset(b.ds, 0, sizeof(DevState)) != cudaSuccess) {
+    if (cudaMemset(b.ds, 0, sizeof(DevState)) != cudaSuccess ||
+        cudaMemcpy(SPH_DS_FIELD(b.ds, test_stall), &params->test_stall, sizeof(int),
+                   cudaMemcpyHostToDevice) != cudaSuccess) {
       r = SPH_ERR_CUDA;
       break;
     }
+    // neighbour lists of the density loop: by particle, and for the blocks
+    // that share a work group (those of a persistent launch; a per-bin launch
+    // uses at most as many)
+    ctx->coop_slots = ctx->grid_dens;
+    if ((r = dalloc(&b.nbr, n * (long long)params->list_cap)) ||
+        (r = dalloc(&b.nbr_coop, G == 1 ? (long long)ctx->coop_slots * WARPS_PER_BLOCK * 32 *
+                                              params->list_cap
+                                        : 1LL)))
+      break;
     if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
       r = SPH_ERR_CUDA;
       break;
@@ -754,6 +806,7 @@ int sph_destroy(sph_ctx *ctx) {
   dfree(b.cell_start); dfree(b.cell_leaf_start); dfree(b.cell_stamp); dfree(b.cell_rel_stamp);
   dfree(b.q_act_cells); dfree(b.leaf_counts); dfree(b.leaf_offsets);
   dfree(b.ds); dfree(b.d_hmax); dfree(b.diag); dfree(b.d_bad);
+  dfree(b.nbr); dfree(b.nbr_coop);
   if (b.h_ds) cudaFreeHost(b.h_ds);
   delete ctx;
   return SPH_OK;
@@ -955,6 +1008,8 @@ int sph_get_counters(sph_ctx *ctx, sph_counters *out) {
   out->rebuilds = ctx->rebuilds;
   out->redone_steps = ctx->redone;
   out->kernel_launches = (int64_t)g_launches.load();
+  out->gathers_density = (int64_t)(h.gathers_density + h.s_gathers_density);
+  out->list_overflows = (int64_t)(h.list_overflows + h.s_list_overflows);
   return SPH_OK;
 }
 

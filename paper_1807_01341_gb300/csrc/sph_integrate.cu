@@ -61,6 +61,7 @@ __global__ void k_begin_step(View v, long long ti_arg) {
   ds->s_pairs_density = ds->s_pairs_force = 0ull;
   ds->s_cand_density = ds->s_cand_force = 0ull;
   ds->s_iters_density = ds->s_active_particles = 0ull;
+  ds->s_gathers_density = ds->s_list_overflows = 0ull;
 }
 
 // One thread per leaf: a leaf holds active particles when its smallest bin is
@@ -492,9 +493,12 @@ __device__ void next_time(View &v, long long *out, int count_step) {
   ds->cand_force += ds->s_cand_force;
   ds->iters_density += ds->s_iters_density;
   ds->active_particles += ds->s_active_particles;
+  ds->gathers_density += ds->s_gathers_density;
+  ds->list_overflows += ds->s_list_overflows;
   ds->s_pairs_density = ds->s_pairs_force = 0ull;
   ds->s_cand_density = ds->s_cand_force = 0ull;
   ds->s_iters_density = ds->s_active_particles = 0ull;
+  ds->s_gathers_density = ds->s_list_overflows = 0ull;
   if (count_step) ds->steps += 1ull;
 }
 
@@ -722,6 +726,12 @@ cudaError_t launch_diagnostics(const sph_particles &p, long long ti, double dt_m
 cudaError_t launch_mark_bin(const View &v, int bin, cudaStream_t st) {
   note_launches(1);
   cudaError_t e = cudaMemsetAsync(SPH_DS_FIELD(v.ds, n_bin_groups), 0, 2 * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  // the heads of the blocks that take the shared groups (head_coop_force follows)
+  static_assert(offsetof(DevState, head_coop_force) ==
+                    offsetof(DevState, head_coop_density) + sizeof(int),
+                "the two coop heads are adjacent");
+  e = cudaMemsetAsync(SPH_DS_FIELD(v.ds, head_coop_density), 0, 2 * sizeof(int), st);
   if (e != cudaSuccess) return e;
   k_mark_bin<<<v.grid_util, UT, 0, st>>>(v, bin);
   return cudaGetLastError();

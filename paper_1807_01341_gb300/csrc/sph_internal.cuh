@@ -40,7 +40,7 @@ struct DevState {
   int n_active_groups;   // work groups holding active particles (light ones from the front of
                          // q_group, heavy ones from its back; see n_heavy_groups)
   int n_heavy_groups;    // active work groups whose estimated cost is well above the mean
-  int pad1;
+  int test_stall;        // testing: density launches whose first warp still has to stall
   unsigned long long group_cost_sum;  // sum over work groups of group_cost (written at build)
   double w;              // cell width
   // queues (written by mark)
@@ -67,9 +67,11 @@ struct DevState {
   // totals when it completes, so a halted attempt leaves no trace)
   unsigned long long s_pairs_density, s_pairs_force, s_cand_density, s_cand_force;
   unsigned long long s_iters_density, s_active_particles;
+  unsigned long long s_gathers_density, s_list_overflows;
   // totals over completed steps
   unsigned long long pairs_density, pairs_force, cand_density, cand_force;
   unsigned long long iters_density, active_particles;
+  unsigned long long gathers_density, list_overflows;
   unsigned long long steps;
   // time-bin occupancy
   int bin_count[MAX_BINS];
@@ -121,9 +123,22 @@ struct View {
                              // [0, n_active_groups), heavy ones at n_groups - 1 - k
   int32_t *q_bin;            // plain form: active work groups holding particles of one bin
                              // (light ones at [0, n_bin_groups), heavy ones from the back)
+  // neighbour lists of the density loop: squared distance and mass of every
+  // candidate within the particle's search radius, list_cap entries per
+  // particle.  nbr: by particle (entry k of lane sub of the particle in slot s
+  // of work group [a, b) at nbr[a * list_cap + (k * G + sub) * (b - a) + s]);
+  // nbr_coop: per warp of the first coop_slots blocks of a launch, for groups
+  // shared by a block (entry k of lane s at [(block * 8 + warp) * 32 * list_cap
+  // + k * 32 + s]).
+  float2 *nbr;
+  float2 *nbr_coop;
   DevState *ds;
   // parameters
   double box, eta, gamma, alpha, cfl, h_tol, dt_min;
+  long long wait_limit;      // polls of a bounded barrier wait (0: the default)
+  float search_margin;       // a density search reaches search_margin x the support
+  int list_cap, coop_slots;  // neighbour-list entries per particle; blocks with coop lists
+  int stage_depth;           // staging buffers per warp (1..3)
   double heavy_factor;       // heavy work group: estimated cost > heavy_factor x mean
   int coop_max_groups;       // steps with at most this many active groups: all cooperative
   int h_max_iter, bin_cap, leaf_max, G, drift_all;

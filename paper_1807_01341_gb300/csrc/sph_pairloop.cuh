@@ -60,8 +60,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 }
 
 // bounded wait for the completion of the barrier phase with this parity
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-  for (long long k = 0; k < WAIT_LIMIT; k++) {
+// (limit: polls; after the first 16 each poll sleeps ~64 ns)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit) {
+  for (long long k = 0; k < limit; k++) {
     if (mbar_try_wait(bar, parity)) return true;
     if (k > 16) __nanosleep(64);
   }
@@ -297,6 +298,7 @@ __device__ __forceinline__ CellFrame frame_of(const View &v, const DevState *ds,
 
 struct WarpCounters {
   unsigned long long pairs, cand, iters, noconv, overflow, timeout;
+  unsigned long long gathers, list_overflows;  // density loop: particle gathers, full lists
 };
 
 // A work group: particles [a, b) in leaves [L0, L1) of one cell, and the
@@ -347,25 +349,33 @@ __device__ __forceinline__ float3 leaf_offset(const View &v, int i, const CellFr
 // ---------------------------------------------------------------------------
 // per-warp staging area in dynamic shared memory
 // ---------------------------------------------------------------------------
+constexpr int STAGE_DEPTH_MAX = 3;  // staging buffers per warp (copies in flight)
+
 template <int S, int NREC, int LC>
 struct Stage {
   static constexpr int LCAP = LC;  // accepted neighbour leaves listed per search pass
   static constexpr int CCAP = 128; // accepted chunks gathered per search segment
-  float4 *rec;     // NREC arrays of S staged records, back to back (first: positions)
+  float4 *rec;     // NREC arrays of S staged records, back to back (first: positions);
+                   // with depth d, buffer b holds slots [b S/d, (b+1) S/d) of each
   float4 *lshift;  // per listed leaf: offset of its corner (x, y, z), first particle (w bits)
   int *lpack;      // per listed leaf: count | cell index << 16
   int *act;        // active particles of the work group
   int *recj;       // per staged record: particle index
   uint8_t *recc;   // per staged record: neighbour-cell index (0..26)
   float4 *sph;     // the round's particles: position (group frame), search radius
-  float4 *tst;     // the round's live particles: position (group frame), squared support
+  float4 *tst;     // the round's live particles: position (group frame), squared test radius
   int2 *chk;       // accepted chunks of a search segment: first leaf, count | cell << 16
-  uint64_t *bar;
-  uint32_t phase;
+  uint64_t *bar;   // one mbarrier per staging buffer
+  int *meta;       // per staging buffer: first listed leaf, leaves, records
+  uint32_t phase;  // parity of the next phase of each buffer's barrier (bit b)
+  int depth;       // staging buffers in use (1..STAGE_DEPTH_MAX)
+  long long wait_limit;  // polls of a bounded barrier wait
+  int *stall_ctr;  // testing: stalls still to make (a launch's first staging claims one)
+  bool stall;      // testing: this staging issues no copy and never arrives
   bool failed;
   static constexpr size_t bytes() {
     return sizeof(float4) * ((size_t)S * NREC + LC + 64) + sizeof(int2) * CCAP +
-           sizeof(int) * (LC + LEAF_MAX_LIMIT + S) + (size_t)S + 16;
+           sizeof(int) * (LC + LEAF_MAX_LIMIT + S) + (size_t)S + 64;
   }
   // sph, tst and chk back to back: free between one round's last consume and
   // the next search, they serve a block's cross-warp reductions (the staged
@@ -382,7 +392,8 @@ struct Stage {
     act = lpack + LC;
     recj = act + LEAF_MAX_LIMIT;
     recc = reinterpret_cast<uint8_t *>(recj + S);
-    bar = reinterpret_cast<uint64_t *>(recc + S);
+    bar = reinterpret_cast<uint64_t *>(recc + S);  // 8-byte aligned: every part above is
+    meta = reinterpret_cast<int *>(bar + STAGE_DEPTH_MAX);
   }
 };
 
@@ -557,81 +568,136 @@ __device__ __forceinline__ int search(const View &v, const CellFrame &F, const R
 }
 
 // Stages the records of listed leaves [0, nlist) into shared memory by bulk
-// copies, as many leaves per batch as fit S records.  When a batch has
-// landed, each position record is moved into the work group's frame (its
+// copies (TMA), through `depth` buffers of S / depth records each: the copies
+// of the next depth - 1 batches are in flight while a batch is consumed.  A
+// batch is as many consecutive listed leaves as fit one buffer.  When a batch
+// has landed, each position record is moved into the work group's frame (its
 // leaf's corner offset added) and tagged with its particle index and
-// neighbour-cell index; then consume(total) sees records 0 .. total-1.
-// Returns the record count when the whole list fitted one batch (the records
-// then stay resident until the next staging), else -1.
+// neighbour-cell index; then consume(base, total) sees records base ..
+// base + total - 1.  Batches are consumed in list order whatever the depth.
+// A barrier wait that gives up sets st.failed and counts a timeout; the warp
+// then waits (bounded again) for every copy it still has in flight before it
+// returns, so that no copy lands in shared memory the warp has left.
 template <int S, int NREC, int LC, class Consume>
-__device__ __forceinline__ int stage_list(const float4 *const *srcs, Stage<S, NREC, LC> &st,
-                                          int nlist, Consume consume, WarpCounters &wc) {
+__device__ __forceinline__ void stage_list(const float4 *const *srcs, Stage<S, NREC, LC> &st,
+                                           int nlist, Consume consume, WarpCounters &wc) {
   const int lane = lane_id();
-  int batches = 0, last_total = 0;
-  for (int e = 0; e < nlist && !st.failed;) {
+  const int depth = st.depth;
+  const int Sb = S / depth;
+  int e_next = 0, issued = 0, done = 0;
+  // the next listed leaves that fit Sb records, into buffer b
+  auto issue = [&](int b) {
+    const int e = e_next;
     const bool in = e + lane < nlist;
     const int c = in ? (st.lpack[e + lane] & 0xffff) : 0;
     const int incl = warp_incl_scan(c);
-    const unsigned take = __ballot_sync(FULL, in && incl <= S);  // a prefix; never empty
+    // a prefix of the list; never empty (a leaf holds at most 32 <= Sb records)
+    const unsigned take = __ballot_sync(FULL, in && incl <= Sb);
     const int k = __popc(take);
     const int total = __shfl_sync(FULL, incl, k - 1);
-    if (lane == 0) mbar_expect_tx(st.bar, (uint32_t)(total * NREC * (int)sizeof(float4)));
-    __syncwarp();
-    if ((take >> lane) & 1u) {
-      const int ja = __float_as_int(st.lshift[e + lane].w);
-      const int slot = incl - c;
-      for (int r = 0; r < NREC; r++)
-        bulk_g2s(st.rec + (size_t)r * S + slot, srcs[r] + ja, (uint32_t)(c * sizeof(float4)), st.bar);
+    if (st.stall_ctr) {
+      // testing: the first warp of the launch to stage claims the stall
+      int claim = 0;
+      if (lane == 0) {
+        claim = atomicSub(st.stall_ctr, 1) > 0 ? 1 : 0;
+        if (!claim) atomicAdd(st.stall_ctr, 1);
+      }
+      st.stall = __shfl_sync(FULL, claim, 0) != 0;
+      st.stall_ctr = nullptr;
+    }
+    const bool stall = st.stall;
+    if (lane == 0) {
+      st.meta[3 * b] = e;
+      st.meta[3 * b + 1] = k;
+      st.meta[3 * b + 2] = total;
+      if (!stall) mbar_expect_tx(&st.bar[b], (uint32_t)(total * NREC * (int)sizeof(float4)));
     }
     __syncwarp();
-    if (lane == 0) mbar_arrive(st.bar);
-    if (!mbar_wait(st.bar, st.phase)) {
+    if (!stall && ((take >> lane) & 1u)) {
+      const int ja = __float_as_int(st.lshift[e + lane].w);
+      const int slot = b * Sb + incl - c;
+      for (int r = 0; r < NREC; r++)
+        bulk_g2s(st.rec + (size_t)r * S + slot, srcs[r] + ja, (uint32_t)(c * sizeof(float4)),
+                 &st.bar[b]);
+    }
+    __syncwarp();
+    if (lane == 0 && !stall) mbar_arrive(&st.bar[b]);
+    e_next = e + k;
+    issued++;
+  };
+  int b = 0, bi = 0;  // next buffer to consume, next buffer to fill
+  for (;;) {
+    // keep every free buffer filling while listed leaves remain
+    while (issued - done < depth && e_next < nlist) {
+      issue(bi);
+      bi = bi + 1 == depth ? 0 : bi + 1;
+    }
+    if (done == issued || st.failed) break;
+    if (!mbar_wait(&st.bar[b], (st.phase >> b) & 1u, st.wait_limit)) {
       st.failed = true;
       wc.timeout++;
+      break;
     }
-    st.phase ^= 1u;
-    if (!st.failed) {
-      int base = 0;
-      for (int q = 0; q < k; q++) {
-        const float4 sh = st.lshift[e + q];
-        const int pk = st.lpack[e + q];
-        const int cq = pk & 0xffff;
-        const int ja = __float_as_int(sh.w);
-        for (int t = lane; t < cq; t += 32) {
-          float4 rr = st.rec[base + t];
-          rr.x += sh.x;
-          rr.y += sh.y;
-          rr.z += sh.z;
-          st.rec[base + t] = rr;
-          st.recj[base + t] = ja + t;
-          st.recc[base + t] = (uint8_t)(pk >> 16);
-        }
-        base += cq;
+    st.phase ^= 1u << b;
+    const int e = st.meta[3 * b], k = st.meta[3 * b + 1], total = st.meta[3 * b + 2];
+    const int base0 = b * Sb;
+    int base = base0;
+    for (int q = 0; q < k; q++) {
+      const float4 sh = st.lshift[e + q];
+      const int pk = st.lpack[e + q];
+      const int cq = pk & 0xffff;
+      const int ja = __float_as_int(sh.w);
+      for (int t = lane; t < cq; t += 32) {
+        float4 rr = st.rec[base + t];
+        rr.x += sh.x;
+        rr.y += sh.y;
+        rr.z += sh.z;
+        st.rec[base + t] = rr;
+        st.recj[base + t] = ja + t;
+        st.recc[base + t] = (uint8_t)(pk >> 16);
       }
-      __syncwarp();
-      consume(total);
+      base += cq;
     }
     __syncwarp();
-    fence_proxy_async();
-    e += k;
-    batches++;
-    last_total = total;
+    consume(base0, total);
+    __syncwarp();
+    fence_proxy_async();  // this warp's reads of the buffer before the next bulk writes
+    done++;
+    b = b + 1 == depth ? 0 : b + 1;
   }
-  return (batches == 1 && !st.failed) ? last_total : (nlist == 0 ? 0 : -1);
+  if (st.failed) {
+    // copies still in flight: wait for them (bounded) before leaving
+    for (; done < issued; done++) {
+      if (!st.stall && mbar_wait(&st.bar[b], (st.phase >> b) & 1u, st.wait_limit))
+        st.phase ^= 1u << b;
+      b = b + 1 == depth ? 0 : b + 1;
+    }
+    st.stall = false;
+  }
+  __syncwarp();
 }
 
 using StageD = Stage<S_DENS, 1, 320>;
 using StageF = Stage<S_FORCE, 3, 256>;
 
+// depth: staging buffers (1..STAGE_DEPTH_MAX, and S / depth >= 32);
+// wait_limit: polls of each bounded barrier wait (<= 0: WAIT_LIMIT);
+// stall_ctr (testing, normally null): a counter of stalls still to make; the
+// first staging of the warp claims one if any is left and then never completes.
 template <class St>
-__device__ __forceinline__ void stage_init(St &st) {
+__device__ __forceinline__ void stage_init(St &st, int depth = 1, long long wait_limit = 0,
+                                           int *stall_ctr = nullptr) {
   extern __shared__ __align__(16) char smem_dyn[];
   const int warp = threadIdx.x >> 5;
   st.carve(smem_dyn + (size_t)warp * St::bytes());
   st.phase = 0u;
   st.failed = false;
+  st.depth = depth < 1 ? 1 : (depth > STAGE_DEPTH_MAX ? STAGE_DEPTH_MAX : depth);
+  st.wait_limit = wait_limit > 0 ? wait_limit : WAIT_LIMIT;
+  st.stall_ctr = stall_ctr;
+  st.stall = false;
   if (lane_id() == 0) {
-    mbar_init(st.bar, 1);
+    for (int b = 0; b < STAGE_DEPTH_MAX; b++) mbar_init(&st.bar[b], 1);
     fence_mbar_init();
   }
   __syncwarp();

@@ -50,10 +50,82 @@ __device__ __forceinline__ float *red_area(int warp) {
 // ---------------------------------------------------------------------------
 // density loop + smoothing-length iteration for the active particles of a group
 // ---------------------------------------------------------------------------
+// Partial sums of one particle: S_w = sum w(q), S_t = sum (3 w + q w'), the
+// mass-weighted pair, sum q^2 w'' and the neighbour count.  The first four
+// are compensated (hi, lo) and folded every DFOLD pairs, so the order and the
+// rounding of every sum depend only on the particle's candidates in record
+// order -- the same whether a pair is taken while its record is staged or
+// later from the particle's neighbour list.
+constexpr int DFOLD = 8;
+
+struct DSum {
+  float n_hi, n_lo, t_hi, t_lo, r_hi, r_lo, rt_hi, rt_lo;
+  float pn, pt, pr, prt, p2;
+  int cnt, since;
+  __device__ __forceinline__ void zero() {
+    n_hi = n_lo = t_hi = t_lo = r_hi = r_lo = rt_hi = rt_lo = 0.0f;
+    pn = pt = pr = prt = p2 = 0.0f;
+    cnt = since = 0;
+  }
+  __device__ __forceinline__ void fold_all() {
+    fold(n_hi, n_lo, pn);
+    fold(t_hi, t_lo, pt);
+    fold(r_hi, r_lo, pr);
+    fold(rt_hi, rt_lo, prt);
+    pn = pt = pr = prt = 0.0f;
+    since = 0;
+  }
+};
+
+// A candidate at squared distance r2 (FP32, group frame) with mass mj, at the
+// support H (H2 = H^2, Hinv = 1/H): a neighbour when r2 < H2 (strict).
+__device__ __forceinline__ void dens_pair(DSum &s, float r2, float mj, float H2, float Hinv) {
+  if (!(r2 < H2)) return;
+  const float rr = r2 * rsqrtf(fmaxf(r2, 1e-30f));
+  const float qq = rr * Hinv;
+  float wq, dwq;
+  kernel_wd(qq, wq, dwq);
+  const float tt = fmaf(qq, dwq, 3.0f * wq);
+  s.p2 = fmaf(qq * qq, kernel_d2w(qq), s.p2);
+  s.pn += wq;
+  s.pt += tt;
+  s.pr = fmaf(mj, wq, s.pr);
+  s.prt = fmaf(mj, tt, s.prt);
+  s.cnt++;
+  if (++s.since == DFOLD) s.fold_all();
+}
+
+// Entries [0, nl) of a neighbour list (entry k at lst[k * ls]), in order; the
+// next entry's load is issued before the current one is evaluated.
+__device__ __forceinline__ void dens_list(DSum &s, const float2 *lst, int ls, int nl, float H2,
+                                          float Hinv) {
+  if (nl <= 0) return;
+  float2 e = __ldcg(lst);
+#pragma unroll 1
+  for (int k = 1; k <= nl; k++) {
+    const float2 cur = e;
+    if (k < nl) e = __ldcg(lst + (size_t)k * ls);
+    dens_pair(s, cur.x, cur.y, H2, Hinv);
+  }
+}
+
 // Newton step on F(h) = h^3 n(h) - eta^3 in dimensionless form: with H = GAMMA_K h,
 // h^3 n = (8/pi) S_w / GAMMA_K^3 and h dF/dh = 3 h^3 n + h^4 dn/dh, so
 // dh / h = -(S_w - C) / (3 S_w - S_t), C = eta^3 GAMMA_K^3 / (8/pi),
 // S_w = sum w(q), S_t = sum (3 w + q w').
+//
+// Gathers and neighbour lists.  A particle's candidates are found by a
+// "gather": the search lists the leaves that the particle's sphere of radius
+// R_i = search_margin x H reaches, their records are staged, and every record
+// with r^2 < R_i^2 goes into the particle's neighbour list (squared distance
+// and mass).  Each h iteration evaluates its sums at its H from the list
+// alone, in record order, as long as H <= R_i; a particle whose h outgrows
+// R_i gathers again.  A list holds list_cap entries per particle (list_cap / G
+// per lane): a gather that accepts more runs in passes over the same leaves,
+// each pass listing (and summing) the next list_cap accepted records, and the
+// particle's list is then not kept (later iterations gather at R_i = H).
+// Whatever the capacity, margin or staging depth, a particle's sums visit the
+// same pairs in the same order with the same arithmetic.
 template <int G, bool COOP>
 __device__ void density_group(const View &v, int wg, int flags, int bin_filter, int m_act,
                               const CellFrame &F, float hcap, float exc, long long ti,
@@ -69,6 +141,7 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
   if (nact == 0) return;
   constexpr int P = 32 / G;
   const int grp = lane / G, sub = lane % G;
+  const unsigned gmask = G == 32 ? FULL : ((1u << G) - 1u) << (grp * G);  // this lane's group
   // the group's box in its cell's frame (for the chunk tests)
   const float qox = F.kx * F.wq, qoy = F.ky * F.wq, qoz = F.kz * F.wq;
   const float clx = W.lx + qox, cly = W.ly + qoy, clz = W.lz + qoz;
@@ -77,186 +150,203 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
   const double Cw = v.eta * v.eta * v.eta * GAMMA_K_D * GAMMA_K_D * GAMMA_K_D / (double)KERNEL_NORM;
   const bool init_entropy = (flags & SPH_DENSITY_INIT_ENTROPY) != 0;
   const float4 *srcs[1] = {v.rec_xm};
+  // neighbour lists: entry k of this lane's list at lst[k * ls].  By particle
+  // (slot s of the group, lane sub of its G): nbr[a * list_cap + (k * G + sub)
+  // * (b - a) + s]; shared groups: per warp of the block, by lane.
+  const int cap = COOP ? v.list_cap : v.list_cap / G;
+  const int ls = COOP ? 32 : G * (b - a);
+  float2 *const lbase =
+      COOP ? v.nbr_coop + ((size_t)blockIdx.x * WARPS_PER_BLOCK + warp) * 32 * v.list_cap + lane
+           : v.nbr + (size_t)a * v.list_cap + sub * (b - a);
 
   for (int r = 0; r < nact && !st.failed; r += P) {
     const int slot = r + grp;
     const bool valid = slot < nact;
     const int i = valid ? st.act[slot] : a;
+    float2 *const lst = COOP ? lbase : lbase + (valid ? slot : 0);
     const float4 xl = v.rec_xm[i];  // position in its own leaf's frame
     const float3 lo3 = leaf_offset(v, i, F);
     const float4 xi = make_float4(xl.x + lo3.x, xl.y + lo3.y, xl.z + lo3.z, xl.w);
     float h = v.h[i];
     double lo = 0.0, hi = INFINITY;
     bool done = !valid;
-    bool have_list = false;  // the leaf list in shared memory covers the round
-    int nsph = 0;            // support spheres of the round's unconverged particles
-    float Ri = 0.0f;         // this particle's radius at the last search
-    int nlist = 0;
-    int resident = -1;       // staged records still in shared memory (whole list), or -1
+    float Ri = 0.0f;         // radius of this lane's neighbour list
+    int nl = -1;             // entries of its list (-1: no list valid)
+    bool keep = true;        // the list may be kept across iterations (not after it filled up)
+    bool have_list = false;  // the shared-memory leaf list is complete for the last search
+    int nlist = 0;           // leaves in the shared-memory leaf list
     for (int it = 0; it < v.h_max_iter && !st.failed; it++) {
       const float H = GAMMA_K * h;
       const float Hs = warp_max(done ? 0.0f : H);
       if (Hs == 0.0f) break;  // every particle of the round has converged
       const float H2 = H * H, Hinv = 1.0f / H;
-      float n_hi = 0.f, n_lo = 0.f, t_hi = 0.f, t_lo = 0.f;
-      float r_hi = 0.f, r_lo = 0.f, rt_hi = 0.f, rt_lo = 0.f;
-      float pn = 0.f, pt = 0.f, pr = 0.f, prt = 0.f;
-      float p2 = 0.f;  // sum q^2 w'' (the second derivative of the h equation)
-      int cur = -1, cnt = 0;
-      // test 32 staged records per pass without branching, then evaluate the
-      // accepted ones; partial sums are folded at neighbour-cell boundaries
-      // the live particles of the round, for the transposed candidate test
-      int ntst = 32 + 1, my_rank = 0;
-      if constexpr (G == 1) {
-        const unsigned vm = __ballot_sync(FULL, !done);
-        ntst = __popc(vm);
-        my_rank = __popc(vm & ((1u << lane) - 1u));
-        if (!done) st.tst[my_rank] = make_float4(xi.x, xi.y, xi.z, H2);
-        __syncwarp();
+      DSum s;
+      s.zero();
+      // lanes without a list valid at this H gather (a whole particle's G lanes together)
+      const bool need = !done && (nl < 0 || H > Ri);
+      if (need) {
+        Ri = keep ? H * v.search_margin : H;
+        nl = 0;
       }
-      // candidate pairs tested: every staged record against every live particle
-      const unsigned nlive = __popc(__ballot_sync(FULL, !done && sub == 0));
-      // accept mask of the staged records kb .. kb+31 for this lane's particle
-      auto test_block = [&](int total, int kb) -> unsigned {
-        unsigned mask = 0u;
-        if (G == 1 && ntst <= TRANSPOSE_MAX) {
-          const bool in = kb + lane < total;
-          const float4 pj = st.rec[min(kb + lane, S_DENS - 1)];
-          const float2 px = make_float2(pj.x, pj.x), py = make_float2(pj.y, pj.y),
-                       pz = make_float2(pj.z, pj.z);
-          int q = 0;
-          for (; q + 1 < ntst; q += 2) {  // two live particles per packed test
-            const float4 t0 = st.tst[q], t1 = st.tst[q + 1];
-            const float2 r2 = dist2_x2(make_float2(t0.x, t1.x), make_float2(t0.y, t1.y),
-                                       make_float2(t0.z, t1.z), px, py, pz);
-            const unsigned m0 = __ballot_sync(FULL, in && r2.x < t0.w);
-            const unsigned m1 = __ballot_sync(FULL, in && r2.y < t1.w);
-            if (q == my_rank) mask = m0;
-            if (q + 1 == my_rank) mask = m1;
+      bool gath = need;   // this lane gathers in the current pass
+      int skipc = 0;      // accepted records this lane has listed in earlier passes
+      bool first = true;
+      int nsph = 0;
+      float R = 0.0f;
+      bool overflowed = false;
+      for (;;) {
+        int acc = 0;  // records this lane accepted in the pass
+        if (__any_sync(FULL, gath)) {
+          // every pass of a gather uses the spheres and reach of its first
+          // pass, so that all passes stage the same records in the same order
+          // (later passes reuse its leaf list when that list was complete)
+          const bool search_now = first || !have_list;
+          if (first) {
+            R = warp_max(gath ? Ri : 0.0f);
+            const unsigned gb = __ballot_sync(FULL, gath);
+            nsph = compact_spheres(st.sph, sub == 0 && (gb & gmask) != 0u,
+                                   make_float4(xi.x, xi.y, xi.z, Ri));
           }
-          if (q < ntst) {
-            const float4 t = st.tst[q];
-            const float dx = t.x - pj.x, dy = t.y - pj.y, dz = t.z - pj.z;
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const unsigned m = __ballot_sync(FULL, in && r2 < t.w);
-            if (q == my_rank) mask = m;
+          const float T2 = Ri * Ri;
+          int ntst = 32 + 1, my_rank = 0;
+          if constexpr (G == 1) {
+            const unsigned vm = __ballot_sync(FULL, gath);
+            ntst = __popc(vm);
+            my_rank = __popc(vm & ((1u << lane) - 1u));
+            if (gath) st.tst[my_rank] = make_float4(xi.x, xi.y, xi.z, T2);
+            __syncwarp();
           }
-        } else if (G == 1) {
-          const float2 xx = make_float2(xi.x, xi.x), yy = make_float2(xi.y, xi.y),
-                       zz = make_float2(xi.z, xi.z);
+          const unsigned nlive = __popc(__ballot_sync(FULL, gath && sub == 0));
+          // accept mask of the staged records base+kb .. base+kb+31 for this lane
+          auto test_block = [&](int base, int total, int kb) -> unsigned {
+            unsigned mask = 0u;
+            if (G == 1 && ntst <= TRANSPOSE_MAX) {
+              const bool in = kb + lane < total;
+              const float4 pj = st.rec[min(base + kb + lane, S_DENS - 1)];
+              const float2 px = make_float2(pj.x, pj.x), py = make_float2(pj.y, pj.y),
+                           pz = make_float2(pj.z, pj.z);
+              int q = 0;
+              for (; q + 1 < ntst; q += 2) {  // two live particles per packed test
+                const float4 t0 = st.tst[q], t1 = st.tst[q + 1];
+                const float2 r2 = dist2_x2(make_float2(t0.x, t1.x), make_float2(t0.y, t1.y),
+                                           make_float2(t0.z, t1.z), px, py, pz);
+                const unsigned m0 = __ballot_sync(FULL, in && r2.x < t0.w);
+                const unsigned m1 = __ballot_sync(FULL, in && r2.y < t1.w);
+                if (q == my_rank) mask = m0;
+                if (q + 1 == my_rank) mask = m1;
+              }
+              if (q < ntst) {
+                const float4 t = st.tst[q];
+                const float dx = t.x - pj.x, dy = t.y - pj.y, dz = t.z - pj.z;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                const unsigned m = __ballot_sync(FULL, in && r2 < t.w);
+                if (q == my_rank) mask = m;
+              }
+            } else if (G == 1) {
+              const float2 xx = make_float2(xi.x, xi.x), yy = make_float2(xi.y, xi.y),
+                           zz = make_float2(xi.z, xi.z);
+#pragma unroll 4
+              for (int u = 0; u < 32; u += 2) {  // two records per packed test
+                const float4 p0 = st.rec[min(base + kb + u, S_DENS - 1)];
+                const float4 p1 = st.rec[min(base + kb + u + 1, S_DENS - 1)];
+                const float2 r2 = dist2_x2(xx, yy, zz, make_float2(p0.x, p1.x),
+                                           make_float2(p0.y, p1.y), make_float2(p0.z, p1.z));
+                mask |= (kb + u < total && r2.x < T2) ? (1u << u) : 0u;
+                mask |= (kb + u + 1 < total && r2.y < T2) ? (2u << u) : 0u;
+              }
+            } else {
 #pragma unroll
-          for (int u = 0; u < 32; u += 2) {  // two records per packed test
-            const float4 p0 = st.rec[min(kb + u, S_DENS - 1)];
-            const float4 p1 = st.rec[min(kb + u + 1, S_DENS - 1)];
-            const float2 r2 = dist2_x2(xx, yy, zz, make_float2(p0.x, p1.x),
-                                       make_float2(p0.y, p1.y), make_float2(p0.z, p1.z));
-            mask |= (kb + u < total && r2.x < H2) ? (1u << u) : 0u;
-            mask |= (kb + u + 1 < total && r2.y < H2) ? (2u << u) : 0u;
-          }
-        } else {
-#pragma unroll
-          for (int u = sub; u < 32; u += G) {
-            const float4 pj = st.rec[min(kb + u, S_DENS - 1)];
-            const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            mask |= (kb + u < total && r2 < H2) ? (1u << u) : 0u;
-          }
-        }
-        return mask;
-      };
-      auto consume = [&](int total) {
-        wc.cand += (unsigned long long)total * nlive;
-        for (int k0 = 0; k0 < total; k0 += 32) {
-          unsigned mask = test_block(total, k0);  // (every lane: the test votes)
-          if (done) mask = 0u;
-          while (mask) {
-            const int k = k0 + __ffs(mask) - 1;
-            mask &= mask - 1;
-            const int ci = st.recc[k];
-            if (ci != cur) {
-              fold(n_hi, n_lo, pn);
-              fold(t_hi, t_lo, pt);
-              fold(r_hi, r_lo, pr);
-              fold(rt_hi, rt_lo, prt);
-              pn = pt = pr = prt = 0.f;
-              cur = ci;
+              for (int u = sub; u < 32; u += G) {
+                const float4 pj = st.rec[min(base + kb + u, S_DENS - 1)];
+                const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                mask |= (kb + u < total && r2 < T2) ? (1u << u) : 0u;
+              }
             }
-            const float4 pj = st.rec[k];
-            const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
-            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float rr = r2 * rsqrtf(fmaxf(r2, 1e-30f));
-            const float qq = rr * Hinv;
-            float wq, dwq;
-            kernel_wd(qq, wq, dwq);
-            const float tt = fmaf(qq, dwq, 3.0f * wq);
-            p2 = fmaf(qq * qq, kernel_d2w(qq), p2);
-            pn += wq;
-            pt += tt;
-            pr = fmaf(pj.w, wq, pr);
-            prt = fmaf(pj.w, tt, prt);
-            cnt++;  // (the particle itself is among the accepted records: one subtracted below)
-          }
+            return mask;
+          };
+          // accepted records go into the list (those past the earlier passes' share)
+          auto consume = [&](int base, int total) {
+            wc.cand += (unsigned long long)total * nlive;
+            for (int k0 = 0; k0 < total; k0 += 32) {
+              unsigned mask = test_block(base, total, k0);  // (every lane: the test votes)
+              if (!gath) mask = 0u;
+              while (mask) {
+                const int k = base + k0 + __ffs(mask) - 1;
+                mask &= mask - 1;
+                const int e = acc - skipc;
+                if (e >= 0 && e < cap) {
+                  const float4 pj = st.rec[k];
+                  const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
+                  __stcg(lst + (size_t)e * ls,
+                         make_float2(fmaf(dx, dx, fmaf(dy, dy, dz * dz)), pj.w));
+                }
+                acc++;
+              }
+            }
+          };
+          const float R2 = R * R * 1.0002f, Rc = R + ceps;
+          auto leaf_ok = [&](int l, float sx, float sy, float sz, LeafBox &lb) {
+            const float4 lo4 = v.leaf_lo[l], hi4 = v.leaf_hi[l];
+            lb = leaf_box(lo4, hi4, sx, sy, sz, 0.0f);
+            return box_gap2(W.lx, W.ly, W.lz, W.hx, W.hy, W.hz, lo4, hi4, sx, sy, sz) < R2;
+          };
+          auto chunk_ok = [&](int g, float sx, float sy, float sz) {
+            return box_gap2(clx, cly, clz, chx, chy, chz, v.chunk_lo[g], v.chunk_hi[g], sx, sy,
+                            sz) < Rc * Rc;
+          };
+          // (the density loop keeps the per-lane sphere test: at its register
+          // limit the transposed form costs more in spills than it saves)
+          const Reach reach = {clx, cly, clz, chx, chy, chz, Rc, exc, st.sph, nsph, true};
+          int skip = 0;
+          bool more = false, complete = true;
+          do {
+            if (search_now) {
+              nlist = search(v, F, reach, st, leaf_ok, chunk_ok, skip, more, part);
+              complete = complete && !more;
+            }
+            stage_list(srcs, st, nlist, consume, wc);
+            skip += nlist;
+          } while (search_now && more && !st.failed);
+          if (search_now) have_list = complete;
+          if (writer) wc.gathers += nlive;
+          if (gath) nl = min(acc - skipc, cap);
         }
-      };
-      // the leaf list in shared memory is reused while every unconverged
-      // particle's support stays inside the radius it was searched with;
-      // otherwise search again (in passes of LCAP leaves)
-      const bool reuse = have_list && __all_sync(FULL, done || H <= Ri);
-      if (!reuse) {
-        Ri = done ? 0.0f : H * 1.05f;  // room for the next iterations to grow h
-        nsph = compact_spheres(st.sph, sub == 0 && Ri > 0.0f, make_float4(xi.x, xi.y, xi.z, Ri));
+        // the list this pass built (or, in the first pass, the one kept from
+        // an earlier iteration), in order
+        if (!done && (gath || first) && nl > 0) dens_list(s, lst, ls, nl, H2, Hinv);
+        // a list that filled up: the next pass lists the records after it (for
+        // several lanes per particle, every lane of the particle goes on)
+        const unsigned ob = __ballot_sync(FULL, gath && acc > skipc + cap);
+        const bool over = gath && (ob & gmask) != 0u;
+        if (over) {
+          skipc += cap;
+          overflowed = true;
+          if (sub == 0 && writer) wc.list_overflows++;
+        }
+        gath = over;
+        first = false;
+        if (ob == 0u || st.failed) break;
       }
-      const float R = Hs * 1.05f;
-      const float R2 = R * R * 1.0002f, Rc = R + ceps;
-      auto leaf_ok = [&](int l, float sx, float sy, float sz, LeafBox &lb) {
-        const float4 lo = v.leaf_lo[l], hi = v.leaf_hi[l];
-        lb = leaf_box(lo, hi, sx, sy, sz, 0.0f);
-        return box_gap2(W.lx, W.ly, W.lz, W.hx, W.hy, W.hz, lo, hi, sx, sy, sz) < R2;
-      };
-      auto chunk_ok = [&](int g, float sx, float sy, float sz) {
-        return box_gap2(clx, cly, clz, chx, chy, chz, v.chunk_lo[g], v.chunk_hi[g], sx, sy, sz) <
-               Rc * Rc;
-      };
-      // (the density loop keeps the per-lane sphere test: at its register
-      // limit the transposed form costs more in spills than it saves)
-      const Reach reach = {clx, cly, clz, chx, chy, chz, Rc, exc, st.sph, nsph, true};
-      if (reuse && resident >= 0) {
-        // the whole list is still staged: evaluate it again at the new h
-        consume(resident);
-        __syncwarp();
-        fence_proxy_async();
-      } else {
-        int skip = 0, passes = 0, staged = -1;
-        bool more = false, complete = true;
-        do {
-          if (!reuse) {
-            nlist = search(v, F, reach, st, leaf_ok, chunk_ok, skip, more, part);
-            complete = complete && !more;
-          }
-          staged = stage_list(srcs, st, nlist, consume, wc);
-          passes++;
-          skip += nlist;
-        } while (!reuse && more && !st.failed);
-        if (!reuse) have_list = complete;
-        resident = passes == 1 ? staged : -1;
+      if (overflowed) {
+        keep = false;
+        nl = -1;  // the list holds only the last pass's share
       }
       if (!COOP && st.failed) break;
-      fold(n_hi, n_lo, pn);
-      fold(t_hi, t_lo, pt);
-      fold(r_hi, r_lo, pr);
-      fold(rt_hi, rt_lo, prt);
+      s.fold_all();
       double sn, stt, s2;
       float sr, srt;
+      int cnt;
       if constexpr (COOP) {
         // combine the 8 warps' partial sums, in warp order
         float *mine = red_area<StageD>(warp);
-        mine[0 * 32 + lane] = n_hi; mine[1 * 32 + lane] = n_lo;
-        mine[2 * 32 + lane] = t_hi; mine[3 * 32 + lane] = t_lo;
-        mine[4 * 32 + lane] = r_hi; mine[5 * 32 + lane] = r_lo;
-        mine[6 * 32 + lane] = rt_hi; mine[7 * 32 + lane] = rt_lo;
-        reinterpret_cast<int *>(mine)[8 * 32 + lane] = cnt;
+        mine[0 * 32 + lane] = s.n_hi; mine[1 * 32 + lane] = s.n_lo;
+        mine[2 * 32 + lane] = s.t_hi; mine[3 * 32 + lane] = s.t_lo;
+        mine[4 * 32 + lane] = s.r_hi; mine[5 * 32 + lane] = s.r_lo;
+        mine[6 * 32 + lane] = s.rt_hi; mine[7 * 32 + lane] = s.rt_lo;
+        reinterpret_cast<int *>(mine)[8 * 32 + lane] = s.cnt;
         reinterpret_cast<int *>(mine)[9 * 32 + lane] = st.failed ? 1 : 0;
-        mine[10 * 32 + lane] = p2;
+        mine[10 * 32 + lane] = s.p2;
         __syncthreads();
         double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, a4 = 0.0;
         int c = 0, fl = 0;
@@ -282,12 +372,12 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
         s2 = a4;
         cnt = c - 1;
       } else {
-        sn = group_sum<G>((double)n_hi + (double)n_lo);
-        stt = group_sum<G>((double)t_hi + (double)t_lo);
-        sr = (float)group_sum<G>((double)r_hi + (double)r_lo);
-        srt = (float)group_sum<G>((double)rt_hi + (double)rt_lo);
-        s2 = group_sum<G>((double)p2);
-        cnt = group_sum_i<G>(cnt) - 1;
+        sn = group_sum<G>((double)s.n_hi + (double)s.n_lo);
+        stt = group_sum<G>((double)s.t_hi + (double)s.t_lo);
+        sr = (float)group_sum<G>((double)s.r_hi + (double)s.r_lo);
+        srt = (float)group_sum<G>((double)s.rt_hi + (double)s.rt_lo);
+        s2 = group_sum<G>((double)s.p2);
+        cnt = group_sum_i<G>(s.cnt) - 1;  // (the particle itself is among its candidates)
       }
       if (!done) {
         // Halley step in FP64 (Newton where its denominator is not positive),
@@ -433,11 +523,11 @@ __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, co
     }
     const unsigned nlive = __popc(__ballot_sync(FULL, valid && sub == 0));
     // accept mask of the staged records kb .. kb+31 for this lane's particle
-    auto test_block = [&](int total, int kb) -> unsigned {
+    auto test_block = [&](int base, int total, int kb) -> unsigned {
       unsigned mask = 0u;
       if (G == 1 && ntst <= TRANSPOSE_MAX) {
         const bool in = kb + lane < total;
-        const float4 pj = sx_rec[min(kb + lane, S_FORCE - 1)];
+        const float4 pj = sx_rec[min(base + kb + lane, S_FORCE - 1)];
         const float Hj2 = pj.w * pj.w;
         const float2 px = make_float2(pj.x, pj.x), py = make_float2(pj.y, pj.y),
                      pz = make_float2(pj.z, pj.z);
@@ -463,8 +553,8 @@ __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, co
                      zz = make_float2(xi.z, xi.z);
 #pragma unroll
         for (int u = 0; u < 32; u += 2) {  // two records per packed test
-          const float4 p0 = sx_rec[min(kb + u, S_FORCE - 1)];
-          const float4 p1 = sx_rec[min(kb + u + 1, S_FORCE - 1)];
+          const float4 p0 = sx_rec[min(base + kb + u, S_FORCE - 1)];
+          const float4 p1 = sx_rec[min(base + kb + u + 1, S_FORCE - 1)];
           const float2 r2 = dist2_x2(xx, yy, zz, make_float2(p0.x, p1.x),
                                      make_float2(p0.y, p1.y), make_float2(p0.z, p1.z));
           mask |= (kb + u < total && (r2.x < Hi2 || r2.x < p0.w * p0.w)) ? (1u << u) : 0u;
@@ -473,7 +563,7 @@ __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, co
       } else {
 #pragma unroll
         for (int u = sub; u < 32; u += G) {
-          const float4 pj = sx_rec[min(kb + u, S_FORCE - 1)];
+          const float4 pj = sx_rec[min(base + kb + u, S_FORCE - 1)];
           const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
           const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
           mask |= (kb + u < total && (r2 < Hi2 || r2 < pj.w * pj.w)) ? (1u << u) : 0u;
@@ -481,7 +571,7 @@ __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, co
       }
       return mask;
     };
-    auto consume = [&](int total) {
+    auto consume = [&](int base, int total) {
       wc.cand += (unsigned long long)total * nlive;
       // two blocks of 32 records per evaluation round: the lanes' accepted
       // counts even out over 64 records (records still in index order; the
@@ -489,13 +579,13 @@ __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, co
       for (int k0 = 0; k0 < total; k0 += 64) {
         // (every lane calls the test, which votes; the second call's
         // condition is the same in all lanes)
-        const unsigned m0 = test_block(total, k0);
-        const unsigned m1 = k0 + 32 < total ? test_block(total, k0 + 32) : 0u;
+        const unsigned m0 = test_block(base, total, k0);
+        const unsigned m1 = k0 + 32 < total ? test_block(base, total, k0 + 32) : 0u;
         unsigned long long mask = valid ? ((unsigned long long)m1 << 32) | m0 : 0ull;
         while (mask) {
           // (the particle itself is accepted too: r = 0, it adds nothing but
           // the signal velocity 2 c_i, the start value; one count subtracted below)
-          const int k = k0 + __ffsll(mask) - 1;
+          const int k = base + k0 + __ffsll(mask) - 1;
           mask &= mask - 1;
           const int ci = st.recc[k];
           if (ci != cur) {
@@ -627,6 +717,13 @@ __device__ __forceinline__ Queues queues(const View &v, const DevState *ds, int 
   return {0, ds->n_active_groups + ds->n_heavy_groups};
 }
 
+// Plain (per-bin) launches: blocks that take the shared groups (each with its
+// own neighbour-list slot), the rest of the grid one group per warp.
+template <int G>
+__device__ __forceinline__ int coop_blocks(const View &v, const Queues &qs) {
+  return G == 1 ? min(qs.ncoop, v.coop_slots) : 0;
+}
+
 __device__ __forceinline__ int coop_group(const View &v, const DevState *ds, int bin_filter, int k) {
   if (bin_filter >= 0) return v.q_bin[ds->n_groups - 1 - k];
   return all_coop(v, ds) ? active_group(v, ds, k) : v.q_group[ds->n_groups - 1 - k];
@@ -640,18 +737,22 @@ __device__ __forceinline__ int warp_group(const View &v, const DevState *ds, int
 __device__ __forceinline__ void flush_counters(DevState *ds, WarpCounters &wc, bool density) {
   // pairs and iterations are held by group leaders; sum over the warp
   unsigned long long p = wc.pairs, it = wc.iters, nc = wc.noconv, ov = wc.overflow;
+  unsigned long long lo = wc.list_overflows;
   for (int o = 16; o; o >>= 1) {
     p += __shfl_xor_sync(FULL, p, o);
     it += __shfl_xor_sync(FULL, it, o);
     nc += __shfl_xor_sync(FULL, nc, o);
     ov += __shfl_xor_sync(FULL, ov, o);
+    lo += __shfl_xor_sync(FULL, lo, o);
   }
-  // candidates and timeouts are warp-uniform (every lane counted the same)
+  // candidates, gathers and timeouts are warp-uniform (every lane counted the same)
   if (lane_id() == 0) {
     if (density) {
       if (p) atomicAdd(&ds->s_pairs_density, p);
       if (wc.cand) atomicAdd(&ds->s_cand_density, wc.cand);
       if (it) atomicAdd(&ds->s_iters_density, it);
+      if (wc.gathers) atomicAdd(&ds->s_gathers_density, wc.gathers);
+      if (lo) atomicAdd(&ds->s_list_overflows, lo);
       if (nc) record_error(ds, SPH_ERR_H_NOCONV, nc, false);
       if (ov) record_error(ds, SPH_ERR_CELL_OVERFLOW, ov, true);
     } else {
@@ -671,7 +772,7 @@ __global__ void __launch_bounds__(PT, 2) k_density(View v, int flags, int bin_fi
   // H + 2 (largest excursion of a particle out of its cell) <= cell width.
   // Thread 0 reads the device state once for the block, so that every warp
   // of a block takes the same decisions (its warps meet at block barriers).
-  __shared__ int s_go;
+  __shared__ int s_go, s_stall;
   __shared__ float s_exc;
   const double w = ds->w;
   if (threadIdx.x == 0) {
@@ -684,20 +785,26 @@ __global__ void __launch_bounds__(PT, 2) k_density(View v, int flags, int bin_fi
     }
     s_go = go;
     s_exc = exc0;
+    // testing (sph_params.test_stall): while stalls are left, the launch's
+    // first warp to stage claims one
+    s_stall = go && ds->test_stall > 0 ? 1 : 0;
   }
   __syncthreads();
   if (!s_go) return;
   const float exc = s_exc;
   StageD st;
-  stage_init(st);
+  stage_init(st, v.stage_depth, v.wait_limit, s_stall ? &ds->test_stall : nullptr);
   const float hcap = (float)((w - 2.0 * (double)exc) / GAMMA_K_D * (1.0 - 1e-6));
   const int m_act = ds->m_act;
   const long long ti = ds->ti;
   const Queues qs = queues<G>(v, ds, bin_filter);
   WarpCounters wc = {0, 0, 0, 0, 0, 0};
-  if (persistent) {
-    if constexpr (G == 1) {
-      // heavy groups first, a block each
+  // (one call site per form of the loop keeps the kernel's code small)
+  const int cb = coop_blocks<G>(v, qs);
+  if constexpr (G == 1) {
+    // shared groups first, a block each, pulled from a head (persistent
+    // launches: every block; per-bin launches: the first cb blocks)
+    if (persistent || (int)blockIdx.x < cb) {
       __shared__ int s_item;
       for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(&ds->head_coop_density, 1);
@@ -706,28 +813,23 @@ __global__ void __launch_bounds__(PT, 2) k_density(View v, int flags, int bin_fi
         __syncthreads();
         if (item >= qs.ncoop || st.failed) break;
         const int wg = coop_group(v, ds, bin_filter, item);
-        density_group<1, true>(v, wg, flags, bin_filter, m_act, frame_of(v, ds, wg), hcap, exc, ti,
-                               st, wc);
+        density_group<1, true>(v, wg, flags, bin_filter, m_act, frame_of(v, ds, wg), hcap, exc,
+                               ti, st, wc);
       }
     }
-    for (;;) {
-      int item = 0;
-      if (lane == 0) item = atomicAdd(&ds->head_density, 1);
-      item = __shfl_sync(FULL, item, 0);
+  }
+  // the other groups one per warp: pulled from a head (persistent) or by index
+  if (persistent || (int)blockIdx.x >= cb) {
+    for (int k = 0;; k++) {
+      int item;
+      if (persistent) {
+        item = 0;
+        if (lane == 0) item = atomicAdd(&ds->head_density, 1);
+        item = __shfl_sync(FULL, item, 0);
+      } else {
+        item = k == 0 ? ((int)blockIdx.x - cb) * WARPS_PER_BLOCK + warp : qs.nwarp;
+      }
       if (item >= qs.nwarp || st.failed) break;
-      const int wg = warp_group<G>(v, ds, bin_filter, item);
-      density_group<G, false>(v, wg, flags, bin_filter, m_act, frame_of(v, ds, wg), hcap, exc, ti,
-                              st, wc);
-    }
-  } else if (G == 1 && (int)blockIdx.x < qs.ncoop) {
-    if constexpr (G == 1) {
-      const int wg = coop_group(v, ds, bin_filter, blockIdx.x);
-      density_group<1, true>(v, wg, flags, bin_filter, m_act, frame_of(v, ds, wg), hcap, exc, ti,
-                             st, wc);
-    }
-  } else {
-    const int item = (blockIdx.x - (G == 1 ? qs.ncoop : 0)) * WARPS_PER_BLOCK + warp;
-    if (item < qs.nwarp) {
       const int wg = warp_group<G>(v, ds, bin_filter, item);
       density_group<G, false>(v, wg, flags, bin_filter, m_act, frame_of(v, ds, wg), hcap, exc, ti,
                               st, wc);
@@ -751,14 +853,15 @@ __global__ void __launch_bounds__(PT, 2) k_force(View v, int bin_filter, int per
   __syncthreads();
   if (!s_go) return;
   StageF st;
-  stage_init(st);
+  stage_init(st, v.stage_depth, v.wait_limit);
   const int m_act = ds->m_act;
   const float Hmax = s_Hmax;
   const float exc = s_exc;
   const Queues qs = queues<G>(v, ds, bin_filter);
   WarpCounters wc = {0, 0, 0, 0, 0, 0};
-  if (persistent) {
-    if constexpr (G == 1) {
+  const int cb = coop_blocks<G>(v, qs);
+  if constexpr (G == 1) {
+    if (persistent || (int)blockIdx.x < cb) {
       __shared__ int s_item;
       for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(&ds->head_coop_force, 1);
@@ -770,22 +873,18 @@ __global__ void __launch_bounds__(PT, 2) k_force(View v, int bin_filter, int per
         force_group<1, true>(v, wg, bin_filter, m_act, frame_of(v, ds, wg), Hmax, exc, st, wc);
       }
     }
-    for (;;) {
-      int item = 0;
-      if (lane == 0) item = atomicAdd(&ds->head_force, 1);
-      item = __shfl_sync(FULL, item, 0);
+  }
+  if (persistent || (int)blockIdx.x >= cb) {
+    for (int k = 0;; k++) {
+      int item;
+      if (persistent) {
+        item = 0;
+        if (lane == 0) item = atomicAdd(&ds->head_force, 1);
+        item = __shfl_sync(FULL, item, 0);
+      } else {
+        item = k == 0 ? ((int)blockIdx.x - cb) * WARPS_PER_BLOCK + warp : qs.nwarp;
+      }
       if (item >= qs.nwarp || st.failed) break;
-      const int wg = warp_group<G>(v, ds, bin_filter, item);
-      force_group<G, false>(v, wg, bin_filter, m_act, frame_of(v, ds, wg), Hmax, exc, st, wc);
-    }
-  } else if (G == 1 && (int)blockIdx.x < qs.ncoop) {
-    if constexpr (G == 1) {
-      const int wg = coop_group(v, ds, bin_filter, blockIdx.x);
-      force_group<1, true>(v, wg, bin_filter, m_act, frame_of(v, ds, wg), Hmax, exc, st, wc);
-    }
-  } else {
-    const int item = (blockIdx.x - (G == 1 ? qs.ncoop : 0)) * WARPS_PER_BLOCK + warp;
-    if (item < qs.nwarp) {
       const int wg = warp_group<G>(v, ds, bin_filter, item);
       force_group<G, false>(v, wg, bin_filter, m_act, frame_of(v, ds, wg), Hmax, exc, st, wc);
     }

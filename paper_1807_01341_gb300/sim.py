@@ -41,6 +41,11 @@ class Params:
     n_cells_override: int = 0
     heavy_factor: float = 0.0
     coop_max_groups: int = -1
+    list_cap: int = 256
+    search_margin: float = 1.02
+    staging_depth: int = 1
+    wait_limit: int = 0
+    test_stall: int = 0
 
     def to_c(self) -> _lib.sph_params:
         p = _lib.sph_params()

@@ -263,3 +263,74 @@ def test_dt_below_t_min_is_reported(sim):
     assert code == L.SPH_ERR_DT_TOO_SMALL and detail == n
     assert np.all(p.numpy()["bin"] == 0)
     ctx.close()
+
+
+@pytest.mark.parametrize("coop_max_groups", [0, 1 << 30])
+def test_lists_margin_and_staging_depth_do_not_change_results(sim, coop_max_groups):
+    """The density loop's neighbour lists (kept across h iterations), their
+    capacity, the search margin of a gather and the number of staging buffers
+    change how the candidates are found, not which pairs are summed nor in
+    what order: 12 steps agree bit for bit.  A list of 32 entries fills up
+    for most particles (their gathers run in passes); coop_max_groups 2^30
+    sends every work group to a whole block (per-warp lists)."""
+    ic = _ic_step(seed=43)
+    base = dict(STEP_PARAMS, coop_max_groups=coop_max_groups)
+    ref, cref, tref = _run_form(sim, ic, "graph", 12,
+                                dict(base, list_cap=128, search_margin=1.1, staging_depth=1))
+    # a list spares most iterations their gather
+    assert 0 < cref["gathers_density"] < cref["iters_density"]
+    variants = [dict(list_cap=512, search_margin=1.5, staging_depth=3),
+                dict(list_cap=64, search_margin=1.0, staging_depth=2),
+                dict(list_cap=32, search_margin=1.1, staging_depth=2)]
+    for var in variants:
+        st, c, t = _run_form(sim, ic, "graph", 12, dict(base, **var))
+        assert t == tref, var
+        for k in ref:
+            assert np.array_equal(st[k], ref[k]), (var, k)
+        for k in ("pairs_density", "pairs_force", "iters_density", "active_particles"):
+            assert c[k] == cref[k], (var, k)
+        if var["list_cap"] == 32:
+            assert c["list_overflows"] > 0
+    # the plain form with three buffers is the same run too
+    st, c, t = _run_form(sim, ic, "plain", 12, dict(base, list_cap=96, staging_depth=3))
+    assert t == tref
+    for k in ref:
+        assert np.array_equal(st[k], ref[k]), ("plain", k)
+
+
+@pytest.mark.parametrize("coop_max_groups", [0, 1 << 30])
+def test_bounded_wait_gives_up_and_context_recovers(sim, coop_max_groups):
+    """A staging barrier that no copy completes (test_stall: one warp of the
+    first density launch issues no copy and never arrives): the bounded wait
+    gives up after wait_limit polls, the step stops with SPH_ERR_TIMEOUT
+    (status word: the timed-out waits counted), nothing traps, and after the
+    status is cleared the same context completes the step and agrees with a
+    run that never stalled."""
+    import torch
+    L = _lib()
+    ic = _ic_step(seed=47)
+    params = dict(STEP_PARAMS, coop_max_groups=coop_max_groups)
+    ref, _, _ = _run_form(sim, ic, "batched", 1, params)
+    ctx, p = gpu_setup(ic, sim.Params(**params, wait_limit=2000, test_stall=1))
+    with pytest.raises(L.SphError) as e:
+        ctx.step(p, L.SPH_FORM_BATCHED)
+    assert e.value.code == L.SPH_ERR_TIMEOUT
+    code, detail = ctx.status()
+    assert code == L.SPH_ERR_TIMEOUT and detail >= 1
+    assert ctx.counters()["steps"] == 0
+    ctx.clear_status()
+    ctx.step(p, L.SPH_FORM_BATCHED)
+    torch.cuda.synchronize()
+    assert ctx.status()[0] == 0 and ctx.counters()["steps"] == 1
+    st = p.numpy()
+    for k in ("x", "y", "z"):
+        assert np.array_equal(st[k], ref[k]), k
+    assert np.array_equal(st["active"], ref["active"])
+    # the redone step starts its h iteration from partly updated guesses:
+    # the same roots to the convergence tolerance
+    for k in ("h", "rho"):
+        assert np.max(np.abs(st[k] / ref[k] - 1)) < 1e-5, k
+    a = np.stack([st["ax"], st["ay"], st["az"]], 1)
+    a_ref = np.stack([ref["ax"], ref["ay"], ref["az"]], 1)
+    assert np.max(np.abs(a - a_ref)) < 1e-4 * np.sqrt((a_ref ** 2).sum(1).mean())
+    ctx.close()

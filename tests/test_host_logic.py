@@ -62,4 +62,4 @@ def test_autotune_keeps_default_inside_margin(monkeypatch, tmp_path, rates, expe
     assert again["cached"] and {k: again[k] for k in cands[0]} == cands[expect]
     assert len(calls) == 3
     with open(cache) as f:
-        assert "w:n=10:steps=3" in json.load(f)
+        assert "w:n=10:steps=3:knobs=cell_margin,leaf_max,threads_per_particle" in json.load(f)
