@@ -19,9 +19,14 @@ e2e         the batched form through the C ABI with host buffers: each step
 roofline    the dominant pair-loop kernel: algorithmic FLOPs per useful pair
             (density 29, force 61) x useful pairs per launch / mean launch time
             (CUDA events in the library, on the launching stream), against the
-            FP32 peak 152 SMs x 128 lanes x 2 x 2.07 GHz; its `traffic` is the
-            DRAM bytes per launch from the kernel's ncu summary under profiles/,
-            reported only while that summary's source digest matches the sources;
+            FP32 peak: the SMs the device reports x 128 lanes x 2 x the median
+            SM clock sampled during the timed steps; `executed` counts instead
+            every candidate test and every pair term of every h iteration; its
+            `traffic` is the DRAM bytes per launch from the kernel's ncu summary
+            under profiles/, reported only while that summary's source digest
+            matches the sources;
+cell_build_ms  one cell build of the initial state (CUDA events; a rebuild
+            inside a timed step is part of that step's time);
 cpu_baseline  the FP64 oracle on a bounded sample of the same workload.
 
 --impl reference times the oracle alone (the CPU reference of this method).
@@ -54,7 +59,16 @@ WORKLOAD = "c3_clustered_2m"
 # algorithmic FP32 operations per useful pair (FMA = 2; sqrt, rsqrt, divide = 1)
 FLOP_DENSITY = 29
 FLOP_FORCE = 61
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# executed FP32 operations per candidate test (3 differences, r^2 by one multiply
+# and two FMAs, the compare; the force test compares with both supports)
+FLOP_TEST_DENSITY = 9
+FLOP_TEST_FORCE = 10
+FP32_LANES_PER_SM = 128  # FP32 lanes per SM (sm_103a)
+
+
+def fp32_peak(sms: int, sm_mhz: float) -> float:
+    """FP32 peak in TFLOP/s from the SM count and the SM clock (FMA = 2)."""
+    return sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 DEFAULT_LAUNCH = dict(threads_per_particle=1, leaf_max=16, cell_margin=2.0, list_cap=256,
                       search_margin=1.02, staging_depth=1, heavy_factor=0.0)
 KNOBS = ("threads_per_particle", "leaf_max", "cell_margin", "list_cap", "search_margin",
@@ -218,11 +232,21 @@ def run_ours(args, rank, world):
     snapshot = {k: t.clone() for k, t in p.arrays().items()}
     stream = torch.cuda.Stream()
 
+    build_ms = []
+
     def restore():
+        """The initial state, its cell build timed (CUDA events on the
+        stream; the build also synchronises on the host to size its grid)."""
         for k, t in p.arrays().items():
             t.copy_(snapshot[k])
         torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
         ctx.build_cells(p, stream)
+        e1.record(stream)
+        e1.synchronize()
+        build_ms.append(e0.elapsed_time(e1))
         ctx.begin_run(stream)
         ctx.reset_kernel_times()
 
@@ -315,15 +339,21 @@ def run_ours(args, rank, world):
     kt = res["ktimes"]
     c = res["counters"]
     dens = dict(ms=kt["density_ms"], n=max(kt["density_launches"], 1),
-                flops=FLOP_DENSITY * c["pairs_density"])
+                flops=FLOP_DENSITY * c["pairs_density"],
+                executed=FLOP_TEST_DENSITY * c["cand_density"] + FLOP_DENSITY * c["evals_density"])
     forc = dict(ms=kt["force_ms"], n=max(kt["force_launches"], 1),
-                flops=FLOP_FORCE * c["pairs_force"])
+                flops=FLOP_FORCE * c["pairs_force"],
+                executed=FLOP_TEST_FORCE * c["cand_force"] + FLOP_FORCE * c["pairs_force"])
     dom_name, dom = max((("density", dens), ("force", forc)), key=lambda kv: kv[1]["ms"])
     per_launch_s = dom["ms"] / dom["n"] / 1e3
     achieved = dom["flops"] / dom["n"] / per_launch_s / 1e12 if per_launch_s > 0 else 0.0
+    executed = dom["executed"] / dom["n"] / per_launch_s / 1e12 if per_launch_s > 0 else 0.0
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     out = dict(pairs=pairs, total_ms=total_ms, res=results, e2e_ms=sum(e2e_ms),
+               sms=sms, build_ms=statistics.median(build_ms) if build_ms else None,
                e2e_pairs=e2e_pairs, h2d=h2d, n=n, t_ic=t_ic,
-               roofline=dict(kernel=dom_name, achieved=achieved, per_launch_ms=per_launch_s * 1e3,
+               roofline=dict(kernel=dom_name, achieved=achieved, executed=executed,
+                             per_launch_ms=per_launch_s * 1e3,
                              density_ms=kt["density_ms"], force_ms=kt["force_ms"]),
                gpu_state={k: t for k, t in p.arrays().items()} if rank == 0 else None,
                ic=ic, tuned=tuned, tune_info=tune_info)
@@ -597,6 +627,10 @@ def main():
             cpu = {"value": r["pairs"] / r["seconds"], "unit": UNIT, "cores": r["threads"],
                    "kind": "oracle", "sample": r["sample"]}
         c = b["counters"]
+        # the roofline denominator: FP32 lanes of the SMs the device reports, at
+        # the median SM clock sampled during the timed steps (else the maximum)
+        mhz = b["clocks"].get("sm_mhz") or b["clocks"].get("sm_max_mhz") or 2070.0
+        peak = fp32_peak(out["sms"], mhz)
         line = {
             "metric": METRIC, "value": pairs_all / (total_ms / 1e3), "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -615,12 +649,20 @@ def main():
             "e2e": {"value": e2e_pairs / (e2e_ms / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": out["h2d"], "d2h_bytes_per_step": out["h2d"]},
             "roofline": {"bound": "alu", "kernel": rf["kernel"], "achieved": rf["achieved"],
-                         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": rf["achieved"] / FP32_PEAK_TFLOPS,
+                         "peak": peak, "unit": "TFLOP/s",
+                         "frac": rf["achieved"] / peak,
                          "traffic": profiled_traffic(rf["kernel"], args.workload, out["tuned"]),
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived)",
+                         "peak_source": f"{out['sms']} SMs (queried) x {FP32_LANES_PER_SM} FP32 "
+                                        f"lanes x 2 x {mhz:.0f} MHz (median SM clock sampled "
+                                        "during the timed steps)",
+                         "achieved_counts": "algorithmic FLOPs of the useful pairs (density at "
+                                            "the final h)",
+                         "executed": {"achieved": rf["executed"], "frac": rf["executed"] / peak,
+                                      "counts": "FP32 work executed: every candidate test "
+                                                "and every pair term of every h iteration"},
                          "launch_ms": rf["per_launch_ms"], "density_ms": rf["density_ms"],
                          "force_ms": rf["force_ms"]},
+            "cell_build_ms": out["build_ms"],
             "cpu_baseline": cpu,
             "gpu_launches": b["launches"],
             # useful pairs / tested (record, particle) pairs; the density loop's
@@ -630,7 +672,7 @@ def main():
                 "force": c["pairs_force"] / max(c["cand_force"], 1)},
             "counters": {k: c[k] for k in ("pairs_density", "pairs_force", "cand_density",
                                            "cand_force", "iters_density", "gathers_density",
-                                           "list_overflows", "active_particles",
+                                           "list_overflows", "evals_density", "active_particles",
                                            "steps", "rebuilds", "redone_steps")},
             "clocks": b["clocks"],
         }

@@ -143,8 +143,10 @@ typedef struct {
                               (graph replays count their kernel nodes) */
   int64_t gathers_density; /* density loop: particle gathers (a particle counted once in
                               every staging pass over its candidates) */
-  int64_t list_overflows;  /* density loop: gathers whose neighbour list filled up (that
-                              particle then took its sums while staging) */
+  int64_t list_overflows;  /* density loop: gathers whose neighbour list filled up (the
+                              gather then ran further passes over the same leaves) */
+  int64_t evals_density;   /* density loop: neighbour-list entries evaluated, all h
+                              iterations (pair terms computed, in or beyond the support) */
 } sph_counters;
 
 void sph_default_params(sph_params *p);
@@ -305,14 +307,18 @@ int sph_reset_kernel_times(sph_ctx *ctx);
  * of the n particles by (cell, Morton code inside the cell) in an
  * n_cells_per_axis^3 grid of the periodic box of side `box` -- exactly the
  * order sph_build_cells produces for that grid from the same positions.  x, y,
- * z (device, FP64) are read, not modified.  No allocation: the sort buffers are
+ * z (device, FP64) are read, not modified; they must be finite (sph_build_cells
+ * rejects a non-finite position; this call does not check, returns SPH_OK and
+ * leaves the order of such input unspecified).  No allocation: the sort buffers are
  * one 1.6 MB array in device memory that the library defines statically, held
  * by every GPU that loads the library until the process exits.
  * Limits and errors: n <= 65536 and 1 <= n_cells_per_axis <= 255, else
  * SPH_ERR_ARG before anything is launched; SPH_ERR_CUDA if a launch or copy
  * fails.  The first call on a device looks up the array's device address
- * (with that device current); make that first call before any stream
- * capture.  Every call on a device uses the same array, so calls whose work
+ * (with that device current) and keeps it for the life of the process; make
+ * that first call before any stream capture, and make no call on a device
+ * after cudaDeviceReset there (the array goes with the context, and the kept
+ * address with it).  Every call on a device uses the same array, so calls whose work
  * overlaps on the GPU (different streams, or host threads) race and must be
  * serialised by the caller; each call writes every part of the array it reads,
  * so a call needs nothing cleared from the last one.  Asynchronous on

@@ -64,7 +64,7 @@ class sph_counters(ctypes.Structure):
     _fields_ = [(k, _i64) for k in ("pairs_density", "pairs_force", "cand_density", "cand_force",
                                     "iters_density", "active_particles", "steps", "rebuilds",
                                     "redone_steps", "kernel_launches", "gathers_density",
-                                    "list_overflows")]
+                                    "list_overflows", "evals_density")]
 
 
 class sph_kernel_times(ctypes.Structure):

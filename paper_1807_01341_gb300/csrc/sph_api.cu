@@ -1010,6 +1010,7 @@ int sph_get_counters(sph_ctx *ctx, sph_counters *out) {
   out->kernel_launches = (int64_t)g_launches.load();
   out->gathers_density = (int64_t)(h.gathers_density + h.s_gathers_density);
   out->list_overflows = (int64_t)(h.list_overflows + h.s_list_overflows);
+  out->evals_density = (int64_t)(h.evals_density + h.s_evals_density);
   return SPH_OK;
 }
 

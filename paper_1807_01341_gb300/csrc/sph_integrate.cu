@@ -61,7 +61,7 @@ __global__ void k_begin_step(View v, long long ti_arg) {
   ds->s_pairs_density = ds->s_pairs_force = 0ull;
   ds->s_cand_density = ds->s_cand_force = 0ull;
   ds->s_iters_density = ds->s_active_particles = 0ull;
-  ds->s_gathers_density = ds->s_list_overflows = 0ull;
+  ds->s_gathers_density = ds->s_list_overflows = ds->s_evals_density = 0ull;
 }
 
 // One thread per leaf: a leaf holds active particles when its smallest bin is
@@ -495,10 +495,11 @@ __device__ void next_time(View &v, long long *out, int count_step) {
   ds->active_particles += ds->s_active_particles;
   ds->gathers_density += ds->s_gathers_density;
   ds->list_overflows += ds->s_list_overflows;
+  ds->evals_density += ds->s_evals_density;
   ds->s_pairs_density = ds->s_pairs_force = 0ull;
   ds->s_cand_density = ds->s_cand_force = 0ull;
   ds->s_iters_density = ds->s_active_particles = 0ull;
-  ds->s_gathers_density = ds->s_list_overflows = 0ull;
+  ds->s_gathers_density = ds->s_list_overflows = ds->s_evals_density = 0ull;
   if (count_step) ds->steps += 1ull;
 }
 

@@ -67,11 +67,11 @@ struct DevState {
   // totals when it completes, so a halted attempt leaves no trace)
   unsigned long long s_pairs_density, s_pairs_force, s_cand_density, s_cand_force;
   unsigned long long s_iters_density, s_active_particles;
-  unsigned long long s_gathers_density, s_list_overflows;
+  unsigned long long s_gathers_density, s_list_overflows, s_evals_density;
   // totals over completed steps
   unsigned long long pairs_density, pairs_force, cand_density, cand_force;
   unsigned long long iters_density, active_particles;
-  unsigned long long gathers_density, list_overflows;
+  unsigned long long gathers_density, list_overflows, evals_density;
   unsigned long long steps;
   // time-bin occupancy
   int bin_count[MAX_BINS];

@@ -28,7 +28,9 @@ constexpr size_t SCRATCH_BYTES = OFF_SCAN + sizeof(unsigned int) * 4096;  // 1.6
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH_BYTES];
 
 // Device address of the scratch array for each device, looked up once per
-// device (with that device current) on its first call.
+// device (with that device current) on its first call and kept for the life
+// of the process (a cudaDeviceReset on that device invalidates it; the header
+// asks callers not to call again after one).
 std::mutex g_mu;
 void *g_addr[64] = {};
 

@@ -299,6 +299,7 @@ __device__ __forceinline__ CellFrame frame_of(const View &v, const DevState *ds,
 struct WarpCounters {
   unsigned long long pairs, cand, iters, noconv, overflow, timeout;
   unsigned long long gathers, list_overflows;  // density loop: particle gathers, full lists
+  unsigned long long evals;                    // density loop: list entries evaluated
 };
 
 // A work group: particles [a, b) in leaves [L0, L1) of one cell, and the

@@ -314,7 +314,10 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
         }
         // the list this pass built (or, in the first pass, the one kept from
         // an earlier iteration), in order
-        if (!done && (gath || first) && nl > 0) dens_list(s, lst, ls, nl, H2, Hinv);
+        if (!done && (gath || first) && nl > 0) {
+          dens_list(s, lst, ls, nl, H2, Hinv);
+          if (writer) wc.evals += (unsigned long long)nl;
+        }
         // a list that filled up: the next pass lists the records after it (for
         // several lanes per particle, every lane of the particle goes on)
         const unsigned ob = __ballot_sync(FULL, gath && acc > skipc + cap);
@@ -737,13 +740,14 @@ __device__ __forceinline__ int warp_group(const View &v, const DevState *ds, int
 __device__ __forceinline__ void flush_counters(DevState *ds, WarpCounters &wc, bool density) {
   // pairs and iterations are held by group leaders; sum over the warp
   unsigned long long p = wc.pairs, it = wc.iters, nc = wc.noconv, ov = wc.overflow;
-  unsigned long long lo = wc.list_overflows;
+  unsigned long long lo = wc.list_overflows, ev = wc.evals;
   for (int o = 16; o; o >>= 1) {
     p += __shfl_xor_sync(FULL, p, o);
     it += __shfl_xor_sync(FULL, it, o);
     nc += __shfl_xor_sync(FULL, nc, o);
     ov += __shfl_xor_sync(FULL, ov, o);
     lo += __shfl_xor_sync(FULL, lo, o);
+    ev += __shfl_xor_sync(FULL, ev, o);
   }
   // candidates, gathers and timeouts are warp-uniform (every lane counted the same)
   if (lane_id() == 0) {
@@ -753,6 +757,7 @@ __device__ __forceinline__ void flush_counters(DevState *ds, WarpCounters &wc, b
       if (it) atomicAdd(&ds->s_iters_density, it);
       if (wc.gathers) atomicAdd(&ds->s_gathers_density, wc.gathers);
       if (lo) atomicAdd(&ds->s_list_overflows, lo);
+      if (ev) atomicAdd(&ds->s_evals_density, ev);
       if (nc) record_error(ds, SPH_ERR_H_NOCONV, nc, false);
       if (ov) record_error(ds, SPH_ERR_CELL_OVERFLOW, ov, true);
     } else {

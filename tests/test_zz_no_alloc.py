@@ -52,7 +52,10 @@ def _build_cells_order(sim, ic, nc):
     return ctx.perm_tensor(n).cpu().numpy()
 
 
-def test_noalloc_order_matches_build_cells_twice(env):
+def test_noalloc_order_matches_build_cells_twice(env, orc):
+    """Two calls in a row (the shared array carries nothing over), each equal
+    bit for bit to the FP64 oracle's stable (cell, Morton) order and to the
+    order sph_build_cells produces."""
     torch, _lib, sim = env
     L = _lib.load()
     cases = [(sph_ics.clumpy_lattice(nside=24, n_clumps=3, per_clump=900, seed=41), 9),
@@ -61,8 +64,36 @@ def test_noalloc_order_matches_build_cells_twice(env):
         ic["pos"][::53, 2] -= 1.0        # outside the box: wrapped, as by the build
         rc, order = _noalloc_order(torch, L, ic["pos"], nc)
         assert rc == _lib.SPH_OK
-        ref = _build_cells_order(sim, ic, nc)
-        assert np.array_equal(order, ref)
+        assert np.array_equal(order, orc.cells(ic["pos"], 1.0, nc)["perm"])
+        assert np.array_equal(order, _build_cells_order(sim, ic, nc))
+
+
+def test_noalloc_at_its_size_limit(env, orc):
+    """Exactly 65,536 particles (the stated limit), with duplicates and ties."""
+    torch, _lib, sim = env
+    L = _lib.load()
+    rng = np.random.default_rng(7)
+    pos = rng.uniform(size=(65536, 3))
+    pos[1000:1100] = pos[0]              # coincident particles: order by index
+    rc, order = _noalloc_order(torch, L, pos, 31)
+    assert rc == _lib.SPH_OK
+    assert np.array_equal(order, orc.cells(pos, 1.0, 31)["perm"])
+
+
+def test_noalloc_non_finite_input_returns(env):
+    """A NaN position: the call (which does not check its input) returns
+    SPH_OK and the context stays usable; the order of such input is not
+    specified."""
+    torch, _lib, sim = env
+    L = _lib.load()
+    pos = np.random.default_rng(8).uniform(size=(1000, 3))
+    pos[17, 1] = np.nan
+    rc, _ = _noalloc_order(torch, L, pos, 5)
+    assert rc == _lib.SPH_OK
+    clean = np.nan_to_num(pos, nan=0.5)
+    rc, order = _noalloc_order(torch, L, clean, 5)
+    assert rc == _lib.SPH_OK
+    assert np.array_equal(np.sort(order), np.arange(1000))
 
 
 def test_noalloc_rejects_sizes_beyond_its_limit(env):
