@@ -18,10 +18,15 @@ scheme" and prints only Eq. 1 and Eq. 2):
   * grad-h factor f = [1 + h/(3 rho) d rho/dh]^-1 (Springel & Hernquist 2002);
   * entropy A = (gamma-1) u / rho^(gamma-1), P = A rho^gamma, c = sqrt(gamma P/rho);
   * Monaghan signal-velocity viscosity with beta = 3 (the form inside Eq. 1),
-    alpha = 0.8, no Balsara switch;
+    alpha = 0.8, no Balsara switch in the base scheme;
   * dt = C h / v_sig (Eq. 1); bin n = floor(log2(dt / dt_min)) (Eq. 2),
     increases synchronised to multiples of the new step; a particle is active
     when its step ends at the current integer time.
+Variants of the scheme (off by default; Gadget-2, the paper's reference code,
+uses all three): velocity divergence and curl from the density loop, the
+Gadget-2 prediction of inactive particles' density and smoothing length from
+their divergence, the Balsara switch on the viscosity, and the Saitoh & Makino
+(2009) limit of a time step to four times its neighbours' smallest one.
 """
 from __future__ import annotations
 
@@ -76,11 +81,18 @@ def lib():
                                       vp, vp, vp, vp, vp, vp]
             L.orc_force.restype = None
             L.orc_force.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
-                                    vp, vp, d, d, d, i32, vp, vp, vp, vp, vp, vp]
+                                    vp, vp, d, d, d, i32, vp, vp, vp, vp, vp, vp, vp, vp,
+                                    vp]
+            L.orc_gradient.restype = None
+            L.orc_gradient.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, d, i32,
+                                       vp, vp, vp, vp]
+            L.orc_balsara.restype = d
+            L.orc_balsara.argtypes = [d, d, d, d]
             L.orc_bin_of_dt.restype = i32
             L.orc_bin_of_dt.argtypes = [d, d, i32]
             L.orc_timestep_bins.restype = i64
-            L.orc_timestep_bins.argtypes = [i64, vp, vp, vp, d, d, i32, i64, vp, vp, vp, vp]
+            L.orc_timestep_bins.argtypes = [i64, vp, vp, vp, d, d, i32, i64, vp, vp, vp, vp,
+                                            vp]
             L.orc_cells.restype = None
             L.orc_cells.argtypes = [i64, vp, vp, vp, d, i32, vp, vp, vp]
             L.orc_num_threads.restype = i32
@@ -195,8 +207,11 @@ def eos(A, rho, gamma):
 # --------------------------------------------------------------------------
 
 def force(pos, vel, m, h, rho, f, P, c, active=None, box=1.0, alpha=0.8, gamma=5.0 / 3.0,
-          use_cells=True):
-    """Hydro accelerations for the active particles: dict(a[n,3], Adot, vsig, count)."""
+          use_cells=True, balsara=None, bins=None):
+    """Hydro accelerations for the active particles: dict(a[n,3], Adot, vsig,
+    count, bin_ngb_min).  balsara (optional): each particle's Balsara factor,
+    the viscosity of a pair scaled by their mean; bins (optional): time bins,
+    whose smallest over each particle's neighbours is returned."""
     x, y, z = (_f64(pos[:, k]) for k in range(3))
     vx, vy, vz = (_f64(vel[:, k]) for k in range(3))
     n = x.shape[0]
@@ -204,10 +219,48 @@ def force(pos, vel, m, h, rho, f, P, c, active=None, box=1.0, alpha=0.8, gamma=5
     act = _mask(active, n)
     ax, ay, az, Adot, vsig = (np.zeros(n) for _ in range(5))
     cnt = np.zeros(n, dtype=np.int64)
+    bal = None if balsara is None else _f64(balsara)
+    b8 = None if bins is None else np.ascontiguousarray(bins, dtype=np.int8)
+    bmin = np.zeros(n, dtype=np.int8)
     lib().orc_force(n, _ptr(x), _ptr(y), _ptr(z), _ptr(vx), _ptr(vy), _ptr(vz),
                     *[_ptr(a) for a in arrs], _ptr(act), box, alpha, gamma, int(use_cells),
-                    _ptr(ax), _ptr(ay), _ptr(az), _ptr(Adot), _ptr(vsig), _ptr(cnt))
-    return dict(a=np.stack([ax, ay, az], axis=1), Adot=Adot, vsig=vsig, count=cnt)
+                    _ptr(bal) if bal is not None else None,
+                    _ptr(b8) if b8 is not None else None,
+                    _ptr(ax), _ptr(ay), _ptr(az), _ptr(Adot), _ptr(vsig), _ptr(cnt),
+                    _ptr(bmin))
+    return dict(a=np.stack([ax, ay, az], axis=1), Adot=Adot, vsig=vsig, count=cnt,
+                bin_ngb_min=bmin if b8 is not None else None)
+
+
+def gradient(pos, vel, m, h, rho, active=None, box=1.0, use_cells=True):
+    """Velocity divergence and curl at each active particle's h:
+    dict(div[n], curl[n, 3])."""
+    x, y, z = (_f64(pos[:, k]) for k in range(3))
+    vx, vy, vz = (_f64(vel[:, k]) for k in range(3))
+    n = x.shape[0]
+    m, h, rho = _f64(m), _f64(h), _f64(rho)
+    act = _mask(active, n)
+    dv, cx, cy, cz = (np.zeros(n) for _ in range(4))
+    lib().orc_gradient(n, _ptr(x), _ptr(y), _ptr(z), _ptr(vx), _ptr(vy), _ptr(vz), _ptr(m),
+                       _ptr(h), _ptr(rho), _ptr(act), box, int(use_cells), _ptr(dv),
+                       _ptr(cx), _ptr(cy), _ptr(cz))
+    return dict(div=dv, curl=np.stack([cx, cy, cz], axis=1))
+
+
+def balsara(divv, curl, c, h):
+    """Balsara factor |div v| / (|div v| + |curl v| + 1e-4 c / h) (per particle)."""
+    f = lib().orc_balsara
+    return np.array([f(float(a), float(b), float(cc), float(hh))
+                     for a, b, cc, hh in zip(np.ravel(divv), np.ravel(curl), np.ravel(c),
+                                             np.ravel(h))])
+
+
+def predict_inactive(rho, h, divv, dt):
+    """Gadget-2 prediction of an inactive particle's density and smoothing
+    length over the time dt since its last density evaluation:
+    rho exp(-div v dt), h exp(div v dt / 3)."""
+    rho, h, divv, dt = (np.asarray(a, dtype=np.float64) for a in (rho, h, divv, dt))
+    return rho * np.exp(-divv * dt), h * np.exp(divv * dt / 3.0)
 
 
 # --------------------------------------------------------------------------
@@ -219,11 +272,14 @@ def bin_of_dt(dt, dt_min, bin_cap):
     return int(lib().orc_bin_of_dt(float(dt), float(dt_min), int(bin_cap)))
 
 
-def timestep_bins(h, vsig, active, cfl, dt_min, bin_cap, ti_current, bin_old):
+def timestep_bins(h, vsig, active, cfl, dt_min, bin_cap, ti_current, bin_old,
+                  bin_ngb_min=None):
     """New bins for active particles: dict(bin, ti_begin, ti_end, dt, n_too_small).
 
     bin_old, and ti_begin / ti_end of the inactive particles, are left as given
-    (the returned ti arrays are zero for inactive particles)."""
+    (the returned ti arrays are zero for inactive particles).  bin_ngb_min
+    (optional): each particle's smallest neighbour bin; a new bin is then at
+    most 2 above it (the Saitoh & Makino limiter)."""
     h, vsig = _f64(h), _f64(vsig)
     n = h.shape[0]
     act = _mask(active, n)
@@ -231,8 +287,10 @@ def timestep_bins(h, vsig, active, cfl, dt_min, bin_cap, ti_current, bin_old):
     tb = np.zeros(n, dtype=np.int64)
     te = np.zeros(n, dtype=np.int64)
     dt = np.zeros(n)
+    lim = None if bin_ngb_min is None else np.ascontiguousarray(bin_ngb_min, dtype=np.int8)
     bad = lib().orc_timestep_bins(n, _ptr(h), _ptr(vsig), _ptr(act), cfl, dt_min, bin_cap,
-                                  int(ti_current), _ptr(b), _ptr(tb), _ptr(te), _ptr(dt))
+                                  int(ti_current), _ptr(lim) if lim is not None else None,
+                                  _ptr(b), _ptr(tb), _ptr(te), _ptr(dt))
     return dict(bin=b, ti_begin=tb, ti_end=te, dt=dt, n_too_small=int(bad))
 
 

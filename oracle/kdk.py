@@ -21,6 +21,20 @@ time ``ti`` to the next time at which some particle's step ends (Sec. II-A):
 The first step (ti = 0, every particle active with a zero-length old step)
 sets the entropy from the initial internal energy after its density pass.
 The integer timeline has ticks of dt_min; the time of tick ti is t_begin + ti dt_min.
+
+Variants (Gadget-2's; off by default):
+  predict   inactive particles' density and smoothing length are predicted
+            from their last density with their velocity divergence over the
+            time since then, rho exp(-div v dt), h exp(div v dt / 3) (an active
+            particle starts its h iteration from its predicted h);
+  balsara   the viscosity of a pair is scaled by the mean of the two
+            particles' Balsara factors;
+  limiter   a new bin is at most 2 above the smallest bin among the
+            particle's force neighbours (Saitoh & Makino 2009; the waking of
+            inactive neighbours is not part of it).
+The divergence and curl (needed by predict and balsara) are taken after the
+density loop at each active particle's new h, with the step's predicted
+velocities.
 """
 from __future__ import annotations
 
@@ -30,13 +44,17 @@ import numpy as np
 class OracleSim:
     def __init__(self, pos, vel, m, u, h0, *, box=1.0, eta=1.2348, gamma=5.0 / 3.0,
                  alpha=0.8, cfl=0.1, dt_min=1e-6, bin_cap=10, h_tol=1e-12, max_iter=100,
-                 use_cells=True, global_step=False):
+                 use_cells=True, global_step=False, predict=False, balsara=False,
+                 limiter=False):
         n = pos.shape[0]
         self.n = n
         self.box, self.eta, self.gamma, self.alpha = box, eta, gamma, alpha
         self.cfl, self.dt_min, self.bin_cap = cfl, dt_min, bin_cap
         self.h_tol, self.max_iter, self.use_cells = h_tol, max_iter, use_cells
         self.global_step = global_step
+        self.predict, self.balsara, self.limiter = predict, balsara, limiter
+        self.divv = np.zeros(n)   # velocity divergence at the last density
+        self.curl = np.zeros(n)   # |curl v| at the last density
         self.pos = np.array(pos, dtype=np.float64) % box
         self.vel = np.array(vel, dtype=np.float64)
         self.m = np.array(m, dtype=np.float64) * np.ones(n)
@@ -77,6 +95,15 @@ class OracleSim:
         dtp = ((ti - self.ti_begin) - 0.5 * step) * self.dt_min
         return self.vel + self.acc * dtp[:, None], self.A + self.Adot * dtp
 
+    def _predict_rho_h(self, ti):
+        """rho and h at ti: the last values, or (predict) those advanced with
+        the velocity divergence over the time since the last density."""
+        if not self.predict:
+            return self.rho.copy(), self.h.copy()
+        import oracle as orc
+        dt = (ti - self.ti_begin) * self.dt_min
+        return orc.predict_inactive(self.rho, self.h, self.divv, dt)
+
     def step(self):
         import oracle as orc
         ti = self.ti
@@ -85,7 +112,8 @@ class OracleSim:
         vpred, Apred = self._predict(ti)
         active = self.ti_end == ti
         self.last_active = active.copy()
-        d = orc.density(self.pos, self.m, self.h, active, self.box, self.eta, self.h_tol,
+        rho_p, h_p = self._predict_rho_h(ti)
+        d = orc.density(self.pos, self.m, h_p, active, self.box, self.eta, self.h_tol,
                         self.max_iter, self.use_cells)
         self.h[active] = d["h"][active]
         self.rho[active] = d["rho"][active]
@@ -95,9 +123,19 @@ class OracleSim:
         if self.first:
             self.A = orc.entropy_from_u(self.u0, self.rho, g)
             Apred = self.A.copy()
-        self.P, self.c = orc.eos(Apred, self.rho, g)
-        fr = orc.force(self.pos, vpred, self.m, self.h, self.rho, self.f, self.P, self.c,
-                       active, self.box, self.alpha, g, self.use_cells)
+        if self.predict or self.balsara:
+            gr = orc.gradient(self.pos, vpred, self.m, self.h, self.rho, active, self.box,
+                              self.use_cells)
+            self.divv[active] = gr["div"][active]
+            self.curl[active] = np.sqrt((gr["curl"] ** 2).sum(1))[active]
+        # inactive neighbours: their last (or predicted) rho and h
+        h_now = np.where(active, self.h, h_p)
+        rho_now = np.where(active, self.rho, rho_p)
+        self.P, self.c = orc.eos(Apred, rho_now, g)
+        bal = orc.balsara(self.divv, self.curl, self.c, h_now) if self.balsara else None
+        fr = orc.force(self.pos, vpred, self.m, h_now, rho_now, self.f, self.P, self.c,
+                       active, self.box, self.alpha, g, self.use_cells, balsara=bal,
+                       bins=self.bin if self.limiter else None)
         self.acc[active] = fr["a"][active]
         self.Adot[active] = fr["Adot"][active]
         self.vsig[active] = fr["vsig"][active]
@@ -113,7 +151,7 @@ class OracleSim:
         # (vi) new time-step and bin
         cap = 0 if self.global_step else self.bin_cap
         tb = orc.timestep_bins(self.h, self.vsig, active, self.cfl, self.dt_min, cap, ti,
-                               self.bin)
+                               self.bin, fr["bin_ngb_min"] if self.limiter else None)
         self.n_dt_too_small = tb["n_too_small"]
         self.bin[active] = tb["bin"][active]
         self.ti_begin[active] = tb["ti_begin"][active]
@@ -147,6 +185,10 @@ class OracleSim:
         s.ti_begin = st["ti_begin"].astype(np.int64).copy()
         s.ti_end = st["ti_end"].astype(np.int64).copy()
         s.ti_drift = st["ti_drift"].astype(np.int64).copy()
+        if "div_v" in st:
+            s.divv = st["div_v"].astype(np.float64).copy()
+        if "curl_v" in st:
+            s.curl = st["curl_v"].astype(np.float64).copy()
         s.ti = int(ti)
         s.first = bool(first)
         return s

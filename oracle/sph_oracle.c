@@ -320,6 +320,68 @@ int64_t orc_density(int64_t n, const double *x, const double *y, const double *z
 }
 
 /* ------------------------------------------------------------------------- */
+/* Velocity divergence and curl at the particle's own h (the standard SPH     */
+/* estimates used by Gadget-2; the paper names Gadget-2 as its reference      */
+/* scheme, Sec. II): with v_ij = v_i - v_j and grad_i W = (r_ij / r) dW/dr,    */
+/*   div v_i  = -(1 / rho_i) sum_j m_j v_ij . grad_i W(r_ij, h_i)              */
+/*   curl v_i =  (1 / rho_i) sum_j m_j v_ij x grad_i W(r_ij, h_i)              */
+/* over j with r_ij < H_i.                                                    */
+/* ------------------------------------------------------------------------- */
+
+void orc_gradient(int64_t n, const double *x, const double *y, const double *z,
+                  const double *vx, const double *vy, const double *vz, const double *m,
+                  const double *h, const double *rho, const uint8_t *active, double box,
+                  int use_cells, double *divv, double *curlx, double *curly, double *curlz) {
+  double hmax = 0.0;
+  for (int64_t i = 0; i < n; i++)
+    if (h[i] > hmax) hmax = h[i];
+  orc_grid g;
+  grid_build(&g, n, x, y, z, box, ORC_GAMMA_K * hmax, use_cells);
+#pragma omp parallel
+  {
+    int64_t *cand = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; i++) {
+      if (active && !active[i]) continue;
+      double Hi = ORC_GAMMA_K * h[i];
+      double sd = 0.0, cx = 0.0, cy = 0.0, cz = 0.0;
+      int64_t nc = grid_candidates(&g, i, Hi, cand);
+      for (int64_t k = 0; k < nc; k++) {
+        int64_t j = cand[k];
+        if (j == i) continue;
+        double dx = min_image(x[i] - x[j], box);
+        double dy = min_image(y[i] - y[j], box);
+        double dz = min_image(z[i] - z[j], box);
+        double r2 = dx * dx + dy * dy + dz * dz;
+        if (!(r2 < Hi * Hi) || r2 == 0.0) continue;
+        double r = sqrt(r2);
+        /* grad_i W = (r_ij / r) dW/dr, dW/dr = H^-4 w'(r / H) */
+        double g1 = m[j] * orc_kernel_dw(r / Hi) / (Hi * Hi * Hi * Hi) / r;
+        double gx = g1 * dx, gy = g1 * dy, gz = g1 * dz;
+        double wx = vx[i] - vx[j], wy = vy[i] - vy[j], wz = vz[i] - vz[j];
+        sd += wx * gx + wy * gy + wz * gz;
+        cx += wy * gz - wz * gy;
+        cy += wz * gx - wx * gz;
+        cz += wx * gy - wy * gx;
+      }
+      divv[i] = -sd / rho[i];
+      curlx[i] = cx / rho[i];
+      curly[i] = cy / rho[i];
+      curlz[i] = cz / rho[i];
+    }
+    free(cand);
+  }
+  grid_free(&g);
+}
+
+/* Balsara (1995) switch in the form Gadget-2 uses:
+ * B = |div v| / (|div v| + |curl v| + 1e-4 c / h). */
+double orc_balsara(double divv, double curl, double c, double h) {
+  double a = fabs(divv);
+  return a / (a + fabs(curl) + 1e-4 * c / h);
+}
+
+/* ------------------------------------------------------------------------- */
 /* Hydro force loop (pressure with grad-h terms plus artificial viscosity)    */
 /* for the active particles; j runs over r_ij < max(H_i, H_j), j != i.        */
 /* ------------------------------------------------------------------------- */
@@ -328,8 +390,9 @@ void orc_force(int64_t n, const double *x, const double *y, const double *z,
                const double *vx, const double *vy, const double *vz, const double *m,
                const double *h, const double *rho, const double *f, const double *P,
                const double *c, const uint8_t *active, double box, double alpha,
-               double gamma, int use_cells, double *ax, double *ay, double *az,
-               double *Adot, double *vsig, int64_t *count) {
+               double gamma, int use_cells, const double *balsara, const int8_t *bin,
+               double *ax, double *ay, double *az, double *Adot, double *vsig,
+               int64_t *count, int8_t *bin_ngb_min) {
   double hmax = 0.0;
   for (int64_t i = 0; i < n; i++)
     if (h[i] > hmax) hmax = h[i];
@@ -347,6 +410,7 @@ void orc_force(int64_t n, const double *x, const double *y, const double *z,
       double sax = 0.0, say = 0.0, saz = 0.0, sA = 0.0;
       double vs = 2.0 * c[i];
       int64_t cnt = 0;
+      int bmin = 127; /* smallest time bin among the neighbours */
       int64_t nc = grid_candidates(&g, i, Hmax, cand);
       for (int64_t k = 0; k < nc; k++) {
         int64_t j = cand[k];
@@ -358,6 +422,7 @@ void orc_force(int64_t n, const double *x, const double *y, const double *z,
         double r2 = dx * dx + dy * dy + dz * dz;
         if (!(r2 < Hi * Hi || r2 < Hj * Hj)) continue;
         cnt++;
+        if (bin && bin[j] < bmin) bmin = bin[j];
         double r = sqrt(r2);
         double dvx = vx[i] - vx[j], dvy = vy[i] - vy[j], dvz = vz[i] - vz[j];
         double dvdr = dvx * dx + dvy * dy + dvz * dz;
@@ -377,6 +442,8 @@ void orc_force(int64_t n, const double *x, const double *y, const double *z,
         if (wij > 0.0) wij = 0.0;
         double vsig_ij = c[i] + c[j] - 3.0 * wij;
         double Pi = -0.5 * alpha * vsig_ij * wij / (0.5 * (rho[i] + rho[j]));
+        /* Balsara switch: the mean of the two particles' factors */
+        if (balsara) Pi *= 0.5 * (balsara[i] + balsara[j]);
         double dWbar = 0.5 * (dWi + dWj);
         /* grad_i W = (r_ij / r) dW/dr */
         double s = m[j] * (PoRho2i * dWi + PoRho2j * dWj + Pi * dWbar) / r;
@@ -392,6 +459,7 @@ void orc_force(int64_t n, const double *x, const double *y, const double *z,
       Adot[i] = 0.5 * (gamma - 1.0) * pow(rho[i], 1.0 - gamma) * sA;
       vsig[i] = vs;
       if (count) count[i] = cnt;
+      if (bin_ngb_min) bin_ngb_min[i] = (int8_t)bmin;
     }
     free(cand);
   }
@@ -418,10 +486,14 @@ int orc_bin_of_dt(double dt, double dt_min, int bin_cap) {
  * accepted only while ti_current is a multiple of the new step (Gadget-2
  * synchronisation); decreases are always accepted.  Returns the number of
  * particles whose dt fell below dt_min (they are put on bin 0). */
+/* With bin_ngb_min (may be NULL): the Saitoh & Makino (2009) time-step
+ * limiter on the neighbours, dt_i <= 4 min_j dt_j, i.e. a new bin at most
+ * 2 above the smallest bin among the particle's force neighbours; applied
+ * before the synchronisation rule. */
 int64_t orc_timestep_bins(int64_t n, const double *h, const double *vsig,
                           const uint8_t *active, double cfl, double dt_min, int bin_cap,
-                          int64_t ti_current, int8_t *bin, int64_t *ti_begin,
-                          int64_t *ti_end, double *dt_out) {
+                          int64_t ti_current, const int8_t *bin_ngb_min, int8_t *bin,
+                          int64_t *ti_begin, int64_t *ti_end, double *dt_out) {
   int64_t bad = 0;
   for (int64_t i = 0; i < n; i++) {
     if (active && !active[i]) continue;
@@ -432,6 +504,7 @@ int64_t orc_timestep_bins(int64_t n, const double *h, const double *vsig,
       bad++;
       b = 0;
     }
+    if (bin_ngb_min && b > bin_ngb_min[i] + 2) b = bin_ngb_min[i] + 2;
     int old = bin[i];
     while (b > old && (ti_current % ((int64_t)1 << b)) != 0) b--;
     bin[i] = (int8_t)b;
