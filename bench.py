@@ -227,7 +227,7 @@ def run_ours(args, rank, world):
                      "trials": [dict(r["cand"], pairs_per_s=r["rate"]) for r in t.get("trials", [])]}
     params = sim.Params(**base, **tuned)
     ctx = sim.Context(params, n)
-    p = sim.Particles.from_ics(ic, with_counts=False)
+    p = sim.Particles.from_ics(ic, with_counts=False, with_gradients=False)
     ctx.build_cells(p)
     snapshot = {k: t.clone() for k, t in p.arrays().items()}
     stream = torch.cuda.Stream()

@@ -52,7 +52,7 @@ enum sph_status_code {
  * dt_min 1e-6, t_begin 0, box 1, cell_margin 2.0, leaf_max 8,
  * threads_per_particle 1, drift_all 0, n_cells_override 0, heavy_factor 0,
  * coop_max_groups -1, list_cap 256, search_margin 1.02, staging_depth 1,
- * wait_limit 0, test_stall 0.
+ * wait_limit 0, test_stall 0, balsara 0, predict_inactive 0, limiter 0.
  * With threads_per_particle = 1 every sum of a particle is taken in an order
  * that depends on the particle alone, so SPH_FORM_PLAIN and SPH_FORM_BATCHED
  * give bit-identical results; with more lanes per particle they agree to
@@ -100,6 +100,19 @@ typedef struct {
                            launches make one warp wait on a staging barrier that no copy
                            completes, so that the wait gives up after wait_limit polls and
                            the step stops with SPH_ERR_TIMEOUT */
+  /* Variants of the scheme, as Gadget-2 (the paper's reference code) has them;
+   * 0 = off (the base scheme), 1 = on.  They need threads_per_particle 1 and,
+   * when balsara or predict_inactive is on, the div_v and curl_v arrays of
+   * sph_particles; sph_step_bwd supports none of them (SPH_ERR_ARG). */
+  int balsara;          /* viscosity of a pair scaled by the mean of the particles'
+                           Balsara factors |div v| / (|div v| + |curl v| + 1e-4 c / h) */
+  int predict_inactive; /* an inactive particle's density and smoothing length are
+                           predicted from its last density with its velocity divergence:
+                           rho exp(-div v dt), h exp(div v dt / 3), dt the time since its
+                           last density; an active one starts its h iteration there */
+  int limiter;          /* Saitoh & Makino (2009): a new time bin is at most 2 above the
+                           smallest bin among the particle's force neighbours (dt <= 4
+                           min_j dt_j); inactive neighbours are not woken */
 } sph_params;
 
 /* Particle state, structure of arrays, all device pointers of length n.
@@ -122,6 +135,10 @@ typedef struct {
   uint8_t *active;      /* out: 1 for the particles active at the current tick */
   int32_t *ngb_density; /* optional (may be NULL): neighbours j != i with r < H_i */
   int32_t *ngb_force;   /* optional (may be NULL): neighbours j != i with r < max(H_i, H_j) */
+  float *div_v, *curl_v;/* velocity divergence and |curl| at each particle's last density
+                           (div v = -(1/rho) sum_j m_j v_ij . grad W(h_i), curl v =
+                           (1/rho) sum_j m_j v_ij x grad W(h_i)); needed (else may be
+                           NULL) with the balsara or predict_inactive variant */
 } sph_particles;
 
 typedef struct sph_ctx sph_ctx;

@@ -38,7 +38,7 @@ class sph_params(ctypes.Structure):
                 ("threads_per_particle", _i), ("drift_all", _i), ("n_cells_override", _i),
                 ("heavy_factor", _d), ("coop_max_groups", _i), ("list_cap", _i),
                 ("search_margin", _d), ("staging_depth", _i), ("wait_limit", _i),
-                ("test_stall", _i)]
+                ("test_stall", _i), ("balsara", _i), ("predict_inactive", _i), ("limiter", _i)]
 
 
 PARTICLE_FIELDS = [("x", "f8"), ("y", "f8"), ("z", "f8"), ("vx", "f4"), ("vy", "f4"),
@@ -46,7 +46,8 @@ PARTICLE_FIELDS = [("x", "f8"), ("y", "f8"), ("z", "f8"), ("vx", "f4"), ("vy", "
                    ("Adot", "f4"), ("h", "f4"), ("rho", "f4"), ("f", "f4"), ("P", "f4"),
                    ("c", "f4"), ("vsig", "f4"), ("m", "f4"), ("bin", "i1"), ("ti_begin", "i8"),
                    ("ti_end", "i8"), ("ti_drift", "i8"), ("active", "u1"),
-                   ("ngb_density", "i4"), ("ngb_force", "i4")]
+                   ("ngb_density", "i4"), ("ngb_force", "i4"), ("div_v", "f4"),
+                   ("curl_v", "f4")]
 
 
 class sph_particles(ctypes.Structure):

@@ -60,7 +60,7 @@ def trial(ic: dict, base: dict, cand: dict, steps: int, flush=None) -> dict:
     import torch
     n = ic["pos"].shape[0]
     ctx = Context(Params(**base, **cand), n)
-    p = Particles.from_ics(ic, with_counts=False)
+    p = Particles.from_ics(ic, with_counts=False, with_gradients=False)
     snap = {k: t.clone() for k, t in p.arrays().items()}
     stream = torch.cuda.Stream()
     ctx.build_cells(p, stream)

@@ -838,6 +838,7 @@ __global__ void k_state_copy(sph_particles src, sph_particles dst, const int32_t
     cp(dst.ti_end, src.ti_end, d, k); cp(dst.ti_drift, src.ti_drift, d, k);
     cp(dst.active, src.active, d, k);
     cp(dst.ngb_density, src.ngb_density, d, k); cp(dst.ngb_force, src.ngb_force, d, k);
+    cp(dst.div_v, src.div_v, d, k); cp(dst.curl_v, src.curl_v, d, k);
   }
 }
 

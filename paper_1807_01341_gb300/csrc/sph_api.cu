@@ -65,6 +65,7 @@ struct Buffers {
   // neighbour lists of the density loop (list_cap entries per particle, and
   // per warp of the first coop_slots blocks)
   float2 *nbr = nullptr, *nbr_coop = nullptr;
+  int8_t *ngb_bin = nullptr;  // limiter: smallest neighbour bin of each active particle
   // state
   DevState *ds = nullptr;
   float *d_hmax = nullptr;
@@ -174,6 +175,10 @@ bool valid_params(const sph_params *p) {
   if (!(p->search_margin >= 1.0 && p->search_margin <= 2.0)) return false;
   if (p->staging_depth < 1 || p->staging_depth > 3) return false;
   if (p->wait_limit < 0 || p->test_stall < 0) return false;
+  const int vars[3] = {p->balsara, p->predict_inactive, p->limiter};
+  for (int f : vars)
+    if (f != 0 && f != 1) return false;
+  if ((p->balsara || p->predict_inactive || p->limiter) && G != 1) return false;
   return true;
 }
 
@@ -185,6 +190,8 @@ bool valid_particles(const sph_ctx *ctx, const sph_particles *p) {
                        p->vsig, p->m, p->bin, p->ti_begin, p->ti_end, p->ti_drift, p->active};
   for (const void *q : req)
     if (!q) return false;
+  // the variants that use the velocity divergence keep it per particle
+  if ((ctx->prm.balsara || ctx->prm.predict_inactive) && (!p->div_v || !p->curl_v)) return false;
   return true;
 }
 
@@ -204,6 +211,8 @@ View make_view(const sph_ctx *ctx, const sph_particles *p) {
     v.active = p->active;
     v.ngb_density = p->ngb_density;
     v.ngb_force = p->ngb_force;
+    v.div_v = p->div_v;
+    v.curl_v = p->curl_v;
   }
   const Buffers &b = ctx->b;
   v.cell_start = b.cell_start;
@@ -261,6 +270,10 @@ View make_view(const sph_ctx *ctx, const sph_particles *p) {
   v.search_margin = (float)q.search_margin;
   v.stage_depth = q.staging_depth;
   v.wait_limit = q.wait_limit;
+  v.balsara = q.balsara;
+  v.predict = q.predict_inactive;
+  v.limiter = q.limiter;
+  v.ngb_bin = b.ngb_bin;
   return v;
 }
 
@@ -403,6 +416,8 @@ int build_cells(sph_ctx *ctx, sph_particles *p, cudaStream_t st) {
   SPH_TRY(permute_array(ctx, p->ti_drift, 8, n, perm, st));
   SPH_TRY(permute_array(ctx, p->ngb_density, 4, n, perm, st));
   SPH_TRY(permute_array(ctx, p->ngb_force, 4, n, perm, st));
+  SPH_TRY(permute_array(ctx, p->div_v, 4, n, perm, st));
+  SPH_TRY(permute_array(ctx, p->curl_v, 4, n, perm, st));
   if (n > 0) {
     SPH_CUDA(launch_gather(b.perm_tmp, b.perm, perm, n, 4, st));
     SPH_CUDA(cudaMemcpyAsync(b.perm, b.perm_tmp, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st));
@@ -467,6 +482,7 @@ int batched_body(sph_ctx *ctx, const View &v, int flags, cudaStream_t st) {
   SPH_CUDA(launch_density(v, flags, -1, true, ctx->grid_dens, st));
   prof_end(ctx, 0, st);
   if (flags & SPH_DENSITY_INIT_ENTROPY) SPH_CUDA(launch_entropy_from_u(v, st));
+  if (v.balsara || v.predict) SPH_CUDA(launch_gradient(v, ctx->grid_force, st));
   prof_begin(ctx, 1, st);
   SPH_CUDA(launch_force(v, -1, true, ctx->grid_force, st));
   prof_end(ctx, 1, st);
@@ -498,6 +514,7 @@ int plain_body(sph_ctx *ctx, const View &v, int flags, cudaStream_t st) {
     prof_end(ctx, 0, st);
   }
   if (flags & SPH_DENSITY_INIT_ENTROPY) SPH_CUDA(launch_entropy_from_u(v, st));
+  if (v.balsara || v.predict) SPH_CUDA(launch_gradient(v, ctx->grid_force, st));
   for (int k = 0; k < nb; k++) {
     SPH_CUDA(launch_mark_bin(v, bins[k], st));
     int nq[2] = {0, 0};
@@ -687,6 +704,9 @@ void sph_default_params(sph_params *p) {
   p->staging_depth = 1;
   p->wait_limit = 0;
   p->test_stall = 0;
+  p->balsara = 0;
+  p->predict_inactive = 0;
+  p->limiter = 0;
 }
 
 const char *sph_strerror(int code) {
@@ -761,11 +781,16 @@ int sph_create(const sph_params *params, int64_t n_max, sph_ctx **out) {
     // that share a work group (those of a persistent launch; a per-bin launch
     // uses at most as many)
     ctx->coop_slots = ctx->grid_dens;
-    if ((r = dalloc(&b.nbr, n * (long long)params->list_cap)) ||
+    if ((r = dalloc(&b.ngb_bin, n)) || (r = dalloc(&b.nbr, n * (long long)params->list_cap)) ||
         (r = dalloc(&b.nbr_coop, G == 1 ? (long long)ctx->coop_slots * WARPS_PER_BLOCK * 32 *
                                               params->list_cap
                                         : 1LL)))
       break;
+    // no neighbour bin known yet: no limit (a bins call without a force pass)
+    if (cudaMemset(b.ngb_bin, 127, (size_t)n) != cudaSuccess) {
+      r = SPH_ERR_CUDA;
+      break;
+    }
     if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
       r = SPH_ERR_CUDA;
       break;
@@ -806,7 +831,7 @@ int sph_destroy(sph_ctx *ctx) {
   dfree(b.cell_start); dfree(b.cell_leaf_start); dfree(b.cell_stamp); dfree(b.cell_rel_stamp);
   dfree(b.q_act_cells); dfree(b.leaf_counts); dfree(b.leaf_offsets);
   dfree(b.ds); dfree(b.d_hmax); dfree(b.diag); dfree(b.d_bad);
-  dfree(b.nbr); dfree(b.nbr_coop);
+  dfree(b.nbr); dfree(b.nbr_coop); dfree(b.ngb_bin);
   if (b.h_ds) cudaFreeHost(b.h_ds);
   delete ctx;
   return SPH_OK;
@@ -853,6 +878,7 @@ int sph_density_active(sph_ctx *ctx, sph_particles *p, int flags, void *stream) 
   View v = make_view(ctx, p);
   SPH_CUDA(launch_density(v, flags, -1, true, ctx->grid_dens, S(stream)));
   if (flags & SPH_DENSITY_INIT_ENTROPY) SPH_CUDA(launch_entropy_from_u(v, S(stream)));
+  if (v.balsara || v.predict) SPH_CUDA(launch_gradient(v, ctx->grid_force, S(stream)));
   return SPH_OK;
 }
 
@@ -1128,6 +1154,8 @@ int sph_step_bwd(sph_ctx *ctx, const sph_particles *pre, const sph_particles *po
   if (!ctx || !valid_particles(ctx, pre) || !valid_particles(ctx, post) || post->n != pre->n ||
       !valid_adjoint(adj, pre->n) || ti < 0)
     return SPH_ERR_ARG;
+  // the reverse pass covers the base scheme only
+  if (ctx->prm.balsara || ctx->prm.predict_inactive || ctx->prm.limiter) return SPH_ERR_ARG;
   const long long n = pre->n;
   if (n == 0) return SPH_OK;
   SPH_TRY(ensure_adj(ctx));

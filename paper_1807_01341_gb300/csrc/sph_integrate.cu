@@ -57,7 +57,7 @@ __global__ void k_begin_step(View v, long long ti_arg) {
   ds->n_heavy_groups = 0;
   ds->head_density = ds->head_force = ds->head_drift = ds->head_kick = 0;
   ds->head_open = ds->head_bins = ds->head_misc = 0;
-  ds->head_coop_density = ds->head_coop_force = 0;
+  ds->head_coop_density = ds->head_coop_force = ds->head_grad = 0;
   ds->s_pairs_density = ds->s_pairs_force = 0ull;
   ds->s_cand_density = ds->s_cand_force = 0ull;
   ds->s_iters_density = ds->s_active_particles = 0ull;
@@ -241,13 +241,20 @@ __device__ void chunk_update(const View &v, int g, bool do_drift, bool do_bins) 
     const float vpy = v.vy[i] + v.ay[i] * fdtp;
     const float vpz = v.vz[i] + v.az[i] * fdtp;
     const float Ap = (float)((double)v.A[i] + (double)v.Adot[i] * dtp);
-    const float H = GAMMA_K * v.h[i], m = v.m[i];
+    float hh = v.h[i], rho = v.rho[i];
+    if (v.predict) {
+      // Gadget-2 prediction from the last density (at the start of the step):
+      // rho exp(-div v dt), h exp(div v dt / 3)
+      const float x = v.div_v[i] * (float)((double)(ti - v.ti_begin[i]) * v.dt_min);
+      rho *= expf(-x);
+      hh *= expf(x * (1.0f / 3.0f));
+    }
+    const float H = GAMMA_K * hh, m = v.m[i];
     v.rec_xm[i] = make_float4(fx, fy, fz, m);
     v.rec_xH[i] = make_float4(fx, fy, fz, H);
     v.rec_v[i] = make_float4(vpx, vpy, vpz, m);
     s_rec[i - pa] = make_float4(fx, fy, fz, H);
     s_bin[i - pa] = (uint8_t)bi;
-    const float rho = v.rho[i];
     float fP = 0.0f, c = 0.0f;
     if (rho > 0.0f) {
       const float P = Ap * powf(rho, g_);
@@ -445,6 +452,8 @@ __global__ void k_bins(View v) {
         bool small;
         nb = bin_of(v, v.h[i], v.vsig[i], small);
         if (small) atomicAdd(&too_small, 1u);
+        // limiter: at most 2 bins above the smallest neighbour's
+        if (v.limiter) nb = min(nb, (int)v.ngb_bin[i] + 2);
         // a longer step only when the current tick is a multiple of it
         while (nb > old && (ti & ((1ll << nb) - 1)) != 0) nb--;
         v.bin[i] = (int8_t)nb;
@@ -548,6 +557,8 @@ __global__ void __launch_bounds__(UT) k_close_step(View v) {
         bool small;
         nb = bin_of(v, v.h[i], v.vsig[i], small);
         if (small) atomicAdd(&too_small, 1u);
+        // limiter: at most 2 bins above the smallest neighbour's
+        if (v.limiter) nb = min(nb, (int)v.ngb_bin[i] + 2);
         while (nb > old && (ti & ((1ll << nb) - 1)) != 0) nb--;
         v.bin[i] = (int8_t)nb;
         v.ti_begin[i] = ti;

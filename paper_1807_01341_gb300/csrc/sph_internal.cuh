@@ -53,6 +53,7 @@ struct DevState {
   int head_density, head_force, head_drift, head_kick;
   int head_open, head_bins, head_misc, head_coop_density;
   int head_coop_force;
+  int head_grad;              // gradient loop (velocity divergence and curl)
   unsigned int blocks_done;   // blocks of the closing kernel of a step that have finished
   // errors
   unsigned int halt;      // a step-invalidating error happened: kernels return
@@ -87,6 +88,8 @@ struct View {
   long long *ti_begin, *ti_end, *ti_drift;
   uint8_t *active;
   int32_t *ngb_density, *ngb_force;
+  float *div_v, *curl_v;     // velocity divergence and |curl| (variants; may be null)
+  int8_t *ngb_bin;           // limiter: smallest bin among the force neighbours (step scratch)
   // cell structure
   int32_t *cell_start;       // [n_cells + 1] first particle of each cell
   int32_t *cell_leaf_start;  // [n_cells + 1] first leaf of each cell
@@ -139,6 +142,7 @@ struct View {
   float search_margin;       // a density search reaches search_margin x the support
   int list_cap, coop_slots;  // neighbour-list entries per particle; blocks with coop lists
   int stage_depth;           // staging buffers per warp (1..3)
+  int balsara, predict, limiter;  // variants of the scheme (0/1)
   double heavy_factor;       // heavy work group: estimated cost > heavy_factor x mean
   int coop_max_groups;       // steps with at most this many active groups: all cooperative
   int h_max_iter, bin_cap, leaf_max, G, drift_all;
@@ -270,6 +274,8 @@ cudaError_t launch_force(const View &v, int bin_filter, bool persistent, int gri
 cudaError_t launch_entropy_from_u(const View &v, cudaStream_t st);
 int persistent_blocks_per_sm(int G, bool density);
 cudaError_t launch_group_cost(const View &v, int grid, cudaStream_t st);
+// velocity divergence and curl of the active particles (after their density)
+cudaError_t launch_gradient(const View &v, int grid, cudaStream_t st);
 // sph_adjoint.cu
 cudaError_t launch_adj_prepare(const sph_particles &pre, const sph_particles &post,
                                const sph_particles &W, const sph_adjoint &adj, long long ti,

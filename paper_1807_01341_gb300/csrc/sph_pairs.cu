@@ -43,7 +43,7 @@ namespace {
 template <class St>
 __device__ __forceinline__ float *red_area(int warp) {
   extern __shared__ __align__(16) char smem_dyn[];
-  static_assert(St::red_bytes() >= 11 * 32 * sizeof(float), "the reduction area holds 11 words");
+  static_assert(St::red_bytes() >= 12 * 32 * sizeof(float), "the reduction area holds 12 words");
   return reinterpret_cast<float *>(smem_dyn + (size_t)warp * St::bytes() + St::red_offset());
 }
 
@@ -167,7 +167,8 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
     const float4 xl = v.rec_xm[i];  // position in its own leaf's frame
     const float3 lo3 = leaf_offset(v, i, F);
     const float4 xi = make_float4(xl.x + lo3.x, xl.y + lo3.y, xl.z + lo3.z, xl.w);
-    float h = v.h[i];
+    // the initial guess: the last h, or (prediction) the h the drift predicted
+    float h = v.predict ? v.rec_xH[i].w * (1.0f / GAMMA_K) : v.h[i];
     double lo = 0.0, hi = INFINITY;
     bool done = !valid;
     float Ri = 0.0f;         // radius of this lane's neighbour list
@@ -462,7 +463,9 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
 // ---------------------------------------------------------------------------
 // force loop for the active particles of a group
 // ---------------------------------------------------------------------------
-template <int G, bool COOP>
+// VAR: the code of the scheme's variants (Balsara switch, neighbour limiter)
+// is compiled in; the base scheme runs the instance without it.
+template <int G, bool COOP, bool VAR>
 __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, const CellFrame &F,
                             float Hmax, float exc, StageF &st, WarpCounters &wc) {
   static_assert(!COOP || G == 1, "cooperative groups use one lane per particle");
@@ -504,6 +507,13 @@ __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, co
     float pax = 0.f, pay = 0.f, paz = 0.f, pad = 0.f;
     float vs = 2.0f * hi4.z;
     int cur = -1, cnt = 0;
+    int bmin = 127;  // limiter: smallest bin among the neighbours
+    // Balsara factor of i: |div v| / (|div v| + |curl v| + 1e-4 c / h), h = 1 / (GAMMA_K / H)
+    float Bi = 1.0f;
+    if ((VAR && v.balsara) && valid) {
+      const float dv = fabsf(v.div_v[i]);
+      Bi = dv / (dv + fabsf(v.curl_v[i]) + 1e-4f * hi4.z * GAMMA_K * hi4.w);
+    }
     auto leaf_ok = [&](int l, float sx, float sy, float sz, LeafBox &lb) {
       const float4 loj = v.leaf_lo[l], hij = v.leaf_hi[l];
       const float R = fmaxf(Hs, loj.w);
@@ -605,6 +615,10 @@ __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, co
           const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
           const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
           cnt++;
+          if ((VAR && v.limiter)) {
+            const int j = st.recj[k];
+            if (j != i) bmin = min(bmin, (int)v.bin[j]);
+          }
           if (r2 > 0.0f) {
             const float rinv = rsqrtf(r2);
             const float rr = r2 * rinv;
@@ -617,7 +631,14 @@ __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, co
             const float wij = fminf(0.0f, dvdr * rinv);
             const float vsij = hi4.z + hj.z - 3.0f * wij;
             // (fast division: 2 ulp, the pair term's only divide)
-            const float Pi = __fdividef(-alpha * vsij * wij, hi4.x + hj.x);
+            float Pi = __fdividef(-alpha * vsij * wij, hi4.x + hj.x);
+            if ((VAR && v.balsara)) {
+              // mean of the pair's Balsara factors (j's from its last density)
+              const int j = st.recj[k];
+              const float dv = fabsf(v.div_v[j]);
+              const float Bj = dv / (dv + fabsf(v.curl_v[j]) + 1e-4f * hj.z * GAMMA_K * hj.w);
+              Pi *= 0.5f * (Bi + Bj);
+            }
             const float dWb = 0.5f * (dwi + dwj);
             const float sc = vj.w * fmaf(hi4.y, dwi, fmaf(hj.y, dwj, Pi * dWb)) * rinv;
             pax = fmaf(-sc, dx, pax);
@@ -656,10 +677,11 @@ __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, co
       mine[8 * 32 + lane] = vs;
       reinterpret_cast<int *>(mine)[9 * 32 + lane] = cnt;
       reinterpret_cast<int *>(mine)[10 * 32 + lane] = st.failed ? 1 : 0;
+      reinterpret_cast<int *>(mine)[11 * 32 + lane] = bmin;
       __syncthreads();
       double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
       float vm = 0.0f;
-      int c = 0, fl = 0;
+      int c = 0, fl = 0, bm = 127;
       for (int w = 0; w < WARPS_PER_BLOCK; w++) {
         const float *rw = red_area<StageF>(w);
         a0 += (double)rw[0 * 32 + lane] + (double)rw[1 * 32 + lane];
@@ -669,6 +691,7 @@ __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, co
         vm = fmaxf(vm, rw[8 * 32 + lane]);
         c += reinterpret_cast<const int *>(rw)[9 * 32 + lane];
         fl |= reinterpret_cast<const int *>(rw)[10 * 32 + lane];
+        bm = min(bm, reinterpret_cast<const int *>(rw)[11 * 32 + lane]);
       }
       fl = __any_sync(FULL, fl != 0) ? 1 : 0;
       __syncthreads();
@@ -681,6 +704,7 @@ __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, co
       sad = a3;
       vs = vm;
       cnt = c - 1;
+      bmin = bm;
     } else {
       sax = group_sum<G>((double)ax_hi + (double)ax_lo);
       say = group_sum<G>((double)ay_hi + (double)ay_lo);
@@ -688,6 +712,10 @@ __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, co
       sad = group_sum<G>((double)ad_hi + (double)ad_lo);
       cnt = group_sum_i<G>(cnt) - 1;
       vs = group_max<G>(vs);
+      if ((VAR && v.limiter)) {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) bmin = min(bmin, __shfl_xor_sync(FULL, bmin, o));
+      }
     }
     if (valid && sub == 0 && writer) {
       wc.pairs += (unsigned long long)cnt;
@@ -697,7 +725,114 @@ __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, co
       v.Adot[i] = 0.5f * (g - 1.0f) * powf(hi4.x, 1.0f - g) * (float)sad;
       v.vsig[i] = vs;
       if (v.ngb_force) v.ngb_force[i] = cnt;
+      if ((VAR && v.limiter)) v.ngb_bin[i] = (int8_t)bmin;
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// velocity divergence and curl of the active particles of a group (for the
+// variants that use them; after the density loop, at the new h):
+//   div v_i  = -(1 / rho_i) sum_j m_j v_ij . grad_i W(r_ij, h_i)
+//   curl v_i =  (1 / rho_i) sum_j m_j v_ij x grad_i W(r_ij, h_i)
+// with grad_i W = (r_ij / r) dW/dr, over j != i with r_ij < H_i, the step's
+// predicted velocities; one lane per particle, the sums folded (compensated)
+// at neighbour-cell boundaries in record order.
+// ---------------------------------------------------------------------------
+__device__ void gradient_group(const View &v, int wg, int m_act, const CellFrame &F, float exc,
+                               StageF &st, WarpCounters &wc) {
+  const int lane = lane_id();
+  const Group W = group_of(v, wg, F);
+  const int a = W.a, b = W.b;
+  const int nact = leaf_actives(v, a, b, m_act, -1, st.act);
+  if (nact == 0) return;
+  const float qox = F.kx * F.wq, qoy = F.ky * F.wq, qoz = F.kz * F.wq;
+  const float clx = W.lx + qox, cly = W.ly + qoy, clz = W.lz + qoz;
+  const float chx = W.hx + qox, chy = W.hy + qoy, chz = W.hz + qoz;
+  const float ceps = 1e-5f * F.wf;
+  const float4 *srcs[3] = {v.rec_xH, v.rec_v, v.rec_h};
+  const float4 *sx_rec = st.rec, *sv_rec = st.rec + S_FORCE;
+  const bool valid = lane < nact;  // (a group holds at most 32 particles)
+  const int i = valid ? st.act[lane] : a;
+  const float4 xl = v.rec_xH[i];
+  const float3 lo3 = leaf_offset(v, i, F);
+  const float4 xi = make_float4(xl.x + lo3.x, xl.y + lo3.y, xl.z + lo3.z, xl.w);
+  const float4 vi = v.rec_v[i];
+  const float Hi2 = xi.w * xi.w, Hinv = 1.0f / xi.w;
+  const float nHi4 = KERNEL_NORM * Hinv * Hinv * Hinv * Hinv;
+  const float Hs = warp_max(valid ? xi.w : 0.0f);
+  const int nsph = compact_spheres(st.sph, valid, make_float4(xi.x, xi.y, xi.z, xi.w));
+  float d_hi = 0.f, d_lo = 0.f, x_hi = 0.f, x_lo = 0.f, y_hi = 0.f, y_lo = 0.f, z_hi = 0.f,
+        z_lo = 0.f;
+  float pd = 0.f, px = 0.f, py = 0.f, pz = 0.f;
+  int cur = -1;
+  auto consume = [&](int base, int total) {
+    wc.cand += (unsigned long long)total * (unsigned long long)nact;
+    for (int k0 = 0; k0 < total; k0 += 32) {
+      unsigned mask = 0u;
+      for (int u = 0; u < 32; u++) {
+        const float4 pj = sx_rec[min(base + k0 + u, S_FORCE - 1)];
+        const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        mask |= (k0 + u < total && r2 < Hi2) ? (1u << u) : 0u;
+      }
+      if (!valid) mask = 0u;
+      while (mask) {
+        const int k = base + k0 + __ffs(mask) - 1;
+        mask &= mask - 1;
+        const int ci = st.recc[k];
+        if (ci != cur) {
+          fold(d_hi, d_lo, pd);
+          fold(x_hi, x_lo, px);
+          fold(y_hi, y_lo, py);
+          fold(z_hi, z_lo, pz);
+          pd = px = py = pz = 0.f;
+          cur = ci;
+        }
+        const float4 pj = sx_rec[k];
+        const float4 vj = sv_rec[k];
+        const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        if (r2 > 0.0f) {  // (the particle itself and coincident ones add nothing)
+          const float rinv = rsqrtf(r2);
+          const float g1 = vj.w * kernel_dw(r2 * rinv * Hinv) * nHi4 * rinv;
+          const float wx = vi.x - vj.x, wy = vi.y - vj.y, wz = vi.z - vj.z;
+          pd = fmaf(fmaf(wx, dx, fmaf(wy, dy, wz * dz)), g1, pd);
+          px = fmaf(fmaf(wy, dz, -wz * dy), g1, px);
+          py = fmaf(fmaf(wz, dx, -wx * dz), g1, py);
+          pz = fmaf(fmaf(wx, dy, -wy * dx), g1, pz);
+        }
+      }
+    }
+  };
+  const float R2 = Hs * Hs * 1.0002f, Rc = Hs + ceps;
+  auto leaf_ok = [&](int l, float sx, float sy, float sz, LeafBox &lb) {
+    const float4 lo4 = v.leaf_lo[l], hi4 = v.leaf_hi[l];
+    lb = leaf_box(lo4, hi4, sx, sy, sz, 0.0f);
+    return box_gap2(W.lx, W.ly, W.lz, W.hx, W.hy, W.hz, lo4, hi4, sx, sy, sz) < R2;
+  };
+  auto chunk_ok = [&](int g, float sx, float sy, float sz) {
+    return box_gap2(clx, cly, clz, chx, chy, chz, v.chunk_lo[g], v.chunk_hi[g], sx, sy, sz) <
+           Rc * Rc;
+  };
+  const Reach reach = {clx, cly, clz, chx, chy, chz, Rc, exc, st.sph, nsph, true};
+  int skip = 0;
+  bool more = false;
+  do {
+    const int nlist = search(v, F, reach, st, leaf_ok, chunk_ok, skip, more);
+    stage_list(srcs, st, nlist, consume, wc);
+    skip += nlist;
+  } while (more && !st.failed);
+  if (st.failed) return;
+  fold(d_hi, d_lo, pd);
+  fold(x_hi, x_lo, px);
+  fold(y_hi, y_lo, py);
+  fold(z_hi, z_lo, pz);
+  if (valid) {
+    const float rho = v.rec_h[i].x;  // this step's density
+    const float cx = x_hi + x_lo, cy = y_hi + y_lo, cz = z_hi + z_lo;
+    v.div_v[i] = -(d_hi + d_lo) / rho;
+    v.curl_v[i] = sqrtf(fmaf(cx, cx, fmaf(cy, cy, cz * cz))) / rho;
   }
 }
 
@@ -843,7 +978,7 @@ __global__ void __launch_bounds__(PT, 2) k_density(View v, int flags, int bin_fi
   flush_counters(ds, wc, true);
 }
 
-template <int G>
+template <int G, bool VAR>
 __global__ void __launch_bounds__(PT, 2) k_force(View v, int bin_filter, int persistent) {
   DevState *ds = v.ds;
   const int warp = threadIdx.x >> 5, lane = lane_id();
@@ -875,7 +1010,8 @@ __global__ void __launch_bounds__(PT, 2) k_force(View v, int bin_filter, int per
         __syncthreads();
         if (item >= qs.ncoop || st.failed) break;
         const int wg = coop_group(v, ds, bin_filter, item);
-        force_group<1, true>(v, wg, bin_filter, m_act, frame_of(v, ds, wg), Hmax, exc, st, wc);
+        force_group<1, true, VAR>(v, wg, bin_filter, m_act, frame_of(v, ds, wg), Hmax, exc, st,
+                                  wc);
       }
     }
   }
@@ -891,10 +1027,40 @@ __global__ void __launch_bounds__(PT, 2) k_force(View v, int bin_filter, int per
       }
       if (item >= qs.nwarp || st.failed) break;
       const int wg = warp_group<G>(v, ds, bin_filter, item);
-      force_group<G, false>(v, wg, bin_filter, m_act, frame_of(v, ds, wg), Hmax, exc, st, wc);
+      force_group<G, false, VAR>(v, wg, bin_filter, m_act, frame_of(v, ds, wg), Hmax, exc, st,
+                                 wc);
     }
   }
   flush_counters(ds, wc, false);
+}
+
+// Velocity divergence and curl of the step's active particles: persistent
+// warps, one work group each, pulled from head_grad.
+__global__ void __launch_bounds__(PT, 2) k_gradient(View v) {
+  DevState *ds = v.ds;
+  __shared__ int s_go;
+  __shared__ float s_exc;
+  if (threadIdx.x == 0) {
+    s_go = ds->halt ? 0 : 1;
+    s_exc = __uint_as_float(ds->excursion_bits);
+  }
+  __syncthreads();
+  if (!s_go) return;
+  StageF st;
+  stage_init(st, v.stage_depth, v.wait_limit);
+  const int lane = lane_id();
+  const int m_act = ds->m_act;
+  const int nq = ds->n_active_groups + ds->n_heavy_groups;
+  WarpCounters wc = {0, 0, 0, 0, 0, 0};
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(&ds->head_grad, 1);
+    item = __shfl_sync(FULL, item, 0);
+    if (item >= nq || st.failed) break;
+    const int wg = active_group(v, ds, item);
+    gradient_group(v, wg, m_act, frame_of(v, ds, wg), s_exc, st, wc);
+  }
+  if (lane == 0 && wc.timeout) record_error(ds, SPH_ERR_TIMEOUT, wc.timeout, true);
 }
 
 // Estimated cost of each work group: the particles in the leaves (in cells of
@@ -978,18 +1144,33 @@ cudaError_t density_g(const View &v, int flags, int bin_filter, bool persistent,
 
 template <int G>
 cudaError_t force_g(const View &v, int bin_filter, bool persistent, int grid, cudaStream_t st) {
-  k_force<G><<<grid, PT, FORCE_SMEM, st>>>(v, bin_filter, persistent ? 1 : 0);
+  if (G == 1 && (v.balsara || v.limiter))
+    k_force<1, true><<<grid, PT, FORCE_SMEM, st>>>(v, bin_filter, persistent ? 1 : 0);
+  else
+    k_force<G, false><<<grid, PT, FORCE_SMEM, st>>>(v, bin_filter, persistent ? 1 : 0);
   return cudaGetLastError();
 }
 
 template <int G>
 int blocks_per_sm_g(bool density) {
-  const void *fn = density ? (const void *)k_density<G> : (const void *)k_force<G>;
+  const void *fn = density ? (const void *)k_density<G> : (const void *)k_force<G, false>;
   const size_t smem = density ? DENS_SMEM : FORCE_SMEM;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess) {
     cudaGetLastError();
     return 0;
+  }
+  if (!density && G == 1) {
+    // the force kernel with the variants' code and the gradient kernel use the
+    // same staging area (set here, at context creation, outside any capture)
+    if (cudaFuncSetAttribute((const void *)k_force<1, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute((const void *)k_gradient, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
   }
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, PT, smem) != cudaSuccess) {
@@ -1055,6 +1236,13 @@ cudaError_t launch_group_cost(const View &v, int grid, cudaStream_t st) {
   e = cudaMemsetAsync(SPH_DS_FIELD(v.ds, group_cost_sum), 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
   k_group_cost<<<grid, PT, DENS_SMEM, st>>>(v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gradient(const View &v, int grid, cudaStream_t st) {
+  if (grid <= 0) return cudaSuccess;
+  note_launches(1);
+  k_gradient<<<grid, PT, FORCE_SMEM, st>>>(v);
   return cudaGetLastError();
 }
 

@@ -46,6 +46,9 @@ class Params:
     staging_depth: int = 1
     wait_limit: int = 0
     test_stall: int = 0
+    balsara: int = 0
+    predict_inactive: int = 0
+    limiter: int = 0
 
     def to_c(self) -> _lib.sph_params:
         p = _lib.sph_params()
@@ -71,11 +74,13 @@ class Particles:
 
     ALIGN = 256
 
-    def __init__(self, n: int, device="cuda", with_counts: bool = True):
+    def __init__(self, n: int, device="cuda", with_counts: bool = True,
+                 with_gradients: bool = True):
         self.n = int(n)
         self.device = torch.device(device)
         fields = [(name, dt) for name, dt in _lib.PARTICLE_FIELDS
-                  if with_counts or name not in ("ngb_density", "ngb_force")]
+                  if (with_counts or name not in ("ngb_density", "ngb_force")) and
+                  (with_gradients or name not in ("div_v", "curl_v"))]
         offs, total = {}, 0
         for name, dt in fields:
             offs[name] = total
@@ -92,12 +97,13 @@ class Particles:
         self._struct = None
 
     @classmethod
-    def from_ics(cls, ic: dict, device="cuda", with_counts: bool = True):
+    def from_ics(cls, ic: dict, device="cuda", with_counts: bool = True,
+                 with_gradients: bool = True):
         """Initial state: positions, velocities, masses, u (held in A until the
         first density pass converts it), h guess; every particle on bin 0 at
         tick 0."""
         n = ic["pos"].shape[0]
-        p = cls(n, device, with_counts)
+        p = cls(n, device, with_counts, with_gradients)
         pos = torch.as_tensor(np.ascontiguousarray(ic["pos"]), dtype=torch.float64)
         vel = torch.as_tensor(np.ascontiguousarray(ic["vel"]), dtype=torch.float32)
         p.x.copy_(pos[:, 0]); p.y.copy_(pos[:, 1]); p.z.copy_(pos[:, 2])

@@ -334,3 +334,82 @@ def test_bounded_wait_gives_up_and_context_recovers(sim, coop_max_groups):
     a_ref = np.stack([ref["ax"], ref["ay"], ref["az"]], 1)
     assert np.max(np.abs(a - a_ref)) < 1e-4 * np.sqrt((a_ref ** 2).sum(1).mean())
     ctx.close()
+
+
+VARIANTS = [dict(balsara=1, predict_inactive=1, limiter=1), dict(balsara=1),
+            dict(predict_inactive=1), dict(limiter=1)]
+
+
+@pytest.mark.parametrize("var", VARIANTS)
+def test_variants_step_parity_each_step_from_same_state(sim, orc, var):
+    """The scheme's variants (Balsara switch, Gadget-2 prediction of inactive
+    rho and h, Saitoh-Makino neighbour limiter) against the oracle run with
+    the same switches, step by step from the GPU's state: active sets and
+    bins exact, the velocity divergence and curl within 1e-4 of their rms,
+    the floating-point state within the hot-path tolerances."""
+    ic = _ic_step(seed=53)
+    n = ic["pos"].shape[0]
+    ctx, p = gpu_setup(ic, sim.Params(**STEP_PARAMS, **var))
+    L = _lib()
+    okw = dict(predict=bool(var.get("predict_inactive")), balsara=bool(var.get("balsara")),
+               limiter=bool(var.get("limiter")))
+    n_partial = 0
+    for k in range(8):
+        st0 = p.numpy()
+        _, ti = ctx.get_time()
+        osim = orc.OracleSim.from_state(st0, ti=ti, first=(k == 0), use_cells=True,
+                                        **STEP_PARAMS, **okw)
+        act_ref = osim.step()
+        ctx.step(p, L.SPH_FORM_BATCHED)
+        st = p.numpy()
+        act = st["active"].astype(bool)
+        assert np.array_equal(act, act_ref), k
+        n_partial += int(0 < act.sum() < n)
+        assert np.max(np.abs(st["h"][act] / osim.h[act] - 1)) < 1e-5
+        assert np.max(np.abs(st["rho"][act] / osim.rho[act] - 1)) < 1e-5
+        if okw["predict"] or okw["balsara"]:
+            for key, ref in (("div_v", osim.divv), ("curl_v", osim.curl)):
+                rms = np.sqrt((ref[act] ** 2).mean()) + 1e-30
+                assert np.max(np.abs(st[key][act] - ref[act])) < 1e-4 * rms, (k, key)
+        a = np.stack([st["ax"], st["ay"], st["az"]], 1)[act]
+        a_ref = osim.acc[act]
+        a_rms = np.sqrt((a_ref ** 2).sum(1).mean())
+        assert np.max(np.abs(a - a_ref)) < 1e-4 * a_rms, k
+        assert np.max(np.abs(st["vsig"][act] / osim.vsig[act] - 1)) < 1e-5
+        q = osim.cfl * osim.h / osim.vsig / osim.dt_min
+        with np.errstate(divide="ignore", invalid="ignore"):
+            edge = np.abs(np.log2(q) - np.round(np.log2(q))) < 2e-5
+        ok = act & ~edge
+        assert np.array_equal(st["bin"][ok], osim.bin[ok]), k
+    assert n_partial >= 2          # individual bins (the limiter narrows them)
+
+
+def test_variants_forms_bitwise_identical(sim):
+    """With all three variants the plain, batched and graph forms agree bit
+    for bit (every sum of a particle still depends on the particle alone)."""
+    ic = _ic_step(seed=59)
+    params = dict(STEP_PARAMS, balsara=1, predict_inactive=1, limiter=1)
+    res = {f: _run_form(sim, ic, f, 10, params) for f in ("plain", "batched", "graph")}
+    ref, cref, tref = res["batched"]
+    for f in ("plain", "graph"):
+        st, c, t = res[f]
+        assert t == tref, f
+        for k in ref:
+            assert np.array_equal(st[k], ref[k]), (f, k)
+
+
+def test_variants_change_the_run_and_need_their_arrays(sim):
+    """The variants act (a run with them differs from the base run) and a
+    state without the divergence arrays is refused with SPH_ERR_ARG; the
+    reverse pass refuses them."""
+    L = _lib()
+    ic = _ic_step(seed=61)
+    a, _, _ = _run_form(sim, ic, "batched", 6, STEP_PARAMS)
+    b, _, _ = _run_form(sim, ic, "batched", 6, dict(STEP_PARAMS, balsara=1, predict_inactive=1,
+                                                     limiter=1))
+    assert not np.array_equal(a["vx"], b["vx"])
+    ctx = sim.Context(sim.Params(**STEP_PARAMS, balsara=1), ic["pos"].shape[0])
+    p = sim.Particles.from_ics(ic, with_gradients=False)
+    with pytest.raises(L.SphError) as e:
+        ctx.build_cells(p)
+    assert e.value.code == L.SPH_ERR_ARG
