@@ -100,3 +100,24 @@ def test_sedov_262k_follows_sedov_taylor(sim):
     assert 0.88 < peak <= 1.0, (t, peak)
     assert abs(e - 1.0) < 0.01, (t, e)
     ctx.close()
+
+
+def test_sedov_262k_with_the_variants(sim):
+    """The same 100 steps with the Balsara switch, the prediction of inactive
+    rho and h, and the neighbour time-step limiter: the shell radius stays
+    within 5 % of R and the energy within 1 % (the density peak, sharper with
+    the Balsara switch, within 12 % either side)."""
+    name = "c2_sedov_262k"
+    ic = workloads.make(name)
+    E0 = float((ic["m"] * ic["u"]).sum())
+    params = sim.Params(**workloads.PARAMS[name], balsara=1, predict_inactive=1, limiter=1)
+    ctx = sim.Context(params, ic["pos"].shape[0])
+    p = sim.Particles.from_ics(ic, with_counts=False)
+    ctx.build_cells(p)
+    ctx.begin_run()
+    _advance(ctx, p, n_steps=workloads.STEPS[name])
+    t, shell, peak, e = _measure(ctx, p, E0, params.dt_min)
+    assert abs(shell - 1.0) < 0.05, (t, shell)
+    assert 0.88 < peak < 1.12, (t, peak)
+    assert abs(e - 1.0) < 0.01, (t, e)
+    ctx.close()
