@@ -62,9 +62,9 @@ struct Buffers {
   unsigned int *cell_stamp = nullptr, *cell_rel_stamp = nullptr;
   int32_t *q_act_cells = nullptr;
   unsigned int *leaf_counts = nullptr, *leaf_offsets = nullptr;
-  // neighbour lists of the density loop (list_cap entries per particle, and
-  // per warp of the first coop_slots blocks)
-  float2 *nbr = nullptr, *nbr_coop = nullptr;
+  // neighbour lists of the density loop: list_cap entries per lane of every
+  // warp of a persistent density launch
+  float2 *nbr = nullptr;
   int8_t *ngb_bin = nullptr;  // limiter: smallest neighbour bin of each active particle
   // state
   DevState *ds = nullptr;
@@ -98,7 +98,7 @@ struct sph_ctx {
   int num_sms = 0;
   int grid_util = 0;
   int grid_dens = 0, grid_force = 0;
-  int coop_slots = 0;  // blocks of a density launch with neighbour lists for shared groups
+  int list_blocks = 0;  // blocks a density launch may have (each warp has a list area)
   Buffers b;
   bool built = false;
   bool entropy_ready = false;  // the first density pass has converted u to A
@@ -264,9 +264,8 @@ View make_view(const sph_ctx *ctx, const sph_particles *p) {
   v.drift_all = q.drift_all;
   v.grid_util = ctx->grid_util;
   v.nbr = b.nbr;
-  v.nbr_coop = b.nbr_coop;
   v.list_cap = q.list_cap;
-  v.coop_slots = ctx->coop_slots;
+  v.list_blocks = ctx->list_blocks;
   v.search_margin = (float)q.search_margin;
   v.stage_depth = q.staging_depth;
   v.wait_limit = q.wait_limit;
@@ -507,10 +506,11 @@ int plain_body(sph_ctx *ctx, const View &v, int flags, cudaStream_t st) {
     SPH_CUDA(cudaStreamSynchronize(st));
     // blocks for the shared groups (at most one per neighbour-list slot), then
     // one warp per group
-    const int ncb = std::min(nq[1], ctx->coop_slots);
+    // the bin's groups pulled from a head by at most the persistent grid's
+    // blocks (each warp has its own neighbour-list area)
+    const int want = nq[1] + (nq[0] + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
     prof_begin(ctx, 0, st);
-    SPH_CUDA(launch_density(v, flags, bins[k], false,
-                            ncb + (nq[0] + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK, st));
+    SPH_CUDA(launch_density(v, flags, bins[k], true, std::min(want, ctx->list_blocks), st));
     prof_end(ctx, 0, st);
   }
   if (flags & SPH_DENSITY_INIT_ENTROPY) SPH_CUDA(launch_entropy_from_u(v, st));
@@ -521,7 +521,7 @@ int plain_body(sph_ctx *ctx, const View &v, int flags, cudaStream_t st) {
     SPH_CUDA(cudaMemcpyAsync(nq, SPH_DS_FIELD(v.ds, n_bin_groups), 2 * sizeof(int),
                              cudaMemcpyDeviceToHost, st));
     SPH_CUDA(cudaStreamSynchronize(st));
-    const int ncb = std::min(nq[1], ctx->coop_slots);
+    const int ncb = std::min(nq[1], ctx->list_blocks);
     prof_begin(ctx, 1, st);
     SPH_CUDA(launch_force(v, bins[k], false,
                           ncb + (nq[0] + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK, st));
@@ -780,11 +780,9 @@ int sph_create(const sph_params *params, int64_t n_max, sph_ctx **out) {
     // neighbour lists of the density loop: by particle, and for the blocks
     // that share a work group (those of a persistent launch; a per-bin launch
     // uses at most as many)
-    ctx->coop_slots = ctx->grid_dens;
-    if ((r = dalloc(&b.ngb_bin, n)) || (r = dalloc(&b.nbr, n * (long long)params->list_cap)) ||
-        (r = dalloc(&b.nbr_coop, G == 1 ? (long long)ctx->coop_slots * WARPS_PER_BLOCK * 32 *
-                                              params->list_cap
-                                        : 1LL)))
+    ctx->list_blocks = ctx->grid_dens;
+    if ((r = dalloc(&b.ngb_bin, n)) ||
+        (r = dalloc(&b.nbr, (long long)ctx->list_blocks * WARPS_PER_BLOCK * 32 * params->list_cap)))
       break;
     // no neighbour bin known yet: no limit (a bins call without a force pass)
     if (cudaMemset(b.ngb_bin, 127, (size_t)n) != cudaSuccess) {
@@ -831,7 +829,7 @@ int sph_destroy(sph_ctx *ctx) {
   dfree(b.cell_start); dfree(b.cell_leaf_start); dfree(b.cell_stamp); dfree(b.cell_rel_stamp);
   dfree(b.q_act_cells); dfree(b.leaf_counts); dfree(b.leaf_offsets);
   dfree(b.ds); dfree(b.d_hmax); dfree(b.diag); dfree(b.d_bad);
-  dfree(b.nbr); dfree(b.nbr_coop); dfree(b.ngb_bin);
+  dfree(b.nbr); dfree(b.ngb_bin);
   if (b.h_ds) cudaFreeHost(b.h_ds);
   delete ctx;
   return SPH_OK;

@@ -745,6 +745,9 @@ cudaError_t launch_mark_bin(const View &v, int bin, cudaStream_t st) {
                 "the two coop heads are adjacent");
   e = cudaMemsetAsync(SPH_DS_FIELD(v.ds, head_coop_density), 0, 2 * sizeof(int), st);
   if (e != cudaSuccess) return e;
+  // (the per-bin density launch pulls its groups from head_density too)
+  e = cudaMemsetAsync(SPH_DS_FIELD(v.ds, head_density), 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
   k_mark_bin<<<v.grid_util, UT, 0, st>>>(v, bin);
   return cudaGetLastError();
 }

@@ -127,20 +127,18 @@ struct View {
   int32_t *q_bin;            // plain form: active work groups holding particles of one bin
                              // (light ones at [0, n_bin_groups), heavy ones from the back)
   // neighbour lists of the density loop: squared distance and mass of every
-  // candidate within the particle's search radius, list_cap entries per
-  // particle.  nbr: by particle (entry k of lane sub of the particle in slot s
-  // of work group [a, b) at nbr[a * list_cap + (k * G + sub) * (b - a) + s]);
-  // nbr_coop: per warp of the first coop_slots blocks of a launch, for groups
-  // shared by a block (entry k of lane s at [(block * 8 + warp) * 32 * list_cap
-  // + k * 32 + s]).
+  // candidate within a particle's search radius, list_cap entries per lane,
+  // one area per warp of the launch's blocks (a launch has at most list_blocks
+  // blocks; entry k of lane s of warp w of block b at
+  // nbr[((b * 8 + w) * list_cap + k) * 32 + s]): the area of a warp is reused
+  // by its next work group, so the lists stay in L2.
   float2 *nbr;
-  float2 *nbr_coop;
   DevState *ds;
   // parameters
   double box, eta, gamma, alpha, cfl, h_tol, dt_min;
   long long wait_limit;      // polls of a bounded barrier wait (0: the default)
   float search_margin;       // a density search reaches search_margin x the support
-  int list_cap, coop_slots;  // neighbour-list entries per particle; blocks with coop lists
+  int list_cap, list_blocks;  // neighbour-list entries per lane; blocks with list areas
   int stage_depth;           // staging buffers per warp (1..3)
   int balsara, predict, limiter;  // variants of the scheme (0/1)
   double heavy_factor;       // heavy work group: estimated cost > heavy_factor x mean

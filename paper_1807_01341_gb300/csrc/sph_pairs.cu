@@ -150,20 +150,16 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
   const double Cw = v.eta * v.eta * v.eta * GAMMA_K_D * GAMMA_K_D * GAMMA_K_D / (double)KERNEL_NORM;
   const bool init_entropy = (flags & SPH_DENSITY_INIT_ENTROPY) != 0;
   const float4 *srcs[1] = {v.rec_xm};
-  // neighbour lists: entry k of this lane's list at lst[k * ls].  By particle
-  // (slot s of the group, lane sub of its G): nbr[a * list_cap + (k * G + sub)
-  // * (b - a) + s]; shared groups: per warp of the block, by lane.
-  const int cap = COOP ? v.list_cap : v.list_cap / G;
-  const int ls = COOP ? 32 : G * (b - a);
-  float2 *const lbase =
-      COOP ? v.nbr_coop + ((size_t)blockIdx.x * WARPS_PER_BLOCK + warp) * 32 * v.list_cap + lane
-           : v.nbr + (size_t)a * v.list_cap + sub * (b - a);
+  // this lane's neighbour list: entry k at lst[k * 32], in the warp's own
+  // area (the launch has at most list_blocks blocks)
+  const int cap = v.list_cap;
+  constexpr int ls = 32;
+  float2 *const lst = v.nbr + ((size_t)blockIdx.x * WARPS_PER_BLOCK + warp) * 32 * v.list_cap + lane;
 
   for (int r = 0; r < nact && !st.failed; r += P) {
     const int slot = r + grp;
     const bool valid = slot < nact;
     const int i = valid ? st.act[slot] : a;
-    float2 *const lst = COOP ? lbase : lbase + (valid ? slot : 0);
     const float4 xl = v.rec_xm[i];  // position in its own leaf's frame
     const float3 lo3 = leaf_offset(v, i, F);
     const float4 xi = make_float4(xl.x + lo3.x, xl.y + lo3.y, xl.z + lo3.z, xl.w);
@@ -859,7 +855,7 @@ __device__ __forceinline__ Queues queues(const View &v, const DevState *ds, int 
 // own neighbour-list slot), the rest of the grid one group per warp.
 template <int G>
 __device__ __forceinline__ int coop_blocks(const View &v, const Queues &qs) {
-  return G == 1 ? min(qs.ncoop, v.coop_slots) : 0;
+  return G == 1 ? min(qs.ncoop, v.list_blocks) : 0;
 }
 
 __device__ __forceinline__ int coop_group(const View &v, const DevState *ds, int bin_filter, int k) {
