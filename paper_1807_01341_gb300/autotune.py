@@ -11,6 +11,8 @@ fastest in useful pairs per second:
   search_margin         how far beyond its support a particle's candidates are
                         gathered (larger: fewer gathers, longer lists)
   list_cap              neighbour-list entries per particle (more: fewer overflow passes)
+  heavy_factor          work groups estimated this many times costlier than the mean
+                        are started first, each by a whole block (0: none)
 
 Each trial starts from the same initial state (its own context and a copy of
 the particles), so the trials do not influence one another; it runs one
@@ -30,7 +32,7 @@ from . import _lib
 from .sim import Context, Params, Particles
 
 _BASE = dict(threads_per_particle=1, leaf_max=16, cell_margin=2.0, list_cap=256,
-             search_margin=1.02, staging_depth=1)
+             search_margin=1.02, staging_depth=1, heavy_factor=0.0)
 DEFAULT_CANDIDATES = [
     _BASE,
     dict(_BASE, staging_depth=2),
@@ -38,7 +40,8 @@ DEFAULT_CANDIDATES = [
     dict(_BASE, search_margin=1.05),
     dict(_BASE, list_cap=128),
     dict(_BASE, leaf_max=12),
-    dict(_BASE, leaf_max=24, cell_margin=2.5),
+    dict(_BASE, leaf_max=20),
+    dict(_BASE, heavy_factor=4.0),
     dict(_BASE, threads_per_particle=2),
 ]
 

@@ -87,7 +87,7 @@ struct AdjBuffers {
   double *work = nullptr;     // ADJ_WORK_ARRAYS double arrays of n_max
   int grid_pairs = 0;
 };
-constexpr int ADJ_WORK_ARRAYS = 20;
+constexpr int ADJ_WORK_ARRAYS = 18;  // the FP64 arrays of AdjWork
 
 }  // namespace
 

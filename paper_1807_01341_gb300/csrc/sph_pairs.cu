@@ -38,8 +38,8 @@ namespace {
 // partial sums of a particle depend only on the particle), and combine their
 // per-lane partial sums through shared memory in warp order.  The reduction
 // area of a warp is the part of its staging buffer that is free between a
-// round's last consume and the next search (Stage::red_offset), so the staged
-// records stay resident for the next h iteration.
+// round's last consume and the next search (Stage::red_offset), so the leaf
+// list of the group's last search stays valid for its next gather.
 template <class St>
 __device__ __forceinline__ float *red_area(int warp) {
   extern __shared__ __align__(16) char smem_dyn[];
