@@ -44,7 +44,32 @@ enum sph_status_code {
   SPH_ERR_DT_TOO_SMALL = 5,  /* a CFL time step fell below dt_min (put on bin 0) */
   SPH_ERR_TIMEOUT = 6,       /* a bounded device wait gave up */
   SPH_ERR_NOMEM = 7,         /* device allocation failed */
-  SPH_ERR_NOT_BUILT = 8      /* sph_build_cells has not been called */
+  SPH_ERR_NOT_BUILT = 8,     /* sph_build_cells has not been called */
+  SPH_ERR_BOUNDS = 9         /* a device bounds check failed (library built with
+                                SPH_CHECKS only; see sph_get_check_report) */
+};
+
+/* Sites of the device bounds checks.  A library compiled with -DSPH_CHECKS
+ * (libsph_gb300_checks.so) tests, before every access through an index that
+ * a kernel reads from device data written by another kernel (queues, cell,
+ * chunk, leaf and work-group ranges, the permutation of a cell build), that
+ * the index lies inside its array.  A failed check records SPH_ERR_BOUNDS in
+ * the status word and the site, index and bound in the check report, skips
+ * the access and halts the step (its remaining kernels return without
+ * writing); it never traps.  The checks change no result; the normal library
+ * has none of them. */
+enum sph_check_site {
+  SPH_CHECK_NONE = 0,
+  SPH_CHECK_GROUP = 1,           /* work group taken from a queue, against the group count */
+  SPH_CHECK_GROUP_LEAVES = 2,    /* a work group's last leaf, against the leaf count */
+  SPH_CHECK_GROUP_SIZE = 3,      /* a work group's particle count, against the room for its
+                                    active particles in shared memory */
+  SPH_CHECK_CELL_LEAVES = 4,     /* a neighbour cell's last leaf, against the leaf count */
+  SPH_CHECK_LEAF = 5,            /* a leaf's last particle, against the particle count */
+  SPH_CHECK_PARTICLE_LEAF = 6,   /* a particle's leaf, against the leaf count */
+  SPH_CHECK_DRIFT_CHUNK = 7,     /* chunk taken from the drift queue, against the chunk count */
+  SPH_CHECK_ACTIVE_LEAF = 8,     /* leaf taken from the active-leaf queue, against the leaf count */
+  SPH_CHECK_SCATTER = 9          /* destination of the cell build's permutation, against n */
 };
 
 /* Parameters.  Defaults (sph_default_params): eta 1.2348, gamma 5/3,
@@ -100,6 +125,11 @@ typedef struct {
                            launches make one warp wait on a staging barrier that no copy
                            completes, so that the wait gives up after wait_limit polls and
                            the step stops with SPH_ERR_TIMEOUT */
+  int test_bad_group;   /* testing only, 0 in normal use; accepted only by a library built
+                           with SPH_CHECKS (SPH_ERR_ARG otherwise): the first test_bad_group
+                           density launches replace the first work group they take from
+                           the queue by an index past the last group, which the
+                           SPH_CHECK_GROUP check catches before any use (SPH_ERR_BOUNDS) */
   /* Variants of the scheme, as Gadget-2 (the paper's reference code) has them;
    * 0 = off (the base scheme), 1 = on.  They need threads_per_particle 1 and,
    * when balsara or predict_inactive is on, the div_v and curl_v arrays of
@@ -293,6 +323,15 @@ int sph_set_time(sph_ctx *ctx, int64_t ti_current, void *stream);
  * number of particles it concerned.  Either pointer may be NULL. */
 int sph_get_status(sph_ctx *ctx, int *status, int64_t *detail);
 int sph_clear_status(sph_ctx *ctx, void *stream);
+/* 1 if this library was compiled with the device bounds checks (SPH_CHECKS),
+ * 0 otherwise. */
+int sph_built_with_checks(void);
+/* The first failed device bounds check since the last sph_clear_status
+ * (synchronising): *site = an sph_check_site (SPH_CHECK_NONE if none failed, and
+ * always in a library built without checks), *index = the index that failed,
+ * *bound = the size of the array it indexed.  Any pointer may be NULL.
+ * Errors: SPH_ERR_ARG, SPH_ERR_CUDA. */
+int sph_get_check_report(sph_ctx *ctx, int *site, int64_t *index, int64_t *bound);
 int sph_get_counters(sph_ctx *ctx, sph_counters *out);
 int sph_reset_counters(sph_ctx *ctx, void *stream);
 /* Occupancy of the time bins (Eq. 2): counts[b] = the number of particles on

@@ -3,7 +3,8 @@
 Argument marshalling only: every step of the hot path runs in the CUDA
 library.  PyTorch provides the device memory (tensors) and the stream.
 Loading fails loudly when the library has not been built: there is no CPU
-fallback.
+fallback.  With SPH_GB300_CHECKS=1 in the environment the process loads the
+build with device bounds checks (libsph_gb300_checks.so) instead.
 """
 from __future__ import annotations
 
@@ -12,6 +13,7 @@ import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libsph_gb300.so")
+CHECKS_LIB_PATH = os.path.join(HERE, "_build", "libsph_gb300_checks.so")
 
 # status codes (include/sph.h)
 SPH_OK = 0
@@ -23,6 +25,12 @@ SPH_ERR_DT_TOO_SMALL = 5
 SPH_ERR_TIMEOUT = 6
 SPH_ERR_NOMEM = 7
 SPH_ERR_NOT_BUILT = 8
+SPH_ERR_BOUNDS = 9
+
+# sites of the device bounds checks (sph_check_site)
+SPH_CHECK_NONE, SPH_CHECK_GROUP, SPH_CHECK_GROUP_LEAVES, SPH_CHECK_GROUP_SIZE = 0, 1, 2, 3
+SPH_CHECK_CELL_LEAVES, SPH_CHECK_LEAF, SPH_CHECK_PARTICLE_LEAF = 4, 5, 6
+SPH_CHECK_DRIFT_CHUNK, SPH_CHECK_ACTIVE_LEAF, SPH_CHECK_SCATTER = 7, 8, 9
 
 SPH_DRIFT, SPH_KICK_CLOSE, SPH_KICK_OPEN = 0, 1, 2
 SPH_DENSITY_INIT_ENTROPY = 1
@@ -38,7 +46,8 @@ class sph_params(ctypes.Structure):
                 ("threads_per_particle", _i), ("drift_all", _i), ("n_cells_override", _i),
                 ("heavy_factor", _d), ("coop_max_groups", _i), ("list_cap", _i),
                 ("search_margin", _d), ("staging_depth", _i), ("wait_limit", _i),
-                ("test_stall", _i), ("balsara", _i), ("predict_inactive", _i), ("limiter", _i)]
+                ("test_stall", _i), ("test_bad_group", _i), ("balsara", _i),
+                ("predict_inactive", _i), ("limiter", _i)]
 
 
 PARTICLE_FIELDS = [("x", "f8"), ("y", "f8"), ("z", "f8"), ("vx", "f4"), ("vy", "f4"),
@@ -76,13 +85,16 @@ class sph_kernel_times(ctypes.Structure):
 _lib = None
 
 
-def load(path: str = LIB_PATH):
-    """Load the library (it must have been built: paper_1807_01341_gb300.build)."""
+def load(path: str = None):
+    """Load the library (it must have been built: paper_1807_01341_gb300.build);
+    the build with device bounds checks when SPH_GB300_CHECKS=1."""
     global _lib
     if _lib is not None:
         return _lib
+    if path is None:
+        path = CHECKS_LIB_PATH if os.environ.get("SPH_GB300_CHECKS") == "1" else LIB_PATH
     if not os.path.exists(path):
-        raise RuntimeError(f"libsph_gb300.so is not built ({path}); run "
+        raise RuntimeError(f"{os.path.basename(path)} is not built ({path}); run "
                            "`python -m paper_1807_01341_gb300.build` -- there is no CPU fallback")
     L = ctypes.CDLL(path)
     P = ctypes.POINTER
@@ -108,6 +120,8 @@ def load(path: str = LIB_PATH):
     L.sph_set_time.argtypes = [_vp, _i64, _vp]
     L.sph_get_status.argtypes = [_vp, P(_i), P(_i64)]
     L.sph_clear_status.argtypes = [_vp, _vp]
+    L.sph_built_with_checks.argtypes = []
+    L.sph_get_check_report.argtypes = [_vp, P(_i), P(_i64), P(_i64)]
     L.sph_get_counters.argtypes = [_vp, P(sph_counters)]
     L.sph_reset_counters.argtypes = [_vp, _vp]
     L.sph_set_profiling.argtypes = [_vp, _i]
@@ -133,7 +147,7 @@ def load(path: str = LIB_PATH):
                  "sph_reset_counters", "sph_set_profiling", "sph_get_kernel_times",
                  "sph_reset_kernel_times", "sph_state_copy", "sph_resume", "sph_grid_density",
                  "sph_grid_density_bwd", "sph_step_bwd", "sph_diagnostics",
-                 "sph_get_bin_counts"):
+                 "sph_get_bin_counts", "sph_built_with_checks", "sph_get_check_report"):
         getattr(L, name).restype = _i
     _lib = L
     return L
@@ -149,7 +163,8 @@ def exported_symbols():
             "sph_get_counters", "sph_reset_counters", "sph_set_profiling",
             "sph_get_kernel_times", "sph_reset_kernel_times", "sph_cell_order_noalloc",
             "sph_state_copy", "sph_resume", "sph_grid_density", "sph_grid_density_bwd",
-            "sph_step_bwd", "sph_diagnostics", "sph_get_bin_counts", "sph_strerror"]
+            "sph_step_bwd", "sph_diagnostics", "sph_get_bin_counts", "sph_strerror",
+            "sph_built_with_checks", "sph_get_check_report"]
 
 
 class SphError(RuntimeError):

@@ -408,6 +408,7 @@ __global__ void __launch_bounds__(PT, 1) k_adj_force(View v, AdjWork w) {
       __syncthreads();
       if (item >= nq || st.failed) break;  // (st.failed is the same in every warp)
       const int wg = active_group(v, ds, item);
+      if (!SPH_IN(ds, wg, ds->n_groups, SPH_CHECK_GROUP)) break;
       force_adj_group<true>(v, w, wg, frame_of(v, ds, wg), st, wc);
     }
   } else {
@@ -417,6 +418,7 @@ __global__ void __launch_bounds__(PT, 1) k_adj_force(View v, AdjWork w) {
       item = __shfl_sync(FULL, item, 0);
       if (item >= nq || st.failed) break;
       const int wg = active_group(v, ds, item);
+      if (!SPH_IN(ds, wg, ds->n_groups, SPH_CHECK_GROUP)) break;
       force_adj_group<false>(v, w, wg, frame_of(v, ds, wg), st, wc);
     }
   }
@@ -666,6 +668,7 @@ __global__ void __launch_bounds__(PT, 1) k_adj_density(View v, AdjWork w) {
       __syncthreads();
       if (item >= nq || st.failed) break;  // (st.failed is the same in every warp)
       const int wg = active_group(v, ds, item);
+      if (!SPH_IN(ds, wg, ds->n_groups, SPH_CHECK_GROUP)) break;
       density_adj_group<PASS, true>(v, w, wg, frame_of(v, ds, wg), st, wc);
     }
   } else {
@@ -675,6 +678,7 @@ __global__ void __launch_bounds__(PT, 1) k_adj_density(View v, AdjWork w) {
       item = __shfl_sync(FULL, item, 0);
       if (item >= nq || st.failed) break;
       const int wg = active_group(v, ds, item);
+      if (!SPH_IN(ds, wg, ds->n_groups, SPH_CHECK_GROUP)) break;
       density_adj_group<PASS, false>(v, w, wg, frame_of(v, ds, wg), st, wc);
     }
   }

@@ -174,7 +174,10 @@ bool valid_params(const sph_params *p) {
   if (p->list_cap < 32 || p->list_cap > 4096) return false;
   if (!(p->search_margin >= 1.0 && p->search_margin <= 2.0)) return false;
   if (p->staging_depth < 1 || p->staging_depth > 3) return false;
-  if (p->wait_limit < 0 || p->test_stall < 0) return false;
+  if (p->wait_limit < 0 || p->test_stall < 0 || p->test_bad_group < 0) return false;
+#ifndef SPH_CHECKS
+  if (p->test_bad_group != 0) return false;  // only a checks build may plant a bad index
+#endif
   const int vars[3] = {p->balsara, p->predict_inactive, p->limiter};
   for (int f : vars)
     if (f != 0 && f != 1) return false;
@@ -351,7 +354,7 @@ void prof_collect(sph_ctx *ctx) {
 int permute_array(sph_ctx *ctx, void *arr, int elem, long long n, const unsigned int *perm,
                   cudaStream_t st) {
   if (!arr) return SPH_OK;
-  SPH_CUDA(launch_gather(ctx->b.scratch, arr, perm, n, elem, st));
+  SPH_CUDA(launch_gather(ctx->b.scratch, arr, perm, n, elem, st, ctx->b.ds));
   SPH_CUDA(cudaMemcpyAsync(arr, ctx->b.scratch, (size_t)n * elem, cudaMemcpyDeviceToDevice, st));
   return SPH_OK;
 }
@@ -400,7 +403,7 @@ int build_cells(sph_ctx *ctx, sph_particles *p, cudaStream_t st) {
   bool alt = false;
   SPH_CUDA(radix_sort_pairs(b.keys[0], b.vals[0], b.keys[1], b.vals[1], (int)n,
                             KEY_MORTON_BITS + cell_bits, b.hist, b.scan_tmp, b.n_hist_max, &alt,
-                            st));
+                            st, b.ds));
   unsigned long long *skeys = alt ? b.keys[1] : b.keys[0];
   unsigned int *perm = alt ? b.vals[1] : b.vals[0];
   SPH_TRY(permute_array(ctx, p->x, 8, n, perm, st));
@@ -418,7 +421,7 @@ int build_cells(sph_ctx *ctx, sph_particles *p, cudaStream_t st) {
   SPH_TRY(permute_array(ctx, p->div_v, 4, n, perm, st));
   SPH_TRY(permute_array(ctx, p->curl_v, 4, n, perm, st));
   if (n > 0) {
-    SPH_CUDA(launch_gather(b.perm_tmp, b.perm, perm, n, 4, st));
+    SPH_CUDA(launch_gather(b.perm_tmp, b.perm, perm, n, 4, st, b.ds));
     SPH_CUDA(cudaMemcpyAsync(b.perm, b.perm_tmp, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st));
     SPH_CUDA(cudaMemsetAsync(p->active, 0, (size_t)n, st));
   }
@@ -704,6 +707,7 @@ void sph_default_params(sph_params *p) {
   p->staging_depth = 1;
   p->wait_limit = 0;
   p->test_stall = 0;
+  p->test_bad_group = 0;
   p->balsara = 0;
   p->predict_inactive = 0;
   p->limiter = 0;
@@ -720,6 +724,7 @@ const char *sph_strerror(int code) {
     case SPH_ERR_TIMEOUT: return "bounded device wait timed out";
     case SPH_ERR_NOMEM: return "device allocation failed";
     case SPH_ERR_NOT_BUILT: return "cells not built";
+    case SPH_ERR_BOUNDS: return "device bounds check failed";
     default: return "unknown error";
   }
 }
@@ -773,6 +778,8 @@ int sph_create(const sph_params *params, int64_t n_max, sph_ctx **out) {
     }
     if (cudaMemset(b.ds, 0, sizeof(DevState)) != cudaSuccess ||
         cudaMemcpy(SPH_DS_FIELD(b.ds, test_stall), &params->test_stall, sizeof(int),
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(SPH_DS_FIELD(b.ds, test_bad_group), &params->test_bad_group, sizeof(int),
                    cudaMemcpyHostToDevice) != cudaSuccess) {
       r = SPH_ERR_CUDA;
       break;
@@ -1003,7 +1010,26 @@ int sph_get_status(sph_ctx *ctx, int *status, int64_t *detail) {
   SPH_CUDA(cudaMemcpy(ctx->b.h_ds, ctx->b.ds, sizeof(DevState), cudaMemcpyDeviceToHost));
   const DevState &h = *ctx->b.h_ds;
   if (status) *status = h.first_error;
-  if (detail) *detail = h.first_error ? (int64_t)h.err_count[h.first_error & 7] : 0;
+  if (detail) *detail = h.first_error ? (int64_t)h.err_count[h.first_error & 15] : 0;
+  return SPH_OK;
+}
+
+int sph_built_with_checks(void) {
+#ifdef SPH_CHECKS
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+int sph_get_check_report(sph_ctx *ctx, int *site, int64_t *index, int64_t *bound) {
+  if (!ctx) return SPH_ERR_ARG;
+  SPH_CUDA(cudaDeviceSynchronize());
+  SPH_CUDA(cudaMemcpy(ctx->b.h_ds, ctx->b.ds, sizeof(DevState), cudaMemcpyDeviceToHost));
+  const DevState &h = *ctx->b.h_ds;
+  if (site) *site = h.check_site;
+  if (index) *index = h.check_site ? (int64_t)h.check_index : 0;
+  if (bound) *bound = h.check_site ? (int64_t)h.check_bound : 0;
   return SPH_OK;
 }
 
@@ -1013,6 +1039,7 @@ int sph_clear_status(sph_ctx *ctx, void *stream) {
   SPH_CUDA(cudaMemsetAsync(SPH_DS_FIELD(ctx->b.ds, halt), 0, sizeof(unsigned int), st));
   SPH_CUDA(cudaMemsetAsync(SPH_DS_FIELD(ctx->b.ds, first_error), 0, sizeof(int), st));
   SPH_CUDA(cudaMemsetAsync(SPH_DS_FIELD(ctx->b.ds, err_count), 0, sizeof(((DevState *)0)->err_count), st));
+  SPH_CUDA(cudaMemsetAsync(SPH_DS_FIELD(ctx->b.ds, check_site), 0, sizeof(int), st));
   return SPH_OK;
 }
 

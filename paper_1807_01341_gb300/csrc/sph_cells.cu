@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(RS_THREADS)
 __global__ void __launch_bounds__(RS_THREADS)
     k_rs_scatter(const unsigned long long *__restrict__ keys, const unsigned int *__restrict__ vals,
                  unsigned long long *__restrict__ okeys, unsigned int *__restrict__ ovals, int n,
-                 int shift, const unsigned int *__restrict__ offs, int n_tiles) {
+                 int shift, const unsigned int *__restrict__ offs, int n_tiles, DevState *ds) {
   __shared__ unsigned int base[256];
   __shared__ unsigned int goff[256];
   __shared__ unsigned int wcnt[RS_THREADS / 32][256];
@@ -236,8 +236,10 @@ __global__ void __launch_bounds__(RS_THREADS)
       unsigned int pre = base[d];
       for (int k = 0; k < warp; k++) pre += wcnt[k][d];
       unsigned int pos = goff[d] + pre + rank;
-      okeys[pos] = key;
-      ovals[pos] = vals[idx];
+      if (SPH_IN(ds, pos, n, SPH_CHECK_SCATTER)) {
+        okeys[pos] = key;
+        ovals[pos] = vals[idx];
+      }
     }
     __syncthreads();
     unsigned int s = 0;
@@ -253,9 +255,12 @@ __global__ void __launch_bounds__(RS_THREADS)
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void k_gather(T *__restrict__ dst, const T *__restrict__ src,
-                         const unsigned int *__restrict__ idx, long long n) {
+                         const unsigned int *__restrict__ idx, long long n, DevState *ds) {
   long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (k < n) dst[k] = src[idx[k]];
+  if (k < n) {
+    const unsigned int s = idx[k];
+    if (SPH_IN(ds, s, n, SPH_CHECK_SCATTER)) dst[k] = src[s];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -573,7 +578,7 @@ cudaError_t exclusive_scan_u32(const unsigned int *in, unsigned int *out, int n,
 cudaError_t radix_sort_pairs(unsigned long long *keys, unsigned int *vals,
                              unsigned long long *keys_alt, unsigned int *vals_alt, int n,
                              int nbits, unsigned int *hist, unsigned int *scan_tmp,
-                             int n_hist_max, bool *result_in_alt, cudaStream_t st) {
+                             int n_hist_max, bool *result_in_alt, cudaStream_t st, DevState *ds) {
   *result_in_alt = false;
   if (n <= 1) return cudaSuccess;
   int n_tiles = (n + RS_TILE - 1) / RS_TILE;
@@ -585,7 +590,7 @@ cudaError_t radix_sort_pairs(unsigned long long *keys, unsigned int *vals,
     k_rs_hist<<<n_tiles, RS_THREADS, 0, st>>>(ka, n, shift, hist, n_tiles);
     cudaError_t e = exclusive_scan_u32(hist, hist, 256 * n_tiles, scan_tmp, st);
     if (e != cudaSuccess) return e;
-    k_rs_scatter<<<n_tiles, RS_THREADS, 0, st>>>(ka, va, kb, vb, n, shift, hist, n_tiles);
+    k_rs_scatter<<<n_tiles, RS_THREADS, 0, st>>>(ka, va, kb, vb, n, shift, hist, n_tiles, ds);
     std::swap(ka, kb);
     std::swap(va, vb);
     *result_in_alt = !*result_in_alt;
@@ -594,15 +599,15 @@ cudaError_t radix_sort_pairs(unsigned long long *keys, unsigned int *vals,
 }
 
 cudaError_t launch_gather(void *dst, const void *src, const unsigned int *idx, long long n,
-                          int elem_bytes, cudaStream_t st) {
+                          int elem_bytes, cudaStream_t st, DevState *ds) {
   note_launches(1);
   if (n == 0) return cudaSuccess;
   int b = blocks_for(n, 256);
   switch (elem_bytes) {
-    case 1: k_gather<uint8_t><<<b, 256, 0, st>>>((uint8_t *)dst, (const uint8_t *)src, idx, n); break;
-    case 4: k_gather<uint32_t><<<b, 256, 0, st>>>((uint32_t *)dst, (const uint32_t *)src, idx, n); break;
+    case 1: k_gather<uint8_t><<<b, 256, 0, st>>>((uint8_t *)dst, (const uint8_t *)src, idx, n, ds); break;
+    case 4: k_gather<uint32_t><<<b, 256, 0, st>>>((uint32_t *)dst, (const uint32_t *)src, idx, n, ds); break;
     case 8: k_gather<unsigned long long><<<b, 256, 0, st>>>((unsigned long long *)dst,
-                                                          (const unsigned long long *)src, idx, n); break;
+                                                          (const unsigned long long *)src, idx, n, ds); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -38,6 +38,7 @@ __global__ void k_mark_clear(View v) {
   const int nq = ds->n_active_leaves;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nq; k += gridDim.x * blockDim.x) {
     const int leaf = v.q_active[k];
+    if (!SPH_IN(ds, leaf, ds->n_leaves, SPH_CHECK_ACTIVE_LEAF)) continue;
     const int a = v.leaf_start[leaf], b = v.leaf_start[leaf + 1];
     for (int i = a; i < b; i++) v.active[i] = 0;
   }
@@ -125,6 +126,7 @@ __device__ void mark_particles_part(View &v, int b0, int nb) {
   unsigned long long cnt = 0;
   for (int k = t0; k < nq; k += nt) {
     const int leaf = v.q_active[k];
+    if (!SPH_IN(ds, leaf, ds->n_leaves, SPH_CHECK_ACTIVE_LEAF)) continue;
     const int a = v.leaf_start[leaf], b = v.leaf_start[leaf + 1];
     for (int i = a; i < b; i++) {
       const bool act = (int)v.bin[i] <= m_act;
@@ -354,6 +356,7 @@ __global__ void __launch_bounds__(UT) k_drift(View v) {
   const int nq = v.drift_all ? ds->n_chunks : ds->n_drift_chunks;
   for (int k = blockIdx.x; k < nq; k += gridDim.x) {
     const int g = v.drift_all ? k : v.q_drift[k];
+    if (!SPH_IN(v.ds, g, ds->n_chunks, SPH_CHECK_DRIFT_CHUNK)) continue;  // (block-uniform)
     chunk_update(v, g, true, false);
   }
 }
@@ -410,6 +413,7 @@ __global__ void k_kick(View v, int phase) {
   const int nq = ds->n_active_leaves, m_act = ds->m_act;
   for (int k = gwarp(); k < nq; k += nwarps()) {
     int leaf = v.q_active[k];
+    if (!SPH_IN(ds, leaf, ds->n_leaves, SPH_CHECK_ACTIVE_LEAF)) continue;  // (warp-uniform)
     int a = v.leaf_start[leaf], b = v.leaf_start[leaf + 1];
     for (int i = a + lane_id(); i < b; i += 32) {
       if ((int)v.bin[i] > m_act) continue;
@@ -437,6 +441,7 @@ __global__ void k_bins(View v) {
   const long long ti = ds->ti;
   for (int k = gwarp(); k < nq && !halted; k += nwarps()) {
     int leaf = v.q_active[k];
+    if (!SPH_IN(ds, leaf, ds->n_leaves, SPH_CHECK_ACTIVE_LEAF)) continue;  // (warp-uniform)
     int a = v.leaf_start[leaf], b = v.leaf_start[leaf + 1];
     int minb = 127;
     unsigned long long mask = 0ull;
@@ -538,6 +543,7 @@ __global__ void __launch_bounds__(UT) k_close_step(View v) {
   const long long ti = ds->ti;
   for (int k = gwarp(); k < nq; k += nwarps()) {
     const int leaf = v.q_active[k];
+    if (!SPH_IN(ds, leaf, ds->n_leaves, SPH_CHECK_ACTIVE_LEAF)) continue;  // (warp-uniform)
     const int a = v.leaf_start[leaf], b = v.leaf_start[leaf + 1];
     int minb = 127;
     unsigned long long mask = 0ull;

@@ -41,6 +41,7 @@ struct DevState {
                          // q_group, heavy ones from its back; see n_heavy_groups)
   int n_heavy_groups;    // active work groups whose estimated cost is well above the mean
   int test_stall;        // testing: density launches whose first warp still has to stall
+  int test_bad_group;    // testing (checks build): density launches still to plant a bad group
   unsigned long long group_cost_sum;  // sum over work groups of group_cost (written at build)
   double w;              // cell width
   // queues (written by mark)
@@ -58,7 +59,11 @@ struct DevState {
   // errors
   unsigned int halt;      // a step-invalidating error happened: kernels return
   int first_error;        // first SPH_ERR_* code recorded
-  unsigned long long err_count[8];
+  unsigned long long err_count[16];
+  // first failed bounds check (a library built with SPH_CHECKS)
+  int check_site;         // sph_check_site (0: none)
+  int check_pad;
+  long long check_index, check_bound;
   // rebuild criterion
   unsigned int excursion_bits;  // max distance (float bits) of a particle outside its cell
   unsigned int Hmax_bits;       // max kernel support H (float bits) over all particles
@@ -170,9 +175,32 @@ struct AdjWork {
 __device__ __forceinline__ void record_error(DevState *ds, int code, unsigned long long count,
                                              bool halt) {
   atomicCAS(&ds->first_error, 0, code);
-  atomicAdd(&ds->err_count[code & 7], count);
+  atomicAdd(&ds->err_count[code & 15], count);
   if (halt) atomicExch(&ds->halt, 1u);
 }
+
+// Device bounds checks.  SPH_IN(ds, i, n, site) is true when 0 <= i < n.  In
+// a library compiled with -DSPH_CHECKS a false result records SPH_ERR_BOUNDS
+// (halting the step) and, for the first failure, the site, index and bound;
+// the caller then skips the access.  (ds may be null: the access is skipped
+// and nothing is recorded.)  Without SPH_CHECKS the test compiles
+// away (always true).
+#ifdef SPH_CHECKS
+static __device__ __noinline__ bool check_failed(DevState *ds, int site, long long i, long long n) {
+  if (!ds) return false;  // (a caller without a device state: the access is skipped)
+  if (atomicCAS(&ds->check_site, 0, site) == 0) {
+    ds->check_index = i;
+    ds->check_bound = n;
+  }
+  record_error(ds, SPH_ERR_BOUNDS, 1, true);
+  return false;
+}
+#define SPH_IN(ds, i, n, site)                                                           \
+  ((unsigned long long)(long long)(i) < (unsigned long long)(long long)(n) ||          \
+   ::sph::check_failed((ds), (site), (long long)(i), (long long)(n)))
+#else
+#define SPH_IN(ds, i, n, site) true
+#endif
 
 __device__ __forceinline__ void atomic_max_float_pos(unsigned int *addr, float v) {
   // non-negative floats order like their bit patterns
@@ -231,11 +259,12 @@ cudaError_t launch_cell_keys(const View &v, int nc, double w, unsigned long long
 cudaError_t radix_sort_pairs(unsigned long long *keys, unsigned int *vals,
                              unsigned long long *keys_alt, unsigned int *vals_alt, int n,
                              int nbits, unsigned int *hist, unsigned int *scan_tmp,
-                             int n_hist_max, bool *result_in_alt, cudaStream_t st);
+                             int n_hist_max, bool *result_in_alt, cudaStream_t st,
+                             DevState *ds);  // ds: where a failed bounds check is recorded (may be null)
 cudaError_t exclusive_scan_u32(const unsigned int *in, unsigned int *out, int n,
                                unsigned int *tmp, cudaStream_t st);
 cudaError_t launch_gather(void *dst, const void *src, const unsigned int *idx, long long n,
-                          int elem_bytes, cudaStream_t st);
+                          int elem_bytes, cudaStream_t st, DevState *ds);
 cudaError_t launch_cell_start(const unsigned long long *sorted_keys, long long n, int n_cells,
                               int32_t *cell_start, int32_t *pcell, cudaStream_t st);
 // Leaves of every cell in particle order (leaf_start[n_leaves] = n), their

@@ -127,7 +127,7 @@ extern "C" int sph_cell_order_noalloc(const double *x, const double *y, const do
   // every buffer the sort reads is written first in each call: nothing to clear
   bool alt = false;
   if (radix_sort_pairs(keys0, vals0, keys1, vals1, (int)n, KEY_MORTON_BITS + cell_bits, hist, scan,
-                       256 * NOALLOC_TILES, &alt, st) != cudaSuccess)
+                       256 * NOALLOC_TILES, &alt, st, nullptr) != cudaSuccess)
     return SPH_ERR_CUDA;
   if (cudaMemcpyAsync(perm, alt ? vals1 : vals0, sizeof(int32_t) * (size_t)n,
                       cudaMemcpyDeviceToDevice, st) != cudaSuccess)

@@ -313,8 +313,19 @@ __device__ __forceinline__ Group group_of(const View &v, int g, const CellFrame 
   Group G;
   G.L0 = v.group_leaf0[g];
   G.L1 = v.group_leaf0[g + 1];
+  // (checks build: at most WG_MAX leaves in range, then at most WG_MAX
+  // particles in range; otherwise an empty group)
+  if (!(SPH_IN(v.ds, G.L0, G.L1, SPH_CHECK_GROUP_LEAVES) &&
+        SPH_IN(v.ds, G.L1 - 1, v.ds->n_leaves, SPH_CHECK_GROUP_LEAVES) &&
+        SPH_IN(v.ds, G.L1 - G.L0 - 1, WG_MAX, SPH_CHECK_GROUP_LEAVES)))
+    G.L0 = G.L1 = 0;
   G.a = v.leaf_start[G.L0];
   G.b = v.leaf_start[G.L1];
+  if (!(SPH_IN(v.ds, G.a, G.b + 1, SPH_CHECK_LEAF) && SPH_IN(v.ds, G.b, v.n + 1, SPH_CHECK_LEAF) &&
+        SPH_IN(v.ds, G.b - G.a, WG_MAX + 1, SPH_CHECK_GROUP_SIZE))) {
+    G.L0 = G.L1 = 0;
+    G.a = G.b = 0;
+  }
   const int lane = lane_id();
   float lx = INFINITY, ly = INFINITY, lz = INFINITY, hx = -INFINITY, hy = -INFINITY, hz = -INFINITY;
   if (G.L0 + lane < G.L1) {
@@ -342,7 +353,9 @@ __device__ __forceinline__ Group group_of(const View &v, int g, const CellFrame 
 
 // offset of particle i's leaf corner from the group frame's corner
 __device__ __forceinline__ float3 leaf_offset(const View &v, int i, const CellFrame &F) {
-  const uint32_t k = v.leaf_k[v.pleaf[i]];
+  const int l = v.pleaf[i];
+  if (!SPH_IN(v.ds, l, v.ds->n_leaves, SPH_CHECK_PARTICLE_LEAF)) return make_float3(0.f, 0.f, 0.f);
+  const uint32_t k = v.leaf_k[l];
   return make_float3((float)(leaf_kx(k) - F.kx) * F.wq, (float)(leaf_ky(k) - F.ky) * F.wq,
                      (float)(leaf_kz(k) - F.kz) * F.wq);
 }
@@ -463,6 +476,13 @@ __device__ __forceinline__ int search(const View &v, const CellFrame &F, const R
       nch = v.cell_chunk_start[cj + 1] - g0;
       l0 = v.cell_leaf_start[cj];
       l1 = v.cell_leaf_start[cj + 1];
+      // (checks build: a cell whose leaf or chunk range is out of bounds is skipped)
+      if (!(SPH_IN(v.ds, l0, l1 + 1, SPH_CHECK_CELL_LEAVES) &&
+            SPH_IN(v.ds, l1, v.ds->n_leaves + 1, SPH_CHECK_CELL_LEAVES) &&
+            SPH_IN(v.ds, g0, v.ds->n_chunks + 1, SPH_CHECK_CELL_LEAVES) &&
+            SPH_IN(v.ds, g0 + nch, v.ds->n_chunks + 1, SPH_CHECK_CELL_LEAVES) &&
+            SPH_IN(v.ds, (long long)CHUNK * nch - (l1 - l0), CHUNK, SPH_CHECK_CELL_LEAVES)))
+        nch = 0;
     }
   }
   const int cstart = warp_incl_scan(nch) - nch;  // first flat chunk index of this lane's cell
@@ -534,7 +554,11 @@ __device__ __forceinline__ int search(const View &v, const CellFrame &F, const R
           const int dxc = ci / 9 - 1, dyc = (ci / 3) % 3 - 1, dzc = ci % 3 - 1;
           // every load of the round depends only on l: one memory round trip
           const uint32_t kl = v.leaf_k[l];
-          const int la = v.leaf_start[l], lb = v.leaf_start[l + 1];
+          int la = v.leaf_start[l], lb = v.leaf_start[l + 1];
+          // (checks build: a leaf whose particle range is out of bounds is empty)
+          if (!(SPH_IN(v.ds, la, lb + 1, SPH_CHECK_LEAF) && SPH_IN(v.ds, lb, v.n + 1, SPH_CHECK_LEAF) &&
+                SPH_IN(v.ds, lb - la, LEAF_MAX_LIMIT + 1, SPH_CHECK_LEAF)))
+            la = lb = 0;
           sx = (float)(dxc * (1 << MORTON_BITS) - F.kx + leaf_kx(kl)) * F.wq;
           sy = (float)(dyc * (1 << MORTON_BITS) - F.ky + leaf_ky(kl)) * F.wq;
           sz = (float)(dzc * (1 << MORTON_BITS) - F.kz + leaf_kz(kl)) * F.wq;
@@ -574,12 +598,13 @@ __device__ __forceinline__ int search(const View &v, const CellFrame &F, const R
 // batch is as many consecutive listed leaves as fit one buffer.  When a batch
 // has landed, each position record is moved into the work group's frame (its
 // leaf's corner offset added) and tagged with its particle index and
-// neighbour-cell index; then consume(base, total) sees records base ..
-// base + total - 1.  Batches are consumed in list order whatever the depth.
+// neighbour-cell index (TAG; a loop that reads only the positions skips the
+// tags); then consume(base, total) sees records base .. base + total - 1.
+// Batches are consumed in list order whatever the depth.
 // A barrier wait that gives up sets st.failed and counts a timeout; the warp
 // then waits (bounded again) for every copy it still has in flight before it
 // returns, so that no copy lands in shared memory the warp has left.
-template <int S, int NREC, int LC, class Consume>
+template <bool TAG = true, int S, int NREC, int LC, class Consume>
 __device__ __forceinline__ void stage_list(const float4 *const *srcs, Stage<S, NREC, LC> &st,
                                            int nlist, Consume consume, WarpCounters &wc) {
   const int lane = lane_id();
@@ -648,14 +673,17 @@ __device__ __forceinline__ void stage_list(const float4 *const *srcs, Stage<S, N
       const int pk = st.lpack[e + q];
       const int cq = pk & 0xffff;
       const int ja = __float_as_int(sh.w);
+      (void)ja;
       for (int t = lane; t < cq; t += 32) {
         float4 rr = st.rec[base + t];
         rr.x += sh.x;
         rr.y += sh.y;
         rr.z += sh.z;
         st.rec[base + t] = rr;
-        st.recj[base + t] = ja + t;
-        st.recc[base + t] = (uint8_t)(pk >> 16);
+        if constexpr (TAG) {
+          st.recj[base + t] = ja + t;
+          st.recc[base + t] = (uint8_t)(pk >> 16);
+        }
       }
       base += cq;
     }

@@ -95,17 +95,28 @@ __device__ __forceinline__ void dens_pair(DSum &s, float r2, float mj, float H2,
   if (++s.since == DFOLD) s.fold_all();
 }
 
-// Entries [0, nl) of a neighbour list (entry k at lst[k * ls]), in order; the
-// next entry's load is issued before the current one is evaluated.
+// Entries [0, nl) of a neighbour list (entry k at lst[k * ls]), in order, in
+// blocks of LQ: the loads of the next block are issued before the current
+// block is evaluated, so a warp running alone (a sparse step) waits for one
+// L2 round trip per LQ entries rather than per entry.
+constexpr int LQ = 4;
 __device__ __forceinline__ void dens_list(DSum &s, const float2 *lst, int ls, int nl, float H2,
                                           float Hinv) {
   if (nl <= 0) return;
-  float2 e = __ldcg(lst);
+  float2 e[LQ];
+#pragma unroll
+  for (int j = 0; j < LQ; j++) e[j] = j < nl ? __ldcg(lst + (size_t)j * ls) : make_float2(INFINITY, 0.0f);
 #pragma unroll 1
-  for (int k = 1; k <= nl; k++) {
-    const float2 cur = e;
-    if (k < nl) e = __ldcg(lst + (size_t)k * ls);
-    dens_pair(s, cur.x, cur.y, H2, Hinv);
+  for (int k = 0; k < nl; k += LQ) {
+    float2 cur[LQ];
+#pragma unroll
+    for (int j = 0; j < LQ; j++) {
+      cur[j] = e[j];
+      const int kn = k + LQ + j;
+      e[j] = kn < nl ? __ldcg(lst + (size_t)kn * ls) : make_float2(INFINITY, 0.0f);
+    }
+#pragma unroll
+    for (int j = 0; j < LQ; j++) dens_pair(s, cur[j].x, cur[j].y, H2, Hinv);
   }
 }
 
@@ -302,7 +313,7 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
               nlist = search(v, F, reach, st, leaf_ok, chunk_ok, skip, more, part);
               complete = complete && !more;
             }
-            stage_list(srcs, st, nlist, consume, wc);
+            stage_list<false>(srcs, st, nlist, consume, wc);  // (positions only: no tags)
             skip += nlist;
           } while (search_now && more && !st.failed);
           if (search_now) have_list = complete;
@@ -900,6 +911,18 @@ __device__ __forceinline__ void flush_counters(DevState *ds, WarpCounters &wc, b
 }
 
 
+// Testing (a library built with SPH_CHECKS; sph_params.test_bad_group): the
+// first test_bad_group claims replace the work group taken from the queue by
+// an index past the last group, which the SPH_CHECK_GROUP check catches.
+__device__ __forceinline__ int planted_group(DevState *ds, int wg) {
+#ifdef SPH_CHECKS
+  if (ds->test_bad_group > 0 && atomicSub(&ds->test_bad_group, 1) > 0) return ds->n_groups + 7;
+#else
+  (void)ds;
+#endif
+  return wg;
+}
+
 template <int G>
 __global__ void __launch_bounds__(PT, 2) k_density(View v, int flags, int bin_filter, int persistent) {
   DevState *ds = v.ds;
@@ -941,14 +964,17 @@ __global__ void __launch_bounds__(PT, 2) k_density(View v, int flags, int bin_fi
     // shared groups first, a block each, pulled from a head (persistent
     // launches: every block; per-bin launches: the first cb blocks)
     if (persistent || (int)blockIdx.x < cb) {
-      __shared__ int s_item;
+      __shared__ int s_item, s_wg;
       for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(&ds->head_coop_density, 1);
+        if (threadIdx.x == 0) {
+          s_item = atomicAdd(&ds->head_coop_density, 1);
+          s_wg = s_item < qs.ncoop ? planted_group(ds, coop_group(v, ds, bin_filter, s_item)) : 0;
+        }
         __syncthreads();
-        const int item = s_item;
+        const int item = s_item, wg = s_wg;
         __syncthreads();
         if (item >= qs.ncoop || st.failed) break;
-        const int wg = coop_group(v, ds, bin_filter, item);
+        if (!SPH_IN(ds, wg, ds->n_groups, SPH_CHECK_GROUP)) break;
         density_group<1, true>(v, wg, flags, bin_filter, m_act, frame_of(v, ds, wg), hcap, exc,
                                ti, st, wc);
       }
@@ -966,7 +992,10 @@ __global__ void __launch_bounds__(PT, 2) k_density(View v, int flags, int bin_fi
         item = k == 0 ? ((int)blockIdx.x - cb) * WARPS_PER_BLOCK + warp : qs.nwarp;
       }
       if (item >= qs.nwarp || st.failed) break;
-      const int wg = warp_group<G>(v, ds, bin_filter, item);
+      int wg = warp_group<G>(v, ds, bin_filter, item);
+      if (lane == 0) wg = planted_group(ds, wg);
+      wg = __shfl_sync(FULL, wg, 0);
+      if (!SPH_IN(ds, wg, ds->n_groups, SPH_CHECK_GROUP)) break;
       density_group<G, false>(v, wg, flags, bin_filter, m_act, frame_of(v, ds, wg), hcap, exc, ti,
                               st, wc);
     }
@@ -1006,6 +1035,7 @@ __global__ void __launch_bounds__(PT, 2) k_force(View v, int bin_filter, int per
         __syncthreads();
         if (item >= qs.ncoop || st.failed) break;
         const int wg = coop_group(v, ds, bin_filter, item);
+        if (!SPH_IN(ds, wg, ds->n_groups, SPH_CHECK_GROUP)) break;
         force_group<1, true, VAR>(v, wg, bin_filter, m_act, frame_of(v, ds, wg), Hmax, exc, st,
                                   wc);
       }
@@ -1023,6 +1053,7 @@ __global__ void __launch_bounds__(PT, 2) k_force(View v, int bin_filter, int per
       }
       if (item >= qs.nwarp || st.failed) break;
       const int wg = warp_group<G>(v, ds, bin_filter, item);
+      if (!SPH_IN(ds, wg, ds->n_groups, SPH_CHECK_GROUP)) break;
       force_group<G, false, VAR>(v, wg, bin_filter, m_act, frame_of(v, ds, wg), Hmax, exc, st,
                                  wc);
     }
@@ -1054,6 +1085,7 @@ __global__ void __launch_bounds__(PT, 2) k_gradient(View v) {
     item = __shfl_sync(FULL, item, 0);
     if (item >= nq || st.failed) break;
     const int wg = active_group(v, ds, item);
+    if (!SPH_IN(ds, wg, ds->n_groups, SPH_CHECK_GROUP)) break;
     gradient_group(v, wg, m_act, frame_of(v, ds, wg), s_exc, st, wc);
   }
   if (lane == 0 && wc.timeout) record_error(ds, SPH_ERR_TIMEOUT, wc.timeout, true);
@@ -1122,6 +1154,7 @@ __global__ void k_entropy_from_u(View v) {
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nq; k += nw) {
     const int leaf = v.q_active[k];
+    if (!SPH_IN(ds, leaf, ds->n_leaves, SPH_CHECK_ACTIVE_LEAF)) continue;
     const int a = v.leaf_start[leaf], b = v.leaf_start[leaf + 1];
     for (int i = a + lane_id(); i < b; i += 32)
       if ((int)v.bin[i] <= m_act) v.A[i] = (g - 1.0f) * v.A[i] / powf(v.rho[i], g - 1.0f);

@@ -46,6 +46,7 @@ class Params:
     staging_depth: int = 1
     wait_limit: int = 0
     test_stall: int = 0
+    test_bad_group: int = 0
     balsara: int = 0
     predict_inactive: int = 0
     limiter: int = 0
@@ -293,6 +294,14 @@ class Context:
 
     def clear_status(self, stream=None):
         check(self.L.sph_clear_status(self.h, _stream_ptr(stream)), "sph_clear_status")
+
+    def check_report(self):
+        """(site, index, bound) of the first failed device bounds check since the
+        status was last cleared (site 0: none; always 0 without SPH_CHECKS)."""
+        site, idx, bound = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64()
+        check(self.L.sph_get_check_report(self.h, ctypes.byref(site), ctypes.byref(idx),
+                                          ctypes.byref(bound)), "sph_get_check_report")
+        return site.value, idx.value, bound.value
 
     def counters(self) -> dict:
         c = _lib.sph_counters()

@@ -39,6 +39,36 @@ def test_library_exports_every_declared_symbol(libpath):
             assert hasattr(lib, name), name
 
 
+def test_checks_library_exports_the_same_symbols_and_reports_its_build(libpath):
+    """The build with device bounds checks (-DSPH_CHECKS) exports every declared
+    entry point, says it was built with checks, and the plain one says it was
+    not (neither call touches a GPU)."""
+    from paper_1807_01341_gb300 import build
+    plain = ctypes.CDLL(libpath)
+    checked = ctypes.CDLL(build.CHECKS_LIB)
+    for name in _declared("sph.h"):
+        assert hasattr(checked, name), name
+    assert plain.sph_built_with_checks() == 0
+    assert checked.sph_built_with_checks() == 1
+
+
+def test_plain_library_refuses_a_planted_bad_index(libpath):
+    """test_bad_group plants an out-of-range work group for the bounds checks to
+    catch; a library without checks must refuse it (sph_create: SPH_ERR_ARG)
+    before anything reaches a GPU."""
+    from paper_1807_01341_gb300 import _lib
+    lib = ctypes.CDLL(libpath)
+    lib.sph_default_params.argtypes = [ctypes.POINTER(_lib.sph_params)]
+    lib.sph_create.argtypes = [ctypes.POINTER(_lib.sph_params), ctypes.c_int64,
+                               ctypes.POINTER(ctypes.c_void_p)]
+    p = _lib.sph_params()
+    lib.sph_default_params(ctypes.byref(p))
+    p.test_bad_group = 1
+    h = ctypes.c_void_p()
+    assert lib.sph_create(ctypes.byref(p), 1000, ctypes.byref(h)) == _lib.SPH_ERR_ARG
+    assert not h.value
+
+
 def test_binding_names_match_header(libpath):
     from paper_1807_01341_gb300 import _lib
     assert sorted(_lib.exported_symbols()) == _declared("sph.h")
