@@ -101,11 +101,12 @@ typedef struct {
                            cell width >= the largest support) */
   double heavy_factor;  /* > 0: a work group whose estimated search cost exceeds
                            heavy_factor times the mean is started first and, with one
-                           lane per particle, shared by the 8 warps of a block; <= 0: no
-                           group is treated so */
+                           lane per particle, shared in the force loop by the 8 warps of
+                           a block; <= 0: no group is treated so */
   int coop_max_groups;  /* with one lane per particle: a step with at most this many
-                           active work groups hands every one to the 8 warps of a block
-                           (0: never; -1: twice the persistent grid's block count) */
+                           active work groups hands every one, in the force loop, to the
+                           8 warps of a block (0: never; -1: twice the persistent grid's
+                           block count).  The density loop takes every group one per warp. */
   int list_cap;         /* density loop: entries of each active particle's neighbour list
                            (squared distance and mass of every candidate within
                            search_margin x its support, kept across the h iterations;

@@ -507,11 +507,9 @@ int plain_body(sph_ctx *ctx, const View &v, int flags, cudaStream_t st) {
     SPH_CUDA(cudaMemcpyAsync(nq, SPH_DS_FIELD(v.ds, n_bin_groups), 2 * sizeof(int),
                              cudaMemcpyDeviceToHost, st));
     SPH_CUDA(cudaStreamSynchronize(st));
-    // blocks for the shared groups (at most one per neighbour-list slot), then
-    // one warp per group
-    // the bin's groups pulled from a head by at most the persistent grid's
-    // blocks (each warp has its own neighbour-list area)
-    const int want = nq[1] + (nq[0] + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
+    // the bin's groups, one per warp, pulled from a head by at most the
+    // persistent grid's blocks (each warp has its own neighbour-list area)
+    const int want = (nq[0] + nq[1] + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
     prof_begin(ctx, 0, st);
     SPH_CUDA(launch_density(v, flags, bins[k], true, std::min(want, ctx->list_blocks), st));
     prof_end(ctx, 0, st);

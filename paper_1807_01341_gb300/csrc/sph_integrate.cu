@@ -58,7 +58,7 @@ __global__ void k_begin_step(View v, long long ti_arg) {
   ds->n_heavy_groups = 0;
   ds->head_density = ds->head_force = ds->head_drift = ds->head_kick = 0;
   ds->head_open = ds->head_bins = ds->head_misc = 0;
-  ds->head_coop_density = ds->head_coop_force = ds->head_grad = 0;
+  ds->head_coop_force = ds->head_grad = 0;
   ds->s_pairs_density = ds->s_pairs_force = 0ull;
   ds->s_cand_density = ds->s_cand_force = 0ull;
   ds->s_iters_density = ds->s_active_particles = 0ull;
@@ -745,13 +745,10 @@ cudaError_t launch_mark_bin(const View &v, int bin, cudaStream_t st) {
   note_launches(1);
   cudaError_t e = cudaMemsetAsync(SPH_DS_FIELD(v.ds, n_bin_groups), 0, 2 * sizeof(int), st);
   if (e != cudaSuccess) return e;
-  // the heads of the blocks that take the shared groups (head_coop_force follows)
-  static_assert(offsetof(DevState, head_coop_force) ==
-                    offsetof(DevState, head_coop_density) + sizeof(int),
-                "the two coop heads are adjacent");
-  e = cudaMemsetAsync(SPH_DS_FIELD(v.ds, head_coop_density), 0, 2 * sizeof(int), st);
+  // the head of the force loop's blocks that take the shared groups
+  e = cudaMemsetAsync(SPH_DS_FIELD(v.ds, head_coop_force), 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  // (the per-bin density launch pulls its groups from head_density too)
+  // (the per-bin density launch pulls its groups from head_density)
   e = cudaMemsetAsync(SPH_DS_FIELD(v.ds, head_density), 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   k_mark_bin<<<v.grid_util, UT, 0, st>>>(v, bin);

@@ -52,8 +52,8 @@ struct DevState {
   int n_bin_coop;        // plain form: the heavy ones among them (back of q_bin)
   // persistent-kernel work heads
   int head_density, head_force, head_drift, head_kick;
-  int head_open, head_bins, head_misc, head_coop_density;
-  int head_coop_force;
+  int head_open, head_bins, head_misc;
+  int head_coop_force;        // force loop: shared work groups taken so far
   int head_grad;              // gradient loop (velocity divergence and curl)
   unsigned int blocks_done;   // blocks of the closing kernel of a step that have finished
   // errors
@@ -148,6 +148,7 @@ struct View {
   int balsara, predict, limiter;  // variants of the scheme (0/1)
   double heavy_factor;       // heavy work group: estimated cost > heavy_factor x mean
   int coop_max_groups;       // steps with at most this many active groups: all cooperative
+                             // (force loop)
   int h_max_iter, bin_cap, leaf_max, G, drift_all;
   int grid_util;             // blocks of the grid-stride utility kernels
 };

@@ -98,14 +98,17 @@ __device__ __forceinline__ void dens_pair(DSum &s, float r2, float mj, float H2,
 // Entries [0, nl) of a neighbour list (entry k at lst[k * ls]), in order, in
 // blocks of LQ: the loads of the next block are issued before the current
 // block is evaluated, so a warp running alone (a sparse step) waits for one
-// L2 round trip per LQ entries rather than per entry.
+// L2 round trip per LQ entries rather than per entry.  The loads may be
+// served by L1 (every later h iteration reads the list again): each lane
+// reads only entries it wrote itself, and a list area is used by one warp of
+// one launch (L1 lines are invalidated between dependent launches).
 constexpr int LQ = 4;
 __device__ __forceinline__ void dens_list(DSum &s, const float2 *lst, int ls, int nl, float H2,
                                           float Hinv) {
   if (nl <= 0) return;
   float2 e[LQ];
 #pragma unroll
-  for (int j = 0; j < LQ; j++) e[j] = j < nl ? __ldcg(lst + (size_t)j * ls) : make_float2(INFINITY, 0.0f);
+  for (int j = 0; j < LQ; j++) e[j] = j < nl ? lst[(size_t)j * ls] : make_float2(INFINITY, 0.0f);
 #pragma unroll 1
   for (int k = 0; k < nl; k += LQ) {
     float2 cur[LQ];
@@ -113,7 +116,7 @@ __device__ __forceinline__ void dens_list(DSum &s, const float2 *lst, int ls, in
     for (int j = 0; j < LQ; j++) {
       cur[j] = e[j];
       const int kn = k + LQ + j;
-      e[j] = kn < nl ? __ldcg(lst + (size_t)kn * ls) : make_float2(INFINITY, 0.0f);
+      e[j] = kn < nl ? lst[(size_t)kn * ls] : make_float2(INFINITY, 0.0f);
     }
 #pragma unroll
     for (int j = 0; j < LQ; j++) dens_pair(s, cur[j].x, cur[j].y, H2, Hinv);
@@ -136,16 +139,18 @@ __device__ __forceinline__ void dens_list(DSum &s, const float2 *lst, int ls, in
 // each pass listing (and summing) the next list_cap accepted records, and the
 // particle's list is then not kept (later iterations gather at R_i = H).
 // Whatever the capacity, margin or staging depth, a particle's sums visit the
-// same pairs in the same order with the same arithmetic.
-template <int G, bool COOP>
+// same pairs in the same order with the same arithmetic.  A work group is
+// handled by one warp (sharing it between the warps of a block, as the force
+// loop does in sparse steps, was measured slower here: every warp pays the
+// search's latency, then waits at the barriers of each h iteration).
+template <int G>
 __device__ void density_group(const View &v, int wg, int flags, int bin_filter, int m_act,
                               const CellFrame &F, float hcap, float exc, long long ti,
                               StageD &st, WarpCounters &wc) {
-  static_assert(!COOP || G == 1, "cooperative groups use one lane per particle");
   const int lane = lane_id();
   const int warp = threadIdx.x >> 5;
-  const int part = COOP ? warp : -1;
-  const bool writer = !COOP || warp == 0;  // the warp that writes results
+  constexpr int part = -1;       // (every chunk of the neighbour cells)
+  constexpr bool writer = true;  // the warp writes its particles' results
   const Group W = group_of(v, wg, F);
   const int a = W.a, b = W.b;
   const int nact = leaf_actives(v, a, b, m_act, bin_filter, st.act);
@@ -343,53 +348,14 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
         keep = false;
         nl = -1;  // the list holds only the last pass's share
       }
-      if (!COOP && st.failed) break;
+      if (st.failed) break;
       s.fold_all();
-      double sn, stt, s2;
-      float sr, srt;
-      int cnt;
-      if constexpr (COOP) {
-        // combine the 8 warps' partial sums, in warp order
-        float *mine = red_area<StageD>(warp);
-        mine[0 * 32 + lane] = s.n_hi; mine[1 * 32 + lane] = s.n_lo;
-        mine[2 * 32 + lane] = s.t_hi; mine[3 * 32 + lane] = s.t_lo;
-        mine[4 * 32 + lane] = s.r_hi; mine[5 * 32 + lane] = s.r_lo;
-        mine[6 * 32 + lane] = s.rt_hi; mine[7 * 32 + lane] = s.rt_lo;
-        reinterpret_cast<int *>(mine)[8 * 32 + lane] = s.cnt;
-        reinterpret_cast<int *>(mine)[9 * 32 + lane] = st.failed ? 1 : 0;
-        mine[10 * 32 + lane] = s.p2;
-        __syncthreads();
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, a4 = 0.0;
-        int c = 0, fl = 0;
-        for (int w = 0; w < WARPS_PER_BLOCK; w++) {
-          const float *rw = red_area<StageD>(w);
-          a0 += (double)rw[0 * 32 + lane] + (double)rw[1 * 32 + lane];
-          a1 += (double)rw[2 * 32 + lane] + (double)rw[3 * 32 + lane];
-          a2 += (double)rw[4 * 32 + lane] + (double)rw[5 * 32 + lane];
-          a3 += (double)rw[6 * 32 + lane] + (double)rw[7 * 32 + lane];
-          c += reinterpret_cast<const int *>(rw)[8 * 32 + lane];
-          fl |= reinterpret_cast<const int *>(rw)[9 * 32 + lane];
-          a4 += (double)rw[10 * 32 + lane];
-        }
-        fl = __any_sync(FULL, fl != 0) ? 1 : 0;
-        __syncthreads();
-        fence_proxy_async();
-        if (fl) st.failed = true;
-        if (st.failed) break;  // the same decision in every warp
-        sn = a0;
-        stt = a1;
-        sr = (float)a2;
-        srt = (float)a3;
-        s2 = a4;
-        cnt = c - 1;
-      } else {
-        sn = group_sum<G>((double)s.n_hi + (double)s.n_lo);
-        stt = group_sum<G>((double)s.t_hi + (double)s.t_lo);
-        sr = (float)group_sum<G>((double)s.r_hi + (double)s.r_lo);
-        srt = (float)group_sum<G>((double)s.rt_hi + (double)s.rt_lo);
-        s2 = group_sum<G>((double)s.p2);
-        cnt = group_sum_i<G>(s.cnt) - 1;  // (the particle itself is among its candidates)
-      }
+      const double sn = group_sum<G>((double)s.n_hi + (double)s.n_lo);
+      const double stt = group_sum<G>((double)s.t_hi + (double)s.t_lo);
+      const float sr = (float)group_sum<G>((double)s.r_hi + (double)s.r_lo);
+      const float srt = (float)group_sum<G>((double)s.rt_hi + (double)s.rt_lo);
+      const double s2 = group_sum<G>((double)s.p2);
+      const int cnt = group_sum_i<G>(s.cnt) - 1;  // (the particle itself is among its candidates)
       if (!done) {
         // Halley step in FP64 (Newton where its denominator is not positive),
         // kept inside the bracket [lo, hi] (F grows with h).  With
@@ -846,8 +812,8 @@ __device__ void gradient_group(const View &v, int wg, int m_act, const CellFrame
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
-// The work of a pair-loop launch: `ncoop` heavy work groups processed by
-// whole blocks (one lane per particle only), then `nwarp` groups one warp each.
+// The work of a force launch: `ncoop` heavy work groups processed by whole
+// blocks (one lane per particle only), then `nwarp` groups one warp each.
 // Batched form: the step's active groups (heavy ones from the back of
 // q_group); plain form: the groups of one bin (q_bin, same layout).
 struct Queues {
@@ -911,6 +877,23 @@ __device__ __forceinline__ void flush_counters(DevState *ds, WarpCounters &wc, b
 }
 
 
+// The work of a density launch: every work group, one per warp.  Per-bin
+// launches take the bin's groups (q_bin: those at the front, then those kept
+// at the back for the force loop's shared groups); whole-step launches take
+// the active queue (heavy groups first).
+__device__ __forceinline__ int density_count(const DevState *ds, int bin_filter) {
+  return bin_filter >= 0 ? ds->n_bin_groups + ds->n_bin_coop
+                         : ds->n_active_groups + ds->n_heavy_groups;
+}
+__device__ __forceinline__ int density_item(const View &v, const DevState *ds, int bin_filter,
+                                            int k) {
+  if (bin_filter >= 0) {
+    const int nl = ds->n_bin_groups;
+    return k < nl ? v.q_bin[k] : v.q_bin[ds->n_groups - 1 - (k - nl)];
+  }
+  return active_group(v, ds, k);
+}
+
 // Testing (a library built with SPH_CHECKS; sph_params.test_bad_group): the
 // first test_bad_group claims replace the work group taken from the queue by
 // an index past the last group, which the SPH_CHECK_GROUP check catches.
@@ -956,49 +939,25 @@ __global__ void __launch_bounds__(PT, 2) k_density(View v, int flags, int bin_fi
   const float hcap = (float)((w - 2.0 * (double)exc) / GAMMA_K_D * (1.0 - 1e-6));
   const int m_act = ds->m_act;
   const long long ti = ds->ti;
-  const Queues qs = queues<G>(v, ds, bin_filter);
+  const int nq = density_count(ds, bin_filter);
   WarpCounters wc = {0, 0, 0, 0, 0, 0};
-  // (one call site per form of the loop keeps the kernel's code small)
-  const int cb = coop_blocks<G>(v, qs);
-  if constexpr (G == 1) {
-    // shared groups first, a block each, pulled from a head (persistent
-    // launches: every block; per-bin launches: the first cb blocks)
-    if (persistent || (int)blockIdx.x < cb) {
-      __shared__ int s_item, s_wg;
-      for (;;) {
-        if (threadIdx.x == 0) {
-          s_item = atomicAdd(&ds->head_coop_density, 1);
-          s_wg = s_item < qs.ncoop ? planted_group(ds, coop_group(v, ds, bin_filter, s_item)) : 0;
-        }
-        __syncthreads();
-        const int item = s_item, wg = s_wg;
-        __syncthreads();
-        if (item >= qs.ncoop || st.failed) break;
-        if (!SPH_IN(ds, wg, ds->n_groups, SPH_CHECK_GROUP)) break;
-        density_group<1, true>(v, wg, flags, bin_filter, m_act, frame_of(v, ds, wg), hcap, exc,
-                               ti, st, wc);
-      }
+  // every work group one per warp: pulled from a head (persistent) or by index
+  // (one call site of the loop keeps the kernel's code small)
+  for (int k = 0;; k++) {
+    int item;
+    if (persistent) {
+      item = 0;
+      if (lane == 0) item = atomicAdd(&ds->head_density, 1);
+      item = __shfl_sync(FULL, item, 0);
+    } else {
+      item = k == 0 ? (int)blockIdx.x * WARPS_PER_BLOCK + warp : nq;
     }
-  }
-  // the other groups one per warp: pulled from a head (persistent) or by index
-  if (persistent || (int)blockIdx.x >= cb) {
-    for (int k = 0;; k++) {
-      int item;
-      if (persistent) {
-        item = 0;
-        if (lane == 0) item = atomicAdd(&ds->head_density, 1);
-        item = __shfl_sync(FULL, item, 0);
-      } else {
-        item = k == 0 ? ((int)blockIdx.x - cb) * WARPS_PER_BLOCK + warp : qs.nwarp;
-      }
-      if (item >= qs.nwarp || st.failed) break;
-      int wg = warp_group<G>(v, ds, bin_filter, item);
-      if (lane == 0) wg = planted_group(ds, wg);
-      wg = __shfl_sync(FULL, wg, 0);
-      if (!SPH_IN(ds, wg, ds->n_groups, SPH_CHECK_GROUP)) break;
-      density_group<G, false>(v, wg, flags, bin_filter, m_act, frame_of(v, ds, wg), hcap, exc, ti,
-                              st, wc);
-    }
+    if (item >= nq || st.failed) break;
+    int wg = density_item(v, ds, bin_filter, item);
+    if (lane == 0) wg = planted_group(ds, wg);
+    wg = __shfl_sync(FULL, wg, 0);
+    if (!SPH_IN(ds, wg, ds->n_groups, SPH_CHECK_GROUP)) break;
+    density_group<G>(v, wg, flags, bin_filter, m_act, frame_of(v, ds, wg), hcap, exc, ti, st, wc);
   }
   flush_counters(ds, wc, true);
 }
