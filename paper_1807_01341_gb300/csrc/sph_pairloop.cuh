@@ -439,6 +439,10 @@ struct Reach {
   const float4 *sph;             // support spheres a leaf must also meet (or nullptr)
   int nsph;
   bool lanes_only = false;       // sphere test per lane only (fewer registers)
+  bool chunk_spheres = false;    // test the spheres on the chunks' boxes too (before
+                                 // their leaves), in the group frame:
+  float fx = 0.f, fy = 0.f, fz = 0.f;  // the group frame's corner in its cell's frame
+  bool grow_own = false;         // a box is also reached within its own largest support
 };
 
 // Lists, in cell-then-leaf order, the leaves of the 27 cells around the work
@@ -447,7 +451,11 @@ struct Reach {
 // chunks passing `chunk_ok`; cells out of `reach` entirely skipped; with
 // part >= 0 only chunks with index = part modulo WARPS_PER_BLOCK): accepted
 // leaves skip, skip + 1, ... up to LCAP of them.  Returns how many were
-// listed; `more` tells whether the list stopped because it was full.  The
+// listed; `more` tells whether the list stopped because it was full.  With
+// reach.chunk_spheres, a chunk whose box (padded by 1e-5 of the cell width)
+// no sphere reaches is dropped before its leaves are read: every leaf box
+// lies inside its chunk's box and has at most its chunk's largest support, so
+// no leaf that the sphere test would accept is lost.  The
 // cells' chunks, then the accepted chunks' leaves, are tested 32 at a time
 // across all 27 cells, so the number of dependent global-memory rounds does
 // not grow with the cell count.
@@ -499,8 +507,9 @@ __device__ __forceinline__ int search(const View &v, const CellFrame &F, const R
       const int cg0 = __shfl_sync(FULL, g0, ci), cnch = __shfl_sync(FULL, nch, ci);
       const int cl0 = __shfl_sync(FULL, l0, ci), cl1 = __shfl_sync(FULL, l1, ci);
       const int cs = __shfl_sync(FULL, cstart, ci);
-      bool okc = false;
+      bool okc = false, tbox = false;
       int la = 0, lb = 0;
+      LeafBox cbx = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       if (t < T) {
         const int k = t - cs;  // chunk number inside cell ci
         la = cl0 + CHUNK * k;
@@ -511,8 +520,23 @@ __device__ __forceinline__ int search(const View &v, const CellFrame &F, const R
         if (okc && cl1 - cl0 > CHUNK) {
           const int dxc = ci / 9 - 1, dyc = (ci / 3) % 3 - 1, dzc = ci % 3 - 1;
           okc = chunk_ok(cg0 + k, dxc * F.wf, dyc * F.wf, dzc * F.wf);
+          if (okc && reach.chunk_spheres) {
+            // (the boxes chunk_ok just read: L1 hits)
+            const float4 lo = v.chunk_lo[cg0 + k], hi = v.chunk_hi[cg0 + k];
+            const float pad = 1e-5f * F.wf;
+            const float sx = dxc * F.wf - reach.fx, sy = dyc * F.wf - reach.fy,
+                        sz = dzc * F.wf - reach.fz;
+            cbx = LeafBox{lo.x + sx - pad, lo.y + sy - pad, lo.z + sz - pad,
+                          hi.x + sx + pad, hi.y + sy + pad, hi.z + sz + pad,
+                          reach.grow_own ? lo.w : 0.0f};
+            tbox = true;
+          }
         }
         (void)cnch;
+      }
+      if (reach.chunk_spheres && reach.sph) {
+        const bool hit = spheres_reach_any(reach.sph, reach.nsph, tbox, cbx, reach.lanes_only);
+        if (tbox) okc = hit;
       }
       const unsigned mk = __ballot_sync(FULL, okc);
       const int room = CCAP - nacc;
