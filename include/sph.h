@@ -75,7 +75,7 @@ enum sph_check_site {
 /* Parameters.  Defaults (sph_default_params): eta 1.2348, gamma 5/3,
  * alpha_visc 0.8, cfl 0.1, h_tol 1e-6, h_max_iter 30, bin_cap 20,
  * dt_min 1e-6, t_begin 0, box 1, cell_margin 2.0, leaf_max 8,
- * threads_per_particle 1, drift_all 0, n_cells_override 0, heavy_factor 0,
+ * threads_per_particle 1, drift_all 0, n_cells_override 0, heavy_factor 2,
  * coop_max_groups -1, list_cap 256, search_margin 1.02, staging_depth 1,
  * wait_limit 0, test_stall 0, balsara 0, predict_inactive 0, limiter 0.
  * With threads_per_particle = 1 every sum of a particle is taken in an order
@@ -100,9 +100,9 @@ typedef struct {
   int n_cells_override; /* > 0: use this many top-level cells per axis (must keep the
                            cell width >= the largest support) */
   double heavy_factor;  /* > 0: a work group whose estimated search cost exceeds
-                           heavy_factor times the mean is started first and, with one
-                           lane per particle, shared in the force loop by the 8 warps of
-                           a block; <= 0: no group is treated so */
+                           heavy_factor times the mean is started first (by the first
+                           warps of a persistent launch, so that it does not end the
+                           launch's tail); <= 0: no group is treated so */
   int coop_max_groups;  /* with one lane per particle: a step with at most this many
                            active work groups hands every one, in the force loop, to the
                            8 warps of a block (0: never; -1: twice the persistent grid's

@@ -698,7 +698,7 @@ void sph_default_params(sph_params *p) {
   p->threads_per_particle = 1;
   p->drift_all = 0;
   p->n_cells_override = 0;
-  p->heavy_factor = 0.0;
+  p->heavy_factor = 2.0;
   p->coop_max_groups = -1;
   p->list_cap = 256;
   p->search_margin = 1.02;

@@ -619,8 +619,8 @@ __global__ void __launch_bounds__(UT) k_mark_rest(View v) {
 }
 
 // One thread per active work group: queues the groups holding particles of
-// one bin; with one lane per particle the heavy ones (all of them in a step
-// with few active groups) go to the back of the queue (blocks process them
+// one bin; with one lane per particle, in a step with few active groups, they
+// go to the back of the queue (the force loop's blocks process them
 // cooperatively, as in the batched form).
 __global__ void k_mark_bin(View v, int bin) {
   DevState *ds = v.ds;
@@ -631,7 +631,7 @@ __global__ void k_mark_bin(View v, int bin) {
     unsigned long long mask = 0ull;
     for (int l = v.group_leaf0[g]; l < v.group_leaf0[g + 1]; l++) mask |= v.leaf_bin_mask[l];
     if (!((mask >> bin) & 1ull)) continue;
-    if (v.G == 1 && (k < nh || all_coop(v, ds))) v.q_bin[ng - 1 - atomicAdd(&ds->n_bin_coop, 1)] = g;
+    if (v.G == 1 && all_coop(v, ds)) v.q_bin[ng - 1 - atomicAdd(&ds->n_bin_coop, 1)] = g;
     else v.q_bin[atomicAdd(&ds->n_bin_groups, 1)] = g;
   }
 }

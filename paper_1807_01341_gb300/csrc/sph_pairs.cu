@@ -815,10 +815,11 @@ __device__ void gradient_group(const View &v, int wg, int m_act, const CellFrame
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
-// The work of a force launch: `ncoop` heavy work groups processed by whole
-// blocks (one lane per particle only), then `nwarp` groups one warp each.
-// Batched form: the step's active groups (heavy ones from the back of
-// q_group); plain form: the groups of one bin (q_bin, same layout).
+// The work of a force launch: `ncoop` work groups processed by whole blocks
+// (one lane per particle, in steps with few active groups: all of them), or
+// `nwarp` groups one warp each (heavy ones first).  Batched form: the step's
+// active groups; plain form: the groups of one bin (q_bin: those of the
+// shared form at its back).
 struct Queues {
   int ncoop, nwarp;
 };
@@ -827,7 +828,6 @@ template <int G>
 __device__ __forceinline__ Queues queues(const View &v, const DevState *ds, int bin_filter) {
   if (bin_filter >= 0) return {ds->n_bin_coop, ds->n_bin_groups};
   if (G == 1 && all_coop(v, ds)) return {ds->n_active_groups + ds->n_heavy_groups, 0};
-  if (G == 1) return {ds->n_heavy_groups, ds->n_active_groups};
   return {0, ds->n_active_groups + ds->n_heavy_groups};
 }
 
@@ -840,13 +840,13 @@ __device__ __forceinline__ int coop_blocks(const View &v, const Queues &qs) {
 
 __device__ __forceinline__ int coop_group(const View &v, const DevState *ds, int bin_filter, int k) {
   if (bin_filter >= 0) return v.q_bin[ds->n_groups - 1 - k];
-  return all_coop(v, ds) ? active_group(v, ds, k) : v.q_group[ds->n_groups - 1 - k];
+  return active_group(v, ds, k);
 }
 
 template <int G>
 __device__ __forceinline__ int warp_group(const View &v, const DevState *ds, int bin_filter, int k) {
   if (bin_filter >= 0) return v.q_bin[k];
-  return G == 1 ? v.q_group[k] : active_group(v, ds, k);
+  return active_group(v, ds, k);
 }
 __device__ __forceinline__ void flush_counters(DevState *ds, WarpCounters &wc, bool density) {
   // pairs and iterations are held by group leaders; sum over the warp

@@ -39,7 +39,7 @@ class Params:
     threads_per_particle: int = 1
     drift_all: int = 0
     n_cells_override: int = 0
-    heavy_factor: float = 0.0
+    heavy_factor: float = 2.0
     coop_max_groups: int = -1
     list_cap: int = 256
     search_margin: float = 1.02

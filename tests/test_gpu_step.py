@@ -43,8 +43,8 @@ def test_step_parity_each_step_from_same_state(sim, orc, heavy_factor):
     """Before every GPU step the oracle integrator is loaded with the GPU's
     state and advanced one step: active sets and bins must agree exactly
     (bins up to dt values within 2e-5 of a power of two), and the floating
-    point state within the hot-path tolerances.  heavy_factor 1e-9 sends every
-    work group through the block-cooperative path."""
+    point state within the hot-path tolerances.  heavy_factor 1e-9 marks every
+    work group heavy (taken from the back of the queue, first)."""
     ic = _ic_step()
     n = ic["pos"].shape[0]
     ctx, p = gpu_setup(ic, sim.Params(**STEP_PARAMS, heavy_factor=heavy_factor))
@@ -106,8 +106,10 @@ def _run_form(sim, ic, form, steps, params):
                                                            (0.0, 1 << 30)])
 def test_plain_batched_graph_bitwise_identical(sim, heavy_factor, coop_max_groups):
     """One lane per particle: every sum's order depends on the particle only,
-    also when work groups are shared by the warps of a block (heavy factor 1:
-    some groups, 1e-9: all; coop_max_groups: every group of every step)."""
+    whichever warp takes a group and in which order (heavy factor 1: some
+    groups started first, 1e-9: all), and also when the force loop's groups
+    are shared by the warps of a block (coop_max_groups: every group of every
+    step)."""
     ic = _ic_step(seed=17)
     params = dict(STEP_PARAMS, heavy_factor=heavy_factor, coop_max_groups=coop_max_groups)
     res = {f: _run_form(sim, ic, f, 12, params) for f in ("plain", "batched", "graph")}
