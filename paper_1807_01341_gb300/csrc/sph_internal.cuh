@@ -49,7 +49,7 @@ struct DevState {
   int n_active_cells;    // cells holding active particles
   int n_drift_chunks;    // leaf chunks of the cells within one cell of an active cell
   int n_bin_groups;      // plain form: active work groups holding particles of one bin
-  int n_bin_coop;        // plain form: the heavy ones among them (back of q_bin)
+  int n_bin_coop;        // plain form: those the force loop shares (back of q_bin)
   // persistent-kernel work heads
   int head_density, head_force, head_drift, head_kick;
   int head_open, head_bins, head_misc;
