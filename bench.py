@@ -69,7 +69,7 @@ FP32_LANES_PER_SM = 128  # FP32 lanes per SM (sm_103a)
 def fp32_peak(sms: int, sm_mhz: float) -> float:
     """FP32 peak in TFLOP/s from the SM count and the SM clock (FMA = 2)."""
     return sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-DEFAULT_LAUNCH = dict(threads_per_particle=1, leaf_max=16, cell_margin=2.0, list_cap=256,
+DEFAULT_LAUNCH = dict(threads_per_particle=1, leaf_max=16, cell_margin=2.0, list_cap=512,
                       search_margin=1.02, staging_depth=1, heavy_factor=2.0)
 KNOBS = ("threads_per_particle", "leaf_max", "cell_margin", "list_cap", "search_margin",
          "staging_depth", "heavy_factor")

@@ -76,7 +76,7 @@ enum sph_check_site {
  * alpha_visc 0.8, cfl 0.1, h_tol 1e-6, h_max_iter 30, bin_cap 20,
  * dt_min 1e-6, t_begin 0, box 1, cell_margin 2.0, leaf_max 8,
  * threads_per_particle 1, drift_all 0, n_cells_override 0, heavy_factor 2,
- * coop_max_groups -1, list_cap 256, search_margin 1.02, staging_depth 1,
+ * coop_max_groups -1, list_cap 512, search_margin 1.02, staging_depth 1,
  * wait_limit 0, test_stall 0, balsara 0, predict_inactive 0, limiter 0.
  * With threads_per_particle = 1 every sum of a particle is taken in an order
  * that depends on the particle alone, so SPH_FORM_PLAIN and SPH_FORM_BATCHED
@@ -111,7 +111,9 @@ typedef struct {
                            (squared distance and mass of every candidate within
                            search_margin x its support, kept across the h iterations;
                            a gather that finds more runs in passes of list_cap); 32..4096.
-                           The library holds 8 x list_cap bytes per particle for them.
+                           The library holds 8 x list_cap bytes per lane of every warp
+                           of the persistent density grid for them (2 blocks of 8 warps
+                           per SM: 319 MB at 512 on 152 SMs), whatever the particle count.
                            Results do not depend on it. */
   double search_margin; /* density loop: a particle's candidates are gathered within
                            search_margin x its support H, and gathered again only once

@@ -31,13 +31,13 @@ import os
 from . import _lib
 from .sim import Context, Params, Particles
 
-_BASE = dict(threads_per_particle=1, leaf_max=16, cell_margin=2.0, list_cap=256,
+_BASE = dict(threads_per_particle=1, leaf_max=16, cell_margin=2.0, list_cap=512,
              search_margin=1.02, staging_depth=1, heavy_factor=2.0)
 DEFAULT_CANDIDATES = [
     _BASE,
     dict(_BASE, staging_depth=2),
     dict(_BASE, search_margin=1.05),
-    dict(_BASE, list_cap=128),
+    dict(_BASE, list_cap=256),
     dict(_BASE, leaf_max=12),
     dict(_BASE, leaf_max=20),
     dict(_BASE, heavy_factor=0.0),

@@ -700,7 +700,7 @@ void sph_default_params(sph_params *p) {
   p->n_cells_override = 0;
   p->heavy_factor = 2.0;
   p->coop_max_groups = -1;
-  p->list_cap = 256;
+  p->list_cap = 512;
   p->search_margin = 1.02;
   p->staging_depth = 1;
   p->wait_limit = 0;

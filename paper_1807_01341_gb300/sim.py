@@ -41,7 +41,7 @@ class Params:
     n_cells_override: int = 0
     heavy_factor: float = 2.0
     coop_max_groups: int = -1
-    list_cap: int = 256
+    list_cap: int = 512
     search_margin: float = 1.02
     staging_depth: int = 1
     wait_limit: int = 0
