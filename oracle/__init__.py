@@ -93,6 +93,8 @@ def lib():
             L.orc_timestep_bins.restype = i64
             L.orc_timestep_bins.argtypes = [i64, vp, vp, vp, d, d, i32, i64, vp, vp, vp, vp,
                                             vp]
+            L.orc_wake_bins.restype = None
+            L.orc_wake_bins.argtypes = [i64, vp, vp, vp, vp, vp, vp, d, i32, vp]
             L.orc_cells.restype = None
             L.orc_cells.argtypes = [i64, vp, vp, vp, d, i32, vp, vp, vp]
             L.orc_num_threads.restype = i32
@@ -292,6 +294,43 @@ def timestep_bins(h, vsig, active, cfl, dt_min, bin_cap, ti_current, bin_old,
                                   int(ti_current), _ptr(lim) if lim is not None else None,
                                   _ptr(b), _ptr(tb), _ptr(te), _ptr(dt))
     return dict(bin=b, ti_begin=tb, ti_end=te, dt=dt, n_too_small=int(bad))
+
+
+def wake_bins(pos, h, active, bins, box=1.0, use_cells=True):
+    """Saitoh & Makino's waking of inactive neighbours: for each inactive
+    particle j, the smallest bin_i + 2 over the active particles i whose
+    force-loop pair with j (r < max(H_i, H_j)) has bin_j > bin_i + 2, else 127."""
+    x, y, z = (_f64(pos[:, k]) for k in range(3))
+    n = x.shape[0]
+    act = _mask(active, n)
+    b8 = np.ascontiguousarray(bins, dtype=np.int8)
+    req = np.zeros(n, dtype=np.int8)
+    lib().orc_wake_bins(n, _ptr(x), _ptr(y), _ptr(z), _ptr(_f64(h)), _ptr(act), _ptr(b8), box,
+                        int(use_cells), _ptr(req))
+    return req
+
+
+def wake(ti, req, active, bins, ti_begin, ti_end, vel, A, acc, Adot, dt_min):
+    """Wakes the inactive particles with req < bin at tick ti (in place): the
+    step of such a particle j now ends at the first multiple of 2^req_j after
+    ti (when that comes before its old end), its bin becomes req_j, and the
+    opening half-kick of its step is cut to the shortened step:
+    v -= a (D_old - D_new) / 2, A -= Adot (D_old - D_new) / 2 (D in ticks of
+    dt_min).  Returns the number of particles woken."""
+    woken = 0
+    for j in np.nonzero((~np.asarray(active, bool)) & (req < bins))[0]:
+        bw = int(req[j])
+        step = 1 << bw
+        tw = (int(ti) // step + 1) * step
+        if tw >= ti_end[j]:
+            continue
+        corr = 0.5 * float(ti_end[j] - tw) * dt_min   # (D_old - D_new) / 2
+        vel[j] -= acc[j] * corr
+        A[j] -= Adot[j] * corr
+        ti_end[j] = tw
+        bins[j] = bw
+        woken += 1
+    return woken
 
 
 # --------------------------------------------------------------------------

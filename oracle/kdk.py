@@ -30,8 +30,11 @@ Variants (Gadget-2's; off by default):
   balsara   the viscosity of a pair is scaled by the mean of the two
             particles' Balsara factors;
   limiter   a new bin is at most 2 above the smallest bin among the
-            particle's force neighbours (Saitoh & Makino 2009; the waking of
-            inactive neighbours is not part of it).
+            particle's force neighbours, and an inactive neighbour whose bin is
+            more than 2 above an active particle's is woken: its step is cut to
+            end at the first multiple of 2^(bin_i + 2) after the current tick
+            (Saitoh & Makino 2009; the waking as Durier & Dalla Vecchia 2012
+            describe it, with the bins of the step being closed).
 The divergence and curl (needed by predict and balsara) are taken after the
 density loop at each active particle's new h, with the step's predicted
 velocities.
@@ -90,8 +93,9 @@ class OracleSim:
         self.ti_drift[:] = ti
 
     def _predict(self, ti):
-        """v_pred and A_pred at ti from the half-step state."""
-        step = (np.int64(1) << self.bin.astype(np.int64))
+        """v_pred and A_pred at ti from the half-step state (the middle of
+        each particle's step: its length is 2^bin, or shorter once woken)."""
+        step = self.ti_end - self.ti_begin
         dtp = ((ti - self.ti_begin) - 0.5 * step) * self.dt_min
         return self.vel + self.acc * dtp[:, None], self.A + self.Adot * dtp
 
@@ -140,6 +144,9 @@ class OracleSim:
         self.Adot[active] = fr["Adot"][active]
         self.vsig[active] = fr["vsig"][active]
         self.pairs_force += int(fr["count"][active].sum())
+        # wake requests from the force loop's pairs, with the bins of this step
+        req = (orc.wake_bins(self.pos, h_now, active, self.bin, self.box, self.use_cells)
+               if self.limiter else None)
         # (v) closing half-kick of the old step
         dt_old = ((self.ti_end - self.ti_begin) * self.dt_min)[active]
         self.vel[active] += self.acc[active] * (0.5 * dt_old)[:, None]
@@ -160,6 +167,11 @@ class OracleSim:
         dt_new = ((self.ti_end - self.ti_begin) * self.dt_min)[active]
         self.vel[active] += self.acc[active] * (0.5 * dt_new)[:, None]
         self.A[active] += self.Adot[active] * (0.5 * dt_new)
+        # (viii) limiter: inactive neighbours of much shorter steps are woken
+        self.n_woken = 0
+        if self.limiter:
+            self.n_woken = orc.wake(ti, req, active, self.bin, self.ti_begin, self.ti_end,
+                                    self.vel, self.A, self.acc, self.Adot, self.dt_min)
         self.first = False
         self.n_steps += 1
         self.ti = int(self.ti_end.min())

@@ -467,6 +467,48 @@ void orc_force(int64_t n, const double *x, const double *y, const double *z,
 }
 
 /* ------------------------------------------------------------------------- */
+/* Waking of inactive neighbours (Saitoh & Makino 2009, second half; the     */
+/* reading of Durier & Dalla Vecchia 2012 with the bins of the step): for    */
+/* every active i and every inactive j != i with r_ij < max(H_i, H_j) (the   */
+/* force loop's pairs) whose bin exceeds bin_i + 2, req[j] = the smallest    */
+/* such bin_i + 2; req[j] = 127 where no active neighbour asks.  A plain     */
+/* serial double loop over the force loop's candidate grid.                  */
+/* ------------------------------------------------------------------------- */
+
+void orc_wake_bins(int64_t n, const double *x, const double *y, const double *z,
+                   const double *h, const uint8_t *active, const int8_t *bin, double box,
+                   int use_cells, int8_t *req) {
+  double hmax = 0.0;
+  for (int64_t i = 0; i < n; i++) {
+    req[i] = 127;
+    if (h[i] > hmax) hmax = h[i];
+  }
+  double Hmax = ORC_GAMMA_K * hmax;
+  orc_grid g;
+  grid_build(&g, n, x, y, z, box, Hmax, use_cells);
+  int64_t *cand = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+  for (int64_t i = 0; i < n; i++) {
+    if (!active[i]) continue;
+    double Hi = ORC_GAMMA_K * h[i];
+    int64_t nc = grid_candidates(&g, i, Hmax, cand);
+    for (int64_t k = 0; k < nc; k++) {
+      int64_t j = cand[k];
+      if (j == i || active[j]) continue;
+      double Hj = ORC_GAMMA_K * h[j];
+      double dx = min_image(x[i] - x[j], box);
+      double dy = min_image(y[i] - y[j], box);
+      double dz = min_image(z[i] - z[j], box);
+      double r2 = dx * dx + dy * dy + dz * dz;
+      if (!(r2 < Hi * Hi || r2 < Hj * Hj)) continue;
+      int want = bin[i] + 2;
+      if (bin[j] > want && want < req[j]) req[j] = (int8_t)want;
+    }
+  }
+  free(cand);
+  grid_free(&g);
+}
+
+/* ------------------------------------------------------------------------- */
 /* Time-step (Eq. 1) and time bins (Eq. 2) on the integer timeline           */
 /* ------------------------------------------------------------------------- */
 

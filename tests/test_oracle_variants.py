@@ -178,6 +178,108 @@ def test_limiter_neighbour_minimum_from_the_force_loop(orc):
     assert fr["bin_ngb_min"][3] == 127  # no neighbour: no cap
 
 
+def test_wake_requests_hand_computed(orc):
+    """The waking half of the limiter: an inactive particle whose bin is more
+    than 2 above an active force-loop neighbour's is asked down to that bin
+    + 2 (the smallest such request wins); active particles and particles
+    with no active neighbour get no request (127).  Particles 0, 1, 2 are
+    mutual neighbours, particle 3 is isolated."""
+    pos = np.array([[5.0, 5.0, 5.0], [5.75, 5.0, 5.0], [5.0, 5.6, 5.0], [8.0, 8.0, 8.0]])
+    H = np.array([1.0, 1.0, 1.2, 1.0])
+    bins = np.array([5, 2, 7, 1], np.int8)
+    act = np.array([0, 1, 0, 1], np.uint8)
+    req = orc.wake_bins(pos, H / orc.GAMMA_K, act, bins, box=10.0, use_cells=False)
+    assert list(req) == [4, 127, 4, 127]
+    # particle 0 active too (bin 5): it asks particle 2 for 7, which is not
+    # below 7; particle 1's request (4) stands
+    act = np.array([1, 1, 0, 1], np.uint8)
+    req = orc.wake_bins(pos, H / orc.GAMMA_K, act, bins, box=10.0, use_cells=False)
+    assert list(req) == [127, 127, 4, 127]
+    # out of reach: the pair must be a force-loop pair (r < max(H_i, H_j))
+    far = pos.copy()
+    far[1] = [6.3, 5.0, 5.0]  # 1.3 from particle 0, 1.43 from particle 2 (H <= 1.2)
+    req = orc.wake_bins(far, H / orc.GAMMA_K, np.array([0, 1, 0, 0], np.uint8), bins,
+                        box=10.0, use_cells=False)
+    assert list(req) == [127, 127, 127, 127]
+
+
+def test_wake_hand_computed(orc):
+    """Waking at tick 4: a particle on bin 6 (step [0, 64)) asked down to bin
+    4 now ends its step at 16, the first multiple of 16 after 4; its opening
+    half-kick is cut from 32 to 8 ticks (v -= a 24 dt_min, A -= Adot 24
+    dt_min).  A particle whose step already ends at the first multiple (bin 3,
+    [0, 8), asked for 2: 8) and one without a request are left alone; the
+    predicted velocity at the current tick does not change."""
+    dt_min = 0.5
+    ti = 4
+    act = np.array([True, False, False, False])
+    req = np.array([127, 4, 2, 127], np.int8)
+    bins = np.array([2, 6, 3, 6], np.int8)
+    tb = np.array([4, 0, 0, 0], np.int64)
+    te = np.array([8, 64, 8, 64], np.int64)
+    vel = np.array([[1.0, 0, 0], [2.0, 1.0, 0], [3.0, 0, 0], [4.0, 0, 0]])
+    acc = np.array([[0.1, 0, 0], [0.5, -0.25, 0], [0.2, 0, 0], [0.3, 0, 0]])
+    A = np.array([1.0, 2.0, 3.0, 4.0])
+    Adot = np.array([0.0, 0.125, 0.0, 0.0])
+    vpred0 = vel + acc * (((ti - tb) - 0.5 * (te - tb)) * dt_min)[:, None]
+    n = orc.wake(ti, req, act, bins, tb, te, vel, A, acc, Adot, dt_min)
+    assert n == 1
+    assert list(bins) == [2, 4, 3, 6]
+    assert list(te) == [8, 16, 8, 64]
+    assert np.allclose(vel[1], [2.0 - 0.5 * 24 * 0.5, 1.0 + 0.25 * 24 * 0.5, 0.0], rtol=0,
+                       atol=1e-15)
+    assert A[1] == 2.0 - 0.125 * 24 * 0.5
+    assert np.array_equal(vel[[0, 2, 3]], [[1.0, 0, 0], [3.0, 0, 0], [4.0, 0, 0]])
+    vpred1 = vel + acc * (((ti - tb) - 0.5 * (te - tb)) * dt_min)[:, None]
+    assert np.allclose(vpred1, vpred0, rtol=0, atol=1e-14)
+
+
+def test_wake_invariant_in_a_kdk_step(orc):
+    """After a limiter step from mixed bins (a clump on bin 2 inside a
+    background on bin 6), every inactive force-loop neighbour of a particle
+    active in the step ends its step within 2^(bin_i + 2) ticks of it (pairs
+    found here by a brute-force periodic double loop), some particles were
+    woken, and the run's later steps see them active."""
+    ic = sph_ics.clumpy_lattice(nside=8, n_clumps=1, per_clump=64, seed=11)
+    n = ic["pos"].shape[0]
+    kw = dict(dt_min=1e-6, bin_cap=14, cfl=0.1)
+    s = orc.OracleSim(ic["pos"], np.zeros((n, 3)), ic["m"], 1.0, ic["h0"], limiter=True, **kw)
+    s.step()  # the first step (all active) sets h, rho, A, a
+    # mixed bins: the clump (the 64 densest) on bin 2, the rest on bin 6,
+    # every step starting at the current tick
+    ti0 = s.ti
+    t0 = ti0 - ti0 % 64
+    dense = np.argsort(-s.rho)[:64]
+    s.bin[:] = 6
+    s.bin[dense] = 2
+    s.ti_begin[:] = t0
+    s.ti_end[:] = t0 + (np.int64(1) << s.bin.astype(np.int64))
+    s.ti = int(s.ti_end.min())
+    ti = s.ti
+    bins_before = s.bin.copy()
+    act = s.step()
+    assert act.sum() == 64 and s.n_woken > 0
+    # brute-force force-loop pairs at the step's positions and supports
+    H = orc.GAMMA_K * s.h
+    d = s.pos[:, None, :] - s.pos[None, :, :]
+    d -= np.round(d)
+    r2 = (d ** 2).sum(-1)
+    pair = (r2 < H[:, None] ** 2) | (r2 < H[None, :] ** 2)
+    np.fill_diagonal(pair, False)
+    for i in np.nonzero(act)[0]:
+        for j in np.nonzero(pair[i] & ~act)[0]:
+            assert s.ti_end[j] - ti <= (1 << (int(bins_before[i]) + 2)), (i, j)
+    woken = (s.bin < bins_before) & ~act
+    assert woken.sum() == s.n_woken
+    # the woken particles are active when their shortened steps end
+    t_w = int(s.ti_end[woken].min())
+    while s.ti < t_w:
+        s.step()
+    assert s.ti == t_w
+    act = s.step()
+    assert act[woken & (s.ti_end > 0)].any()
+
+
 def test_variants_kdk_run(orc):
     """A short run with all three variants: momentum is conserved to
     roundoff (the Balsara factor is symmetric in the pair), the predicted
