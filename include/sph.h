@@ -69,7 +69,8 @@ enum sph_check_site {
   SPH_CHECK_PARTICLE_LEAF = 6,   /* a particle's leaf, against the leaf count */
   SPH_CHECK_DRIFT_CHUNK = 7,     /* chunk taken from the drift queue, against the chunk count */
   SPH_CHECK_ACTIVE_LEAF = 8,     /* leaf taken from the active-leaf queue, against the leaf count */
-  SPH_CHECK_SCATTER = 9          /* destination of the cell build's permutation, against n */
+  SPH_CHECK_SCATTER = 9,         /* destination of the cell build's permutation, against n */
+  SPH_CHECK_WAKE = 10            /* particle taken from the limiter's wake queue, against n */
 };
 
 /* Parameters.  Defaults (sph_default_params): eta 1.2348, gamma 5/3,
@@ -145,7 +146,12 @@ typedef struct {
                            last density; an active one starts its h iteration there */
   int limiter;          /* Saitoh & Makino (2009): a new time bin is at most 2 above the
                            smallest bin among the particle's force neighbours (dt <= 4
-                           min_j dt_j); inactive neighbours are not woken */
+                           min_j dt_j), and an inactive force neighbour whose bin is more
+                           than 2 above an active particle's is woken at the step's close:
+                           its step is cut to end at the first multiple of 2^(bin_i + 2)
+                           after the current tick, its bin becomes bin_i + 2 and its
+                           opening half-kick is cut to the shorter step (as Durier & Dalla
+                           Vecchia 2012 describe it; sph_counters.wakes counts them) */
 } sph_params;
 
 /* Particle state, structure of arrays, all device pointers of length n.
@@ -197,6 +203,8 @@ typedef struct {
                               gather then ran further passes over the same leaves) */
   int64_t evals_density;   /* density loop: neighbour-list entries evaluated, all h
                               iterations (pair terms computed, in or beyond the support) */
+  int64_t wakes;           /* limiter: inactive particles woken (their steps cut short
+                              because an active neighbour's bin was more than 2 below) */
 } sph_counters;
 
 void sph_default_params(sph_params *p);

@@ -31,6 +31,7 @@ SPH_ERR_BOUNDS = 9
 SPH_CHECK_NONE, SPH_CHECK_GROUP, SPH_CHECK_GROUP_LEAVES, SPH_CHECK_GROUP_SIZE = 0, 1, 2, 3
 SPH_CHECK_CELL_LEAVES, SPH_CHECK_LEAF, SPH_CHECK_PARTICLE_LEAF = 4, 5, 6
 SPH_CHECK_DRIFT_CHUNK, SPH_CHECK_ACTIVE_LEAF, SPH_CHECK_SCATTER = 7, 8, 9
+SPH_CHECK_WAKE = 10
 
 SPH_DRIFT, SPH_KICK_CLOSE, SPH_KICK_OPEN = 0, 1, 2
 SPH_DENSITY_INIT_ENTROPY = 1
@@ -74,7 +75,7 @@ class sph_counters(ctypes.Structure):
     _fields_ = [(k, _i64) for k in ("pairs_density", "pairs_force", "cand_density", "cand_force",
                                     "iters_density", "active_particles", "steps", "rebuilds",
                                     "redone_steps", "kernel_launches", "gathers_density",
-                                    "list_overflows", "evals_density")]
+                                    "list_overflows", "evals_density", "wakes")]
 
 
 class sph_kernel_times(ctypes.Structure):

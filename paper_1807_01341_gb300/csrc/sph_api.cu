@@ -66,6 +66,7 @@ struct Buffers {
   // warp of a persistent density launch
   float2 *nbr = nullptr;
   int8_t *ngb_bin = nullptr;  // limiter: smallest neighbour bin of each active particle
+  int32_t *wake_bin = nullptr, *q_wake = nullptr;  // limiter: wake requests and their queue
   // state
   DevState *ds = nullptr;
   float *d_hmax = nullptr;
@@ -276,6 +277,8 @@ View make_view(const sph_ctx *ctx, const sph_particles *p) {
   v.predict = q.predict_inactive;
   v.limiter = q.limiter;
   v.ngb_bin = b.ngb_bin;
+  v.wake_bin = b.wake_bin;
+  v.q_wake = b.q_wake;
   return v;
 }
 
@@ -471,6 +474,8 @@ int build_cells(sph_ctx *ctx, sph_particles *p, cudaStream_t st) {
   ctx->h_floor = 0.0f;
   ctx->nc = nc;
   ctx->w = w;
+  // no wake request survives a reordering (a halted step may have left some)
+  SPH_CUDA(cudaMemsetAsync(b.wake_bin, 0x7f, sizeof(int32_t) * (size_t)ctx->n_max, st));
   ctx->built = true;
   ctx->rebuilds++;
   return SPH_OK;
@@ -786,11 +791,14 @@ int sph_create(const sph_params *params, int64_t n_max, sph_ctx **out) {
     // that share a work group (those of a persistent launch; a per-bin launch
     // uses at most as many)
     ctx->list_blocks = ctx->grid_dens;
-    if ((r = dalloc(&b.ngb_bin, n)) ||
+    if ((r = dalloc(&b.ngb_bin, n)) || (r = dalloc(&b.wake_bin, n)) ||
+        (r = dalloc(&b.q_wake, n)) ||
         (r = dalloc(&b.nbr, (long long)ctx->list_blocks * WARPS_PER_BLOCK * 32 * params->list_cap)))
       break;
-    // no neighbour bin known yet: no limit (a bins call without a force pass)
-    if (cudaMemset(b.ngb_bin, 127, (size_t)n) != cudaSuccess) {
+    // no neighbour bin known yet: no limit (a bins call without a force pass);
+    // no wake request
+    if (cudaMemset(b.ngb_bin, 127, (size_t)n) != cudaSuccess ||
+        cudaMemset(b.wake_bin, 0x7f, sizeof(int32_t) * (size_t)n) != cudaSuccess) {
       r = SPH_ERR_CUDA;
       break;
     }
@@ -834,7 +842,7 @@ int sph_destroy(sph_ctx *ctx) {
   dfree(b.cell_start); dfree(b.cell_leaf_start); dfree(b.cell_stamp); dfree(b.cell_rel_stamp);
   dfree(b.q_act_cells); dfree(b.leaf_counts); dfree(b.leaf_offsets);
   dfree(b.ds); dfree(b.d_hmax); dfree(b.diag); dfree(b.d_bad);
-  dfree(b.nbr); dfree(b.ngb_bin);
+  dfree(b.nbr); dfree(b.ngb_bin); dfree(b.wake_bin); dfree(b.q_wake);
   if (b.h_ds) cudaFreeHost(b.h_ds);
   delete ctx;
   return SPH_OK;
@@ -1038,6 +1046,9 @@ int sph_clear_status(sph_ctx *ctx, void *stream) {
   SPH_CUDA(cudaMemsetAsync(SPH_DS_FIELD(ctx->b.ds, first_error), 0, sizeof(int), st));
   SPH_CUDA(cudaMemsetAsync(SPH_DS_FIELD(ctx->b.ds, err_count), 0, sizeof(((DevState *)0)->err_count), st));
   SPH_CUDA(cudaMemsetAsync(SPH_DS_FIELD(ctx->b.ds, check_site), 0, sizeof(int), st));
+  // (a halted step may have left wake requests that its close never applied)
+  if (ctx->n_max > 0)
+    SPH_CUDA(cudaMemsetAsync(ctx->b.wake_bin, 0x7f, sizeof(int32_t) * (size_t)ctx->n_max, st));
   return SPH_OK;
 }
 
@@ -1060,6 +1071,7 @@ int sph_get_counters(sph_ctx *ctx, sph_counters *out) {
   out->gathers_density = (int64_t)(h.gathers_density + h.s_gathers_density);
   out->list_overflows = (int64_t)(h.list_overflows + h.s_list_overflows);
   out->evals_density = (int64_t)(h.evals_density + h.s_evals_density);
+  out->wakes = (int64_t)h.wakes;
   return SPH_OK;
 }
 

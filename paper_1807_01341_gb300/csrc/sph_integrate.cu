@@ -59,6 +59,7 @@ __global__ void k_begin_step(View v, long long ti_arg) {
   ds->head_density = ds->head_force = ds->head_drift = ds->head_kick = 0;
   ds->head_open = ds->head_bins = ds->head_misc = 0;
   ds->head_coop_force = ds->head_grad = 0;
+  ds->n_wake = 0;
   ds->s_pairs_density = ds->s_pairs_force = 0ull;
   ds->s_cand_density = ds->s_cand_force = 0ull;
   ds->s_iters_density = ds->s_active_particles = 0ull;
@@ -237,7 +238,10 @@ __device__ void chunk_update(const View &v, int g, bool do_drift, bool do_bins) 
     const float fx = (float)rel_periodic(x - lx, v.box), fy = (float)rel_periodic(y - ly, v.box),
                 fz = (float)rel_periodic(z - lz, v.box);
     const int bi = v.bin[i] & (MAX_BINS - 1);
-    const double dtp = ((double)(ti - v.ti_begin[i]) - 0.5 * (double)(1ll << bi)) * v.dt_min;
+    // (the middle of the particle's step: its length is 2^bin, or shorter once
+    // the limiter woke it)
+    const double dtp =
+        ((double)(ti - v.ti_begin[i]) - 0.5 * (double)(v.ti_end[i] - v.ti_begin[i])) * v.dt_min;
     const float fdtp = (float)dtp;
     const float vpx = v.vx[i] + v.ax[i] * fdtp;
     const float vpy = v.vy[i] + v.ay[i] * fdtp;
@@ -608,6 +612,66 @@ __global__ void __launch_bounds__(UT) k_close_step(View v) {
   }
 }
 
+// smallest bin of a leaf lowered to b (a byte of a 4-byte word: compare-and-swap
+// on the word)
+__device__ __forceinline__ void atomic_min_u8(uint8_t *p, int b) {
+  unsigned int *w = reinterpret_cast<unsigned int *>(reinterpret_cast<uintptr_t>(p) & ~(uintptr_t)3);
+  const int sh = (int)(reinterpret_cast<uintptr_t>(p) & 3) * 8;
+  unsigned int old = *w, assumed;
+  do {
+    assumed = old;
+    if ((int)((assumed >> sh) & 0xffu) <= b) return;
+    old = atomicCAS(w, assumed, (assumed & ~(0xffu << sh)) | ((unsigned int)b << sh));
+  } while (old != assumed);
+}
+
+// The limiter's waking of inactive neighbours (Saitoh & Makino 2009, as
+// Durier & Dalla Vecchia 2012 describe it): the force loop asked each
+// inactive particle j with an active neighbour i of bin_j > bin_i + 2 down to
+// the smallest such bin_i + 2 (wake_bin).  After the step's close, j's step
+// is cut to end at the first multiple of 2^b after the current tick, when
+// that comes before its old end: its bin becomes b (it is active then), and
+// the opening half-kick of its step is cut to the shortened step,
+// v -= a (D_old - D_new) / 2, A -= Adot (D_old - D_new) / 2 (D in ticks).
+// The particle's leaf learns the new bin (its smallest bin and bin mask;
+// the leaf's next close recomputes both exactly); with adjust_next, the
+// step's next tick (already computed) is lowered to the woken ends.  Every
+// request is reset, applied or not.
+__global__ void k_wake(View v, int adjust_next) {
+  DevState *ds = v.ds;
+  if (ds->halt) return;
+  const int nw = ds->n_wake;
+  const long long ti = ds->ti;
+  unsigned long long woken = 0;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nw; k += gridDim.x * blockDim.x) {
+    const int j = v.q_wake[k];
+    if (!SPH_IN(ds, j, v.n, SPH_CHECK_WAKE)) continue;
+    const int b = v.wake_bin[j];
+    v.wake_bin[j] = WAKE_NONE;
+    const int old = v.bin[j];
+    if (b >= old || b < 0) continue;
+    const long long tw = ((ti >> b) + 1) << b;
+    if (tw >= v.ti_end[j]) continue;
+    const double corr = 0.5 * (double)(v.ti_end[j] - tw) * v.dt_min;  // (D_old - D_new) / 2
+    const float cf = (float)corr;
+    v.vx[j] -= v.ax[j] * cf;
+    v.vy[j] -= v.ay[j] * cf;
+    v.vz[j] -= v.az[j] * cf;
+    v.A[j] = (float)((double)v.A[j] - (double)v.Adot[j] * corr);
+    v.ti_end[j] = tw;
+    v.bin[j] = (int8_t)b;
+    atomicSub(&ds->bin_count[old], 1);
+    atomicAdd(&ds->bin_count[b], 1);
+    const int leaf = v.pleaf[j];
+    atomic_min_u8(&v.leaf_min_bin[leaf], b);
+    atomicOr(&v.leaf_bin_mask[leaf], 1ull << b);
+    if (adjust_next) atomicMin(&ds->ti_next, tw);
+    woken++;
+  }
+  for (int o = 16; o; o >>= 1) woken += __shfl_xor_sync(0xffffffffu, woken, o);
+  if (lane_id() == 0 && woken) atomicAdd(&ds->wakes, woken);
+}
+
 // Active work groups, active particles and the cells to drift, in one launch
 // (the three read only what k_mark_leaves wrote): the blocks of the grid are
 // split into three ranges, one per task.
@@ -652,8 +716,8 @@ k_diag(const sph_particles p, long long ti, double dt_min, double gamma, double 
   for (int k = 0; k < DIAG_FIELDS; k++) acc[k] = 0.0;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
-    const int bi = p.bin[i] & (MAX_BINS - 1);
-    const double dtp = ((double)(ti - p.ti_begin[i]) - 0.5 * (double)(1ll << bi)) * dt_min;
+    const double dtp =
+        ((double)(ti - p.ti_begin[i]) - 0.5 * (double)(p.ti_end[i] - p.ti_begin[i])) * dt_min;
     const double m = (double)p.m[i];
     const double vx = (double)p.vx[i] + (double)p.ax[i] * dtp;
     const double vy = (double)p.vy[i] + (double)p.ay[i] * dtp;
@@ -709,8 +773,9 @@ cudaError_t launch_mark(const View &v, long long ti_or_neg, cudaStream_t st) {
 }
 
 cudaError_t launch_close_step(const View &v, cudaStream_t st) {
-  note_launches(1);
+  note_launches(v.limiter ? 2 : 1);
   k_close_step<<<v.grid_util, UT, 0, st>>>(v);
+  if (v.limiter) k_wake<<<v.grid_util, UT, 0, st>>>(v, 1);
   return cudaGetLastError();
 }
 
@@ -727,8 +792,9 @@ cudaError_t launch_kick(const View &v, int phase, cudaStream_t st) {
 }
 
 cudaError_t launch_bins(const View &v, long long *ti_next_out, int count_step, cudaStream_t st) {
-  note_launches(2);
+  note_launches(v.limiter ? 3 : 2);
   k_bins<<<v.grid_util, UT, 0, st>>>(v);
+  if (v.limiter) k_wake<<<v.grid_util, UT, 0, st>>>(v, 0);
   k_next_time<<<1, 1, 0, st>>>(v, ti_next_out, count_step);
   return cudaGetLastError();
 }

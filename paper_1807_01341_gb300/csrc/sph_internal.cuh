@@ -50,6 +50,7 @@ struct DevState {
   int n_drift_chunks;    // leaf chunks of the cells within one cell of an active cell
   int n_bin_groups;      // plain form: active work groups holding particles of one bin
   int n_bin_coop;        // plain form: those the force loop shares (back of q_bin)
+  int n_wake;            // limiter: inactive particles asked to wake in this step (q_wake)
   // persistent-kernel work heads
   int head_density, head_force, head_drift, head_kick;
   int head_open, head_bins, head_misc;
@@ -79,6 +80,7 @@ struct DevState {
   unsigned long long iters_density, active_particles;
   unsigned long long gathers_density, list_overflows, evals_density;
   unsigned long long steps;
+  unsigned long long wakes;   // limiter: inactive particles whose steps were cut
   // time-bin occupancy
   int bin_count[MAX_BINS];
 };
@@ -95,6 +97,9 @@ struct View {
   int32_t *ngb_density, *ngb_force;
   float *div_v, *curl_v;     // velocity divergence and |curl| (variants; may be null)
   int8_t *ngb_bin;           // limiter: smallest bin among the force neighbours (step scratch)
+  int32_t *wake_bin;         // limiter: smallest bin an active neighbour asks an inactive
+                             // particle down to (WAKE_NONE: none; reset once applied)
+  int32_t *q_wake;           // limiter: the particles with a request, in request order
   // cell structure
   int32_t *cell_start;       // [n_cells + 1] first particle of each cell
   int32_t *cell_leaf_start;  // [n_cells + 1] first leaf of each cell
@@ -179,6 +184,10 @@ __device__ __forceinline__ void record_error(DevState *ds, int code, unsigned lo
   atomicAdd(&ds->err_count[code & 15], count);
   if (halt) atomicExch(&ds->halt, 1u);
 }
+
+// No wake request (the limiter's waking of inactive neighbours): the byte
+// pattern 0x7f of a cudaMemset, above every bin.
+constexpr int32_t WAKE_NONE = 0x7f7f7f7f;
 
 // Device bounds checks.  SPH_IN(ds, i, n, site) is true when 0 <= i < n.  In
 // a library compiled with -DSPH_CHECKS a false result records SPH_ERR_BOUNDS

@@ -396,9 +396,9 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
             const float Hinv3 = Hinv * Hinv * Hinv;
             const float rho = KERNEL_NORM * sr * Hinv3;
             const float f = 3.0f * sr / (3.0f * sr - srt);
-            const int bi = v.bin[i] & (MAX_BINS - 1);
             const double dtp =
-                ((double)(ti - v.ti_begin[i]) - 0.5 * (double)(1ll << bi)) * v.dt_min;
+                ((double)(ti - v.ti_begin[i]) - 0.5 * (double)(v.ti_end[i] - v.ti_begin[i])) *
+                v.dt_min;
             float Ap = v.A[i] + v.Adot[i] * (float)dtp;
             const float g = (float)v.gamma;
             if (init_entropy) Ap = (g - 1.0f) * v.A[i] / powf(rho, g - 1.0f);  // A holds u
@@ -437,6 +437,12 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
 // ---------------------------------------------------------------------------
 // force loop for the active particles of a group
 // ---------------------------------------------------------------------------
+// The limiter's request that inactive particle j wake down to bin b (the
+// smallest request stands; the first one queues j for the step's close).
+__device__ __forceinline__ void request_wake(const View &v, int j, int b) {
+  if (atomicMin(&v.wake_bin[j], b) == WAKE_NONE) v.q_wake[atomicAdd(&v.ds->n_wake, 1)] = j;
+}
+
 // VAR: the code of the scheme's variants (Balsara switch, neighbour limiter)
 // is compiled in; the base scheme runs the instance without it.
 template <int G, bool COOP, bool VAR>
@@ -482,6 +488,7 @@ __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, co
     float vs = 2.0f * hi4.z;
     int cur = -1, cnt = 0;
     int bmin = 127;  // limiter: smallest bin among the neighbours
+    const int bi = ((VAR && v.limiter) && valid) ? (int)v.bin[i] : 0;  // limiter: i's bin
     // Balsara factor of i: |div v| / (|div v| + |curl v| + 1e-4 c / h), h = 1 / (GAMMA_K / H)
     float Bi = 1.0f;
     if ((VAR && v.balsara) && valid) {
@@ -591,7 +598,12 @@ __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, co
           cnt++;
           if ((VAR && v.limiter)) {
             const int j = st.recj[k];
-            if (j != i) bmin = min(bmin, (int)v.bin[j]);
+            if (j != i) {
+              const int bj = v.bin[j];
+              bmin = min(bmin, bj);
+              // waking: an inactive neighbour on a step more than 4x longer
+              if (bj > m_act && bj > bi + 2) request_wake(v, j, bi + 2);
+            }
           }
           if (r2 > 0.0f) {
             const float rinv = rsqrtf(r2);

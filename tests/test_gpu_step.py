@@ -386,6 +386,59 @@ def test_variants_step_parity_each_step_from_same_state(sim, orc, var):
     assert n_partial >= 2          # individual bins (the limiter narrows them)
 
 
+def test_limiter_wakes_inactive_neighbours(sim, orc):
+    """The limiter's waking (Saitoh & Makino 2009): from a state with the
+    densest particles on bin 2 and the rest on bin 6 (steps from tick 0), the
+    step at tick 4 wakes the bin-6 force neighbours of the active particles:
+    their steps now end at tick 16 (bin 4) and their opening half-kicks are
+    cut to the shorter step.  Against the oracle from the same state, step by
+    step: active sets, bins and step ends exact, the woken count equal,
+    velocities within the hot-path tolerance."""
+    import torch
+    ic = _ic_step(seed=67)
+    n = ic["pos"].shape[0]
+    params = dict(STEP_PARAMS, limiter=1)
+    ctx, p = gpu_setup(ic, sim.Params(**params))
+    L = _lib()
+    ctx.step(p, L.SPH_FORM_BATCHED)  # the first step: h, rho, entropy, a
+    st = p.numpy()
+    dense = np.argsort(-st["rho"])[: n // 8]
+    b = np.full(n, 6, np.int64)
+    b[dense] = 2
+    p.bin.copy_(torch.as_tensor(b.astype(np.int8)))
+    p.ti_begin.zero_()
+    p.ti_end.copy_(torch.as_tensor(np.left_shift(1, b)))
+    p.ti_drift.zero_()
+    ctx.build_cells(p)  # (bin occupancy and leaf bins from the new bins)
+    ctx.set_time(4)
+    woken_total = 0
+    for k in range(4):
+        st0 = p.numpy()
+        _, ti = ctx.get_time()
+        w0 = ctx.counters()["wakes"]
+        osim = orc.OracleSim.from_state(st0, ti=ti, use_cells=True, limiter=True, **STEP_PARAMS)
+        act_ref = osim.step()
+        ctx.step(p, L.SPH_FORM_BATCHED)
+        st = p.numpy()
+        assert ctx.status()[0] == 0
+        act = st["active"].astype(bool)
+        assert np.array_equal(act, act_ref), k
+        woken = ctx.counters()["wakes"] - w0
+        assert woken == osim.n_woken, (k, woken, osim.n_woken)
+        woken_total += woken
+        q = osim.cfl * osim.h / osim.vsig / osim.dt_min
+        with np.errstate(divide="ignore", invalid="ignore"):
+            edge = np.abs(np.log2(q) - np.round(np.log2(q))) < 2e-5
+        ok = ~(act & edge)
+        assert np.array_equal(st["bin"][ok], osim.bin[ok]), k
+        assert np.array_equal(st["ti_end"][ok], osim.ti_end[ok]), k
+        v = np.stack([st["vx"], st["vy"], st["vz"]], 1).astype(np.float64)
+        v_rms = np.sqrt((osim.vel ** 2).sum(1).mean())
+        assert np.max(np.abs(v - osim.vel)) < 1e-4 * v_rms, k
+        assert np.max(np.abs(st["A"] / osim.A - 1)) < 1e-5, k
+    assert woken_total > 0
+
+
 def test_variants_forms_bitwise_identical(sim):
     """With all three variants the plain, batched and graph forms agree bit
     for bit (every sum of a particle still depends on the particle alone)."""
