@@ -26,7 +26,8 @@ Variants of the scheme (off by default; Gadget-2, the paper's reference code,
 uses all three): velocity divergence and curl from the density loop, the
 Gadget-2 prediction of inactive particles' density and smoothing length from
 their divergence, the Balsara switch on the viscosity, and the Saitoh & Makino
-(2009) limit of a time step to four times its neighbours' smallest one.
+(2009) limit of a time step to four times its neighbours' smallest one, with
+the waking of inactive neighbours on much longer steps.
 """
 from __future__ import annotations
 
