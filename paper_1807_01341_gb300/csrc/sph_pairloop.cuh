@@ -617,7 +617,8 @@ __device__ __forceinline__ int search(const View &v, const CellFrame &F, const R
 }
 
 // Stages the records of listed leaves [0, nlist) into shared memory by bulk
-// copies (TMA), through `depth` buffers of S / depth records each: the copies
+// copies (TMA), through `depth` buffers of S / depth records (rounded down to
+// a multiple of 32) each: the copies
 // of the next depth - 1 batches are in flight while a batch is consumed.  A
 // batch is as many consecutive listed leaves as fit one buffer.  When a batch
 // has landed, each position record is moved into the work group's frame (its
@@ -633,7 +634,8 @@ __device__ __forceinline__ void stage_list(const float4 *const *srcs, Stage<S, N
                                            int nlist, Consume consume, WarpCounters &wc) {
   const int lane = lane_id();
   const int depth = st.depth;
-  const int Sb = S / depth;
+  // (a multiple of 32 records per buffer: the tests read whole blocks of 32)
+  const int Sb = (S / depth) & ~31;
   int e_next = 0, issued = 0, done = 0;
   // the next listed leaves that fit Sb records, into buffer b
   auto issue = [&](int b) {

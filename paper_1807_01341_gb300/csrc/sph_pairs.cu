@@ -231,11 +231,13 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
           }
           const unsigned nlive = __popc(__ballot_sync(FULL, gath && sub == 0));
           // accept mask of the staged records base+kb .. base+kb+31 for this lane
+          // (a staging buffer holds a multiple of 32 records, so the block
+          // is read whole and the records past the batch are masked off)
           auto test_block = [&](int base, int total, int kb) -> unsigned {
             unsigned mask = 0u;
+            const unsigned bvalid = total - kb >= 32 ? FULL : (1u << (total - kb)) - 1u;
             if (G == 1 && ntst <= TRANSPOSE_MAX) {
-              const bool in = kb + lane < total;
-              const float4 pj = st.rec[min(base + kb + lane, S_DENS - 1)];
+              const float4 pj = st.rec[base + kb + lane];
               const float2 px = make_float2(pj.x, pj.x), py = make_float2(pj.y, pj.y),
                            pz = make_float2(pj.z, pj.z);
               int q = 0;
@@ -243,8 +245,8 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
                 const float4 t0 = st.tst[q], t1 = st.tst[q + 1];
                 const float2 r2 = dist2_x2(make_float2(t0.x, t1.x), make_float2(t0.y, t1.y),
                                            make_float2(t0.z, t1.z), px, py, pz);
-                const unsigned m0 = __ballot_sync(FULL, in && r2.x < t0.w);
-                const unsigned m1 = __ballot_sync(FULL, in && r2.y < t1.w);
+                const unsigned m0 = __ballot_sync(FULL, r2.x < t0.w);
+                const unsigned m1 = __ballot_sync(FULL, r2.y < t1.w);
                 if (q == my_rank) mask = m0;
                 if (q + 1 == my_rank) mask = m1;
               }
@@ -252,7 +254,7 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
                 const float4 t = st.tst[q];
                 const float dx = t.x - pj.x, dy = t.y - pj.y, dz = t.z - pj.z;
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                const unsigned m = __ballot_sync(FULL, in && r2 < t.w);
+                const unsigned m = __ballot_sync(FULL, r2 < t.w);
                 if (q == my_rank) mask = m;
               }
             } else if (G == 1) {
@@ -260,23 +262,23 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
                            zz = make_float2(xi.z, xi.z);
 #pragma unroll 4
               for (int u = 0; u < 32; u += 2) {  // two records per packed test
-                const float4 p0 = st.rec[min(base + kb + u, S_DENS - 1)];
-                const float4 p1 = st.rec[min(base + kb + u + 1, S_DENS - 1)];
+                const float4 p0 = st.rec[base + kb + u];
+                const float4 p1 = st.rec[base + kb + u + 1];
                 const float2 r2 = dist2_x2(xx, yy, zz, make_float2(p0.x, p1.x),
                                            make_float2(p0.y, p1.y), make_float2(p0.z, p1.z));
-                mask |= (kb + u < total && r2.x < T2) ? (1u << u) : 0u;
-                mask |= (kb + u + 1 < total && r2.y < T2) ? (2u << u) : 0u;
+                mask |= r2.x < T2 ? (1u << u) : 0u;
+                mask |= r2.y < T2 ? (2u << u) : 0u;
               }
             } else {
 #pragma unroll
               for (int u = sub; u < 32; u += G) {
-                const float4 pj = st.rec[min(base + kb + u, S_DENS - 1)];
+                const float4 pj = st.rec[base + kb + u];
                 const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                mask |= (kb + u < total && r2 < T2) ? (1u << u) : 0u;
+                mask |= r2 < T2 ? (1u << u) : 0u;
               }
             }
-            return mask;
+            return mask & bvalid;
           };
           // accepted records go into the list (those past the earlier passes' share)
           auto consume = [&](int base, int total) {
@@ -517,6 +519,8 @@ __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, co
     }
     const unsigned nlive = __popc(__ballot_sync(FULL, valid && sub == 0));
     // accept mask of the staged records kb .. kb+31 for this lane's particle
+    // (each record tested against the batch's end: reading the block whole
+    // and masking the tail, as the density loop does, measured slower here)
     auto test_block = [&](int base, int total, int kb) -> unsigned {
       unsigned mask = 0u;
       if (G == 1 && ntst <= TRANSPOSE_MAX) {
