@@ -290,7 +290,7 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
                 const int k = base + k0 + __ffs(mask) - 1;
                 mask &= mask - 1;
                 const int e = acc - skipc;
-                if (e >= 0 && e < cap) {
+                if ((unsigned)e < (unsigned)cap) {
                   const float4 pj = st.rec[k];
                   const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
                   __stcg(lst + (size_t)e * ls,
@@ -374,7 +374,9 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
           hn = hd;
         } else if (dFr > 0.0) {
           const double den = 2.0 * dFr * dFr - Fr * (s2 - 2.0 * dFr);
-          hn = den > 0.0 ? hd - hd * (2.0 * Fr * dFr / den) : hd - hd * (Fr / dFr);
+          // (Halley, or Newton where its denominator is not positive: one division)
+          const bool hal = den > 0.0;
+          hn = hd - hd * ((hal ? 2.0 * Fr * dFr : Fr) / (hal ? den : dFr));
         } else {
           hn = NAN;
         }
