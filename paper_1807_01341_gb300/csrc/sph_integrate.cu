@@ -163,16 +163,30 @@ __device__ void relevant_part(View &v, int b0, int nb) {
 // ---------------------------------------------------------------------------
 // drift / refresh of one leaf (one warp)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double rel_periodic(double d, double box) {
-  if (d > 0.5 * box) d -= box;
-  else if (d < -0.5 * box) d += box;
-  return d;
+// x - g wq (g: a corner's index on the box-wide grid of step wq) rounded
+// once, then to FP32, as the periodic image nearest the corner
+__device__ __forceinline__ float leaf_rel(double x, int g, double wq, double box, float hbox) {
+  double d = fma(-(double)g, wq, x);
+  float f = (float)d;
+  if (fabsf(f) > hbox) {  // (only across the periodic boundary)
+    d -= copysign(box, d);
+    f = (float)d;
+  }
+  return f;
 }
 
 __device__ __forceinline__ double wrap_pos(double x, double box) {
   if (x < 0.0) x += box;
   if (x >= box) x -= box;
   return x;
+}
+
+// wrap_pos with the test done on the bit patterns (no FP64 instruction in the
+// common case): x is outside [0, box) exactly when its sign bit is set or,
+// for positive x, its bits order at or above box's
+__device__ __forceinline__ double wrap_pos_fast(double x, double box) {
+  const long long xb = __double_as_longlong(x);
+  return (xb < 0 || xb >= __double_as_longlong(box)) ? wrap_pos(x, box) : x;
 }
 
 // One block per chunk (up to CHUNK leaves of one cell, contiguous particles):
@@ -205,8 +219,9 @@ __device__ void chunk_update(const View &v, int g, bool do_drift, bool do_bins) 
   const double w = ds->w;
   const long long ti = ds->ti;
   const int cx = cell / (nc * nc), cy = (cell / nc) % nc, cz = cell % nc;
-  const double ox = cx * w, oy = cy * w, oz = cz * w;
   const double wq = w / (double)(1 << MORTON_BITS);
+  const float wf = (float)w, wqf = (float)wq, hbox = (float)(0.5 * v.box);
+  const int gcx = cx << MORTON_BITS, gcy = cy << MORTON_BITS, gcz = cz << MORTON_BITS;
   const float g_ = (float)v.gamma;
   float exc = 0.0f;
   // phase 1: particles, coalesced
@@ -216,27 +231,28 @@ __device__ void chunk_update(const View &v, int g, bool do_drift, bool do_bins) 
       const long long td = v.ti_drift[i];
       if (td != ti) {
         const double dt = (double)(ti - td) * v.dt_min;
-        x = wrap_pos(x + (double)v.vx[i] * dt, v.box);
-        y = wrap_pos(y + (double)v.vy[i] * dt, v.box);
-        z = wrap_pos(z + (double)v.vz[i] * dt, v.box);
+        x = wrap_pos_fast(x + (double)v.vx[i] * dt, v.box);
+        y = wrap_pos_fast(y + (double)v.vy[i] * dt, v.box);
+        z = wrap_pos_fast(z + (double)v.vz[i] * dt, v.box);
         v.x[i] = x;
         v.y[i] = y;
         v.z[i] = z;
         v.ti_drift[i] = ti;
       }
     }
-    // distance outside the particle's cell (the rebuild criterion)
-    const double cxr = rel_periodic(x - ox, v.box), cyr = rel_periodic(y - oy, v.box),
-                 czr = rel_periodic(z - oz, v.box);
-    const float e = (float)fmax(fmax(fmax(-cxr, cxr - w), fmax(-cyr, cyr - w)), fmax(-czr, czr - w));
-    exc = fmaxf(exc, e);
-    // position relative to the leaf corner
+    // position relative to the leaf corner (the periodic image nearest it).
+    // FP64 runs at 1/64 of the FP32 rate on this GPU and bounds this pass,
+    // so the only FP64 step is one fused multiply-add from the corner's
+    // index on the box-wide Morton grid (one rounding).
     const uint32_t lk = v.leaf_k[v.pleaf[i]];
-    const double lx = (double)(cx * (1 << MORTON_BITS) + leaf_kx(lk)) * wq;
-    const double ly = (double)(cy * (1 << MORTON_BITS) + leaf_ky(lk)) * wq;
-    const double lz = (double)(cz * (1 << MORTON_BITS) + leaf_kz(lk)) * wq;
-    const float fx = (float)rel_periodic(x - lx, v.box), fy = (float)rel_periodic(y - ly, v.box),
-                fz = (float)rel_periodic(z - lz, v.box);
+    const int kx = leaf_kx(lk), ky = leaf_ky(lk), kz = leaf_kz(lk);
+    const float fx = leaf_rel(x, gcx + kx, wq, v.box, hbox);
+    const float fy = leaf_rel(y, gcy + ky, wq, v.box, hbox);
+    const float fz = leaf_rel(z, gcz + kz, wq, v.box, hbox);
+    // distance outside the particle's cell (the rebuild criterion), in FP32
+    // (the bound is padded by 1e-6 of the cell width below)
+    const float ex = fx + (float)kx * wqf, ey = fy + (float)ky * wqf, ez = fz + (float)kz * wqf;
+    exc = fmaxf(exc, fmaxf(fmaxf(fmaxf(-ex, ex - wf), fmaxf(-ey, ey - wf)), fmaxf(-ez, ez - wf)));
     const int bi = v.bin[i] & (MAX_BINS - 1);
     // (the middle of the particle's step: its length is 2^bin, or shorter once
     // the limiter woke it)
@@ -246,7 +262,7 @@ __device__ void chunk_update(const View &v, int g, bool do_drift, bool do_bins) 
     const float vpx = v.vx[i] + v.ax[i] * fdtp;
     const float vpy = v.vy[i] + v.ay[i] * fdtp;
     const float vpz = v.vz[i] + v.az[i] * fdtp;
-    const float Ap = (float)((double)v.A[i] + (double)v.Adot[i] * dtp);
+    const float Ap = v.A[i] + v.Adot[i] * fdtp;  // (as the density loop predicts it)
     float hh = v.h[i], rho = v.rho[i];
     if (v.predict) {
       // Gadget-2 prediction from the last density (at the start of the step):
@@ -275,7 +291,6 @@ __device__ void chunk_update(const View &v, int g, bool do_drift, bool do_bins) 
   if (lane == 0) s_exc[warp] = exc;
   __syncthreads();  // the chunk's records are in shared memory
   // phase 2: one leaf per warp, one particle per lane
-  const float wqf = (float)wq;
   for (int q = warp; q < l1 - l0; q += (int)(blockDim.x >> 5)) {
     const int leaf = l0 + q;
     const int a = v.leaf_start[leaf], cnt = v.leaf_start[leaf + 1] - a;
@@ -343,7 +358,7 @@ __device__ void chunk_update(const View &v, int g, bool do_drift, bool do_bins) 
     if (lane == 0) {
       v.chunk_lo[g] = make_float4(lx, ly, lz, Hm);
       v.chunk_hi[g] = make_float4(hx, hy, hz, 0.0f);
-      atomic_max_float_pos(&v.ds->excursion_bits, exc);
+      atomic_max_float_pos(&v.ds->excursion_bits, exc + 1e-6f * wf);
       atomic_max_float_pos(&v.ds->Hmax_bits, Hm);
     }
   }
