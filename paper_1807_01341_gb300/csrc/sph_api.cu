@@ -45,8 +45,8 @@ struct Buffers {
   // leaves (at most one per particle)
   int32_t *leaf_start = nullptr, *leaf_cell = nullptr;
   uint32_t *leaf_k = nullptr;
-  // chunks of CHUNK leaves (at most one per particle)
-  int32_t *chunk_cell = nullptr;
+  // chunks: octree nodes of at most CHUNK leaves (at most one per particle)
+  int32_t *chunk_cell = nullptr, *chunk_leaf_start = nullptr, *leaf_chunk = nullptr;
   float4 *chunk_lo = nullptr, *chunk_hi = nullptr;
   float4 *leaf_lo = nullptr, *leaf_hi = nullptr;
   uint8_t *leaf_min_bin = nullptr;
@@ -223,6 +223,8 @@ View make_view(const sph_ctx *ctx, const sph_particles *p) {
   v.cell_leaf_start = b.cell_leaf_start;
   v.cell_chunk_start = b.cell_chunk_start;
   v.chunk_cell = b.chunk_cell;
+  v.chunk_leaf_start = b.chunk_leaf_start;
+  v.leaf_chunk = b.leaf_chunk;
   v.chunk_lo = b.chunk_lo;
   v.chunk_hi = b.chunk_hi;
   v.cell_stamp = b.cell_stamp;
@@ -448,10 +450,17 @@ int build_cells(sph_ctx *ctx, sph_particles *p, cudaStream_t st) {
                          st));
   SPH_CUDA(cudaMemcpyAsync(SPH_DS_FIELD(b.ds, n_groups), b.leaf_offsets + n_cells, sizeof(int),
                            cudaMemcpyDeviceToDevice, st));
-  // chunks of CHUNK consecutive leaves per cell (the leaf counters are free again)
-  SPH_CUDA(launch_chunks(b.cell_leaf_start, (int)n_cells, b.leaf_counts, b.leaf_offsets, b.scan_tmp,
-                         b.cell_chunk_start, b.chunk_cell, st));
-  SPH_CUDA(cudaMemcpyAsync(SPH_DS_FIELD(b.ds, n_chunks), b.leaf_offsets + n_cells, sizeof(int),
+  // chunks: octree nodes of at most CHUNK leaves (scratch free again by now:
+  // the leaves' first keys in the spare key buffer, the node lists in the
+  // sorted keys' buffer, the marks in b.scratch, the counters in the
+  // histogram, the unused corners in b.vals[0])
+  const unsigned int *d_n_chunks = nullptr;
+  SPH_CUDA(launch_chunks(skeys, b.leaf_start, b.cell_leaf_start, (int)n_cells, n_leaves_h,
+                         alt ? b.keys[0] : b.keys[1], (uint8_t *)b.scratch,
+                         reinterpret_cast<int2 *>(skeys), b.hist, b.scan_tmp,
+                         reinterpret_cast<uint32_t *>(b.vals[0]), b.chunk_leaf_start, b.chunk_cell,
+                         b.cell_chunk_start, b.leaf_chunk, 2 * ctx->grid_util, &d_n_chunks, st));
+  SPH_CUDA(cudaMemcpyAsync(SPH_DS_FIELD(b.ds, n_chunks), d_n_chunks, sizeof(int),
                            cudaMemcpyDeviceToDevice, st));
   // device state of the new structure
   int ncs[2] = {nc, (int)n_cells};
@@ -764,7 +773,8 @@ int sph_create(const sph_params *params, int64_t n_max, sph_ctx **out) {
         (r = dalloc(&b.scan_tmp, 4096)) || (r = dalloc((char **)&b.scratch, 8 * n)) ||
         (r = dalloc(&b.perm, n)) || (r = dalloc(&b.perm_tmp, n)) || (r = dalloc(&b.pcell, n)) ||
         (r = dalloc(&b.leaf_start, n + 1)) || (r = dalloc(&b.leaf_cell, n)) || (r = dalloc(&b.leaf_k, n)) ||
-        (r = dalloc(&b.chunk_cell, n)) || (r = dalloc(&b.chunk_lo, n)) || (r = dalloc(&b.chunk_hi, n)) ||
+        (r = dalloc(&b.chunk_cell, n)) || (r = dalloc(&b.chunk_leaf_start, n + 1)) ||
+        (r = dalloc(&b.leaf_chunk, n)) || (r = dalloc(&b.chunk_lo, n)) || (r = dalloc(&b.chunk_hi, n)) ||
         (r = dalloc(&b.leaf_lo, n)) || (r = dalloc(&b.leaf_hi, n)) ||
         (r = dalloc(&b.leaf_min_bin, n)) || (r = dalloc(&b.leaf_bin_mask, n)) ||
         (r = dalloc(&b.q_active, n)) || (r = dalloc(&b.q_drift, n)) || (r = dalloc(&b.q_bin, n)) ||
@@ -834,7 +844,7 @@ int sph_destroy(sph_ctx *ctx) {
   if (b.scratch) cudaFree(b.scratch);
   dfree(b.perm); dfree(b.perm_tmp); dfree(b.pcell);
   dfree(b.leaf_start); dfree(b.leaf_cell); dfree(b.leaf_k);
-  dfree(b.chunk_cell); dfree(b.chunk_lo); dfree(b.chunk_hi); dfree(b.leaf_lo); dfree(b.leaf_hi);
+  dfree(b.chunk_cell); dfree(b.chunk_leaf_start); dfree(b.leaf_chunk); dfree(b.chunk_lo); dfree(b.chunk_hi); dfree(b.leaf_lo); dfree(b.leaf_hi);
   dfree(b.leaf_min_bin); dfree(b.leaf_bin_mask);
   dfree(b.q_active); dfree(b.q_drift); dfree(b.q_bin); dfree(b.q_group);
   dfree(b.pleaf); dfree(b.group_leaf0); dfree(b.group_cell); dfree(b.group_cost);

@@ -459,21 +459,28 @@ __global__ void k_bin_hist(const int8_t *__restrict__ bin, long long n, int *__r
   if (threadIdx.x < MAX_BINS && h[threadIdx.x]) atomicAdd(&out[threadIdx.x], h[threadIdx.x]);
 }
 
-__global__ void k_chunk_count(const int32_t *__restrict__ cell_leaf_start, int n_cells,
-                              unsigned int *__restrict__ counts) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c > n_cells) return;
-  counts[c] = c == n_cells ? 0u
-                           : (unsigned int)((cell_leaf_start[c + 1] - cell_leaf_start[c] + CHUNK - 1) / CHUNK);
+// Chunks: the leaves of a cell placed in the cell's octree by the Morton code
+// of their first particles and split as the particles are split into leaves
+// (k_leaf_cells, k_leaf_level), with CHUNK leaves in place of leaf_max
+// particles.  A chunk is then an octree node (or a run of consecutive sibling
+// nodes) holding at most CHUNK leaves, so its box stays compact; runs of CHUNK
+// consecutive leaves in Morton order can straddle the boundary of a large
+// node and span a box far wider than their leaves.
+__global__ void k_leaf_keys(const unsigned long long *__restrict__ keys,
+                            const int32_t *__restrict__ leaf_start, int n_leaves,
+                            unsigned long long *__restrict__ leaf_keys) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l < n_leaves) leaf_keys[l] = keys[leaf_start[l]];
 }
 
-__global__ void k_chunk_write(const unsigned int *__restrict__ offsets, int n_cells,
-                              int32_t *__restrict__ cell_chunk_start, int32_t *__restrict__ chunk_cell) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c > n_cells) return;
-  cell_chunk_start[c] = (int32_t)offsets[c];
-  if (c == n_cells) return;
-  for (unsigned int g = offsets[c]; g < offsets[c + 1]; g++) chunk_cell[g] = c;
+// leaf -> chunk, one thread per chunk (at most n_leaves of them)
+__global__ void k_leaf_chunk(const int32_t *__restrict__ chunk_leaf_start,
+                             const unsigned int *__restrict__ n_chunks, int n_leaves,
+                             int32_t *__restrict__ leaf_chunk) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (int)*n_chunks) return;
+  const int a = chunk_leaf_start[g], b = min(chunk_leaf_start[g + 1], n_leaves);
+  for (int l = a; l < b; l++) leaf_chunk[l] = g;
 }
 
 // Work groups: the leaves of a cell taken in order, a new group whenever the
@@ -658,16 +665,29 @@ cudaError_t launch_leaves(const unsigned long long *sorted_keys, const int32_t *
   return cudaGetLastError();
 }
 
-// Chunks: the leaves of each cell in groups of CHUNK, numbered cell by cell.
-cudaError_t launch_chunks(const int32_t *cell_leaf_start, int n_cells, unsigned int *counts,
-                          unsigned int *offsets, unsigned int *scan_tmp, int32_t *cell_chunk_start,
-                          int32_t *chunk_cell, cudaStream_t st) {
-  note_launches(2);
-  k_chunk_count<<<blocks_for(n_cells + 1, 256), 256, 0, st>>>(cell_leaf_start, n_cells, counts);
-  cudaError_t e = exclusive_scan_u32(counts, offsets, n_cells + 1, scan_tmp, st);
-  if (e != cudaSuccess) return e;
-  k_chunk_write<<<blocks_for(n_cells + 1, 256), 256, 0, st>>>(offsets, n_cells, cell_chunk_start,
-                                                              chunk_cell);
+// Chunks: octree nodes of at most CHUNK leaves (k_leaf_keys), numbered cell by
+// cell; the leaf build's kernels run over the leaves' first keys.  `nodes`
+// holds n_leaves int2, `lead` n_leaves bytes, `corner_tmp` n_leaves words
+// (written, unused), `work` the counters of launch_leaves.
+cudaError_t launch_chunks(const unsigned long long *sorted_keys, const int32_t *leaf_start,
+                          const int32_t *cell_leaf_start, int n_cells, int n_leaves,
+                          unsigned long long *leaf_keys, uint8_t *lead, int2 *nodes,
+                          unsigned int *work, unsigned int *scan_tmp, uint32_t *corner_tmp,
+                          int32_t *chunk_leaf_start, int32_t *chunk_cell,
+                          int32_t *cell_chunk_start, int32_t *leaf_chunk, int grid,
+                          const unsigned int **n_chunks, cudaStream_t st) {
+  if (n_leaves > 0) {
+    note_launches(1);
+    k_leaf_keys<<<blocks_for(n_leaves, 256), 256, 0, st>>>(sorted_keys, leaf_start, n_leaves,
+                                                            leaf_keys);
+  }
+  cudaError_t e = launch_leaves(leaf_keys, cell_leaf_start, n_cells, n_leaves, CHUNK, lead, nodes,
+                                work, scan_tmp, chunk_leaf_start, chunk_cell, corner_tmp,
+                                cell_chunk_start, grid, n_chunks, st);
+  if (e != cudaSuccess || n_leaves == 0) return e;
+  note_launches(1);
+  k_leaf_chunk<<<blocks_for(n_leaves, 256), 256, 0, st>>>(chunk_leaf_start, *n_chunks, n_leaves,
+                                                           leaf_chunk);
   return cudaGetLastError();
 }
 

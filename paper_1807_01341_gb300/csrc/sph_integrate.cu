@@ -212,8 +212,8 @@ __device__ void chunk_update(const View &v, int g, bool do_drift, bool do_bins) 
   const DevState *ds = v.ds;
   const int lane = lane_id(), warp = threadIdx.x >> 5;
   const int cell = v.chunk_cell[g];
-  const int l0 = v.cell_leaf_start[cell] + CHUNK * (g - v.cell_chunk_start[cell]);
-  const int l1 = min(l0 + CHUNK, v.cell_leaf_start[cell + 1]);
+  const int l0 = v.chunk_leaf_start[g];
+  const int l1 = min(v.chunk_leaf_start[g + 1], l0 + CHUNK);  // (at most CHUNK by construction)
   const int pa = v.leaf_start[l0], pb = v.leaf_start[l1];
   const int nc = ds->nc;
   const double w = ds->w;

@@ -19,7 +19,7 @@ constexpr int KEY_MORTON_BITS = 3 * MORTON_BITS;
 constexpr int MAX_BINS = 64;
 constexpr int WARPS_PER_BLOCK = 8;
 constexpr int LEAF_MAX_LIMIT = 64;
-constexpr int CHUNK = 16;          // leaves per chunk (at most 32: one warp ballot)
+constexpr int CHUNK = 16;          // most leaves in a chunk (at most 32: one warp ballot)
 constexpr int WG_MAX = 32;         // particles per work group of the pair loops (one per lane)
 
 // Device-resident state of the context: the integer timeline, the sizes of
@@ -35,7 +35,7 @@ struct DevState {
   int nc;                // cells per axis
   int n_cells;           // nc^3
   int n_leaves;
-  int n_chunks;          // groups of up to CHUNK consecutive leaves of one cell
+  int n_chunks;          // octree nodes of up to CHUNK leaves of one cell (see launch_chunks)
   int n_groups;          // work groups: runs of consecutive leaves of one cell, <= WG_MAX particles
   int n_active_groups;   // work groups holding active particles (light ones from the front of
                          // q_group, heavy ones from its back; see n_heavy_groups)
@@ -106,8 +106,9 @@ struct View {
   unsigned int *cell_stamp;  // [n_cells] epoch at which the cell was last marked active
   unsigned int *cell_rel_stamp;  // [n_cells] epoch at which the cell was queued for drift
   int32_t *cell_chunk_start; // [n_cells + 1] first chunk of each cell
-  int32_t *chunk_cell;       // [n_chunks] cell of each chunk (its leaves: CHUNK from
-                             // cell_leaf_start + CHUNK * (chunk - cell_chunk_start))
+  int32_t *chunk_cell;       // [n_chunks] cell of each chunk
+  int32_t *chunk_leaf_start; // [n_chunks + 1] first leaf of each chunk (at most CHUNK leaves)
+  int32_t *leaf_chunk;       // [n_leaves] chunk of each leaf
   float4 *chunk_lo;          // chunk bbox min, cell frame; w = max H in the chunk
   float4 *chunk_hi;          // chunk bbox max, cell frame
   int32_t *leaf_start;       // [n_leaves + 1] first particle of each leaf
@@ -291,9 +292,13 @@ cudaError_t launch_groups(const int32_t *cell_leaf_start, const int32_t *leaf_st
                           int n_leaves_max, unsigned int *counts, unsigned int *offsets,
                           unsigned int *scan_tmp, int32_t *group_leaf0, int32_t *group_cell,
                           int32_t *pleaf, int n_leaves_host, cudaStream_t st);
-cudaError_t launch_chunks(const int32_t *cell_leaf_start, int n_cells, unsigned int *counts,
-                          unsigned int *offsets, unsigned int *scan_tmp, int32_t *cell_chunk_start,
-                          int32_t *chunk_cell, cudaStream_t st);
+cudaError_t launch_chunks(const unsigned long long *sorted_keys, const int32_t *leaf_start,
+                          const int32_t *cell_leaf_start, int n_cells, int n_leaves,
+                          unsigned long long *leaf_keys, uint8_t *lead, int2 *nodes,
+                          unsigned int *work, unsigned int *scan_tmp, uint32_t *corner_tmp,
+                          int32_t *chunk_leaf_start, int32_t *chunk_cell,
+                          int32_t *cell_chunk_start, int32_t *leaf_chunk, int grid,
+                          const unsigned int **n_chunks, cudaStream_t st);
 // sph_integrate.cu
 cudaError_t launch_refresh_all(const View &v, cudaStream_t st);
 cudaError_t launch_mark(const View &v, long long ti_or_neg, cudaStream_t st);

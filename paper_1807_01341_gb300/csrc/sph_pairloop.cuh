@@ -488,8 +488,7 @@ __device__ __forceinline__ int search(const View &v, const CellFrame &F, const R
       if (!(SPH_IN(v.ds, l0, l1 + 1, SPH_CHECK_CELL_LEAVES) &&
             SPH_IN(v.ds, l1, v.ds->n_leaves + 1, SPH_CHECK_CELL_LEAVES) &&
             SPH_IN(v.ds, g0, v.ds->n_chunks + 1, SPH_CHECK_CELL_LEAVES) &&
-            SPH_IN(v.ds, g0 + nch, v.ds->n_chunks + 1, SPH_CHECK_CELL_LEAVES) &&
-            SPH_IN(v.ds, (long long)CHUNK * nch - (l1 - l0), CHUNK, SPH_CHECK_CELL_LEAVES)))
+            SPH_IN(v.ds, g0 + nch, v.ds->n_chunks + 1, SPH_CHECK_CELL_LEAVES)))
         nch = 0;
     }
   }
@@ -512,8 +511,13 @@ __device__ __forceinline__ int search(const View &v, const CellFrame &F, const R
       LeafBox cbx = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       if (t < T) {
         const int k = t - cs;  // chunk number inside cell ci
-        la = cl0 + CHUNK * k;
-        lb = min(la + CHUNK, cl1);
+        la = v.chunk_leaf_start[cg0 + k];
+        lb = v.chunk_leaf_start[cg0 + k + 1];
+        // (checks build: a chunk whose leaves leave its cell's range is empty)
+        if (!(SPH_IN(v.ds, la - cl0, cl1 - cl0 + 1, SPH_CHECK_CELL_LEAVES) &&
+              SPH_IN(v.ds, lb - la, CHUNK + 1, SPH_CHECK_CELL_LEAVES) &&
+              SPH_IN(v.ds, lb - cl0, cl1 - cl0 + 1, SPH_CHECK_CELL_LEAVES)))
+          lb = la;
         // part >= 0: a warp of a cooperating block takes only the chunks
         // whose index is its warp number modulo WARPS_PER_BLOCK
         okc = part < 0 || ((cg0 + k) & (WARPS_PER_BLOCK - 1)) == part;

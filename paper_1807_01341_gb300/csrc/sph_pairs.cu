@@ -430,8 +430,7 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
     float Hm = 0.0f;
     for (int k = v.leaf_start[leaf]; k < v.leaf_start[leaf + 1]; k++) Hm = fmaxf(Hm, v.rec_xH[k].w);
     reinterpret_cast<float *>(&v.leaf_lo[leaf])[3] = Hm;
-    const int cell = v.leaf_cell[leaf];
-    const int g = v.cell_chunk_start[cell] + (leaf - v.cell_leaf_start[cell]) / CHUNK;
+    const int g = v.leaf_chunk[leaf];
     atomic_max_float_pos(reinterpret_cast<unsigned int *>(&v.chunk_lo[g]) + 3, Hm);
     atomic_max_float_pos(&v.ds->Hmax_bits, Hm);
   }
@@ -1103,10 +1102,7 @@ __global__ void __launch_bounds__(PT, 2) k_group_cost(View v) {
     };
     auto chunk_ok = [&](int c, float sx, float sy, float sz) {
       if (box_gap2(clx, cly, clz, chx, chy, chz, v.chunk_lo[c], v.chunk_hi[c], sx, sy, sz) < Rc * Rc) {
-        const int cell = v.chunk_cell[c];
-        const int la = v.cell_leaf_start[cell] + CHUNK * (c - v.cell_chunk_start[cell]);
-        const int lb = min(la + CHUNK, v.cell_leaf_start[cell + 1]);
-        count += v.leaf_start[lb] - v.leaf_start[la];
+        count += v.leaf_start[v.chunk_leaf_start[c + 1]] - v.leaf_start[v.chunk_leaf_start[c]];
       }
       return false;
     };
