@@ -69,7 +69,7 @@ struct DevState {
   unsigned int excursion_bits;  // max distance (float bits) of a particle outside its cell
   unsigned int Hmax_bits;       // max kernel support H (float bits) over all particles
   unsigned int want_h_bits;     // largest h an iteration wanted beyond the cell limit
-  unsigned int pad3;
+  int dens_split;               // parts per work group of the last whole-step density launch
   // counters of the step in progress (reset when a step starts, added to the
   // totals when it completes, so a halted attempt leaves no trace)
   unsigned long long s_pairs_density, s_pairs_force, s_cand_density, s_cand_force;

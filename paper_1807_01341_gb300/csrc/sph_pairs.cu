@@ -47,6 +47,20 @@ __device__ __forceinline__ float *red_area(int warp) {
   return reinterpret_cast<float *>(smem_dyn + (size_t)warp * St::bytes() + St::red_offset());
 }
 
+// The largest support of each leaf [L0, L1) of a work group (one lane per
+// leaf) after its particles' h changed; the chunk's and the global largest
+// support keep upper bounds.
+__device__ __forceinline__ void leaf_hmax_update(const View &v, int L0, int L1) {
+  const int leaf = L0 + lane_id();
+  if (leaf >= L1) return;
+  float Hm = 0.0f;
+  for (int k = v.leaf_start[leaf]; k < v.leaf_start[leaf + 1]; k++) Hm = fmaxf(Hm, v.rec_xH[k].w);
+  reinterpret_cast<float *>(&v.leaf_lo[leaf])[3] = Hm;
+  const int g = v.leaf_chunk[leaf];
+  atomic_max_float_pos(reinterpret_cast<unsigned int *>(&v.chunk_lo[g]) + 3, Hm);
+  atomic_max_float_pos(&v.ds->Hmax_bits, Hm);
+}
+
 // ---------------------------------------------------------------------------
 // density loop + smoothing-length iteration for the active particles of a group
 // ---------------------------------------------------------------------------
@@ -142,11 +156,17 @@ __device__ __forceinline__ void dens_list(DSum &s, const float2 *lst, int ls, in
 // same pairs in the same order with the same arithmetic.  A work group is
 // handled by one warp (sharing it between the warps of a block, as the force
 // loop does in sparse steps, was measured slower here: every warp pays the
-// search's latency, then waits at the barriers of each h iteration).
+// search's latency, then waits at the barriers of each h iteration), or, in
+// steps with few active groups, split by its active particles into `nslices`
+// consecutive slices, each a warp's own work item (slice `slice`): no warp
+// waits for another, and a slice's sums are those the whole group would give
+// (a particle's candidates and their order do not depend on the particles it
+// shares a warp with).  A split group's leaves get their largest support from
+// k_leaf_hmax, after every slice is done.
 template <int G>
-__device__ void density_group(const View &v, int wg, int flags, int bin_filter, int m_act,
-                              const CellFrame &F, float hcap, float exc, long long ti,
-                              StageD &st, WarpCounters &wc) {
+__device__ void density_group(const View &v, int wg, int slice, int nslices, int flags,
+                              int bin_filter, int m_act, const CellFrame &F, float hcap, float exc,
+                              long long ti, StageD &st, WarpCounters &wc) {
   const int lane = lane_id();
   const int warp = threadIdx.x >> 5;
   constexpr int part = -1;       // (every chunk of the neighbour cells)
@@ -155,6 +175,14 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
   const int a = W.a, b = W.b;
   const int nact = leaf_actives(v, a, b, m_act, bin_filter, st.act);
   if (nact == 0) return;
+  // this warp's slice [s0, s1) of the group's active particles
+  int s0 = 0, s1 = nact;
+  if (nslices > 1) {
+    const int per = (nact + nslices - 1) / nslices;
+    s0 = min(nact, slice * per);
+    s1 = min(nact, s0 + per);
+    if (s0 == s1) return;
+  }
   constexpr int P = 32 / G;
   const int grp = lane / G, sub = lane % G;
   const unsigned gmask = G == 32 ? FULL : ((1u << G) - 1u) << (grp * G);  // this lane's group
@@ -172,9 +200,9 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
   constexpr int ls = 32;
   float2 *const lst = v.nbr + ((size_t)blockIdx.x * WARPS_PER_BLOCK + warp) * 32 * v.list_cap + lane;
 
-  for (int r = 0; r < nact && !st.failed; r += P) {
+  for (int r = s0; r < s1 && !st.failed; r += P) {
     const int slot = r + grp;
-    const bool valid = slot < nact;
+    const bool valid = slot < s1;
     const int i = valid ? st.act[slot] : a;
     const float4 xl = v.rec_xm[i];  // position in its own leaf's frame
     const float3 lo3 = leaf_offset(v, i, F);
@@ -423,17 +451,9 @@ __device__ void density_group(const View &v, int wg, int flags, int bin_filter, 
       }
     }
   }
-  // largest support of each leaf after the update; the chunk's keeps a bound
+  // largest support of each leaf after the update (a split group's: k_leaf_hmax)
   __syncwarp();
-  if (writer && W.L0 + lane < W.L1) {
-    const int leaf = W.L0 + lane;
-    float Hm = 0.0f;
-    for (int k = v.leaf_start[leaf]; k < v.leaf_start[leaf + 1]; k++) Hm = fmaxf(Hm, v.rec_xH[k].w);
-    reinterpret_cast<float *>(&v.leaf_lo[leaf])[3] = Hm;
-    const int g = v.leaf_chunk[leaf];
-    atomic_max_float_pos(reinterpret_cast<unsigned int *>(&v.chunk_lo[g]) + 3, Hm);
-    atomic_max_float_pos(&v.ds->Hmax_bits, Hm);
-  }
+  if (writer && nslices == 1) leaf_hmax_update(v, W.L0, W.L1);
   __syncwarp();
 }
 
@@ -449,8 +469,9 @@ __device__ __forceinline__ void request_wake(const View &v, int j, int b) {
 // VAR: the code of the scheme's variants (Balsara switch, neighbour limiter)
 // is compiled in; the base scheme runs the instance without it.
 template <int G, bool COOP, bool VAR>
-__device__ void force_group(const View &v, int wg, int bin_filter, int m_act, const CellFrame &F,
-                            float Hmax, float exc, StageF &st, WarpCounters &wc) {
+__device__ void force_group(const View &v, int wg, int slice, int nslices, int bin_filter, int m_act,
+                            const CellFrame &F, float Hmax, float exc, StageF &st,
+                            WarpCounters &wc) {
   static_assert(!COOP || G == 1, "cooperative groups use one lane per particle");
   const int lane = lane_id();
   const int warp = threadIdx.x >> 5;
@@ -460,6 +481,14 @@ __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, co
   const int a = W.a, b = W.b;
   const int nact = leaf_actives(v, a, b, m_act, bin_filter, st.act);
   if (nact == 0) return;
+  // this warp's slice [s0, s1) of the group's active particles (a split group)
+  int s0 = 0, s1 = nact;
+  if (nslices > 1) {
+    const int per = (nact + nslices - 1) / nslices;
+    s0 = min(nact, slice * per);
+    s1 = min(nact, s0 + per);
+    if (s0 == s1) return;
+  }
   constexpr int P = 32 / G;
   const int grp = lane / G, sub = lane % G;
   const float qox = F.kx * F.wq, qoy = F.ky * F.wq, qoz = F.kz * F.wq;
@@ -471,9 +500,9 @@ __device__ void force_group(const View &v, int wg, int bin_filter, int m_act, co
   const float4 *srcs[3] = {v.rec_xH, v.rec_v, v.rec_h};
   const float4 *sx_rec = st.rec, *sv_rec = st.rec + S_FORCE, *sh_rec = st.rec + 2 * S_FORCE;
 
-  for (int r = 0; r < nact && !st.failed; r += P) {
+  for (int r = s0; r < s1 && !st.failed; r += P) {
     const int slot = r + grp;
-    const bool valid = slot < nact;
+    const bool valid = slot < s1;
     const int i = valid ? st.act[slot] : a;
     const float4 xl = v.rec_xH[i];
     const float3 lo3 = leaf_offset(v, i, F);
@@ -914,6 +943,16 @@ __device__ __forceinline__ int density_item(const View &v, const DevState *ds, i
   return active_group(v, ds, k);
 }
 
+// Work groups are split into at most SPLIT_MAX slices of their active
+// particles, each taken by its own warp, when a whole-step launch (one lane
+// per particle) has at least twice as many warps as active groups: the
+// slices fill the warps that would otherwise idle, and a step's time is that
+// of its slowest work item.
+constexpr int SPLIT_MAX = 8;
+__device__ __forceinline__ int split_parts(int nq, int nwarps) {
+  return nq > 0 ? max(1, min(SPLIT_MAX, nwarps / nq)) : 1;
+}
+
 // Testing (a library built with SPH_CHECKS; sph_params.test_bad_group): the
 // first test_bad_group claims replace the work group taken from the queue by
 // an index past the last group, which the SPH_CHECK_GROUP check catches.
@@ -960,8 +999,14 @@ __global__ void __launch_bounds__(PT, 2) k_density(View v, int flags, int bin_fi
   const int m_act = ds->m_act;
   const long long ti = ds->ti;
   const int nq = density_count(ds, bin_filter);
+  // whole-step persistent launches split the groups of sparse steps (their
+  // leaves' largest supports then come from k_leaf_hmax, which reads nparts)
+  const int nparts = (G == 1 && bin_filter < 0 && persistent)
+                         ? split_parts(nq, (int)gridDim.x * WARPS_PER_BLOCK) : 1;
+  if (bin_filter < 0 && blockIdx.x == 0 && threadIdx.x == 0) ds->dens_split = nparts;
+  const int nitems = nq * nparts;
   WarpCounters wc = {0, 0, 0, 0, 0, 0};
-  // every work group one per warp: pulled from a head (persistent) or by index
+  // every work item one per warp: pulled from a head (persistent) or by index
   // (one call site of the loop keeps the kernel's code small)
   for (int k = 0;; k++) {
     int item;
@@ -970,14 +1015,16 @@ __global__ void __launch_bounds__(PT, 2) k_density(View v, int flags, int bin_fi
       if (lane == 0) item = atomicAdd(&ds->head_density, 1);
       item = __shfl_sync(FULL, item, 0);
     } else {
-      item = k == 0 ? (int)blockIdx.x * WARPS_PER_BLOCK + warp : nq;
+      item = k == 0 ? (int)blockIdx.x * WARPS_PER_BLOCK + warp : nitems;
     }
-    if (item >= nq || st.failed) break;
-    int wg = density_item(v, ds, bin_filter, item);
+    if (item >= nitems || st.failed) break;
+    const int q = item / nparts;
+    int wg = density_item(v, ds, bin_filter, q);
     if (lane == 0) wg = planted_group(ds, wg);
     wg = __shfl_sync(FULL, wg, 0);
     if (!SPH_IN(ds, wg, ds->n_groups, SPH_CHECK_GROUP)) break;
-    density_group<G>(v, wg, flags, bin_filter, m_act, frame_of(v, ds, wg), hcap, exc, ti, st, wc);
+    density_group<G>(v, wg, item - q * nparts, nparts, flags, bin_filter, m_act,
+                     frame_of(v, ds, wg), hcap, exc, ti, st, wc);
   }
   flush_counters(ds, wc, true);
 }
@@ -1015,12 +1062,17 @@ __global__ void __launch_bounds__(PT, 2) k_force(View v, int bin_filter, int per
         if (item >= qs.ncoop || st.failed) break;
         const int wg = coop_group(v, ds, bin_filter, item);
         if (!SPH_IN(ds, wg, ds->n_groups, SPH_CHECK_GROUP)) break;
-        force_group<1, true, VAR>(v, wg, bin_filter, m_act, frame_of(v, ds, wg), Hmax, exc, st,
-                                  wc);
+        force_group<1, true, VAR>(v, wg, 0, 1, bin_filter, m_act, frame_of(v, ds, wg), Hmax, exc,
+                                  st, wc);
       }
     }
   }
   if (persistent || (int)blockIdx.x >= cb) {
+    // (whole-step persistent launches split the groups when warps outnumber
+    // them, as the density loop does)
+    const int nparts = (G == 1 && bin_filter < 0 && persistent)
+                           ? split_parts(qs.nwarp, (int)gridDim.x * WARPS_PER_BLOCK) : 1;
+    const int nitems = qs.nwarp * nparts;
     for (int k = 0;; k++) {
       int item;
       if (persistent) {
@@ -1028,16 +1080,38 @@ __global__ void __launch_bounds__(PT, 2) k_force(View v, int bin_filter, int per
         if (lane == 0) item = atomicAdd(&ds->head_force, 1);
         item = __shfl_sync(FULL, item, 0);
       } else {
-        item = k == 0 ? ((int)blockIdx.x - cb) * WARPS_PER_BLOCK + warp : qs.nwarp;
+        item = k == 0 ? ((int)blockIdx.x - cb) * WARPS_PER_BLOCK + warp : nitems;
       }
-      if (item >= qs.nwarp || st.failed) break;
-      const int wg = warp_group<G>(v, ds, bin_filter, item);
+      if (item >= nitems || st.failed) break;
+      const int q = item / nparts;
+      const int wg = warp_group<G>(v, ds, bin_filter, q);
       if (!SPH_IN(ds, wg, ds->n_groups, SPH_CHECK_GROUP)) break;
-      force_group<G, false, VAR>(v, wg, bin_filter, m_act, frame_of(v, ds, wg), Hmax, exc, st,
-                                 wc);
+      force_group<G, false, VAR>(v, wg, item - q * nparts, nparts, bin_filter, m_act,
+                                 frame_of(v, ds, wg), Hmax, exc, st, wc);
     }
   }
   flush_counters(ds, wc, false);
+}
+
+// The largest support of the leaves of every work group that the last
+// whole-step density launch split (one warp per group; nothing when it split
+// none).
+__global__ void __launch_bounds__(PT) k_leaf_hmax(View v) {
+  DevState *ds = v.ds;
+  if (ds->halt || ds->dens_split <= 1) return;
+  const int nq = ds->n_active_groups + ds->n_heavy_groups;
+  const int nw = (int)(gridDim.x * blockDim.x) >> 5;
+  for (int k = (int)(blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nq; k += nw) {
+    const int wg = active_group(v, ds, k);
+    if (!SPH_IN(ds, wg, ds->n_groups, SPH_CHECK_GROUP)) break;
+    const int L0 = v.group_leaf0[wg], L1 = v.group_leaf0[wg + 1];
+    // (checks build: a leaf range out of bounds is skipped, as group_of does)
+    if (!(SPH_IN(ds, L0, L1, SPH_CHECK_GROUP_LEAVES) &&
+          SPH_IN(ds, L1 - 1, ds->n_leaves, SPH_CHECK_GROUP_LEAVES) &&
+          SPH_IN(ds, L1 - L0 - 1, WG_MAX, SPH_CHECK_GROUP_LEAVES)))
+      continue;
+    leaf_hmax_update(v, L0, L1);
+  }
 }
 
 // Velocity divergence and curl of the step's active particles: persistent
@@ -1144,7 +1218,14 @@ template <int G>
 cudaError_t density_g(const View &v, int flags, int bin_filter, bool persistent, int grid,
                       cudaStream_t st) {
   k_density<G><<<grid, PT, DENS_SMEM, st>>>(v, flags, bin_filter, persistent ? 1 : 0);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  // after a whole-step launch: the leaves of the groups it split
+  if (e == cudaSuccess && G == 1 && bin_filter < 0 && persistent) {
+    note_launches(1);
+    k_leaf_hmax<<<v.grid_util / 2 > 0 ? v.grid_util / 2 : 1, PT, 0, st>>>(v);
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 template <int G>
