@@ -269,6 +269,7 @@ __device__ void density_group(const View &v, int wg, int slice, int nslices, int
               const float2 px = make_float2(pj.x, pj.x), py = make_float2(pj.y, pj.y),
                            pz = make_float2(pj.z, pj.z);
               int q = 0;
+#pragma unroll 2
               for (; q + 1 < ntst; q += 2) {  // two live particles per packed test
                 const float4 t0 = st.tst[q], t1 = st.tst[q + 1];
                 const float2 r2 = dist2_x2(make_float2(t0.x, t1.x), make_float2(t0.y, t1.y),
