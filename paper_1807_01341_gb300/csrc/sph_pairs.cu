@@ -949,7 +949,7 @@ __device__ __forceinline__ int density_item(const View &v, const DevState *ds, i
 // per particle) has at least twice as many warps as active groups: the
 // slices fill the warps that would otherwise idle, and a step's time is that
 // of its slowest work item.
-constexpr int SPLIT_MAX = 8;
+constexpr int SPLIT_MAX = 16;
 __device__ __forceinline__ int split_parts(int nq, int nwarps) {
   return nq > 0 ? max(1, min(SPLIT_MAX, nwarps / nq)) : 1;
 }
@@ -1054,17 +1054,22 @@ __global__ void __launch_bounds__(PT, 2) k_force(View v, int bin_filter, int per
   const int cb = coop_blocks<G>(v, qs);
   if constexpr (G == 1) {
     if (persistent || (int)blockIdx.x < cb) {
+      // (whole-step persistent launches split the shared groups too when
+      // blocks outnumber them: each slice is one block's work item)
+      const int nparts = (bin_filter < 0 && persistent) ? split_parts(qs.ncoop, (int)gridDim.x) : 1;
+      const int nitems = qs.ncoop * nparts;
       __shared__ int s_item;
       for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(&ds->head_coop_force, 1);
         __syncthreads();
         const int item = s_item;
         __syncthreads();
-        if (item >= qs.ncoop || st.failed) break;
-        const int wg = coop_group(v, ds, bin_filter, item);
+        if (item >= nitems || st.failed) break;
+        const int q = item / nparts;
+        const int wg = coop_group(v, ds, bin_filter, q);
         if (!SPH_IN(ds, wg, ds->n_groups, SPH_CHECK_GROUP)) break;
-        force_group<1, true, VAR>(v, wg, 0, 1, bin_filter, m_act, frame_of(v, ds, wg), Hmax, exc,
-                                  st, wc);
+        force_group<1, true, VAR>(v, wg, item - q * nparts, nparts, bin_filter, m_act,
+                                  frame_of(v, ds, wg), Hmax, exc, st, wc);
       }
     }
   }
