@@ -12,7 +12,7 @@ fastest in useful pairs per second:
                         gathered (larger: fewer gathers, longer lists)
   list_cap              neighbour-list entries per particle (more: fewer overflow passes)
   heavy_factor          work groups estimated this many times costlier than the mean
-                        are started first, each by a whole block (0: none)
+                        are started first (0: none)
 
 Each trial starts from the same initial state (its own context and a copy of
 the particles), so the trials do not influence one another; it runs one
