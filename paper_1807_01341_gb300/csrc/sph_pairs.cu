@@ -17,9 +17,10 @@
 // Record positions are relative to each leaf's corner on its cell's 1024^3
 // Morton grid; the offset between two leaves is an exact integer number of
 // grid steps times w / 1024, so FP32 keeps a relative precision set by the
-// leaf size even deep inside clumps.  Per-cell partial sums are folded into
-// compensated (hi, lo) accumulators, the G lanes of a group are combined in
-// FP64, and the Newton update of h is done in FP64.  The order of every sum
+// leaf size even deep inside clumps.  The force loop folds per-cell partial
+// sums into compensated (hi, lo) accumulators, the density loop adds every
+// term to its (hi, lo) pair by Fast2Sum; the G lanes of a group are combined
+// in FP64, and the Halley update of h is done in FP64.  The order of every sum
 // depends only on the particle, so the plain and batched forms agree bit for
 // bit.
 //
@@ -64,30 +65,33 @@ __device__ __forceinline__ void leaf_hmax_update(const View &v, int L0, int L1) 
 // ---------------------------------------------------------------------------
 // density loop + smoothing-length iteration for the active particles of a group
 // ---------------------------------------------------------------------------
-// Partial sums of one particle: S_w = sum w(q), S_t = sum (3 w + q w'), the
+// Sums of one particle: S_w = sum w(q), S_t = sum (3 w + q w'), the
 // mass-weighted pair, sum q^2 w'' and the neighbour count.  The first four
-// are compensated (hi, lo) and folded every DFOLD pairs, so the order and the
-// rounding of every sum depend only on the particle's candidates in record
-// order -- the same whether a pair is taken while its record is staged or
-// later from the particle's neighbour list.
-constexpr int DFOLD = 8;
+// are compensated (hi, lo) pairs: each term goes in by Dekker's Fast2Sum
+// (t = hi + x; lo += x - (t - hi); hi = t), whose lo collects the rounding
+// error of every addition exactly while |hi| >= |x| (the running sum of a
+// particle's terms is, after its first terms, much larger than one term), at
+// three adds per term and no branch.  The order and the rounding of every sum
+// depend only on the particle's accepted candidates in record order -- not on
+// the list entries beyond its support nor on the particles sharing its warp.
+// (Partial sums of 8 terms folded into (hi, lo) by a six-add two-sum, the
+// form this replaced, cost 8 % more step-0 density time: the fold branch of
+// the lane that reached 8 terms was taken by almost every warp at almost
+// every entry.)
+__device__ __forceinline__ void fast2sum(float &hi, float &lo, float x) {
+  const float t = hi + x;
+  lo += x - (t - hi);
+  hi = t;
+}
 
 struct DSum {
   float n_hi, n_lo, t_hi, t_lo, r_hi, r_lo, rt_hi, rt_lo;
-  float pn, pt, pr, prt, p2;
-  int cnt, since;
+  float p2;
+  int cnt;
   __device__ __forceinline__ void zero() {
     n_hi = n_lo = t_hi = t_lo = r_hi = r_lo = rt_hi = rt_lo = 0.0f;
-    pn = pt = pr = prt = p2 = 0.0f;
-    cnt = since = 0;
-  }
-  __device__ __forceinline__ void fold_all() {
-    fold(n_hi, n_lo, pn);
-    fold(t_hi, t_lo, pt);
-    fold(r_hi, r_lo, pr);
-    fold(rt_hi, rt_lo, prt);
-    pn = pt = pr = prt = 0.0f;
-    since = 0;
+    p2 = 0.0f;
+    cnt = 0;
   }
 };
 
@@ -101,12 +105,11 @@ __device__ __forceinline__ void dens_pair(DSum &s, float r2, float mj, float H2,
   kernel_wd(qq, wq, dwq);
   const float tt = fmaf(qq, dwq, 3.0f * wq);
   s.p2 = fmaf(qq * qq, kernel_d2w(qq), s.p2);
-  s.pn += wq;
-  s.pt += tt;
-  s.pr = fmaf(mj, wq, s.pr);
-  s.prt = fmaf(mj, tt, s.prt);
+  fast2sum(s.n_hi, s.n_lo, wq);
+  fast2sum(s.t_hi, s.t_lo, tt);
+  fast2sum(s.r_hi, s.r_lo, mj * wq);
+  fast2sum(s.rt_hi, s.rt_lo, mj * tt);
   s.cnt++;
-  if (++s.since == DFOLD) s.fold_all();
 }
 
 // Entries [0, nl) of a neighbour list (entry k at lst[k * ls]), in order, in
@@ -315,17 +318,27 @@ __device__ void density_group(const View &v, int wg, int slice, int nslices, int
             for (int k0 = 0; k0 < total; k0 += 32) {
               unsigned mask = test_block(base, total, k0);  // (every lane: the test votes)
               if (!gath) mask = 0u;
+              // two accepted records per round (independent load-compute-store
+              // chains), listed in record order
               while (mask) {
-                const int k = base + k0 + __ffs(mask) - 1;
+                const int ka = base + k0 + __ffs(mask) - 1;
                 mask &= mask - 1;
+                const bool two = mask != 0u;
+                const int kb = two ? base + k0 + __ffs(mask) - 1 : ka;
+                mask &= mask - 1;
+                const float4 pa = st.rec[ka], pb = st.rec[kb];
                 const int e = acc - skipc;
                 if ((unsigned)e < (unsigned)cap) {
-                  const float4 pj = st.rec[k];
-                  const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
+                  const float dx = xi.x - pa.x, dy = xi.y - pa.y, dz = xi.z - pa.z;
                   __stcg(lst + (size_t)e * ls,
-                         make_float2(fmaf(dx, dx, fmaf(dy, dy, dz * dz)), pj.w));
+                         make_float2(fmaf(dx, dx, fmaf(dy, dy, dz * dz)), pa.w));
                 }
-                acc++;
+                if (two && (unsigned)(e + 1) < (unsigned)cap) {
+                  const float dx = xi.x - pb.x, dy = xi.y - pb.y, dz = xi.z - pb.z;
+                  __stcg(lst + (size_t)(e + 1) * ls,
+                         make_float2(fmaf(dx, dx, fmaf(dy, dy, dz * dz)), pb.w));
+                }
+                acc += two ? 2 : 1;
               }
             }
           };
@@ -381,7 +394,6 @@ __device__ void density_group(const View &v, int wg, int slice, int nslices, int
         nl = -1;  // the list holds only the last pass's share
       }
       if (st.failed) break;
-      s.fold_all();
       const double sn = group_sum<G>((double)s.n_hi + (double)s.n_lo);
       const double stt = group_sum<G>((double)s.t_hi + (double)s.t_lo);
       const float sr = (float)group_sum<G>((double)s.r_hi + (double)s.r_lo);
