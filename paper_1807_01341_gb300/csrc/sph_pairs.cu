@@ -17,10 +17,9 @@
 // Record positions are relative to each leaf's corner on its cell's 1024^3
 // Morton grid; the offset between two leaves is an exact integer number of
 // grid steps times w / 1024, so FP32 keeps a relative precision set by the
-// leaf size even deep inside clumps.  The force loop folds per-cell partial
-// sums into compensated (hi, lo) accumulators, the density loop adds every
-// term to its (hi, lo) pair by Fast2Sum; the G lanes of a group are combined
-// in FP64, and the Halley update of h is done in FP64.  The order of every sum
+// leaf size even deep inside clumps.  Both loops add every term to a
+// compensated (hi, lo) FP32 pair by Fast2Sum; the G lanes of a group are
+// combined in FP64, and the Halley update of h is done in FP64.  The order of every sum
 // depends only on the particle, so the plain and batched forms agree bit for
 // bit.
 //
@@ -529,9 +528,8 @@ __device__ void force_group(const View &v, int wg, int slice, int nslices, int b
     const int nsph = compact_spheres(st.sph, sub == 0 && valid, make_float4(xi.x, xi.y, xi.z, xi.w));
     float ax_hi = 0.f, ax_lo = 0.f, ay_hi = 0.f, ay_lo = 0.f, az_hi = 0.f, az_lo = 0.f;
     float ad_hi = 0.f, ad_lo = 0.f;
-    float pax = 0.f, pay = 0.f, paz = 0.f, pad = 0.f;
     float vs = 2.0f * hi4.z;
-    int cur = -1, cnt = 0;
+    int cnt = 0;
     int bmin = 127;  // limiter: smallest bin among the neighbours
     const int bi = ((VAR && v.limiter) && valid) ? (int)v.bin[i] : 0;  // limiter: i's bin
     // Balsara factor of i: |div v| / (|div v| + |curl v| + 1e-4 c / h), h = 1 / (GAMMA_K / H)
@@ -628,15 +626,6 @@ __device__ void force_group(const View &v, int wg, int slice, int nslices, int b
           // the signal velocity 2 c_i, the start value; one count subtracted below)
           const int k = base + k0 + __ffsll(mask) - 1;
           mask &= mask - 1;
-          const int ci = st.recc[k];
-          if (ci != cur) {
-            fold(ax_hi, ax_lo, pax);
-            fold(ay_hi, ay_lo, pay);
-            fold(az_hi, az_lo, paz);
-            fold(ad_hi, ad_lo, pad);
-            pax = pay = paz = pad = 0.f;
-            cur = ci;
-          }
           const float4 pj = sx_rec[k];
           const float4 vj = sv_rec[k];
           const float4 hj = sh_rec[k];
@@ -674,10 +663,13 @@ __device__ void force_group(const View &v, int wg, int slice, int nslices, int b
             }
             const float dWb = 0.5f * (dwi + dwj);
             const float sc = vj.w * fmaf(hi4.y, dwi, fmaf(hj.y, dwj, Pi * dWb)) * rinv;
-            pax = fmaf(-sc, dx, pax);
-            pay = fmaf(-sc, dy, pay);
-            paz = fmaf(-sc, dz, paz);
-            pad = fmaf(vj.w * Pi * dWb, dvdr * rinv, pad);
+            // (the terms of a cancel in part, so a term can exceed the running
+            // sum; that addition then keeps an error of about one unit in the
+            // last place of the sum, as a plain FP32 partial sum would)
+            fast2sum(ax_hi, ax_lo, -sc * dx);
+            fast2sum(ay_hi, ay_lo, -sc * dy);
+            fast2sum(az_hi, az_lo, -sc * dz);
+            fast2sum(ad_hi, ad_lo, vj.w * Pi * dWb * (dvdr * rinv));
             vs = fmaxf(vs, vsij);
           } else {
             vs = fmaxf(vs, hi4.z + hj.z);
@@ -697,10 +689,6 @@ __device__ void force_group(const View &v, int wg, int slice, int nslices, int b
       skip += nlist;
     } while (more && !st.failed);
     if (!COOP && st.failed) break;
-    fold(ax_hi, ax_lo, pax);
-    fold(ay_hi, ay_lo, pay);
-    fold(az_hi, az_lo, paz);
-    fold(ad_hi, ad_lo, pad);
     double sax, say, saz, sad;
     if constexpr (COOP) {
       // combine the 8 warps' partial sums, in warp order
