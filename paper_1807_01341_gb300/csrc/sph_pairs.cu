@@ -564,7 +564,10 @@ __device__ void force_group(const View &v, int wg, int slice, int nslices, int b
     // and masking the tail, as the density loop does, measured slower here)
     auto test_block = [&](int base, int total, int kb) -> unsigned {
       unsigned mask = 0u;
-      if (G == 1 && ntst <= TRANSPOSE_MAX) {
+      // (one lane per particle: always the transposed form here -- with its
+      // test on the record's support as well, it measured faster than the
+      // per-lane form for every count of live particles)
+      if (G == 1) {
         const bool in = kb + lane < total;
         const float4 pj = sx_rec[min(base + kb + lane, S_FORCE - 1)];
         const float Hj2 = pj.w * pj.w;
@@ -586,18 +589,6 @@ __device__ void force_group(const View &v, int wg, int slice, int nslices, int b
           const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
           const unsigned m = __ballot_sync(FULL, in && (r2 < t.w || r2 < Hj2));
           if (q == my_rank) mask = m;
-        }
-      } else if (G == 1) {
-        const float2 xx = make_float2(xi.x, xi.x), yy = make_float2(xi.y, xi.y),
-                     zz = make_float2(xi.z, xi.z);
-#pragma unroll
-        for (int u = 0; u < 32; u += 2) {  // two records per packed test
-          const float4 p0 = sx_rec[min(base + kb + u, S_FORCE - 1)];
-          const float4 p1 = sx_rec[min(base + kb + u + 1, S_FORCE - 1)];
-          const float2 r2 = dist2_x2(xx, yy, zz, make_float2(p0.x, p1.x),
-                                     make_float2(p0.y, p1.y), make_float2(p0.z, p1.z));
-          mask |= (kb + u < total && (r2.x < Hi2 || r2.x < p0.w * p0.w)) ? (1u << u) : 0u;
-          mask |= (kb + u + 1 < total && (r2.y < Hi2 || r2.y < p1.w * p1.w)) ? (2u << u) : 0u;
         }
       } else {
 #pragma unroll
@@ -685,7 +676,7 @@ __device__ void force_group(const View &v, int wg, int slice, int nslices, int b
     bool more = false;
     do {
       nlist = search(v, F, reach, st, leaf_ok, chunk_ok, skip, more, part);
-      stage_list(srcs, st, nlist, consume, wc);
+      stage_list<VAR>(srcs, st, nlist, consume, wc);  // (particle tags for the variants only)
       skip += nlist;
     } while (more && !st.failed);
     if (!COOP && st.failed) break;
