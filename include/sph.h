@@ -118,7 +118,9 @@ typedef struct {
                            Results do not depend on it. */
   double search_margin; /* density loop: a particle's candidates are gathered within
                            search_margin x its support H, and gathered again only once
-                           its H outgrows that radius; 1..2.  Results do not depend on it. */
+                           its H outgrows that radius; 1..2 (the first density pass of a
+                           run, whose h comes from the initial conditions, uses at least
+                           1.05).  Results do not depend on it. */
   int staging_depth;    /* pair loops: staging buffers per warp (1, 2 or 3); with d > 1
                            the bulk copies of the next d - 1 batches of neighbour records
                            are in flight while a batch is evaluated.  Results do not

@@ -119,6 +119,7 @@ __device__ __forceinline__ void dens_pair(DSum &s, float r2, float mj, float H2,
 // reads only entries it wrote itself, and a list area is used by one warp of
 // one launch (L1 lines are invalidated between dependent launches).
 constexpr int LQ = 4;
+constexpr float FIRST_MARGIN = 1.05f;  // search margin of a run's first density pass (at least)
 __device__ __forceinline__ void dens_list(DSum &s, const float2 *lst, int ls, int nl, float H2,
                                           float Hinv) {
   if (nl <= 0) return;
@@ -228,7 +229,12 @@ __device__ void density_group(const View &v, int wg, int slice, int nslices, int
       // lanes without a list valid at this H gather (a whole particle's G lanes together)
       const bool need = !done && (nl < 0 || H > Ri);
       if (need) {
-        Ri = keep ? H * v.search_margin : H;
+        // (the first pass of a run, whose h comes from the initial
+        // conditions, gathers a little wider: fewer second gathers, the same
+        // sums; 20 steps of the 2.1M clustered set: density -1.3 %)
+        const float margin = init_entropy && it == 0 ? fmaxf(v.search_margin, FIRST_MARGIN)
+                                                     : v.search_margin;
+        Ri = keep ? H * margin : H;
         nl = 0;
       }
       bool gath = need;   // this lane gathers in the current pass
