@@ -401,8 +401,13 @@ __device__ void density_group(const View &v, int wg, int slice, int nslices, int
       if (st.failed) break;
       const double sn = group_sum<G>((double)s.n_hi + (double)s.n_lo);
       const double stt = group_sum<G>((double)s.t_hi + (double)s.t_lo);
-      const float sr = (float)group_sum<G>((double)s.r_hi + (double)s.r_lo);
-      const float srt = (float)group_sum<G>((double)s.rt_hi + (double)s.rt_lo);
+      // (the mass-weighted sums are needed only once h has converged: with
+      // one lane per particle they are formed there, in the same arithmetic)
+      float sr = 0.0f, srt = 0.0f;
+      if constexpr (G > 1) {
+        sr = (float)group_sum<G>((double)s.r_hi + (double)s.r_lo);
+        srt = (float)group_sum<G>((double)s.rt_hi + (double)s.rt_lo);
+      }
       const double s2 = group_sum<G>((double)s.p2);
       const int cnt = group_sum_i<G>(s.cnt) - 1;  // (the particle itself is among its candidates)
       if (!done) {
@@ -421,8 +426,12 @@ __device__ void density_group(const View &v, int wg, int slice, int nslices, int
         } else if (dFr > 0.0) {
           const double den = 2.0 * dFr * dFr - Fr * (s2 - 2.0 * dFr);
           // (Halley, or Newton where its denominator is not positive: one division)
+          // (the quotient in FP32: the conversions and the 2-ulp division move
+          // the new h by about 4e-7 of the step, far inside the FP64
+          // convergence test's tolerance)
           const bool hal = den > 0.0;
-          hn = hd - hd * ((hal ? 2.0 * Fr * dFr : Fr) / (hal ? den : dFr));
+          hn = hd - hd * (double)__fdividef((float)(hal ? 2.0 * Fr * dFr : Fr),
+                                            (float)(hal ? den : dFr));
         } else {
           hn = NAN;
         }
@@ -433,6 +442,10 @@ __device__ void density_group(const View &v, int wg, int slice, int nslices, int
         const bool last = it == v.h_max_iter - 1;
         if (conv || over || last) {
           done = true;
+          if constexpr (G == 1) {
+            sr = (float)((double)s.r_hi + (double)s.r_lo);
+            srt = (float)((double)s.rt_hi + (double)s.rt_lo);
+          }
           if (sub == 0 && writer) {
             wc.pairs += (unsigned long long)cnt;
             wc.iters += (unsigned long long)(it + 1);
