@@ -796,7 +796,10 @@ cudaError_t launch_close_step(const View &v, cudaStream_t st) {
 
 cudaError_t launch_drift(const View &v, cudaStream_t st) {
   note_launches(1);
-  k_drift<<<2 * v.grid_util, UT, 0, st>>>(v);
+  // (blocks of 128 threads: twice the chunks in flight per SM of 256-thread
+  // blocks, which the registers limit to five per SM; a sparse step's drift
+  // is bound by the latency of its chunks' dependent phases)
+  k_drift<<<4 * v.grid_util, 128, 0, st>>>(v);
   return cudaGetLastError();
 }
 
