@@ -47,18 +47,28 @@ __device__ __forceinline__ float *red_area(int warp) {
   return reinterpret_cast<float *>(smem_dyn + (size_t)warp * St::bytes() + St::red_offset());
 }
 
-// The largest support of each leaf [L0, L1) of a work group (one lane per
-// leaf) after its particles' h changed; the chunk's and the global largest
-// support keep upper bounds.
+// The largest support of each leaf [L0, L1) of a work group after its
+// particles' h changed; the chunk's and the global largest support keep upper
+// bounds.  One lane per particle of the group (at most 32), then one warp-wide
+// max per leaf (every lane of the warp calls it).
 __device__ __forceinline__ void leaf_hmax_update(const View &v, int L0, int L1) {
-  const int leaf = L0 + lane_id();
-  if (leaf >= L1) return;
-  float Hm = 0.0f;
-  for (int k = v.leaf_start[leaf]; k < v.leaf_start[leaf + 1]; k++) Hm = fmaxf(Hm, v.rec_xH[k].w);
-  reinterpret_cast<float *>(&v.leaf_lo[leaf])[3] = Hm;
-  const int g = v.leaf_chunk[leaf];
-  atomic_max_float_pos(reinterpret_cast<unsigned int *>(&v.chunk_lo[g]) + 3, Hm);
-  atomic_max_float_pos(&v.ds->Hmax_bits, Hm);
+  const int lane = lane_id();
+  const int a = v.leaf_start[L0], b = v.leaf_start[L1];
+  const int i = a + lane;
+  unsigned hb = 0u;  // support (positive float bits: ordered as unsigned), 0 past the group
+  int leaf = -1;
+  if (i < b && lane < WG_MAX) {
+    hb = __float_as_uint(v.rec_xH[i].w);
+    leaf = v.pleaf[i];
+  }
+  for (int l = L0; l < L1; l++) {
+    const float Hm = __uint_as_float(__reduce_max_sync(FULL, leaf == l ? hb : 0u));
+    if (lane == 0) {
+      reinterpret_cast<float *>(&v.leaf_lo[l])[3] = Hm;
+      atomic_max_float_pos(reinterpret_cast<unsigned int *>(&v.chunk_lo[v.leaf_chunk[l]]) + 3, Hm);
+      atomic_max_float_pos(&v.ds->Hmax_bits, Hm);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
