@@ -655,11 +655,17 @@ def main():
                          "peak_source": f"{out['sms']} SMs (queried) x {FP32_LANES_PER_SM} FP32 "
                                         f"lanes x 2 x {mhz:.0f} MHz (median SM clock sampled "
                                         "during the timed steps)",
-                         "achieved_counts": "algorithmic FLOPs of the useful pairs (density at "
-                                            "the final h)",
+                         "achieved_counts": (
+                             "algorithmic FLOPs of the useful pairs (at the final h)"
+                             if rf["kernel"] == "density" else
+                             "algorithmic FLOPs of the useful pairs (r < max(H_i, H_j))"),
                          "executed": {"achieved": rf["executed"], "frac": rf["executed"] / peak,
-                                      "counts": "FP32 work executed: every candidate test "
-                                                "and every pair term of every h iteration"},
+                                      "counts": (
+                                          "FP32 work executed: every candidate test and every "
+                                          "pair term of every h iteration"
+                                          if rf["kernel"] == "density" else
+                                          "FP32 work executed: every candidate test and every "
+                                          "pair term")},
                          "launch_ms": rf["per_launch_ms"], "density_ms": rf["density_ms"],
                          "force_ms": rf["force_ms"]},
             "cell_build_ms": out["build_ms"],
