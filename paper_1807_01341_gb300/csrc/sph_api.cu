@@ -123,6 +123,8 @@ struct sph_ctx {
   cudaStream_t cap_stream = nullptr;
   long long graph_version = -1;
   bool graph_profiled = false;
+  bool uniform_mass = false;   // every particle has the same mass (last cell build)
+  bool graph_uniform = false;  // uniform_mass when the graph was captured
   int graph_kernels = 0;       // kernel nodes in the captured step
   sph_particles graph_p;
   AdjBuffers *adj = nullptr;
@@ -268,6 +270,7 @@ View make_view(const sph_ctx *ctx, const sph_particles *p) {
   v.leaf_max = q.leaf_max;
   v.G = q.threads_per_particle;
   v.drift_all = q.drift_all;
+  v.uniform_mass = ctx->uniform_mass ? 1 : 0;
   v.grid_util = ctx->grid_util;
   v.nbr = b.nbr;
   v.list_cap = q.list_cap;
@@ -476,10 +479,15 @@ int build_cells(sph_ctx *ctx, sph_particles *p, cudaStream_t st) {
   SPH_CUDA(launch_refresh_all(v, st));
   // cost estimate of every work group (only heavy-group scheduling uses it)
   if (ctx->prm.heavy_factor > 0.0) SPH_CUDA(launch_group_cost(v, ctx->grid_dens, st));
+  // equal masses: the density loop sums the kernel alone (rho = m sum w)
+  SPH_CUDA(launch_mass_uniform(v, st));
   int nl = 0;
+  float mu = 0.0f;
   SPH_CUDA(cudaMemcpyAsync(&nl, SPH_DS_FIELD(b.ds, n_leaves), sizeof(int), cudaMemcpyDeviceToHost, st));
+  SPH_CUDA(cudaMemcpyAsync(&mu, SPH_DS_FIELD(b.ds, m_uniform), sizeof(float), cudaMemcpyDeviceToHost, st));
   SPH_CUDA(cudaStreamSynchronize(st));
   ctx->n_leaves = nl;
+  ctx->uniform_mass = mu > 0.0f;
   ctx->h_floor = 0.0f;
   ctx->nc = nc;
   ctx->w = w;
@@ -604,6 +612,7 @@ int capture_graph(sph_ctx *ctx, sph_particles *p) {
   ctx->prof_n[0] = saved_n[0];
   ctx->prof_n[1] = saved_n[1];
   ctx->graph_profiled = ctx->prof_on;
+  ctx->graph_uniform = ctx->uniform_mass;
   if (r != SPH_OK) {
     if (g) cudaGraphDestroy(g);
     return r;
@@ -947,7 +956,8 @@ int sph_step_async(sph_ctx *ctx, sph_particles *p, int form, void *stream) {
     ctx->init_pending = true;
   } else if (form == SPH_FORM_BATCHED) {
     if (!ctx->graph || ctx->graph_version != ctx->alloc_version ||
-        ctx->graph_profiled != ctx->prof_on || std::memcmp(&ctx->graph_p, p, sizeof(*p)) != 0) {
+        ctx->graph_profiled != ctx->prof_on || ctx->graph_uniform != ctx->uniform_mass ||
+        std::memcmp(&ctx->graph_p, p, sizeof(*p)) != 0) {
       prof_collect(ctx);
       SPH_TRY(capture_graph(ctx, p));
     }

@@ -37,6 +37,34 @@ __global__ void k_reduce_hmax(const float *__restrict__ h, long long n, unsigned
   if ((threadIdx.x & 31) == 0) atomic_max_float_pos(out, m);
 }
 
+// The particles' common mass, or 0 when the masses differ (one block: it
+// runs once per cell build).
+__global__ void k_mass_uniform(const float *__restrict__ m, long long n, float *out) {
+  __shared__ float s_lo[32], s_hi[32];
+  float lo = INFINITY, hi = -INFINITY;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    const float x = m[i];
+    lo = fminf(lo, x);
+    hi = fmaxf(hi, x);
+  }
+  for (int o = 16; o; o >>= 1) {
+    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s_lo[threadIdx.x >> 5] = lo;
+    s_hi[threadIdx.x >> 5] = hi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++) {
+      lo = fminf(lo, s_lo[w]);
+      hi = fmaxf(hi, s_hi[w]);
+    }
+    *out = (n > 0 && lo == hi && lo > 0.0f && isfinite(lo)) ? lo : 0.0f;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // cell keys: exact FP64 arithmetic (no contraction) so the cell of every
 // particle is a function of its FP64 position alone
@@ -554,6 +582,12 @@ cudaError_t launch_reduce_hmax(const View &v, float *out_max, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   int blocks = (int)std::min<long long>(1024, std::max<long long>(1, (v.n + 255) / 256));
   k_reduce_hmax<<<blocks, 256, 0, st>>>(v.h, v.n, reinterpret_cast<unsigned int *>(out_max));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mass_uniform(const View &v, cudaStream_t st) {
+  note_launches(1);
+  k_mass_uniform<<<1, 1024, 0, st>>>(v.m, v.n, SPH_DS_FIELD(v.ds, m_uniform));
   return cudaGetLastError();
 }
 

@@ -63,7 +63,7 @@ struct DevState {
   unsigned long long err_count[16];
   // first failed bounds check (a library built with SPH_CHECKS)
   int check_site;         // sph_check_site (0: none)
-  int check_pad;
+  float m_uniform;        // the particles' common mass (0: the masses differ), set at build
   long long check_index, check_bound;
   // rebuild criterion
   unsigned int excursion_bits;  // max distance (float bits) of a particle outside its cell
@@ -156,6 +156,7 @@ struct View {
   int coop_max_groups;       // steps with at most this many active groups: all cooperative
                              // (force loop)
   int h_max_iter, bin_cap, leaf_max, G, drift_all;
+  int uniform_mass;          // every particle has the same mass (found at the last cell build)
   int grid_util;             // blocks of the grid-stride utility kernels
 };
 
@@ -263,6 +264,7 @@ void note_launches(int n);
 // ---------------------------------------------------------------------------
 // sph_cells.cu
 cudaError_t launch_reduce_hmax(const View &v, float *out_max, cudaStream_t st);
+cudaError_t launch_mass_uniform(const View &v, cudaStream_t st);
 // (bad: a device counter, incremented per particle with a non-finite position
 // or an h that is not a positive finite number)
 cudaError_t launch_cell_keys(const View &v, int nc, double w, unsigned long long *keys,

@@ -105,7 +105,10 @@ struct DSum {
 };
 
 // A candidate at squared distance r2 (FP32, group frame) with mass mj, at the
-// support H (H2 = H^2, Hinv = 1/H): a neighbour when r2 < H2 (strict).
+// support H (H2 = H^2, Hinv = 1/H): a neighbour when r2 < H2 (strict).  With
+// equal masses (UM) the mass-weighted sums are not formed: they are the common
+// mass times S_w and S_t.
+template <bool UM>
 __device__ __forceinline__ void dens_pair(DSum &s, float r2, float mj, float H2, float Hinv) {
   if (!(r2 < H2)) return;
   const float rr = r2 * rsqrtf(fmaxf(r2, 1e-30f));
@@ -116,8 +119,10 @@ __device__ __forceinline__ void dens_pair(DSum &s, float r2, float mj, float H2,
   s.p2 = fmaf(qq * qq, kernel_d2w(qq), s.p2);
   fast2sum(s.n_hi, s.n_lo, wq);
   fast2sum(s.t_hi, s.t_lo, tt);
-  fast2sum(s.r_hi, s.r_lo, mj * wq);
-  fast2sum(s.rt_hi, s.rt_lo, mj * tt);
+  if constexpr (!UM) {
+    fast2sum(s.r_hi, s.r_lo, mj * wq);
+    fast2sum(s.rt_hi, s.rt_lo, mj * tt);
+  }
   s.cnt++;
 }
 
@@ -130,6 +135,7 @@ __device__ __forceinline__ void dens_pair(DSum &s, float r2, float mj, float H2,
 // one launch (L1 lines are invalidated between dependent launches).
 constexpr int LQ = 4;
 constexpr float FIRST_MARGIN = 1.05f;  // search margin of a run's first density pass (at least)
+template <bool UM>
 __device__ __forceinline__ void dens_list(DSum &s, const float2 *lst, int ls, int nl, float H2,
                                           float Hinv) {
   if (nl <= 0) return;
@@ -146,7 +152,7 @@ __device__ __forceinline__ void dens_list(DSum &s, const float2 *lst, int ls, in
       e[j] = kn < nl ? lst[(size_t)kn * ls] : make_float2(INFINITY, 0.0f);
     }
 #pragma unroll
-    for (int j = 0; j < LQ; j++) dens_pair(s, cur[j].x, cur[j].y, H2, Hinv);
+    for (int j = 0; j < LQ; j++) dens_pair<UM>(s, cur[j].x, cur[j].y, H2, Hinv);
   }
 }
 
@@ -176,7 +182,7 @@ __device__ __forceinline__ void dens_list(DSum &s, const float2 *lst, int ls, in
 // (a particle's candidates and their order do not depend on the particles it
 // shares a warp with).  A split group's leaves get their largest support from
 // k_leaf_hmax, after every slice is done.
-template <int G>
+template <int G, bool UM>
 __device__ void density_group(const View &v, int wg, int slice, int nslices, int flags,
                               int bin_filter, int m_act, const CellFrame &F, float hcap, float exc,
                               long long ti, StageD &st, WarpCounters &wc) {
@@ -388,7 +394,7 @@ __device__ void density_group(const View &v, int wg, int slice, int nslices, int
         // the list this pass built (or, in the first pass, the one kept from
         // an earlier iteration), in order
         if (!done && (gath || first) && nl > 0) {
-          dens_list(s, lst, ls, nl, H2, Hinv);
+          dens_list<UM>(s, lst, ls, nl, H2, Hinv);
           if (writer) wc.evals += (unsigned long long)nl;
         }
         // a list that filled up: the next pass lists the records after it (for
@@ -452,7 +458,11 @@ __device__ void density_group(const View &v, int wg, int slice, int nslices, int
         const bool last = it == v.h_max_iter - 1;
         if (conv || over || last) {
           done = true;
-          if constexpr (G == 1) {
+          if constexpr (UM) {
+            const double mu = (double)v.ds->m_uniform;
+            sr = (float)(mu * sn);
+            srt = (float)(mu * stt);
+          } else if constexpr (G == 1) {
             sr = (float)((double)s.r_hi + (double)s.r_lo);
             srt = (float)((double)s.rt_hi + (double)s.rt_lo);
           }
@@ -986,7 +996,7 @@ __device__ __forceinline__ int planted_group(DevState *ds, int wg) {
   return wg;
 }
 
-template <int G>
+template <int G, bool UM>
 __global__ void __launch_bounds__(PT, 2) k_density(View v, int flags, int bin_filter, int persistent) {
   DevState *ds = v.ds;
   const int warp = threadIdx.x >> 5, lane = lane_id();
@@ -1044,8 +1054,8 @@ __global__ void __launch_bounds__(PT, 2) k_density(View v, int flags, int bin_fi
     if (lane == 0) wg = planted_group(ds, wg);
     wg = __shfl_sync(FULL, wg, 0);
     if (!SPH_IN(ds, wg, ds->n_groups, SPH_CHECK_GROUP)) break;
-    density_group<G>(v, wg, item - q * nparts, nparts, flags, bin_filter, m_act,
-                     frame_of(v, ds, wg), hcap, exc, ti, st, wc);
+    density_group<G, UM>(v, wg, item - q * nparts, nparts, flags, bin_filter, m_act,
+                         frame_of(v, ds, wg), hcap, exc, ti, st, wc);
   }
   flush_counters(ds, wc, true);
 }
@@ -1243,7 +1253,14 @@ constexpr size_t FORCE_SMEM = StageF::bytes() * WARPS_PER_BLOCK;
 template <int G>
 cudaError_t density_g(const View &v, int flags, int bin_filter, bool persistent, int grid,
                       cudaStream_t st) {
-  k_density<G><<<grid, PT, DENS_SMEM, st>>>(v, flags, bin_filter, persistent ? 1 : 0);
+  if constexpr (G == 1) {
+    if (v.uniform_mass)
+      k_density<1, true><<<grid, PT, DENS_SMEM, st>>>(v, flags, bin_filter, persistent ? 1 : 0);
+    else
+      k_density<1, false><<<grid, PT, DENS_SMEM, st>>>(v, flags, bin_filter, persistent ? 1 : 0);
+  } else {
+    k_density<G, false><<<grid, PT, DENS_SMEM, st>>>(v, flags, bin_filter, persistent ? 1 : 0);
+  }
   cudaError_t e = cudaGetLastError();
   // after a whole-step launch: the leaves of the groups it split
   if (e == cudaSuccess && G == 1 && bin_filter < 0 && persistent) {
@@ -1265,12 +1282,20 @@ cudaError_t force_g(const View &v, int bin_filter, bool persistent, int grid, cu
 
 template <int G>
 int blocks_per_sm_g(bool density) {
-  const void *fn = density ? (const void *)k_density<G> : (const void *)k_force<G, false>;
+  const void *fn = density ? (const void *)k_density<G, false> : (const void *)k_force<G, false>;
   const size_t smem = density ? DENS_SMEM : FORCE_SMEM;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess) {
     cudaGetLastError();
     return 0;
+  }
+  if (density && G == 1) {
+    // the equal-mass instance uses the same staging area
+    if (cudaFuncSetAttribute((const void *)k_density<1, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
   }
   if (!density && G == 1) {
     // the force kernel with the variants' code and the gradient kernel use the

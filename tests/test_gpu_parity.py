@@ -134,6 +134,50 @@ def test_density_parity_all_active(sim, orc, G, leaf_max):
     assert bad.size <= n // 500
 
 
+def test_density_parity_unequal_masses(sim, orc):
+    """Masses that differ (uniform in [0.7, 1.3] of the mean): the density loop
+    forms the mass-weighted sums itself (with equal masses it takes them as
+    the common mass times the kernel sums); h, rho and f against the oracle."""
+    ic = sph_ics.lattice(16, 0.1, seed=5)
+    n = ic["pos"].shape[0]
+    rng = np.random.default_rng(5)
+    ic["m"] = ic["m"] * rng.uniform(0.7, 1.3, n)
+    ctx, p = gpu_setup(ic, sim.Params())
+    _density_pass(sim, ctx, p)
+    assert ctx.status()[0] == 0
+    perm = ctx.perm_tensor(n).cpu().numpy()
+    g = p.numpy()
+    ref = orc.density(_pos(g), _f64(g["m"]), _f64(np.float32(ic["h0"])[perm]), np.ones(n, np.uint8))
+    assert ref["n_unconverged"] == 0
+    assert np.max(np.abs(g["h"] / ref["h"] - 1)) < H_TOL
+    assert np.max(np.abs(g["rho"] / ref["rho"] - 1)) < RHO_TOL
+    f_ref = orc.gradh_f(ref["h"], ref["rho"], ref["drho_dh"])
+    assert np.max(np.abs(g["f"] - f_ref)) < 1e-5
+
+
+def test_density_equal_masses_path_agrees_with_general_path(sim):
+    """The same particle set twice: equal masses (the common-mass path), and
+    with one mass changed by one part in 10^6 (the general path): h, rho and f
+    agree to rounding."""
+    ic = sph_ics.clumpy_lattice(nside=12, n_clumps=2, per_clump=200, seed=9)
+    n = ic["pos"].shape[0]
+    out = []
+    for bump in (False, True):
+        icb = dict(ic)
+        m = np.array(np.broadcast_to(ic["m"], (n,)), dtype=np.float64)
+        if bump:
+            m[n // 2] *= 1.0 + 1e-6
+        icb["m"] = m
+        ctx, p = gpu_setup(icb, sim.Params())
+        _density_pass(sim, ctx, p)
+        assert ctx.status()[0] == 0
+        out.append(p.numpy())
+    a, b = out
+    assert np.array_equal(a["bin"], b["bin"])
+    for k, tol in (("h", 1e-6), ("rho", 2e-6), ("f", 1e-6)):
+        assert np.max(np.abs(a[k].astype(np.float64) / b[k] - 1)) < tol, k
+
+
 def test_density_clumpy_subset_and_inactive_untouched(sim, orc):
     """Clumps (leaves at depth, many leaves per cell) and a random active subset
     selected through the time bins: inactive particles are not written."""
