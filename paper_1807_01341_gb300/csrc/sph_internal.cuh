@@ -138,7 +138,9 @@ struct View {
   int32_t *q_bin;            // plain form: active work groups holding particles of one bin
                              // (light ones at [0, n_bin_groups), heavy ones from the back)
   // neighbour lists of the density loop: squared distance and mass of every
-  // candidate within a particle's search radius, list_cap entries per lane,
+  // candidate within a particle's search radius (with equal masses the squared
+  // distance alone, 4-byte entries in the first half of the area), list_cap
+  // entries per lane,
   // one area per warp of the launch's blocks (a launch has at most list_blocks
   // blocks; entry k of lane s of warp w of block b at
   // nbr[((b * 8 + w) * list_cap + k) * 32 + s]): the area of a warp is reused

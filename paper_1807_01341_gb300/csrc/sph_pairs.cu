@@ -156,6 +156,27 @@ __device__ __forceinline__ void dens_list(DSum &s, const float2 *lst, int ls, in
   }
 }
 
+// The same for a list of squared distances alone (equal masses).
+__device__ __forceinline__ void dens_list_r(DSum &s, const float *lst, int ls, int nl, float H2,
+                                            float Hinv) {
+  if (nl <= 0) return;
+  float e[LQ];
+#pragma unroll
+  for (int j = 0; j < LQ; j++) e[j] = j < nl ? lst[(size_t)j * ls] : INFINITY;
+#pragma unroll 1
+  for (int k = 0; k < nl; k += LQ) {
+    float cur[LQ];
+#pragma unroll
+    for (int j = 0; j < LQ; j++) {
+      cur[j] = e[j];
+      const int kn = k + LQ + j;
+      e[j] = kn < nl ? lst[(size_t)kn * ls] : INFINITY;
+    }
+#pragma unroll
+    for (int j = 0; j < LQ; j++) dens_pair<true>(s, cur[j], 0.0f, H2, Hinv);
+  }
+}
+
 // Newton step on F(h) = h^3 n(h) - eta^3 in dimensionless form: with H = GAMMA_K h,
 // h^3 n = (8/pi) S_w / GAMMA_K^3 and h dF/dh = 3 h^3 n + h^4 dn/dh, so
 // dh / h = -(S_w - C) / (3 S_w - S_t), C = eta^3 GAMMA_K^3 / (8/pi),
@@ -218,6 +239,10 @@ __device__ void density_group(const View &v, int wg, int slice, int nslices, int
   const int cap = v.list_cap;
   constexpr int ls = 32;
   float2 *const lst = v.nbr + ((size_t)blockIdx.x * WARPS_PER_BLOCK + warp) * 32 * v.list_cap + lane;
+  // (equal masses: the entries are the squared distances alone, in the first
+  // half of the warp's area)
+  float *const lstr = reinterpret_cast<float *>(v.nbr + ((size_t)blockIdx.x * WARPS_PER_BLOCK + warp) *
+                                                             32 * v.list_cap) + lane;
 
   for (int r = s0; r < s1 && !st.failed; r += P) {
     const int slot = r + grp;
@@ -351,13 +376,15 @@ __device__ void density_group(const View &v, int wg, int slice, int nslices, int
                 const int e = acc - skipc;
                 if ((unsigned)e < (unsigned)cap) {
                   const float dx = xi.x - pa.x, dy = xi.y - pa.y, dz = xi.z - pa.z;
-                  __stcg(lst + (size_t)e * ls,
-                         make_float2(fmaf(dx, dx, fmaf(dy, dy, dz * dz)), pa.w));
+                  const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                  if constexpr (UM) __stcg(lstr + (size_t)e * ls, r2);
+                  else __stcg(lst + (size_t)e * ls, make_float2(r2, pa.w));
                 }
                 if (two && (unsigned)(e + 1) < (unsigned)cap) {
                   const float dx = xi.x - pb.x, dy = xi.y - pb.y, dz = xi.z - pb.z;
-                  __stcg(lst + (size_t)(e + 1) * ls,
-                         make_float2(fmaf(dx, dx, fmaf(dy, dy, dz * dz)), pb.w));
+                  const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                  if constexpr (UM) __stcg(lstr + (size_t)(e + 1) * ls, r2);
+                  else __stcg(lst + (size_t)(e + 1) * ls, make_float2(r2, pb.w));
                 }
                 acc += two ? 2 : 1;
               }
@@ -394,7 +421,8 @@ __device__ void density_group(const View &v, int wg, int slice, int nslices, int
         // the list this pass built (or, in the first pass, the one kept from
         // an earlier iteration), in order
         if (!done && (gath || first) && nl > 0) {
-          dens_list<UM>(s, lst, ls, nl, H2, Hinv);
+          if constexpr (UM) dens_list_r(s, lstr, ls, nl, H2, Hinv);
+          else dens_list<false>(s, lst, ls, nl, H2, Hinv);
           if (writer) wc.evals += (unsigned long long)nl;
         }
         // a list that filled up: the next pass lists the records after it (for
