@@ -124,6 +124,7 @@ struct sph_ctx {
   long long graph_version = -1;
   bool graph_profiled = false;
   bool uniform_mass = false;   // every particle has the same mass (last cell build)
+  float m_uniform = 0.0f;      // that mass (0: the masses differ)
   bool graph_uniform = false;  // uniform_mass when the graph was captured
   int graph_kernels = 0;       // kernel nodes in the captured step
   sph_particles graph_p;
@@ -480,14 +481,25 @@ int build_cells(sph_ctx *ctx, sph_particles *p, cudaStream_t st) {
   // cost estimate of every work group (only heavy-group scheduling uses it)
   if (ctx->prm.heavy_factor > 0.0) SPH_CUDA(launch_group_cost(v, ctx->grid_dens, st));
   // equal masses: the density loop sums the kernel alone (rho = m sum w)
-  SPH_CUDA(launch_mass_uniform(v, st));
+  SPH_CUDA(launch_mass_range(v, st));
   int nl = 0;
-  float mu = 0.0f;
+  unsigned int mr[2] = {0u, 0u};
   SPH_CUDA(cudaMemcpyAsync(&nl, SPH_DS_FIELD(b.ds, n_leaves), sizeof(int), cudaMemcpyDeviceToHost, st));
-  SPH_CUDA(cudaMemcpyAsync(&mu, SPH_DS_FIELD(b.ds, m_uniform), sizeof(float), cudaMemcpyDeviceToHost, st));
+  SPH_CUDA(cudaMemcpyAsync(mr, SPH_DS_FIELD(b.ds, m_lo_bits), 2 * sizeof(unsigned int),
+                           cudaMemcpyDeviceToHost, st));
   SPH_CUDA(cudaStreamSynchronize(st));
   ctx->n_leaves = nl;
-  ctx->uniform_mass = mu > 0.0f;
+  {
+    float lo, hi;
+    std::memcpy(&lo, &mr[0], sizeof(float));
+    std::memcpy(&hi, &mr[1], sizeof(float));
+    ctx->m_uniform = (n > 0 && mr[0] == mr[1] && lo > 0.0f && std::isfinite(lo)) ? lo : 0.0f;
+    (void)hi;
+  }
+  ctx->uniform_mass = ctx->m_uniform > 0.0f;
+  SPH_CUDA(cudaMemcpyAsync(SPH_DS_FIELD(b.ds, m_uniform), &ctx->m_uniform, sizeof(float),
+                           cudaMemcpyHostToDevice, st));
+  SPH_CUDA(cudaStreamSynchronize(st));  // (the build is complete on return, as before)
   ctx->h_floor = 0.0f;
   ctx->nc = nc;
   ctx->w = w;

@@ -37,31 +37,23 @@ __global__ void k_reduce_hmax(const float *__restrict__ h, long long n, unsigned
   if ((threadIdx.x & 31) == 0) atomic_max_float_pos(out, m);
 }
 
-// The particles' common mass, or 0 when the masses differ (one block: it
-// runs once per cell build).
-__global__ void k_mass_uniform(const float *__restrict__ m, long long n, float *out) {
-  __shared__ float s_lo[32], s_hi[32];
-  float lo = INFINITY, hi = -INFINITY;
-  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
-    const float x = m[i];
-    lo = fminf(lo, x);
-    hi = fmaxf(hi, x);
+// Smallest and largest particle mass, as float bits (atomic min and max on
+// the bit patterns: masses are positive, and any other value only makes the
+// two differ, which selects the general density loop).
+__global__ void k_mass_range(const float *__restrict__ m, long long n, unsigned int *lo_bits,
+                             unsigned int *hi_bits) {
+  unsigned int lo = 0xffffffffu, hi = 0u;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const unsigned int b = __float_as_uint(m[i]);
+    lo = min(lo, b);
+    hi = max(hi, b);
   }
-  for (int o = 16; o; o >>= 1) {
-    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-  }
+  lo = __reduce_min_sync(0xffffffffu, lo);
+  hi = __reduce_max_sync(0xffffffffu, hi);
   if ((threadIdx.x & 31) == 0) {
-    s_lo[threadIdx.x >> 5] = lo;
-    s_hi[threadIdx.x >> 5] = hi;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); w++) {
-      lo = fminf(lo, s_lo[w]);
-      hi = fmaxf(hi, s_hi[w]);
-    }
-    *out = (n > 0 && lo == hi && lo > 0.0f && isfinite(lo)) ? lo : 0.0f;
+    atomicMin(lo_bits, lo);
+    atomicMax(hi_bits, hi);
   }
 }
 
@@ -585,9 +577,14 @@ cudaError_t launch_reduce_hmax(const View &v, float *out_max, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_mass_uniform(const View &v, cudaStream_t st) {
+cudaError_t launch_mass_range(const View &v, cudaStream_t st) {
   note_launches(1);
-  k_mass_uniform<<<1, 1024, 0, st>>>(v.m, v.n, SPH_DS_FIELD(v.ds, m_uniform));
+  cudaError_t e = cudaMemsetAsync(SPH_DS_FIELD(v.ds, m_lo_bits), 0xff, sizeof(unsigned int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(SPH_DS_FIELD(v.ds, m_hi_bits), 0, sizeof(unsigned int), st);
+  if (e != cudaSuccess || v.n == 0) return e;
+  const int blocks = (int)std::min<long long>(v.grid_util, (v.n + 255) / 256);
+  k_mass_range<<<blocks, 256, 0, st>>>(v.m, v.n, SPH_DS_FIELD(v.ds, m_lo_bits),
+                                       SPH_DS_FIELD(v.ds, m_hi_bits));
   return cudaGetLastError();
 }
 

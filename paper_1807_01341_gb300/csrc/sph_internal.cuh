@@ -83,6 +83,8 @@ struct DevState {
   unsigned long long wakes;   // limiter: inactive particles whose steps were cut
   // time-bin occupancy
   int bin_count[MAX_BINS];
+  // smallest and largest particle mass (float bits), found at each cell build
+  unsigned int m_lo_bits, m_hi_bits;
 };
 
 // Pointers and constants handed to every kernel (by value).
@@ -266,7 +268,7 @@ void note_launches(int n);
 // ---------------------------------------------------------------------------
 // sph_cells.cu
 cudaError_t launch_reduce_hmax(const View &v, float *out_max, cudaStream_t st);
-cudaError_t launch_mass_uniform(const View &v, cudaStream_t st);
+cudaError_t launch_mass_range(const View &v, cudaStream_t st);
 // (bad: a device counter, incremented per particle with a non-finite position
 // or an h that is not a positive finite number)
 cudaError_t launch_cell_keys(const View &v, int nc, double w, unsigned long long *keys,
