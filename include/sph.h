@@ -224,8 +224,10 @@ int sph_destroy(sph_ctx *ctx);
  * their previous order -- and permutes every array of `p` in place.  Each
  * cell is split into leaves: octree nodes of the Morton order holding at most
  * leaf_max particles.  Refreshes the FP32 cell-relative records every pair
- * loop reads.  Synchronises `stream` (to size the grid and to check the
- * input).  Errors: SPH_ERR_ARG (also when a position is not finite or an h
+ * loop reads, and finds whether every particle has the same mass (the density
+ * loop then sums the kernel alone: rho = m sum w; masses are taken to stay
+ * as they are until the next build).  Synchronises `stream` (to size the
+ * grid and to check the input).  Errors: SPH_ERR_ARG (also when a position is not finite or an h
  * is not a positive finite number; nothing is reordered then),
  * SPH_ERR_CUDA. */
 int sph_build_cells(sph_ctx *ctx, sph_particles *p, void *stream);
